@@ -1,0 +1,353 @@
+"""Benchmark of the spectrum sweeping DOS hot path on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path on the 2D Anderson workload
+(256 x 256 periodic, hopping -1, on-site U[-2, 2]; N = 65536, nnz = 327680),
+N_v = 200 Rademacher probes, degree M = 1000, 400 sweep points, sigma = 0.02:
+  ssm_moments  - spectral map, M/2 recurrence steps with the doubling Gram
+                 products, float64 moments;
+  ssm_dos      - Alg. 1 / Prop. 1 coefficient tables, per-point assembly,
+                 Alg. 4 + Alg. 6 solves (RESS-DGC) and the KPM line.
+Metric: effective matrix-applies/s = nnz * n_tot * M / t_step.
+
+--impl reference times the CPU oracle (plain float64 numpy/scipy from the
+paper's formulas) on a bounded sample of the same workload.
+Multi-GPU: the operator is not partitioned; every rank runs an independent
+replica on its own GPU (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+CONFIG = "anderson2d_256"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", 0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _workload():
+    c = dict(wl.CONFIGS[CONFIG])
+    st = wl.make_operator(CONFIG)
+    W = wl.random_block(st.n, c["n_v"] + c["n_vh"], c["probe_seed"], c["probe"])
+    csr = wl.stencil_to_csr(st)
+    return c, st, W, csr
+
+
+def _hash_sources(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1504_07690_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, null if the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    if d.get("source_hash") != _hash_sources(d["sources"]):
+        return None
+    return d["dram_bytes_per_launch"]
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(c, st, W, csr, rec_steps: int = 24, points: int = 6):
+    """Time the CPU oracle on a bounded sample of the workload, scaled to one full step.
+
+    Sample: the first `rec_steps` of the paper's M+1 three-term steps (Alg. 7
+    loop with X_l = W^T V_l), and assembly + Alg. 4/6 at `points` sweep points
+    with full-length moment tables; both scaled linearly to M+1 steps and n_t
+    points (their costs are linear in those counts).
+    """
+    from oracle import ssm_oracle as O
+
+    A = O.csr_matrix(csr.n, csr.rowptr, csr.colind, csr.val)
+    a, b = O.spectral_interval(A)
+    At = O.transform(A, a, b)
+    M, n_t, nv, sigma = c["M"], c["n_t"], c["n_v"], c["sigma"]
+    t0 = time.perf_counter()
+    Xs = O.moments_direct(At, W, rec_steps - 1)
+    t_rec = time.perf_counter() - t0
+    X = np.zeros((M + 1,) + Xs.shape[1:])
+    X[: Xs.shape[0]] = Xs
+    lo, hi = O.gershgorin(A)
+    tpts = np.linspace(lo, hi, n_t)[:: max(1, n_t // points)][:points]
+    t1 = time.perf_counter()
+    tab = O.coefficient_tables(tpts, M, sigma, A.shape[0], a, b)
+    gm = O.g_max(sigma, A.shape[0])
+    for i in range(tpts.size):
+        K = O.assemble(tab["mu_half"][i], tab["nu"][i], X, nv)
+        O.ress_dos_point(*K, gm)
+    O.kpm_dos(tab["mu_full"], X)
+    t_pts = time.perf_counter() - t1
+    t_step = t_rec * (M + 1) / rec_steps + t_pts * n_t / tpts.size
+    sample = (f"{rec_steps} of {M + 1} recurrence+moment steps and {tpts.size} of {n_t} sweep points "
+              f"(coefficients, assembly, Alg. 4/6), scaled linearly to one full step")
+    return t_step, sample
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        info = threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, c, st, W, csr):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    nnz = csr.nnz
+    n_tot = c["n_v"] + c["n_vh"]
+    units = float(nnz) * n_tot * c["M"]
+    times = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        t, sample = cpu_oracle_sample(c, st, W, csr, rec_steps=args.ref_rec_steps, points=args.ref_points)
+        if i >= args.warmup:
+            times.append(t)
+    t_step = float(np.mean(times))
+    value = units / t_step
+    line = {
+        "impl": "reference", "metric": "ssm_dos_effective_matrix_applies_per_s", "value": value,
+        "unit": "matrix-applies/s (nnz*n_tot*M/s)", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "anderson2d_256: N=65536 nnz=327680, N_v=200 rademacher, M=1000, "
+                               "400 sweep points, sigma=0.02", "l2": "working set > L2"},
+        "cpu_baseline": {"value": value, "unit": "matrix-applies/s", "cores": _blas_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "matrix-applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, c, st, W, csr):
+    import torch
+
+    import paper_1504_07690_gb300 as S
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.backend == "nccl" else "gloo")
+    dev = torch.device("cuda", local)
+    n_tot = c["n_v"] + c["n_vh"]
+    M, n_t, sigma = c["M"], c["n_t"], c["sigma"]
+    plan = S.ssm_plan_create(stencil=st, n_v=c["n_v"], n_vh=c["n_vh"], degree=M, precision=args.precision)
+    info = S.ssm_plan_info(plan)
+    t = np.linspace(info["lo"], info["hi"], n_t)
+    Wd = torch.from_numpy(W).to(dev)
+    td = torch.from_numpy(t).to(dev)
+    nnz = info["nnz"]
+    units = float(nnz) * n_tot * M
+
+    def step():
+        S.ssm_moments(plan, Wd)
+        return S.ssm_dos(plan, td, sigma, want_rank=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    S.ssm_stats_reset(plan)
+    S.ssm_timing_enable(plan, True)
+    clocks = Clocks(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    S.ssm_timing_enable(plan, False)
+    stats = S.ssm_stats_get(plan)
+    value = units * ws / (ms * 1e-3)
+
+    # dominant kernel of the timed region and its roofline
+    hbm, bf16, bf16s, peak_kind = _peaks()
+    phases = {k: stats[k] / args.steps for k in ("ms_coeffs", "ms_recurrence", "ms_gram", "ms_reduce",
+                                                  "ms_assemble", "ms_solve", "ms_kpm")}
+    esz = 4 if args.precision == "mixed" else 8
+    rec_bytes = 3.0 * st.n * n_tot * esz + st.n * esz
+    rec_launch_ms = stats["ms_recurrence"] / max(1, stats["recurrence_launches"])
+    rec_achieved = rec_bytes / (rec_launch_ms * 1e-3) / 1e9
+    roofline = {"kernel": "stencil_step_kernel", "bound": "hbm", "achieved": rec_achieved, "peak": hbm,
+                "unit": "GB/s", "frac": rec_achieved / hbm, "traffic": _traffic("stencil_step_kernel"),
+                "bytes_per_launch": rec_bytes, "launch_ms": rec_launch_ms,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.from_numpy(W).pin_memory()
+        th = torch.from_numpy(t).pin_memory()
+        outs = torch.empty((2, n_t), dtype=torch.float64).pin_memory()
+
+        def step_host():
+            S.ssm_moments(plan, Wh)
+            ss, kp, _ = S.ssm_dos(plan, th, sigma, want_rank=False)
+            return ss, kp
+
+        step_host()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        h0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        hs = (time.perf_counter() - h0) / args.steps
+        if dist is not None:
+            tt = torch.tensor([hs], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            hs = float(tt.item())
+        e2e = {"value": units * ws / hs, "unit": "matrix-applies/s (nnz*n_tot*M/s)",
+               "h2d_bytes_per_step": int(W.nbytes + t.nbytes), "d2h_bytes_per_step": int(2 * t.nbytes)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_cpu, sample = cpu_oracle_sample(c, st, W, csr, rec_steps=args.ref_rec_steps, points=args.ref_points)
+        cpu = {"value": units / t_cpu, "unit": "matrix-applies/s", "cores": _blas_threads(), "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "ssm_dos_effective_matrix_applies_per_s", "value": value,
+            "unit": "matrix-applies/s (nnz*n_tot*M/s)", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "anderson2d_256: 2D Anderson 256x256 periodic, N=65536, nnz=%d, N_v=200 "
+                                   "rademacher, M=1000, 400 sweep points, sigma=0.02" % nnz,
+                       "precision": args.precision,
+                       "l2": "inputs larger than L2 (3 recurrence blocks of 52 MB + 320 MB of moments)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": roofline, "phases_ms_per_step": phases, "gpu_launches": int(stats["launches"]),
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rec-steps", type=int, default=100)
+    ap.add_argument("--ref-points", type=int, default=20)
+    args = ap.parse_args()
+    c, st, W, csr = _workload()
+    if args.impl == "reference":
+        run_reference(args, c, st, W, csr)
+    else:
+        run_gpu(args, c, st, W, csr)
+
+
+if __name__ == "__main__":
+    main()

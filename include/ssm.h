@@ -1,0 +1,220 @@
+/*
+ * ssm.h - C ABI of the GB300 spectrum sweeping library.
+ *
+ * The library estimates the regularised density of states (DOS)
+ *
+ *     phi_sigma(t) = sum_i g_sigma(t - lambda_i),
+ *     g_sigma(s)   = exp(-s^2 / (2 sigma^2)) / (N sqrt(2 pi sigma^2))
+ *
+ * of a large sparse real symmetric matrix A (Section 2, Eq. DOS0 and
+ * Eq. gaussian of L. Lin, "Randomized estimation of spectral densities of
+ * large matrices made accurate", arXiv 1504.07690) with two estimators on the
+ * same random probe block W:
+ *
+ *   - RESS-DGC, the robust spectrum sweeping estimate (Algorithm 7, built on
+ *     Algorithms 1, 4 and 6, Proposition 1 and Theorem 4), and
+ *   - the DGC / KPM line (Algorithm 2),
+ *
+ * and Tr f(A) from either DOS by Gaussian deconvolution (Section 5,
+ * Algorithm 8).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Every array argument may be a host pointer or a device pointer
+ *   of the plan's device; the library tells them apart itself.  The caller
+ *   owns every buffer it passes; the library copies what it needs and never
+ *   keeps a caller pointer past the call.
+ * Layout.  Dense blocks are row-major with an explicit leading dimension in
+ *   elements.  Moment tensors are (M+1) x n_tot x n_tot, row-major.
+ * Units.  sigma, the sweep points t and the trace grid are in the units of
+ *   A (not of the shifted and scaled A~).
+ * Ordering.  Calls on one plan run on the plan's CUDA stream and return
+ *   after their results are complete (they synchronise that stream).  A
+ *   plan is not thread-safe; distinct plans are independent.
+ * Errors.  Nothing is thrown across the ABI and no kernel traps.  A call
+ *   returns an ssm_status; ssm_last_error() gives a one-line message for the
+ *   last failing call on that plan.  On failure output buffers are left in
+ *   an unspecified state.
+ */
+#ifndef SSM_H
+#define SSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SSM_OK = 0,
+    SSM_EINVAL = 1,      /* bad argument (sizes, null pointers, odd M, sigma <= 0, ...) */
+    SSM_ENOMEM = 2,      /* a device allocation failed */
+    SSM_ECUDA = 3,       /* a CUDA runtime call failed */
+    SSM_ETIMEOUT = 4,    /* a device-side bounded wait gave up */
+    SSM_ENONFINITE = 5,  /* an input or an intermediate was NaN or Inf */
+    SSM_ENOTSYM = 6,     /* the CSR operator is not symmetric */
+    SSM_EDOMAIN = 7,     /* the function of Tr f(A) is not finite on the grid */
+    SSM_ESTATE = 8       /* call out of order (e.g. ssm_dos before ssm_moments) */
+} ssm_status;
+
+typedef enum {
+    SSM_FP64 = 0,   /* recurrence, Gram products and everything after in float64 */
+    SSM_MIXED = 1   /* float32 recurrence, split-bf16 tensor-core Gram products with
+                       float32 accumulation, float64 moments and per-point solves */
+} ssm_precision;
+
+/* Constant-coefficient stencil operator on a grid of up to three axes:
+ *   (A v)_i = diag[i] v_i + sum_axis offdiag[axis] (v_{i-s_axis} + v_{i+s_axis}),
+ * row index i = (i0 * dims[1] + i1) * dims[2] + i2 (last axis fastest).  A
+ * neighbour wraps around on a periodic axis and is absent past a
+ * non-periodic edge.  Unused trailing axes have extent 1.  diag has
+ * N = dims[0]*dims[1]*dims[2] entries (host or device).  This is the
+ * 5- and 7-point finite-difference operator of Section 6. */
+typedef struct {
+    int64_t dims[3];
+    int32_t periodic[3];
+    const double* diag;
+    double offdiag[3];
+} ssm_stencil;
+
+/* General sparse symmetric operator, full (both triangles) storage. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* rowptr;  /* n + 1 entries, rowptr[0] = 0, nondecreasing */
+    const int32_t* colind;  /* nnz entries in [0, n) */
+    const double* val;      /* nnz entries */
+} ssm_csr;
+
+typedef struct {
+    int32_t n_v;        /* probe columns for the low-rank part (N_v of Alg. 7), >= 1 */
+    int32_t n_vh;       /* probe columns for the hybrid correction (N~_v of Alg. 7), >= 0 */
+    int32_t degree;     /* Chebyshev degree M of Alg. 7: even, >= 2 */
+    int32_t precision;  /* ssm_precision */
+    double lo, hi;      /* spectral interval (a, b) of Section 2; lo >= hi selects the
+                           Gershgorin interval padded by 1e-3 of its width per side */
+    double tau;         /* truncation of Alg. 4 (keep s_j >= tau max s); <= 0 selects 1e-7 */
+    double kappa;       /* slack of Alg. 4's range filter [-kappa g_max, (1+kappa) g_max];
+                           < 0 selects 1e-6 */
+    int32_t n_theta;    /* quadrature size N_theta of Alg. 1 (> M); 0 selects 2M */
+    int32_t reserved;
+    double eps_floor;   /* rounding unit of the floor of Alg. 4's truncation: an eigenvalue
+                           of K_W(t) is also dropped below
+                           8 n_v eps_floor max_i X_0[i][i] sum_{l<=M/2} (l+1)|mu_l(t)|,
+                           the size of the rounding error of K_W(t), so that points where
+                           K_W(t) is numerically zero give no spurious terms; 0 selects the
+                           working precision (2^-52 for SSM_FP64, 2^-23 for SSM_MIXED),
+                           a negative value disables the floor */
+} ssm_params;
+
+typedef struct ssm_plan_s* ssm_plan_t;
+
+/* Create a plan for one operator (Section 2, spectral transform; Alg. 7
+ * setup).  Exactly one of `st` and `csr` is non-NULL.  The operator is copied
+ * to the device, checked (finite values; for CSR also structural and
+ * numerical symmetry), and the interval (a, b) is fixed.  `stream` is a
+ * cudaStream_t (NULL = the legacy default stream).  The plan owns all its
+ * device memory; probe blocks, moments and per-point work buffers are
+ * allocated on first use and reused.  Returns SSM_EINVAL, SSM_ENOTSYM,
+ * SSM_ENONFINITE, SSM_ENOMEM or SSM_ECUDA on failure, with *out = NULL. */
+ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr* csr,
+                           const ssm_params* params, void* stream);
+
+/* The plan's Chebyshev interval (a, b), its spectral bounds [lo, hi] (the
+ * unpadded Gershgorin interval, or the caller's interval), and the problem
+ * size.  Any output may be NULL. */
+ssm_status ssm_plan_info(ssm_plan_t plan, double* a, double* b, double* lo, double* hi, int64_t* n,
+                         int64_t* nnz);
+
+/* Chebyshev moments X_l = W^T T_l(A~) W, l = 0..M (Alg. 7's X_W, X_C and
+ * X_W~ for all column pairs at once; Alg. 2's zeta_l = Tr X_l / n_tot).
+ * W is N x n_tot (n_tot = n_v + n_vh) float64, row-major with leading
+ * dimension ldw >= n_tot; columns [0, n_v) are W, [n_v, n_tot) are W~.
+ * The block recurrence V_{k+1} = 2 A~ V_k - V_{k-1} runs M/2 steps and the
+ * moments come from the Gram products V_k^T V_k and V_{k+1}^T V_k by
+ * T_{2k} = 2 T_k^2 - T_0 and T_{2k+1} = 2 T_{k+1} T_k - T_1.  The moments stay on
+ * the device for ssm_dos / ssm_trace_f; if `moments` is non-NULL they are
+ * also copied there ((M+1) x n_tot x n_tot float64, symmetrised).
+ * Returns SSM_ENONFINITE if W or the moments are not finite. */
+ssm_status ssm_moments(ssm_plan_t plan, const double* W, int64_t ldw, double* moments);
+
+/* DOS at n_t sweep points (Alg. 7 final loop and Alg. 2 final loop) from the
+ * moments of the last ssm_moments call.  t: n_t points (host or device).
+ * dos_ss: RESS-DGC estimate of Tr g_sigma^{M/2}(tI - A) (Theorem 4);
+ * dos_kpm: DGC/KPM estimate sum_{l<=M} mu_l(t) Tr X_l / n_tot.  Either output
+ * may be NULL.  rank (nullable): n_t x 2 int32, the kept ranks after Alg. 4's
+ * truncation and after its range filter.  Returns SSM_ESTATE without
+ * moments, SSM_EINVAL for sigma <= 0 or n_t < 0 (n_t = 0 is a no-op). */
+ssm_status ssm_dos(ssm_plan_t plan, const double* t, int64_t n_t, double sigma,
+                   double* dos_ss, double* dos_kpm, int32_t* rank);
+
+/* Tr f(A) (Section 5, Eq. hform, Eq. pifunc, Alg. 8).  The spectral bounds
+ * [lo, hi] of the plan's Gershgorin interval are mapped onto [-a, a] of a
+ * unit variable (0 < a < 1); on the periodic grid of n_t points the
+ * library evaluates f (host callback f(x, ctx)) at every grid point and at
+ * both ends, forms h, deconvolves it by the unit-mass Gaussian of width
+ * sigma (frequencies where the Gaussian's DFT is below 1e-14 of its peak are
+ * dropped), evaluates both DOS estimates at the grid points and returns
+ * N dx sum_i f~(x_i) phi(x_i) for each.  Either output may be NULL.  Returns
+ * SSM_EDOMAIN if f is not finite at a grid point. */
+ssm_status ssm_trace_f(ssm_plan_t plan, double (*f)(double x, void* ctx), void* ctx,
+                       int64_t n_t, double sigma, double sigma_tilde, double a,
+                       double* tr_ss, double* tr_kpm);
+
+/* Gram pair of two row-major device blocks (float64): G_aa = A^T A and
+ * G_ab = A^T B, the products behind the doubling identities
+ * T_{2k} = 2 T_k^2 - T_0 and T_{2k+1} = 2 T_{k+1} T_k - T_1 (the product rule
+ * used in Proposition 1's proof), for callers that run their own
+ * recurrence.  A and B are n_rows x n_cols with leading dimension ld >= n_cols
+ * (elements); B may be NULL (then G_ab is not written).  Outputs are
+ * n_cols x n_cols row-major, device memory.  All pointers must be device
+ * pointers of the current device.  Partial sums over row slices are added
+ * in a fixed order, so repeated calls give identical results.  The call
+ * allocates its partial-sum buffer with cudaMalloc, runs on `stream` and
+ * returns after completion.  SSM_EINVAL for bad sizes or host pointers. */
+ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32_t n_cols, int64_t ld,
+                         double* G_aa, double* G_ab, void* stream);
+
+/* Chebyshev coefficient tables of Alg. 1 and Proposition 1 at n_t points
+ * (host or device t): mu: n_t x (M+1), mu_l(t_i) of g_sigma(t_i - .) in T_l(A~);
+ * nu: n_t x (M+1), the coefficients of the square of the degree-M/2 series.
+ * Either output may be NULL.  Needs no moments. */
+ssm_status ssm_coefficients(ssm_plan_t plan, const double* t, int64_t n_t, double sigma,
+                            double* mu, double* nu);
+
+/* Per-phase device times and launch counts, accumulated over calls since the
+ * last reset while timing is enabled.  Timing records CUDA events on the
+ * plan's stream around each phase and around every recurrence launch. */
+typedef struct {
+    double ms_coeffs;       /* Alg. 1 + Prop. 1 tables */
+    double ms_recurrence;   /* sum over the stencil / CSR recurrence launches */
+    double ms_gram;         /* Gram products of the doubling identities */
+    double ms_reduce;       /* partial-Gram reduction into the moments */
+    double ms_assemble;     /* K_W, K_Z, K_C, K_W~ at every sweep point */
+    double ms_solve;        /* Alg. 4 + Alg. 6 per sweep point */
+    double ms_kpm;          /* Alg. 2 line */
+    double ms_trace;        /* Alg. 8 deconvolution and quadrature */
+    int64_t recurrence_launches;
+    int64_t gram_launches;
+    int64_t launches;       /* every kernel launch of the library */
+} ssm_stats;
+
+ssm_status ssm_timing_enable(ssm_plan_t plan, int32_t on);
+ssm_status ssm_stats_get(ssm_plan_t plan, ssm_stats* out);
+ssm_status ssm_stats_reset(ssm_plan_t plan);
+
+/* Release the plan and all its device memory.  NULL is a no-op. */
+void ssm_plan_destroy(ssm_plan_t plan);
+
+/* Message for the last failing call on `plan` (or for the last failing
+ * ssm_plan_create when plan is NULL).  Valid until the next call. */
+const char* ssm_last_error(ssm_plan_t plan);
+
+/* Static name of a status code. */
+const char* ssm_status_string(ssm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSM_H */

@@ -21,7 +21,8 @@ ambiguous the reading taken is stated in the docstring:
   the square of the degree-M/2 series, which Theorem 4 requires.
 * Moments are symmetrised, X_l <- (X_l + X_l^T)/2 (exact in exact arithmetic).
 * Algorithm 4's truncation keeps s_j >= tau * max s (tau default 1e-7, the
-  value the paper uses for its pseudo-inverse variant); nothing is kept when
+  value the paper uses for its pseudo-inverse variant) and s_j above the
+  rounding floor of K_W(t) (see rounding_floor); nothing is kept when
   max s <= 0.  The range filter keeps xi in [-kappa g_max, (1+kappa) g_max],
   a rounding slack around the paper's closed interval [0, g_max].
 * Algorithm 8 uses the unit-mass Gaussian N g_sigma for the deconvolution
@@ -42,7 +43,7 @@ __all__ = [
     "csr_matrix", "gershgorin", "spectral_interval", "transform",
     "g_sigma", "g_max", "dgc_coefficients", "squared_coefficients",
     "coefficient_tables", "moments_direct", "moments_doubling",
-    "kpm_dos", "assemble", "geneig", "ress_dos_point", "ress_dgc",
+    "kpm_dos", "assemble", "rounding_floor", "geneig", "ress_dos_point", "ress_dgc",
     "exact_dos", "relative_l1_error", "trace_grid", "deconvolve_h",
     "trace_f",
 ]
@@ -237,13 +238,36 @@ def assemble(mu_row: np.ndarray, nu_row: np.ndarray, X: np.ndarray, n_v: int):
     return K[:n_v, :n_v], KZ, K[n_v:, :n_v], K[n_v:, n_v:]
 
 
+def rounding_floor(mu_half_row: np.ndarray, X: np.ndarray, n_v: int, eps: float) -> float:
+    """Size below which an eigenvalue of K_W(t) is rounding noise.
+
+    K_W(t) = sum_l mu_l X_l[W,W] with |X_l[i][j]| <= max_i X_0[i][i] (Cauchy-
+    Schwarz, |T_l| <= 1); the three-term recurrence lets the rounding error
+    of X_l grow at most linearly in l, so the error of K_W is of order
+    eps * max_i X_0[i][i] * sum_l (l+1) |mu_l|; times n_v for the 2-norm of an
+    n_v x n_v perturbation and a safety factor.
+    """
+    x0 = float(np.max(np.diag(X[0])[:n_v]))
+    l = np.arange(mu_half_row.size)
+    return FLOOR_SAFETY * n_v * eps * x0 * float(np.sum((l + 1.0) * np.abs(mu_half_row)))
+
+
+FLOOR_SAFETY = 8.0
+EPS_FP64 = 2.0 ** -52
+
+
 def geneig(K_W: np.ndarray, K_Z: np.ndarray, gmax: float, tau: float = 1e-7,
-           kappa: float = 1e-6, flag_eps: float = 0.0):
+           kappa: float = 1e-6, flag_eps: float = 0.0, floor: float = 0.0):
     """Generalised eigenproblem K_Z C = K_W C Xi restricted as in Alg. 4.
 
-    1. K_W = U S U^T;  2. keep s_j >= tau max s;  3. eigh of
+    1. K_W = U S U^T;  2. keep s_j >= max(tau max s, floor);  3. eigh of
     S~^-1/2 U~^T K_Z U~ S~^-1/2 = X Xi X^T;  4. keep xi in the range of
     g_sigma, [-kappa gmax, (1+kappa) gmax];  5. C~ = U~ S~^-1/2 X~.
+
+    `floor` is the rounding floor of K_W (see rounding_floor): where K_W(t)
+    is numerically zero (t outside the spectrum) the paper's relative rule
+    alone would keep pure rounding noise, whose ratios xi land anywhere in
+    the filter range.
 
     Returns (xi_kept, C_kept, info) where info has the kept ranks and a
     flag that is set when some s_j or xi lies within flag_eps (relative to
@@ -256,7 +280,7 @@ def geneig(K_W: np.ndarray, K_Z: np.ndarray, gmax: float, tau: float = 1e-7,
     if smax <= 0.0:
         n = K_W.shape[0]
         return np.zeros(0), np.zeros((n, 0)), dict(rank_s=0, rank_xi=0, flagged=False)
-    thr = tau * smax
+    thr = max(tau * smax, floor)
     keep = s >= thr
     if flag_eps > 0.0 and np.any(np.abs(s - thr) <= flag_eps * smax):
         flagged = True
@@ -274,13 +298,13 @@ def geneig(K_W: np.ndarray, K_Z: np.ndarray, gmax: float, tau: float = 1e-7,
 
 
 def ress_dos_point(K_W, K_Z, K_C, K_Wt, gmax: float, tau: float = 1e-7,
-                   kappa: float = 1e-6, flag_eps: float = 0.0):
+                   kappa: float = 1e-6, flag_eps: float = 0.0, floor: float = 0.0):
     """One sweep point of Alg. 7 (Alg. 6's estimate applied to g^{M/2}(tI - A)).
 
     phi = Tr Xi~ + (1/N~_v) (Tr K_W~ - Tr K_C C~ C~^T K_C^T); the hybrid
     correction is absent when N~_v = 0.
     """
-    xi, C, info = geneig(K_W, K_Z, gmax, tau, kappa, flag_eps)
+    xi, C, info = geneig(K_W, K_Z, gmax, tau, kappa, flag_eps, floor)
     phi = float(np.sum(xi))
     nvh = K_Wt.shape[0]
     if nvh > 0:
@@ -293,11 +317,12 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
              sigma: float, tau: float = 1e-7, kappa: float = 1e-6,
              interval: Optional[Tuple[float, float]] = None,
              n_theta: Optional[int] = None, flag_eps: float = 0.0,
-             moments: str = "direct") -> Dict[str, np.ndarray]:
+             moments: str = "direct", eps_floor: float = EPS_FP64) -> Dict[str, np.ndarray]:
     """RESS-DGC (Alg. 7) and the DGC/KPM line (Alg. 2) on the same probes.
 
-    W_all = [W, W~] (N x (n_v + n_vh)).  Returns dos_ss, dos_kpm, the kept
-    ranks, the flags, the interval and the moments.
+    W_all = [W, W~] (N x (n_v + n_vh)).  eps_floor sets the rounding floor
+    of Alg. 4's truncation (0 disables it).  Returns dos_ss, dos_kpm, the
+    kept ranks, the flags, the interval and the moments.
     """
     A = sp.csr_matrix(A)
     N = A.shape[0]
@@ -313,7 +338,8 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
     flags = np.zeros(nt, dtype=bool)
     for i in range(nt):
         K_W, K_Z, K_C, K_Wt = assemble(tab["mu_half"][i], tab["nu"][i], X, n_v)
-        dos_ss[i], info = ress_dos_point(K_W, K_Z, K_C, K_Wt, gm, tau, kappa, flag_eps)
+        fl = rounding_floor(tab["mu_half"][i], X, n_v, eps_floor) if eps_floor > 0 else 0.0
+        dos_ss[i], info = ress_dos_point(K_W, K_Z, K_C, K_Wt, gm, tau, kappa, flag_eps, fl)
         rank_s[i], rank_xi[i], flags[i] = info["rank_s"], info["rank_xi"], info["flagged"]
     dos_kpm = kpm_dos(tab["mu_full"], X)
     return dict(dos_ss=dos_ss, dos_kpm=dos_kpm, rank_s=rank_s, rank_xi=rank_xi,

@@ -1,0 +1,13 @@
+"""GB300-native spectrum sweeping (RESS-DGC) DOS estimator.
+
+The computation lives in libssm.so (CUDA for sm_103a, C ABI in
+include/ssm.h); this package builds it (``build.build``) and binds it
+(``api``).  There is no CPU fallback: calls fail when the library is missing.
+"""
+from .api import (Plan, ssm_coefficients, ssm_dos, ssm_gram_pair, ssm_moments, ssm_plan_create, ssm_plan_destroy,
+                  ssm_plan_info, ssm_stats_get, ssm_stats_reset, ssm_timing_enable, ssm_trace_f)
+from ._native import SSMError
+
+__all__ = ["Plan", "SSMError", "ssm_coefficients", "ssm_dos", "ssm_gram_pair", "ssm_moments", "ssm_plan_create",
+           "ssm_plan_destroy", "ssm_plan_info", "ssm_stats_get", "ssm_stats_reset", "ssm_timing_enable",
+           "ssm_trace_f"]

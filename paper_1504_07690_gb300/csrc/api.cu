@@ -1,0 +1,798 @@
+// api.cu - the C ABI: plan life cycle, argument checks, host<->device staging
+// and the order of the kernels of Alg. 7 / Alg. 2 / Alg. 8.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ssm;
+
+struct ssm_plan_s {
+    Plan P;
+    std::vector<cudaEvent_t> events;   // pool for per-phase timing
+    size_t next_event = 0;
+    struct Mark {
+        int phase;
+        size_t e0, e1;
+    };
+    std::vector<Mark> marks;
+    // per-point buffers
+    double* d_t = nullptr;
+    double* d_mu = nullptr;
+    double* d_nu = nullptr;
+    double* d_K = nullptr;
+    double* d_KZ = nullptr;
+    double* d_zeta = nullptr;
+    double* d_dos_ss = nullptr;
+    double* d_dos_kpm = nullptr;
+    int32_t* d_rank = nullptr;
+    double* d_solve = nullptr;
+    size_t cap_t = 0;       // capacity (points) of d_t, d_dos_*, d_rank
+    size_t cap_batch = 0;   // capacity (points) of the batch buffers
+    // trace buffers
+    double* d_tr = nullptr;
+    size_t cap_tr = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum Phase { PH_COEFFS, PH_REC, PH_GRAM, PH_REDUCE, PH_ASSEMBLE, PH_SOLVE, PH_KPM, PH_TRACE };
+
+constexpr int64_t BATCH_T = 256;     // sweep points per assembly / solve batch
+constexpr double DECONV_CUTOFF = 1e-14;
+
+ssm_status fail(ssm_plan_s* h, ssm_status st, const std::string& msg) {
+    if (h)
+        h->P.err = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+#define CUDA_OR_FAIL(h, call)                                                                            \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA,                  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+        }                                                                                                \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+// Copy `bytes` from a host or device pointer to device memory.
+cudaError_t to_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s);
+}
+
+cudaError_t from_device(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           s);
+}
+
+// ------------------------------------------------------------- timing marks
+
+size_t take_event(ssm_plan_s* h) {
+    if (h->next_event == h->events.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+        h->events.push_back(e);
+    }
+    return h->next_event++;
+}
+
+struct Scope {
+    ssm_plan_s* h;
+    int phase;
+    size_t e0 = (size_t)-1;
+    Scope(ssm_plan_s* hh, int ph) : h(hh), phase(ph) {
+        if (h->P.timing) {
+            e0 = take_event(h);
+            if (e0 != (size_t)-1) cudaEventRecord(h->events[e0], h->P.stream);
+        }
+    }
+    ~Scope() {
+        if (h->P.timing && e0 != (size_t)-1) {
+            size_t e1 = take_event(h);
+            if (e1 != (size_t)-1) {
+                cudaEventRecord(h->events[e1], h->P.stream);
+                h->marks.push_back({phase, e0, e1});
+            }
+        }
+    }
+};
+
+// Resolve the marks of the finished call into the statistics.
+void settle_marks(ssm_plan_s* h) {
+    for (const auto& m : h->marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->events[m.e0], h->events[m.e1]) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        ssm_stats& s = h->P.stats;
+        switch (m.phase) {
+            case PH_COEFFS: s.ms_coeffs += ms; break;
+            case PH_REC: s.ms_recurrence += ms; break;
+            case PH_GRAM: s.ms_gram += ms; break;
+            case PH_REDUCE: s.ms_reduce += ms; break;
+            case PH_ASSEMBLE: s.ms_assemble += ms; break;
+            case PH_SOLVE: s.ms_solve += ms; break;
+            case PH_KPM: s.ms_kpm += ms; break;
+            case PH_TRACE: s.ms_trace += ms; break;
+        }
+    }
+    h->marks.clear();
+    h->next_event = 0;
+}
+
+ssm_status sync_and_settle(ssm_plan_s* h) {
+    cudaError_t e = cudaStreamSynchronize(h->P.stream);
+    if (e != cudaSuccess) return fail(h, SSM_ECUDA, std::string("stream sync: ") + cudaGetErrorString(e));
+    settle_marks(h);
+    return SSM_OK;
+}
+
+ssm_status read_flag(ssm_plan_s* h, int* value) {
+    Plan& P = h->P;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(value, P.d_flag, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
+    return SSM_OK;
+}
+
+void free_plan(ssm_plan_s* h) {
+    Plan& P = h->P;
+    dev_free(P.d_diag64);
+    dev_free(P.d_diag32);
+    dev_free(P.d_rowptr);
+    dev_free(P.d_colind);
+    dev_free(P.d_val64);
+    dev_free(P.d_val32);
+    for (auto& v : P.d_V) dev_free(v);
+    dev_free(P.d_part);
+    dev_free(P.d_X);
+    dev_free(P.d_flag);
+    dev_free(P.d_stage);
+    dev_free(P.d_ctab);
+    dev_free(P.d_work);
+    dev_free(h->d_t);
+    dev_free(h->d_mu);
+    dev_free(h->d_nu);
+    dev_free(h->d_K);
+    dev_free(h->d_KZ);
+    dev_free(h->d_zeta);
+    dev_free(h->d_dos_ss);
+    dev_free(h->d_dos_kpm);
+    dev_free(h->d_rank);
+    dev_free(h->d_solve);
+    dev_free(h->d_tr);
+    for (auto e : h->events) cudaEventDestroy(e);
+    delete h;
+}
+
+ssm_status ensure_stage(ssm_plan_s* h, size_t bytes) {
+    Plan& P = h->P;
+    if (P.stage_bytes >= bytes) return SSM_OK;
+    dev_free(P.d_stage);
+    P.d_stage = nullptr;
+    P.stage_bytes = 0;
+    CUDA_OR_FAIL(h, cudaMalloc((void**)&P.d_stage, bytes));
+    P.stage_bytes = bytes;
+    return SSM_OK;
+}
+
+// Buffers for n_t sweep points (outputs) and one batch of assembly / solve.
+ssm_status ensure_points(ssm_plan_s* h, int64_t n_t) {
+    Plan& P = h->P;
+    const int M = P.p.degree;
+    if ((size_t)n_t > h->cap_t) {
+        dev_free(h->d_t);
+        dev_free(h->d_dos_ss);
+        dev_free(h->d_dos_kpm);
+        dev_free(h->d_rank);
+        h->d_t = h->d_dos_ss = h->d_dos_kpm = nullptr;
+        h->d_rank = nullptr;
+        h->cap_t = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_t, n_t));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_dos_ss, n_t));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_dos_kpm, n_t));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_rank, 2 * n_t));
+        h->cap_t = n_t;
+    }
+    const int64_t nb = n_t < BATCH_T ? n_t : BATCH_T;
+    if ((size_t)nb > h->cap_batch) {
+        dev_free(h->d_mu);
+        dev_free(h->d_nu);
+        dev_free(h->d_K);
+        dev_free(h->d_KZ);
+        h->d_mu = h->d_nu = h->d_K = h->d_KZ = nullptr;
+        h->cap_batch = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_mu, (size_t)nb * (M + 1)));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_nu, (size_t)nb * (M + 1)));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_K, (size_t)nb * P.n_tot * P.n_tot));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_KZ, (size_t)nb * P.p.n_v * P.p.n_v));
+        h->cap_batch = nb;
+    }
+    if (!h->d_zeta) CUDA_OR_FAIL(h, dev_alloc(&h->d_zeta, M + 1));
+    if (!h->d_solve) {
+        CUDA_OR_FAIL(h, cudaMalloc((void**)&h->d_solve, solve_workspace_bytes(P.p.n_v)));
+    }
+    return SSM_OK;
+}
+
+// Coefficient tables for n points at d_tpts (device): mu -> dmu, nu -> dnu (ld M+1).
+ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, double sigma, double* dmu,
+                            double* dnu) {
+    Plan& P = h->P;
+    const int M = P.p.degree;
+    const double inv_norm = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
+    Scope sc(h, PH_COEFFS);
+    CUDA_OR_FAIL(h, launch_mu(d_tpts, n, sigma, inv_norm, P.a, P.b, M, P.n_theta, P.d_ctab, dmu, M + 1, P.stream));
+    P.stats.launches++;
+    if (dnu) {
+        CUDA_OR_FAIL(h, launch_nu(dmu, M + 1, n, M, dnu, M + 1, P.stream));
+        P.stats.launches++;
+    }
+    return SSM_OK;
+}
+
+// DOS at n device points d_tpts into h->d_dos_ss / h->d_dos_kpm (device), ranks into h->d_rank.
+ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigma) {
+    Plan& P = h->P;
+    const int M = P.p.degree, K = M / 2;
+    const int nv = P.p.n_v, nvh = P.p.n_vh, n_tot = P.n_tot;
+    const double gmax = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
+    const double xlo = -P.p.kappa * gmax, xhi = (1.0 + P.p.kappa) * gmax;
+    for (int64_t t0 = 0; t0 < n_t; t0 += BATCH_T) {
+        const int64_t nb = (n_t - t0) < BATCH_T ? (n_t - t0) : BATCH_T;
+        ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, h->d_nu);
+        if (st != SSM_OK) return st;
+        {
+            Scope sc(h, PH_ASSEMBLE);
+            CUDA_OR_FAIL(h, launch_assemble(h->d_mu, M + 1, nb, K + 1, P.d_X, n_tot, n_tot, n_tot, h->d_K, P.stream));
+            CUDA_OR_FAIL(h, launch_assemble(h->d_nu, M + 1, nb, M + 1, P.d_X, n_tot, nv, nv, h->d_KZ, P.stream));
+            P.stats.launches += 2;
+        }
+        {
+            Scope sc(h, PH_SOLVE);
+            const double floor_scale = 8.0 * nv * P.eps_floor * P.x0max;
+            CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, h->d_mu, M + 1, K,
+                                         floor_scale, h->d_solve, h->d_dos_ss + t0, h->d_rank + 2 * t0,
+                                         P.stream));
+            P.stats.launches++;
+        }
+        {
+            Scope sc(h, PH_KPM);
+            CUDA_OR_FAIL(h, launch_kpm(h->d_mu, M + 1, nb, M, P.d_X, n_tot, h->d_zeta, h->d_dos_kpm + t0, P.stream));
+            P.stats.launches += 2;
+        }
+    }
+    return SSM_OK;
+}
+
+}  // namespace
+
+// =====================================================================
+// ABI
+// =====================================================================
+
+extern "C" {
+
+const char* ssm_status_string(ssm_status s) {
+    switch (s) {
+        case SSM_OK: return "SSM_OK";
+        case SSM_EINVAL: return "SSM_EINVAL";
+        case SSM_ENOMEM: return "SSM_ENOMEM";
+        case SSM_ECUDA: return "SSM_ECUDA";
+        case SSM_ETIMEOUT: return "SSM_ETIMEOUT";
+        case SSM_ENONFINITE: return "SSM_ENONFINITE";
+        case SSM_ENOTSYM: return "SSM_ENOTSYM";
+        case SSM_EDOMAIN: return "SSM_EDOMAIN";
+        case SSM_ESTATE: return "SSM_ESTATE";
+    }
+    return "SSM_UNKNOWN";
+}
+
+const char* ssm_last_error(ssm_plan_t plan) {
+    if (!plan) return g_create_error.c_str();
+    return plan->P.err.c_str();
+}
+
+ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr* csr, const ssm_params* params,
+                           void* stream) {
+    if (!out) return fail(nullptr, SSM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params) return fail(nullptr, SSM_EINVAL, "params is NULL");
+    if ((st == nullptr) == (csr == nullptr)) return fail(nullptr, SSM_EINVAL, "give exactly one of stencil and csr");
+    const ssm_params& p = *params;
+    if (p.n_v < 1 || p.n_vh < 0 || p.n_v > 1024 || p.n_vh > 1024)
+        return fail(nullptr, SSM_EINVAL, "need 1 <= n_v <= 1024 and 0 <= n_vh <= 1024");
+    if (p.degree < 2 || (p.degree & 1) || p.degree > (1 << 20))
+        return fail(nullptr, SSM_EINVAL, "degree M must be even and in [2, 2^20]");
+    if (p.precision != SSM_FP64 && p.precision != SSM_MIXED) return fail(nullptr, SSM_EINVAL, "unknown precision");
+    if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
+    if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
+
+    ssm_plan_s* h = new ssm_plan_s();
+    Plan& P = h->P;
+    P.p = p;
+    if (P.p.tau <= 0.0) P.p.tau = 1e-7;
+    if (P.p.kappa < 0.0) P.p.kappa = 1e-6;
+    if (P.p.eps_floor == 0.0)
+        P.eps_floor = (p.precision == SSM_MIXED) ? 1.0 / 8388608.0 : 1.0 / 4503599627370496.0;
+    else
+        P.eps_floor = P.p.eps_floor > 0.0 ? P.p.eps_floor : 0.0;
+    if (!isfinite(p.eps_floor)) return fail(nullptr, SSM_EINVAL, "eps_floor must be finite");
+    P.n_theta = p.n_theta ? p.n_theta : 2 * p.degree;
+    P.n_tot = p.n_v + p.n_vh;
+    P.mixed = (p.precision == SSM_MIXED);
+    P.stream = (cudaStream_t)stream;
+    cudaGetDevice(&P.device);
+    double* d_raw = nullptr;   // raw diag (stencil) or raw values (csr), float64
+    double* d_bnd = nullptr;   // per-block Gershgorin bounds
+    auto bail = [&](ssm_status s, const std::string& m) {
+        cudaStreamSynchronize(P.stream);
+        dev_free(d_raw);
+        dev_free(d_bnd);
+        free_plan(h);
+        return fail(nullptr, s, m);
+    };
+#define CREATE_CUDA(call)                                                                                     \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess)                                                                                \
+            return bail(e_ == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA,                            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                                  \
+    } while (0)
+
+    CREATE_CUDA(cudaMalloc((void**)&P.d_flag, sizeof(int)));
+    CREATE_CUDA(cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
+    double extra = 0.0;
+    double raw_off[3] = {0, 0, 0};
+    if (st) {
+        P.is_stencil = true;
+        for (int a = 0; a < 3; ++a)
+            if (st->dims[a] < 1) return bail(SSM_EINVAL, "stencil dims must be >= 1");
+        const int64_t n = st->dims[0] * st->dims[1] * st->dims[2];
+        if (n < 1 || n > (1LL << 31)) return bail(SSM_EINVAL, "stencil size out of range");
+        if (!st->diag) return bail(SSM_EINVAL, "stencil diag is NULL");
+        for (int a = 0; a < 3; ++a)
+            if (!isfinite(st->offdiag[a])) return bail(SSM_ENONFINITE, "stencil offdiag not finite");
+        P.n = n;
+        P.geom.d0 = (uint32_t)st->dims[0];
+        P.geom.d1 = (uint32_t)st->dims[1];
+        P.geom.d2 = (uint32_t)st->dims[2];
+        int64_t nnz = n;
+        for (int a = 0; a < 3; ++a) {
+            const uint32_t ext = (uint32_t)st->dims[a];
+            P.geom.per[a] = st->periodic[a] ? 1u : 0u;
+            raw_off[a] = st->offdiag[a];
+            if (st->offdiag[a] == 0.0 || (ext == 1 && !st->periodic[a])) {
+                P.geom.active[a] = 0;
+            } else if (ext == 1) {
+                // a periodic axis of extent one couples a row to itself twice
+                extra += 2.0 * st->offdiag[a];
+                P.geom.active[a] = 0;
+            } else {
+                P.geom.active[a] = 1;
+                nnz += (ext == 2 && st->periodic[a]) ? n : 2 * n;
+                if (!st->periodic[a]) nnz -= 2 * (n / ext);
+            }
+        }
+        P.nnz = nnz;
+        CREATE_CUDA(dev_alloc(&d_raw, n));
+        CREATE_CUDA(to_device(d_raw, st->diag, n * sizeof(double), P.stream));
+        const int nb = operator_bound_blocks(n);
+        CREATE_CUDA(dev_alloc(&d_bnd, 2 * nb));
+        CREATE_CUDA(launch_stencil_bounds(P, d_raw, raw_off, extra, d_bnd, P.d_flag, P.stream));
+    } else {
+        if (csr->n < 1 || csr->n > (1LL << 31) - 1 || csr->nnz < 0)
+            return bail(SSM_EINVAL, "csr size out of range");
+        if (!csr->rowptr || (csr->nnz > 0 && (!csr->colind || !csr->val)))
+            return bail(SSM_EINVAL, "csr arrays are NULL");
+        P.n = csr->n;
+        P.nnz = csr->nnz;
+        CREATE_CUDA(dev_alloc(&P.d_rowptr, P.n + 1));
+        CREATE_CUDA(dev_alloc(&P.d_colind, P.nnz));
+        CREATE_CUDA(dev_alloc(&d_raw, P.nnz));
+        CREATE_CUDA(to_device(P.d_rowptr, csr->rowptr, (P.n + 1) * sizeof(int64_t), P.stream));
+        CREATE_CUDA(to_device(P.d_colind, csr->colind, P.nnz * sizeof(int32_t), P.stream));
+        CREATE_CUDA(to_device(d_raw, csr->val, P.nnz * sizeof(double), P.stream));
+        int64_t rp[2] = {0, 0};
+        CREATE_CUDA(cudaMemcpyAsync(&rp[0], P.d_rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, P.stream));
+        CREATE_CUDA(cudaMemcpyAsync(&rp[1], P.d_rowptr + P.n, sizeof(int64_t), cudaMemcpyDeviceToHost, P.stream));
+        CREATE_CUDA(cudaStreamSynchronize(P.stream));
+        if (rp[0] != 0 || rp[1] != P.nnz) return bail(SSM_EINVAL, "csr rowptr must start at 0 and end at nnz");
+        CREATE_CUDA(launch_csr_validate(P, d_raw, P.d_flag, P.stream));
+        int flag = 0;
+        CREATE_CUDA(cudaMemcpyAsync(&flag, P.d_flag, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+        CREATE_CUDA(cudaStreamSynchronize(P.stream));
+        if (flag) {
+            if (flag & 2) return bail(SSM_EINVAL, "csr structure invalid (rowptr, column range or order)");
+            if (flag & 1) return bail(SSM_ENONFINITE, "csr values not finite");
+            return bail(SSM_ENOTSYM, "csr matrix is not symmetric");
+        }
+        const int nb = operator_bound_blocks(P.n);
+        CREATE_CUDA(dev_alloc(&d_bnd, 2 * nb));
+        CREATE_CUDA(launch_csr_bounds(P, d_raw, d_bnd, P.stream));
+    }
+    // Gershgorin interval (per-block results reduced here in block order)
+    {
+        const int nb = operator_bound_blocks(P.n);
+        std::vector<double> hb(2 * nb);
+        int flag = 0;
+        CREATE_CUDA(cudaMemcpyAsync(hb.data(), d_bnd, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+        CREATE_CUDA(cudaMemcpyAsync(&flag, P.d_flag, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+        CREATE_CUDA(cudaStreamSynchronize(P.stream));
+        dev_free(d_bnd);
+        d_bnd = nullptr;
+        if (flag) return bail(SSM_ENONFINITE, "operator diagonal not finite");
+        double lo = hb[0], hi = hb[1];
+        for (int i = 1; i < nb; ++i) {
+            lo = fmin(lo, hb[2 * i]);
+            hi = fmax(hi, hb[2 * i + 1]);
+        }
+        if (p.lo < p.hi) {
+            P.glo = p.lo;
+            P.ghi = p.hi;
+            P.a = p.lo;
+            P.b = p.hi;
+        } else {
+            P.glo = lo;
+            P.ghi = hi;
+            double w = hi - lo;
+            if (w <= 0.0) w = fmax(fabs(lo), 1.0);
+            P.a = lo - 1e-3 * w;
+            P.b = hi + 1e-3 * w;
+        }
+        P.alpha = 4.0 / (P.b - P.a);
+        P.beta = -2.0 * (P.a + P.b) / (P.b - P.a);
+    }
+    // fold the map into the operator
+    if (P.is_stencil) {
+        CREATE_CUDA(dev_alloc(&P.d_diag64, P.n));
+        CREATE_CUDA(dev_alloc(&P.d_diag32, P.n));
+        for (int a = 0; a < 3; ++a) {
+            P.off64[a] = P.alpha * raw_off[a];
+            P.off32[a] = (float)P.off64[a];
+        }
+        CREATE_CUDA(launch_fold_stencil(P, d_raw, extra, P.stream));
+    } else {
+        CREATE_CUDA(dev_alloc(&P.d_val64, P.nnz));
+        CREATE_CUDA(dev_alloc(&P.d_val32, P.nnz));
+        CREATE_CUDA(launch_fold_csr(P, d_raw, P.stream));
+    }
+    CREATE_CUDA(cudaStreamSynchronize(P.stream));
+    dev_free(d_raw);
+    d_raw = nullptr;
+    // recurrence and moment buffers
+    const int vec = P.mixed ? 4 : 2;
+    P.ld = (P.n_tot + vec - 1) / vec * vec;
+    if ((uint64_t)P.n * (uint64_t)(P.ld / vec) >= (1ULL << 32)) return bail(SSM_EINVAL, "N x n_tot too large");
+    const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
+    for (auto& v : P.d_V) CREATE_CUDA(cudaMalloc(&v, (size_t)P.n * P.ld * esz));
+    P.n_split = gram_split_count(P.n, P.n_tot);
+    CREATE_CUDA(dev_alloc(&P.d_part, (size_t)P.n_split * 2 * P.n_tot * P.n_tot));
+    CREATE_CUDA(dev_alloc(&P.d_X, (size_t)(p.degree + 1) * P.n_tot * P.n_tot));
+    CREATE_CUDA(dev_alloc(&P.d_ctab, 2 * (size_t)P.n_theta));
+    CREATE_CUDA(launch_cos_table(P.d_ctab, P.n_theta, P.stream));
+    CREATE_CUDA(cudaStreamSynchronize(P.stream));
+#undef CREATE_CUDA
+    *out = h;
+    return SSM_OK;
+}
+
+ssm_status ssm_plan_info(ssm_plan_t h, double* a, double* b, double* lo, double* hi, int64_t* n, int64_t* nnz) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    if (a) *a = h->P.a;
+    if (b) *b = h->P.b;
+    if (lo) *lo = h->P.glo;
+    if (hi) *hi = h->P.ghi;
+    if (n) *n = h->P.n;
+    if (nnz) *nnz = h->P.nnz;
+    return SSM_OK;
+}
+
+ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* moments) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (!W) return fail(h, SSM_EINVAL, "W is NULL");
+    if (ldw < P.n_tot) return fail(h, SSM_EINVAL, "ldw < n_v + n_vh");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    P.have_moments = false;
+    const int M = P.p.degree, S = M / 2;
+    const size_t nn = (size_t)P.n_tot * P.n_tot;
+    // W -> V_0 (working precision, zero-padded to ld)
+    const double* src = W;
+    int64_t ldsrc = ldw;
+    if (!is_device_ptr(W)) {
+        ssm_status s = ensure_stage(h, (size_t)P.n * P.n_tot * sizeof(double));
+        if (s != SSM_OK) return s;
+        CUDA_OR_FAIL(h, cudaMemcpy2DAsync(P.d_stage, P.n_tot * sizeof(double), W, ldw * sizeof(double),
+                                          P.n_tot * sizeof(double), P.n, cudaMemcpyHostToDevice, P.stream));
+        src = P.d_stage;
+        ldsrc = P.n_tot;
+    }
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
+    if (ldsrc == P.n_tot) {
+        CUDA_OR_FAIL(h, launch_check_finite(src, P.n * (int64_t)P.n_tot, P.d_flag, P.stream));
+        P.stats.launches++;
+    }
+    CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, P.stream));
+    P.stats.launches++;
+    auto gram = [&](const void* A, const void* B) -> cudaError_t {
+        if (P.mixed)
+            return launch_gram_f32((const float*)A, (const float*)B, P.ld, P.n_tot, P.n, P.n_split, P.d_part,
+                                   P.stream);
+        return launch_gram_f64((const double*)A, (const double*)B, P.ld, P.n_tot, P.n, P.n_split, P.d_part,
+                               P.stream);
+    };
+    {
+        Scope sc(h, PH_GRAM);
+        CUDA_OR_FAIL(h, gram(P.d_V[0], nullptr));
+        P.stats.launches++;
+        P.stats.gram_launches++;
+    }
+    {
+        Scope sc(h, PH_REDUCE);
+        CUDA_OR_FAIL(h, launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, -1, P.stream));
+        P.stats.launches++;
+    }
+    for (int k = 0; k < S; ++k) {
+        void* Vc = P.d_V[k % 3];
+        void* Vp = P.d_V[(k + 2) % 3];
+        void* Vn = P.d_V[(k + 1) % 3];
+        const double c = (k == 0) ? 0.5 : 1.0, d = (k == 0) ? 0.0 : 1.0;
+        {
+            Scope sc(h, PH_REC);
+            cudaError_t e;
+            if (P.mixed) {
+                e = P.is_stencil ? launch_stencil_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn,
+                                                           (float)c, (float)d, P.stream)
+                                 : launch_csr_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn, (float)c,
+                                                       (float)d, P.stream);
+            } else {
+                e = P.is_stencil ? launch_stencil_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c,
+                                                           d, P.stream)
+                                 : launch_csr_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d,
+                                                       P.stream);
+            }
+            CUDA_OR_FAIL(h, e);
+            P.stats.launches++;
+            P.stats.recurrence_launches++;
+        }
+        {
+            Scope sc(h, PH_GRAM);
+            CUDA_OR_FAIL(h, gram(Vn, Vc));
+            P.stats.launches++;
+            P.stats.gram_launches++;
+        }
+        {
+            Scope sc(h, PH_REDUCE);
+            CUDA_OR_FAIL(h, launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, k, P.stream));
+            P.stats.launches++;
+        }
+    }
+    CUDA_OR_FAIL(h, launch_check_finite(P.d_X, (int64_t)(M + 1) * nn, P.d_flag, P.stream));
+    P.stats.launches++;
+    if (moments) CUDA_OR_FAIL(h, from_device(moments, P.d_X, (size_t)(M + 1) * nn * sizeof(double), P.stream));
+    ssm_status s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    int flag = 0;
+    s = read_flag(h, &flag);
+    if (s != SSM_OK) return s;
+    if (flag) return fail(h, SSM_ENONFINITE, "W or the moments contain NaN/Inf");
+    {
+        std::vector<double> d0(P.p.n_v);
+        CUDA_OR_FAIL(h, cudaMemcpy2DAsync(d0.data(), sizeof(double), P.d_X, (P.n_tot + 1) * sizeof(double),
+                                          sizeof(double), P.p.n_v, cudaMemcpyDeviceToHost, P.stream));
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+        double m = 0.0;
+        for (double v : d0) m = fmax(m, v);
+        P.x0max = m;
+    }
+    P.have_moments = true;
+    return SSM_OK;
+}
+
+ssm_status ssm_coefficients(ssm_plan_t h, const double* t, int64_t n_t, double sigma, double* mu, double* nu) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (n_t < 0 || !(sigma > 0.0) || !isfinite(sigma)) return fail(h, SSM_EINVAL, "need n_t >= 0 and sigma > 0");
+    if (n_t == 0) return SSM_OK;
+    if (!t) return fail(h, SSM_EINVAL, "t is NULL");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    const int M = P.p.degree;
+    double *dmu = nullptr, *dnu = nullptr, *dt = nullptr;
+    CUDA_OR_FAIL(h, dev_alloc(&dt, n_t));
+    cudaError_t e = dev_alloc(&dmu, (size_t)n_t * (M + 1));
+    if (e == cudaSuccess) e = dev_alloc(&dnu, (size_t)n_t * (M + 1));
+    if (e == cudaSuccess) e = to_device(dt, t, n_t * sizeof(double), P.stream);
+    ssm_status s = SSM_OK;
+    if (e != cudaSuccess) {
+        s = fail(h, e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA, cudaGetErrorString(e));
+    } else {
+        s = coefficients_dev(h, dt, n_t, sigma, dmu, dnu);
+    }
+    if (s == SSM_OK && mu) {
+        e = from_device(mu, dmu, (size_t)n_t * (M + 1) * sizeof(double), P.stream);
+        if (e != cudaSuccess) s = fail(h, SSM_ECUDA, cudaGetErrorString(e));
+    }
+    if (s == SSM_OK && nu) {
+        e = from_device(nu, dnu, (size_t)n_t * (M + 1) * sizeof(double), P.stream);
+        if (e != cudaSuccess) s = fail(h, SSM_ECUDA, cudaGetErrorString(e));
+    }
+    if (s == SSM_OK) s = sync_and_settle(h);
+    cudaStreamSynchronize(P.stream);
+    dev_free(dt);
+    dev_free(dmu);
+    dev_free(dnu);
+    return s;
+}
+
+ssm_status ssm_dos(ssm_plan_t h, const double* t, int64_t n_t, double sigma, double* dos_ss, double* dos_kpm,
+                   int32_t* rank) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (n_t < 0 || !(sigma > 0.0) || !isfinite(sigma)) return fail(h, SSM_EINVAL, "need n_t >= 0 and sigma > 0");
+    if (!P.have_moments) return fail(h, SSM_ESTATE, "ssm_dos needs ssm_moments first");
+    if (n_t == 0) return SSM_OK;
+    if (!t) return fail(h, SSM_EINVAL, "t is NULL");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    ssm_status s = ensure_points(h, n_t);
+    if (s != SSM_OK) return s;
+    CUDA_OR_FAIL(h, to_device(h->d_t, t, n_t * sizeof(double), P.stream));
+    s = dos_dev(h, h->d_t, n_t, sigma);
+    if (s != SSM_OK) return s;
+    if (dos_ss) CUDA_OR_FAIL(h, from_device(dos_ss, h->d_dos_ss, n_t * sizeof(double), P.stream));
+    if (dos_kpm) CUDA_OR_FAIL(h, from_device(dos_kpm, h->d_dos_kpm, n_t * sizeof(double), P.stream));
+    if (rank) CUDA_OR_FAIL(h, from_device(rank, h->d_rank, 2 * n_t * sizeof(int32_t), P.stream));
+    return sync_and_settle(h);
+}
+
+ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int64_t n_t, double sigma,
+                       double sigma_tilde, double a, double* tr_ss, double* tr_kpm) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (!f) return fail(h, SSM_EINVAL, "f is NULL");
+    if (n_t < 2 || !(sigma > 0.0) || !(sigma_tilde > 0.0) || !(a > 0.0 && a < 1.0))
+        return fail(h, SSM_EINVAL, "need n_t >= 2, sigma > 0, sigma_tilde > 0, 0 < a < 1");
+    if (!P.have_moments) return fail(h, SSM_ESTATE, "ssm_trace_f needs ssm_moments first");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    // periodic grid: lo/hi onto [-a, a]
+    const double c = 0.5 * (P.glo + P.ghi);
+    double hw = 0.5 * (P.ghi - P.glo) / a;
+    if (!(hw > 0.0)) hw = 1.0;
+    const double dx = hw * 2.0 / (double)n_t;
+    std::vector<double> host(3 * n_t);
+    double* tt = host.data();
+    double* x = tt + n_t;
+    double* fx = x + n_t;
+    for (int64_t i = 0; i < n_t; ++i) {
+        tt[i] = -1.0 + 2.0 * (double)i / (double)n_t;
+        x[i] = c + hw * tt[i];
+        fx[i] = f(x[i], ctx);
+        if (!isfinite(fx[i])) return fail(h, SSM_EDOMAIN, "f is not finite on the trace grid");
+    }
+    const double f0 = f(c - hw, ctx), f1 = f(c + hw, ctx);
+    if (!isfinite(f0) || !isfinite(f1)) return fail(h, SSM_EDOMAIN, "f is not finite at the grid ends");
+    const double fend = 0.5 * (f0 + f1);
+    ssm_status s = ensure_points(h, n_t);
+    if (s != SSM_OK) return s;
+    if ((size_t)(10 * n_t + 2) > h->cap_tr) {
+        dev_free(h->d_tr);
+        h->d_tr = nullptr;
+        h->cap_tr = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_tr, 10 * n_t + 2));
+        h->cap_tr = 10 * n_t + 2;
+    }
+    double* d_tt = h->d_tr;
+    double* d_x = d_tt + n_t;
+    double* d_fx = d_x + n_t;
+    double* d_h = d_fx + n_t;
+    double* d_ft = d_h + n_t;
+    double* d_work = d_ft + n_t;   // 5 n_t
+    double* d_out = h->d_tr + 10 * n_t;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(d_tt, host.data(), 3 * n_t * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+    {
+        Scope sc(h, PH_TRACE);
+        CUDA_OR_FAIL(h, launch_trace_h(d_tt, d_fx, n_t, fend, a, sigma_tilde, d_h, P.stream));
+        CUDA_OR_FAIL(h, launch_deconvolve(d_h, n_t, dx, sigma, DECONV_CUTOFF, d_work, d_ft, P.stream));
+        P.stats.launches += 4;
+    }
+    s = dos_dev(h, d_x, n_t, sigma);
+    if (s != SSM_OK) return s;
+    const double scale = (double)P.n * dx;
+    {
+        Scope sc(h, PH_TRACE);
+        CUDA_OR_FAIL(h, launch_trace_dot(d_ft, h->d_dos_ss, n_t, scale, d_out, P.stream));
+        CUDA_OR_FAIL(h, launch_trace_dot(d_ft, h->d_dos_kpm, n_t, scale, d_out + 1, P.stream));
+        P.stats.launches += 2;
+    }
+    double res[2] = {0, 0};
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(res, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    if (tr_ss) *tr_ss = res[0];
+    if (tr_kpm) *tr_kpm = res[1];
+    return SSM_OK;
+}
+
+ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32_t n_cols, int64_t ld,
+                         double* G_aa, double* G_ab, void* stream) {
+    if (!A || !G_aa || (B && !G_ab)) return fail(nullptr, SSM_EINVAL, "A and G_aa (and G_ab with B) are required");
+    if (n_rows < 0 || n_cols < 1 || ld < n_cols || n_cols > 4096)
+        return fail(nullptr, SSM_EINVAL, "need n_rows >= 0, 1 <= n_cols <= 4096, ld >= n_cols");
+    if (!is_device_ptr(A) || (B && !is_device_ptr(B)) || !is_device_ptr(G_aa) || (G_ab && !is_device_ptr(G_ab)))
+        return fail(nullptr, SSM_EINVAL, "ssm_gram_pair takes device pointers only");
+    if (ld > INT32_MAX) return fail(nullptr, SSM_EINVAL, "ld too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n_split = gram_split_count(n_rows, n_cols);
+    double* part = nullptr;
+    cudaError_t e = cudaMalloc((void**)&part, (size_t)n_split * 2 * n_cols * n_cols * sizeof(double));
+    if (e != cudaSuccess)
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA, cudaGetErrorString(e));
+    e = launch_gram_f64(A, B, (int)ld, n_cols, n_rows, n_split, part, s);
+    if (e == cudaSuccess) e = launch_reduce_gram_pair(part, n_split, n_cols, G_aa, B ? G_ab : nullptr, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(part);
+    if (e != cudaSuccess) return fail(nullptr, SSM_ECUDA, cudaGetErrorString(e));
+    return SSM_OK;
+}
+
+ssm_status ssm_timing_enable(ssm_plan_t h, int32_t on) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    h->P.timing = (on != 0);
+    return SSM_OK;
+}
+
+ssm_status ssm_stats_get(ssm_plan_t h, ssm_stats* out) {
+    if (!h || !out) return fail(h, SSM_EINVAL, "plan or out is NULL");
+    *out = h->P.stats;
+    return SSM_OK;
+}
+
+ssm_status ssm_stats_reset(ssm_plan_t h) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    memset(&h->P.stats, 0, sizeof(ssm_stats));
+    return SSM_OK;
+}
+
+void ssm_plan_destroy(ssm_plan_t h) {
+    if (!h) return;
+    cudaSetDevice(h->P.device);
+    cudaStreamSynchronize(h->P.stream);
+    free_plan(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// assemble.cu - per-sweep-point matrices of Alg. 7 (float64).
+//
+//   K_W(t_i) = sum_{l<=M/2} mu_l(t_i) X_l[W, W]     K_C(t_i) = sum_{l<=M/2} mu_l(t_i) X_l[W~, W]
+//   K_Z(t_i) = sum_{l<=M}   nu_l(t_i) X_l[W, W]     K_W~(t_i) = sum_{l<=M/2} mu_l(t_i) X_l[W~, W~]
+//
+// The paper accumulates these inside the recurrence loop, one rank-one-in-l
+// update per step and per point (Alg. 7); after the loop they are one dense
+// contraction [n_t x L] . [L x (rows*cols)] over the stored moments, which is
+// what this kernel computes: out[t][i*cols + j] = sum_{l<L} coef[t][l] X_l[i][j].
+// 64 x 64 output tiles, 16-deep slabs of l staged in shared memory, 4 x 4
+// outputs per thread, summation over l in increasing order.
+#include "internal.h"
+
+namespace ssm {
+
+namespace {
+
+constexpr int TT = 64;   // sweep points per tile
+constexpr int TE = 64;   // matrix entries per tile
+constexpr int TL = 16;   // l per slab
+
+__global__ void __launch_bounds__(256)
+assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, const double* __restrict__ X,
+                int n_tot, int rows, int cols, double* __restrict__ out) {
+    __shared__ double Cs[TL][TT + 1];
+    __shared__ double Xs[TL][TE];
+    __shared__ int xoff[TE];
+    const int64_t ne = (int64_t)rows * cols;
+    const int64_t t0 = (int64_t)blockIdx.y * TT;
+    const int64_t e0 = (int64_t)blockIdx.x * TE;
+    const size_t nn = (size_t)n_tot * n_tot;
+    if (threadIdx.x < TE) {
+        const int64_t e = e0 + threadIdx.x;
+        int off = -1;
+        if (e < ne) {
+            const int i = (int)(e / cols), j = (int)(e - (int64_t)i * cols);
+            off = i * n_tot + j;
+        }
+        xoff[threadIdx.x] = off;
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = 0.0;
+    __syncthreads();
+    for (int l0 = 0; l0 < L; l0 += TL) {
+        for (int e = threadIdx.x; e < TL * TT; e += 256) {
+            const int ll = e / TT, tt = e - ll * TT;
+            const int64_t ti = t0 + tt;
+            const int l = l0 + ll;
+            Cs[ll][tt] = (ti < n_t && l < L) ? coef[ti * ldc + l] : 0.0;
+        }
+        for (int e = threadIdx.x; e < TL * TE; e += 256) {
+            const int ll = e / TE, ee = e - ll * TE;
+            const int l = l0 + ll;
+            const int off = xoff[ee];
+            Xs[ll][ee] = (off >= 0 && l < L) ? X[(size_t)l * nn + off] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ll = 0; ll < TL; ++ll) {
+            double c[4], x[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) c[p] = Cs[ll][ty * 4 + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = Xs[ll][tx + 16 * q];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fma(c[p], x[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int64_t ti = t0 + ty * 4 + p;
+        if (ti >= n_t) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = e0 + tx + 16 * q;
+            if (e < ne) out[ti * ne + e] = acc[p][q];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X, int n_tot,
+                            int rows, int cols, double* out, cudaStream_t s) {
+    const int64_t ne = (int64_t)rows * cols;
+    dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
+    assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ssm

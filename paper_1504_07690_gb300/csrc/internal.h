@@ -1,0 +1,146 @@
+// internal.h - shared declarations of the spectrum sweeping library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ssm.h"
+
+namespace ssm {
+
+// ---------------------------------------------------------------- geometry
+
+// Stencil operator with the spectral map folded in: the recurrence needs
+// 2 A~ v = alpha A v + beta v, alpha = 4/(b-a), beta = -2(a+b)/(b-a)
+// (Section 2).  diag2[i] = alpha diag[i] + beta, off2[axis] = alpha off[axis].
+struct StencilGeom {
+    uint32_t d0, d1, d2;     // extents
+    uint32_t per[3];         // periodic flags
+    uint32_t active[3];      // axis contributes (offdiag != 0 and has a neighbour)
+};
+
+// ---------------------------------------------------------------- plan
+
+struct Plan {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ssm_params p{};
+    int64_t n = 0, nnz = 0;
+    int n_tot = 0;        // n_v + n_vh
+    int ld = 0;           // padded leading dimension of the recurrence blocks
+    bool mixed = false;
+    bool is_stencil = false;
+
+    // operator
+    StencilGeom geom{};
+    double off64[3] = {0, 0, 0};       // alpha * offdiag
+    float off32[3] = {0, 0, 0};
+    double* d_diag64 = nullptr;        // alpha * diag + beta
+    float* d_diag32 = nullptr;
+    int64_t* d_rowptr = nullptr;
+    int32_t* d_colind = nullptr;
+    double* d_val64 = nullptr;         // alpha * val (beta applied separately)
+    float* d_val32 = nullptr;
+    double a = 0, b = 0;               // Chebyshev interval
+    double glo = 0, ghi = 0;           // spectral bounds (Gershgorin or user)
+    double alpha = 0, beta = 0;
+
+    // recurrence + moments
+    void* d_V[3] = {nullptr, nullptr, nullptr};
+    double* d_part = nullptr;          // Gram partials [n_split][2][n_tot][n_tot]
+    int n_split = 0;
+    double* d_X = nullptr;             // (M+1) x n_tot x n_tot
+    bool have_moments = false;
+    double x0max = 0;                  // max_i X_0[i][i] over the first n_v probes
+    double eps_floor = 0;              // rounding unit of Alg. 4's floor (0 = off)
+    int* d_flag = nullptr;             // device status word
+    double* d_stage = nullptr;         // staging for host<->device conversions
+    size_t stage_bytes = 0;
+
+    // coefficient tables
+    double* d_ctab = nullptr;          // cos(pi m / N_theta), m < 2 N_theta
+    int n_theta = 0;
+
+    // per-point work
+    size_t work_bytes = 0;
+    void* d_work = nullptr;
+    int64_t work_nt = 0;
+
+    // timing
+    bool timing = false;
+    ssm_stats stats{};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    std::string err;
+};
+
+// ---------------------------------------------------------------- launchers
+
+// Recurrence: Vn = c (2 A~ Vc) - d Vp, row-major blocks with leading dim ld.
+cudaError_t launch_stencil_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
+                                    double c, double d, cudaStream_t s);
+cudaError_t launch_stencil_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
+                                    float c, float d, cudaStream_t s);
+cudaError_t launch_csr_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
+                                double c, double d, cudaStream_t s);
+cudaError_t launch_csr_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
+                                float c, float d, cudaStream_t s);
+
+// Operator set-up (operator.cu).
+int operator_bound_blocks(int64_t n);
+cudaError_t launch_stencil_bounds(const Plan& P, const double* diag, const double* off, double extra, double* out,
+                                  int* flag, cudaStream_t s);
+cudaError_t launch_csr_bounds(const Plan& P, const double* val, double* out, cudaStream_t s);
+cudaError_t launch_csr_validate(const Plan& P, const double* val, int* flag, cudaStream_t s);
+cudaError_t launch_fold_stencil(const Plan& P, const double* diag, double extra, cudaStream_t s);
+cudaError_t launch_fold_csr(const Plan& P, const double* val, cudaStream_t s);
+
+// Gram partials: part[s][0] = upper tiles of A^T A, part[s][1] = A^T B (if B).
+int gram_split_count(int64_t n_rows, int n_tot);
+cudaError_t launch_gram_f64(const double* A, const double* B, int ld, int n_tot, int64_t n_rows,
+                            int n_split, double* part, cudaStream_t s);
+cudaError_t launch_gram_f32(const float* A, const float* B, int ld, int n_tot, int64_t n_rows,
+                            int n_split, double* part, cudaStream_t s);
+
+// G_aa[i][j] = sum_s part[s][0][min(i,j)][max(i,j)], G_ab = sum_s part[s][1] (gram.cu).
+cudaError_t launch_reduce_gram_pair(const double* part, int n_split, int n, double* gaa, double* gab,
+                                    cudaStream_t s);
+
+// Reduce partials into the moments of step k (see moments.cu).
+cudaError_t launch_reduce_moments(const double* part, int n_split, int n_tot, double* X, int step,
+                                  cudaStream_t s);
+cudaError_t launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t s);
+cudaError_t launch_convert_in(const double* src, int64_t ldsrc, void* dst, int ld, int64_t n_rows,
+                              int n_cols, bool to_f32, cudaStream_t s);
+
+// Coefficients (coeffs.cu).
+cudaError_t launch_cos_table(double* ctab, int n_theta, cudaStream_t s);
+cudaError_t launch_mu(const double* t, int64_t n_t, double sigma, double inv_norm, double a, double b,
+                      int M, int n_theta, const double* ctab, double* mu, int ldmu, cudaStream_t s);
+cudaError_t launch_nu(const double* mu, int ldmu, int64_t n_t, int M, double* nu, int ldnu,
+                      cudaStream_t s);
+cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const double* X, int n_tot,
+                       double* zeta, double* out, cudaStream_t s);
+
+// Assembly: out[t][i*cols+j] = sum_{l<L} coef[t][l] X[l][i][j] (assemble.cu).
+cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X,
+                            int n_tot, int rows, int cols, double* out, cudaStream_t s);
+
+// Per-point Alg. 4 + Alg. 6 solve (solve.cu).
+size_t solve_workspace_bytes(int n_v);
+// floor(t) = floor_scale * sum_{l<=K} (l+1) |mu[t][l]| (see ssm_params.eps_floor).
+cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh,
+                         double tau, double xlo, double xhi, const double* mu, int ldmu, int K,
+                         double floor_scale, void* work, double* dos, int32_t* rank, cudaStream_t s);
+
+// Alg. 8 pieces (trace.cu).
+cudaError_t launch_trace_h(const double* tt, const double* fx, int64_t n_t, double fend, double a,
+                           double sigma_tilde, double* h, cudaStream_t s);
+cudaError_t launch_deconvolve(const double* h, int64_t n_t, double dx, double sigma, double cutoff,
+                              double* work, double* ftilde, cudaStream_t s);
+cudaError_t launch_trace_dot(const double* ftilde, const double* dos, int64_t n_t, double scale,
+                             double* out, cudaStream_t s);
+
+}  // namespace ssm

@@ -1,0 +1,270 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances:
+* float64 path: moments to 1e-11 of max|X| (doubling vs the paper's M-step
+  loop differ only by rounding), coefficient tables to 1e-12 of their max,
+  KPM DOS to 1e-10 relative L1 (Eq. error).
+* RESS-DGC DOS (float64): Alg. 4 divides by eigenvalues of K_W(t) down to
+  tau = 1e-7 of the largest, so rounding-level differences in the moments
+  are amplified by up to ~1/tau.  The tolerance is therefore
+  max(1e-10, 10 x spread), spread = the relative L1 difference between the
+  oracle's own two float64 evaluations (the paper's M-step loop and the
+  doubling products), measured on the sweep points the oracle does not flag
+  as within 1e-8 of an Alg. 4 threshold.
+* mixed path (float32 recurrence, float32-accumulated Gram): DOS within
+  1e-4 relative L1 of the float64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as wl  # noqa: E402
+from oracle import ssm_oracle as O  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1504_07690_gb300 as S
+
+    return S
+
+
+def _csr_A(st_or_csr):
+    c = wl.stencil_to_csr(st_or_csr) if isinstance(st_or_csr, wl.Stencil) else st_or_csr
+    return O.csr_matrix(c.n, c.rowptr, c.colind, c.val)
+
+
+def _run(S, op, W, n_v, n_vh, M, sigma, t=None, precision="fp64", n_t=101, kind="stencil",
+         moments=True, **kw):
+    if kind == "stencil":
+        plan = S.ssm_plan_create(stencil=op, n_v=n_v, n_vh=n_vh, degree=M, precision=precision, **kw)
+    else:
+        plan = S.ssm_plan_create(csr=op, n_v=n_v, n_vh=n_vh, degree=M, precision=precision, **kw)
+    info = S.ssm_plan_info(plan)
+    if t is None:
+        t = np.linspace(info["lo"], info["hi"], n_t)
+    X = S.ssm_moments(plan, torch.from_numpy(W).cuda(), return_moments=moments)
+    ss, kpm, rank = S.ssm_dos(plan, torch.from_numpy(t).cuda(), sigma)
+    out = dict(plan=plan, info=info, t=t, X=None if X is None else X.cpu().numpy(), ss=ss.cpu().numpy(),
+               kpm=kpm.cpu().numpy(), rank=rank.cpu().numpy())
+    return out
+
+
+def _oracle(op, W, n_v, t, M, sigma, info, flag_eps=1e-8, **kw):
+    A = _csr_A(op)
+    return O.ress_dgc(A, W, n_v, t, M, sigma, interval=(info["a"], info["b"]), flag_eps=flag_eps, **kw)
+
+
+def _ss_tolerance(op, W, n_v, t, M, sigma, info, r, ok):
+    """max(1e-10, 10 x the oracle's own direct-vs-doubling spread) on the points `ok`."""
+    r2 = _oracle(op, W, n_v, t, M, sigma, info, moments="doubling")
+    ok = ok & ~r2["flagged"]
+    spread = O.relative_l1_error(r2["dos_ss"][ok], r["dos_ss"][ok])
+    return max(1e-10, 10.0 * spread), ok
+
+
+# ------------------------------------------------------------------ config 1
+
+@pytest.fixture(scope="module")
+def cfg1(S):
+    st = wl.make_operator("lap2d_dirichlet_32")
+    c = wl.CONFIGS["lap2d_dirichlet_32"]
+    W = wl.random_block(st.n, c["n_v"], c["probe_seed"], c["probe"])
+    g = _run(S, st, W, c["n_v"], 0, c["M"], c["sigma"], n_t=c["n_t"])
+    r = _oracle(st, W, c["n_v"], g["t"], c["M"], c["sigma"], g["info"])
+    return st, W, c, g, r
+
+
+def test_interval_matches_oracle_gershgorin(cfg1):
+    st, W, c, g, r = cfg1
+    a, b = O.spectral_interval(_csr_A(st))
+    assert abs(g["info"]["a"] - a) <= 1e-12 * (b - a)
+    assert abs(g["info"]["b"] - b) <= 1e-12 * (b - a)
+
+
+def test_coefficients_fp64(S, cfg1):
+    st, W, c, g, r = cfg1
+    mu, nu = S.ssm_coefficients(g["plan"], g["t"], c["sigma"])
+    assert np.max(np.abs(mu - r["mu_full"])) <= 1e-12 * np.max(np.abs(r["mu_full"]))
+    assert np.max(np.abs(nu - r["nu"])) <= 1e-12 * np.max(np.abs(r["nu"]))
+
+
+def test_moments_fp64(cfg1):
+    st, W, c, g, r = cfg1
+    scale = np.max(np.abs(r["X"]))
+    assert np.max(np.abs(g["X"] - r["X"])) <= 1e-11 * scale
+
+
+def test_kpm_dos_fp64(cfg1):
+    st, W, c, g, r = cfg1
+    assert O.relative_l1_error(g["kpm"], r["dos_kpm"]) <= 1e-10
+
+
+def test_ress_dos_fp64(cfg1):
+    st, W, c, g, r = cfg1
+    ok = ~r["flagged"]
+    assert ok.sum() >= 0.9 * ok.size
+    tol, ok = _ss_tolerance(st, W, c["n_v"], g["t"], c["M"], c["sigma"], g["info"], r, ok)
+    assert tol <= 1e-8
+    assert O.relative_l1_error(g["ss"][ok], r["dos_ss"][ok]) <= tol
+    assert np.array_equal(g["rank"][ok, 0], r["rank_s"][ok])
+    assert np.array_equal(g["rank"][ok, 1], r["rank_xi"][ok])
+
+
+def test_hybrid_fp64_ragged_columns(S):
+    # 20 + 17 columns: n_tot not a multiple of the vector width; Alg. 6 correction on.
+    st = wl.make_operator("lap2d_dirichlet_32", nx=23)
+    W = wl.random_block(st.n, 37, 77)
+    M, sigma = 120, 0.08
+    g = _run(S, st, W, 20, 17, M, sigma, n_t=53)
+    r = _oracle(st, W, 20, g["t"], M, sigma, g["info"])
+    assert np.max(np.abs(g["X"] - r["X"])) <= 1e-11 * np.max(np.abs(r["X"]))
+    assert O.relative_l1_error(g["kpm"], r["dos_kpm"]) <= 1e-10
+    tol, ok = _ss_tolerance(st, W, 20, g["t"], M, sigma, g["info"], r, ~r["flagged"])
+    assert O.relative_l1_error(g["ss"][ok], r["dos_ss"][ok]) <= tol
+
+
+def test_csr_operator_fp64(S):
+    csr = wl.er_normalized_laplacian(1500, 8.0, 1004)
+    W = wl.random_block(csr.n, 24, 2004)
+    M, sigma = 80, 0.05
+    g = _run(S, csr, W, 16, 8, M, sigma, n_t=41, kind="csr")
+    r = _oracle(csr, W, 16, g["t"], M, sigma, g["info"])
+    assert np.max(np.abs(g["X"] - r["X"])) <= 1e-11 * np.max(np.abs(r["X"]))
+    assert O.relative_l1_error(g["kpm"], r["dos_kpm"]) <= 1e-10
+    tol, ok = _ss_tolerance(csr, W, 16, g["t"], M, sigma, g["info"], r, ~r["flagged"])
+    assert O.relative_l1_error(g["ss"][ok], r["dos_ss"][ok]) <= tol
+
+
+def test_3d_periodic_prime_and_self_loop_axes(S):
+    # 3D periodic 7x5x3 (odd extents), then a 1-D prime-length chain whose
+    # periodic unit axes fold into the diagonal.
+    rng = np.random.default_rng(5)
+    st = wl.Stencil(dims=(7, 5, 3), periodic=(True, True, True), diag=6 + rng.normal(0, .3, 105),
+                    offdiag=(-1.0, -0.7, -1.3))
+    W = wl.random_block(105, 9, 6)
+    g = _run(S, st, W, 9, 0, 40, 0.2, n_t=21)
+    r = _oracle(st, W, 9, g["t"], 40, 0.2, g["info"])
+    assert np.max(np.abs(g["X"] - r["X"])) <= 1e-11 * np.max(np.abs(r["X"]))
+    st2 = wl.Stencil(dims=(1009, 1, 1), periodic=(False, True, True), diag=rng.uniform(-1, 1, 1009),
+                     offdiag=(-1.0, 0.25, 0.5))
+    W2 = wl.random_block(1009, 5, 7)
+    g2 = _run(S, st2, W2, 5, 0, 30, 0.1, n_t=11)
+    r2 = _oracle(st2, W2, 5, g2["t"], 30, 0.1, g2["info"])
+    assert np.max(np.abs(g2["X"] - r2["X"])) <= 1e-11 * np.max(np.abs(r2["X"]))
+    assert O.relative_l1_error(g2["kpm"], r2["dos_kpm"]) <= 1e-10
+
+
+def test_minimal_degree_and_host_buffers(S):
+    st = wl.make_operator("lap2d_dirichlet_32", nx=6)
+    W = wl.random_block(36, 3, 8)
+    plan = S.ssm_plan_create(stencil=st, n_v=3, degree=2)
+    info = S.ssm_plan_info(plan)
+    X = S.ssm_moments(plan, W, return_moments=True)  # host W, host output
+    t = np.linspace(info["lo"], info["hi"], 5)
+    ss, kpm, rank = S.ssm_dos(plan, t, 0.5)
+    r = _oracle(st, W, 3, t, 2, 0.5, info)
+    assert isinstance(X, np.ndarray) and X.shape == (3, 3, 3)
+    assert np.max(np.abs(X - r["X"])) <= 1e-12 * np.max(np.abs(r["X"]))
+    assert O.relative_l1_error(kpm, r["dos_kpm"]) <= 1e-12
+
+
+# ------------------------------------------------------------------ mixed path
+
+def test_mixed_precision_config1_shape(S, cfg1):
+    st, W, c, g64, r = cfg1
+    g = _run(S, st, W, c["n_v"], 0, c["M"], c["sigma"], t=g64["t"], precision="mixed")
+    assert O.relative_l1_error(g["kpm"], r["dos_kpm"]) <= 1e-4
+    # the oracle with the same rounding floor (the float32 unit) the mixed plan uses
+    rm = _oracle(st, W, c["n_v"], g64["t"], c["M"], c["sigma"], g64["info"], flag_eps=1e-3,
+                 eps_floor=2.0 ** -23)
+    ok = ~rm["flagged"]
+    assert ok.sum() >= 0.6 * ok.size
+    assert O.relative_l1_error(g["ss"][ok], rm["dos_ss"][ok]) <= 1e-4
+
+
+# ------------------------------------------------------------------ errors
+
+def test_error_paths(S):
+    st = wl.make_operator("lap2d_dirichlet_32", nx=8)
+    plan = S.ssm_plan_create(stencil=st, n_v=4, degree=10)
+    with pytest.raises(S.SSMError) as e:
+        S.ssm_dos(plan, np.zeros(3), 0.1)
+    assert e.value.name == "SSM_ESTATE"
+    W = wl.random_block(64, 4, 1)
+    W[3, 2] = np.nan
+    with pytest.raises(S.SSMError) as e:
+        S.ssm_moments(plan, W)
+    assert e.value.name == "SSM_ENONFINITE"
+    W[3, 2] = 0.0
+    S.ssm_moments(plan, W)
+    ss, kpm, rk = S.ssm_dos(plan, np.zeros(0), 0.1)
+    assert ss.shape == (0,)
+    with pytest.raises(S.SSMError) as e:
+        S.ssm_dos(plan, np.zeros(3), -1.0)
+    assert e.value.name == "SSM_EINVAL"
+    bad = wl.er_normalized_laplacian(200, 5.0, 3)
+    bad.val = bad.val.copy()
+    rows = np.repeat(np.arange(bad.n), np.diff(bad.rowptr))
+    e = int(np.nonzero(bad.colind != rows)[0][0])
+    bad.val[e] += 1e-3  # an off-diagonal entry: breaks numerical symmetry
+    with pytest.raises(S.SSMError) as e:
+        S.ssm_plan_create(csr=bad, n_v=4, degree=10)
+    assert e.value.name == "SSM_ENOTSYM"
+    st2 = wl.make_operator("lap2d_dirichlet_32", nx=8)
+    st2.diag = st2.diag.copy()
+    st2.diag[5] = np.inf
+    with pytest.raises(S.SSMError) as e:
+        S.ssm_plan_create(stencil=st2, n_v=4, degree=10)
+    assert e.value.name == "SSM_ENONFINITE"
+
+
+# ------------------------------------------------------------------ trace
+
+def test_trace_f_fp64(S):
+    st = wl.make_operator("lap2d_dirichlet_32", nx=12)
+    W = wl.random_block(st.n, 24, 12)
+    M, sigma, n_t = 400, 0.05, 256
+    plan = S.ssm_plan_create(stencil=st, n_v=16, n_vh=8, degree=M)
+    info = S.ssm_plan_info(plan)
+    S.ssm_moments(plan, torch.from_numpy(W).cuda())
+    f = lambda x: math.exp(-0.5 * x)  # noqa: E731
+    tr_ss, tr_kpm = S.ssm_trace_f(plan, f, n_t, sigma, 0.016, 0.93)
+    A = _csr_A(st)
+    x, dx, ft, h = O.deconvolve_h(lambda v: np.exp(-0.5 * v), n_t, info["lo"], info["hi"], sigma, 0.016, 0.93)
+    r = O.ress_dgc(A, W, 16, x, M, sigma, interval=(info["a"], info["b"]), flag_eps=1e-8)
+    r2 = O.ress_dgc(A, W, 16, x, M, sigma, interval=(info["a"], info["b"]), moments="doubling")
+    ref_ss = st.n * dx * np.sum(ft * r["dos_ss"])
+    ref_kpm = st.n * dx * np.sum(ft * r["dos_kpm"])
+    spread = abs(st.n * dx * np.sum(ft * r2["dos_ss"]) - ref_ss)
+    assert abs(tr_kpm - ref_kpm) <= 1e-9 * abs(ref_kpm)
+    assert abs(tr_ss - ref_ss) <= max(1e-9 * abs(ref_ss), 10.0 * spread)
+    # both estimates are close to the exact trace of the function
+    ev = np.linalg.eigvalsh(A.toarray())
+    exact = np.sum(np.exp(-0.5 * ev))
+    assert abs(tr_kpm - exact) < 0.05 * exact
+
+
+# ------------------------------------------------------------------ Gram pair
+
+def test_gram_pair_fp64_matches_definition_and_repeats(S):
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((5003, 70))
+    B = rng.standard_normal((5003, 70))
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    gaa, gab = S.ssm_gram_pair(Ad, Bd)
+    ref_aa, ref_ab = A.T @ A, A.T @ B
+    assert np.max(np.abs(gaa.cpu().numpy() - ref_aa)) <= 1e-13 * np.max(np.abs(ref_aa))
+    assert np.max(np.abs(gab.cpu().numpy() - ref_ab)) <= 1e-13 * np.max(np.abs(ref_ab))
+    assert np.array_equal(gaa.cpu().numpy(), gaa.cpu().numpy().T)
+    gaa2, gab2 = S.ssm_gram_pair(Ad, Bd)
+    assert torch.equal(gaa, gaa2) and torch.equal(gab, gab2)
+    g1, none = S.ssm_gram_pair(Ad[:1])
+    assert none is None and np.allclose(g1.cpu().numpy(), np.outer(A[0], A[0]), rtol=1e-15, atol=0)

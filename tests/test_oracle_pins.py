@@ -299,3 +299,29 @@ def test_ss_identity_probes_underresolved_selects_filtered_eigenvalues():
         Tf = np.cos(np.outer(np.arccos(lt), np.arange(M + 1)))
         mf = O.dgc_coefficients(ti, M, sigma, N, a, b, n_theta=2 * M)
         assert abs(r["dos_kpm"][i] - (Tf @ mf).sum() / N) < 1e-12 * gm
+
+
+def test_rounding_floor_drops_noise_only():
+    # A spectral gap: at sweep points more than 12 sigma from every eigenvalue
+    # g_sigma(tI - A) is below 1e-31 of its peak, so K_W(t) is rounding noise;
+    # the floor must keep nothing there (phi = 0), while inside the spectrum
+    # it must not change the estimate.
+    rng = np.random.default_rng(7)
+    N, sigma, M = 60, 0.03, 600
+    lam = np.concatenate([rng.uniform(-0.9, -0.4, N // 2), rng.uniform(0.4, 0.9, N // 2)])
+    Q, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    A = sp.csr_matrix(Q @ np.diag(lam) @ Q.T)
+    W = wl.random_block(N, 12, 8)
+    gap = np.linspace(-0.02, 0.02, 5)
+    r = O.ress_dgc(A, W, 12, gap, M, sigma, interval=(-1.0, 1.0))
+    assert np.all(r["dos_ss"] == 0.0) and np.all(r["rank_s"] == 0)
+    inside = np.linspace(-0.85, -0.45, 7)
+    r1 = O.ress_dgc(A, W, 12, inside, M, sigma, interval=(-1.0, 1.0))
+    r0 = O.ress_dgc(A, W, 12, inside, M, sigma, interval=(-1.0, 1.0), eps_floor=0.0)
+    assert np.array_equal(r1["dos_ss"], r0["dos_ss"])
+    # the floor is far below tau * max s inside the spectrum
+    tab = O.coefficient_tables(inside, M, sigma, N, -1.0, 1.0)
+    for i in range(inside.size):
+        K = O.assemble(tab["mu_half"][i], tab["nu"][i], r1["X"], 12)
+        s = np.linalg.eigvalsh(K[0])
+        assert O.rounding_floor(tab["mu_half"][i], r1["X"], 12, O.EPS_FP64) < 1e-3 * 1e-7 * s.max()
