@@ -175,6 +175,33 @@ ssm_status ssm_trace_f(ssm_plan_t plan, double (*f)(double x, void* ctx), void* 
 ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32_t n_cols, int64_t ld,
                          double* G_aa, double* G_ab, void* stream);
 
+/* ssm_gram_pair for callers that cannot allocate device memory (the paper
+ * has no counterpart; this is a service of the library).  Some callers
+ * cannot call cudaMalloc: code running while another component owns all
+ * device memory through its own pool, latency-critical code that cannot
+ * accept cudaMalloc's implicit device synchronisation, or plug-ins whose
+ * host forbids raw CUDA allocations.  This variant computes the same
+ * G_aa = A^T A and G_ab = A^T B (same arguments, device pointers only) but
+ * keeps its partial sums in a fixed 4 MiB device array inside the library
+ * instead of allocating: it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *   Limit: n_cols <= 512; larger sizes return SSM_EINVAL.
+ *   The array exists on every GPU that loads the library, until the
+ *   process exits.  The first call on a device looks up the array's device
+ *   address (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.
+ *   Every call on a device shares the array and it keeps the last call's
+ *   contents; no part of it needs to start at zero (a call overwrites every
+ *   partial sum it reads).  Calls whose work overlaps on the GPU (different
+ *   streams, or host threads racing on one device) race on the array and
+ *   give wrong results: order them.
+ *   The call only enqueues work on `stream` and returns; synchronise the
+ *   stream before reading G_aa / G_ab.  Rows are split into as many slices
+ *   as the array holds, so results may differ from ssm_gram_pair's in the
+ *   last bits (different summation order). */
+ssm_status ssm_gram_pair_noalloc(const double* A, const double* B, int64_t n_rows, int32_t n_cols,
+                                 int64_t ld, double* G_aa, double* G_ab, void* stream);
+
 /* Chebyshev coefficient tables of Alg. 1 and Proposition 1 at n_t points
  * (host or device t): mu: n_t x (M+1), mu_l(t_i) of g_sigma(t_i - .) in T_l(A~);
  * nu: n_t x (M+1), the coefficients of the square of the degree-M/2 series.

@@ -55,6 +55,8 @@ SIGNATURES = {
                                    C.c_void_p]),
     "ssm_gram_pair": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+    "ssm_gram_pair_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int64,
+                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssm_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssm_stats_get": (C.c_int, [C.c_void_p, C.POINTER(ssm_stats)]),
     "ssm_stats_reset": (C.c_int, [C.c_void_p]),

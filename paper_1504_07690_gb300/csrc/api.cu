@@ -302,6 +302,8 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
 
 }  // namespace
 
+void ssm::set_global_error(const char* msg) { g_create_error = msg; }
+
 // =====================================================================
 // ABI
 // =====================================================================

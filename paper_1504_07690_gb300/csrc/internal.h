@@ -76,6 +76,9 @@ struct Plan {
     std::string err;
 };
 
+// Message returned by ssm_last_error(NULL) (api.cu).
+void set_global_error(const char* msg);
+
 // ---------------------------------------------------------------- launchers
 
 // Recurrence: Vn = c (2 A~ Vc) - d Vp, row-major blocks with leading dim ld.
