@@ -54,7 +54,8 @@ typedef enum {
     SSM_ENONFINITE = 5,  /* an input or an intermediate was NaN or Inf */
     SSM_ENOTSYM = 6,     /* the CSR operator is not symmetric */
     SSM_EDOMAIN = 7,     /* the function of Tr f(A) is not finite on the grid */
-    SSM_ESTATE = 8       /* call out of order (e.g. ssm_dos before ssm_moments) */
+    SSM_ESTATE = 8,      /* call out of order (e.g. ssm_dos before ssm_moments) */
+    SSM_ENOCONV = 9      /* a per-point eigenvalue iteration did not converge within its bound */
 } ssm_status;
 
 typedef enum {
@@ -97,7 +98,9 @@ typedef struct {
     double kappa;       /* slack of Alg. 4's range filter [-kappa g_max, (1+kappa) g_max];
                            < 0 selects 1e-6 */
     int32_t n_theta;    /* quadrature size N_theta of Alg. 1 (> M); 0 selects 2M */
-    int32_t reserved;
+    int32_t options;    /* bit 0: the SSM_MIXED path forms its Gram products on CUDA cores
+                           (float32) instead of the tensor cores (split bf16); used for
+                           cross-checks.  Other bits must be 0. */
     double eps_floor;   /* rounding unit of the floor of Alg. 4's truncation: an eigenvalue
                            of K_W(t) is also dropped below
                            8 n_v eps_floor max_i X_0[i][i] sum_{l<=M/2} (l+1)|mu_l(t)|,

@@ -9,7 +9,8 @@ LIB_PATH = os.path.join(HERE, "libssm.so")
 
 SSM_OK = 0
 STATUS_NAMES = {0: "SSM_OK", 1: "SSM_EINVAL", 2: "SSM_ENOMEM", 3: "SSM_ECUDA", 4: "SSM_ETIMEOUT",
-                5: "SSM_ENONFINITE", 6: "SSM_ENOTSYM", 7: "SSM_EDOMAIN", 8: "SSM_ESTATE"}
+                5: "SSM_ENONFINITE", 6: "SSM_ENOTSYM", 7: "SSM_EDOMAIN", 8: "SSM_ESTATE",
+                9: "SSM_ENOCONV"}
 SSM_FP64 = 0
 SSM_MIXED = 1
 
@@ -27,7 +28,7 @@ class ssm_csr(C.Structure):
 class ssm_params(C.Structure):
     _fields_ = [("n_v", C.c_int32), ("n_vh", C.c_int32), ("degree", C.c_int32), ("precision", C.c_int32),
                 ("lo", C.c_double), ("hi", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
-                ("n_theta", C.c_int32), ("reserved", C.c_int32), ("eps_floor", C.c_double)]
+                ("n_theta", C.c_int32), ("options", C.c_int32), ("eps_floor", C.c_double)]
 
 
 class ssm_stats(C.Structure):

@@ -96,12 +96,13 @@ class Plan:
 
 def ssm_plan_create(stencil=None, csr=None, *, n_v: int, degree: int, n_vh: int = 0,
                     precision: str = "fp64", lo: float = 0.0, hi: float = 0.0, tau: float = 0.0,
-                    kappa: float = -1.0, n_theta: int = 0, eps_floor: float = 0.0, stream=None) -> Plan:
+                    kappa: float = -1.0, n_theta: int = 0, eps_floor: float = 0.0, options: int = 0,
+                    stream=None) -> Plan:
     """ssm_plan_create: operator (stencil descriptor or CSR) + parameters -> Plan."""
     lib = N.load()
     p = N.ssm_params(n_v=n_v, n_vh=n_vh, degree=degree,
                      precision={"fp64": N.SSM_FP64, "mixed": N.SSM_MIXED}[precision],
-                     lo=lo, hi=hi, tau=tau, kappa=kappa, n_theta=n_theta, reserved=0, eps_floor=eps_floor)
+                     lo=lo, hi=hi, tau=tau, kappa=kappa, n_theta=n_theta, options=options, eps_floor=eps_floor)
     keep = []
     st_p = None
     csr_p = None

@@ -170,6 +170,15 @@ ssm_status read_flag(ssm_plan_s* h, int* value) {
     return SSM_OK;
 }
 
+// Bit 4 of the status word: an eigenvalue iteration of the per-point solver hit its bound.
+ssm_status check_solver_flag(ssm_plan_s* h) {
+    int flag = 0;
+    ssm_status s = read_flag(h, &flag);
+    if (s != SSM_OK) return s;
+    if (flag & 4) return fail(h, SSM_ENOCONV, "an eigenvalue iteration of Alg. 4 did not converge within 60 sweeps");
+    return SSM_OK;
+}
+
 void free_plan(ssm_plan_s* h) {
     Plan& P = h->P;
     dev_free(P.d_diag64);
@@ -180,6 +189,7 @@ void free_plan(ssm_plan_s* h) {
     dev_free(P.d_val32);
     for (auto& v : P.d_V) dev_free(v);
     dev_free(P.d_part);
+    dev_free(P.d_part_tc);
     dev_free(P.d_X);
     dev_free(P.d_flag);
     dev_free(P.d_stage);
@@ -288,7 +298,7 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
             const double floor_scale = 8.0 * nv * P.eps_floor * P.x0max;
             CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, h->d_mu, M + 1, K,
                                          floor_scale, h->d_solve, h->d_dos_ss + t0, h->d_rank + 2 * t0,
-                                         P.stream));
+                                         P.d_flag, P.stream));
             P.stats.launches++;
         }
         {
@@ -321,6 +331,7 @@ const char* ssm_status_string(ssm_status s) {
         case SSM_ENOTSYM: return "SSM_ENOTSYM";
         case SSM_EDOMAIN: return "SSM_EDOMAIN";
         case SSM_ESTATE: return "SSM_ESTATE";
+        case SSM_ENOCONV: return "SSM_ENOCONV";
     }
     return "SSM_UNKNOWN";
 }
@@ -503,8 +514,14 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if ((uint64_t)P.n * (uint64_t)(P.ld / vec) >= (1ULL << 32)) return bail(SSM_EINVAL, "N x n_tot too large");
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
     for (auto& v : P.d_V) CREATE_CUDA(cudaMalloc(&v, (size_t)P.n * P.ld * esz));
-    P.n_split = gram_split_count(P.n, P.n_tot);
-    CREATE_CUDA(dev_alloc(&P.d_part, (size_t)P.n_split * 2 * P.n_tot * P.n_tot));
+    P.use_tc = P.mixed && !(p.options & 1) && gram_tc_supported(P.n_tot, P.ld);
+    if (P.use_tc) {
+        gram_tc_slabs(P.n, &P.tc_ne, &P.tc_no);
+        CREATE_CUDA(dev_alloc(&P.d_part_tc, gram_tc_partial_floats_total(P.tc_ne, P.tc_no, P.n_tot) + 2));
+    } else {
+        P.n_split = gram_split_count(P.n, P.n_tot);
+        CREATE_CUDA(dev_alloc(&P.d_part, (size_t)P.n_split * 2 * P.n_tot * P.n_tot));
+    }
     CREATE_CUDA(dev_alloc(&P.d_X, (size_t)(p.degree + 1) * P.n_tot * P.n_tot));
     CREATE_CUDA(dev_alloc(&P.d_ctab, 2 * (size_t)P.n_theta));
     CREATE_CUDA(launch_cos_table(P.d_ctab, P.n_theta, P.stream));
@@ -553,6 +570,9 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, P.stream));
     P.stats.launches++;
     auto gram = [&](const void* A, const void* B) -> cudaError_t {
+        if (P.use_tc)
+            return launch_gram_tc((const float*)A, (const float*)B, P.ld, P.n_tot, P.n, P.tc_ne, P.tc_no,
+                                  P.d_part_tc, P.d_flag, P.stream);
         if (P.mixed)
             return launch_gram_f32((const float*)A, (const float*)B, P.ld, P.n_tot, P.n, P.n_split, P.d_part,
                                    P.stream);
@@ -567,7 +587,8 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     }
     {
         Scope sc(h, PH_REDUCE);
-        CUDA_OR_FAIL(h, launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, -1, P.stream));
+        CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, -1, P.stream)
+                                 : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, -1, P.stream));
         P.stats.launches++;
     }
     for (int k = 0; k < S; ++k) {
@@ -601,7 +622,8 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         }
         {
             Scope sc(h, PH_REDUCE);
-            CUDA_OR_FAIL(h, launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, k, P.stream));
+            CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k, P.stream)
+                                     : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, k, P.stream));
             P.stats.launches++;
         }
     }
@@ -613,6 +635,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     int flag = 0;
     s = read_flag(h, &flag);
     if (s != SSM_OK) return s;
+    if (flag & 2) return fail(h, SSM_ETIMEOUT, "a tensor-core Gram wait gave up (bounded mbarrier wait)");
     if (flag) return fail(h, SSM_ENONFINITE, "W or the moments contain NaN/Inf");
     {
         std::vector<double> d0(P.p.n_v);
@@ -679,7 +702,9 @@ ssm_status ssm_dos(ssm_plan_t h, const double* t, int64_t n_t, double sigma, dou
     if (dos_ss) CUDA_OR_FAIL(h, from_device(dos_ss, h->d_dos_ss, n_t * sizeof(double), P.stream));
     if (dos_kpm) CUDA_OR_FAIL(h, from_device(dos_kpm, h->d_dos_kpm, n_t * sizeof(double), P.stream));
     if (rank) CUDA_OR_FAIL(h, from_device(rank, h->d_rank, 2 * n_t * sizeof(int32_t), P.stream));
-    return sync_and_settle(h);
+    s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    return check_solver_flag(h);
 }
 
 ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int64_t n_t, double sigma,
@@ -744,6 +769,8 @@ ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int6
     double res[2] = {0, 0};
     CUDA_OR_FAIL(h, cudaMemcpyAsync(res, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
     s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    s = check_solver_flag(h);
     if (s != SSM_OK) return s;
     if (tr_ss) *tr_ss = res[0];
     if (tr_kpm) *tr_kpm = res[1];

@@ -8,7 +8,12 @@
 // contraction [n_t x L] . [L x (rows*cols)] over the stored moments, which is
 // what this kernel computes: out[t][i*cols + j] = sum_{l<L} coef[t][l] X_l[i][j].
 // 64 x 64 output tiles, 16-deep slabs of l staged in shared memory, 4 x 4
-// outputs per thread, summation over l in increasing order.
+// outputs per thread, summation over l in increasing order.  Every X_l is
+// symmetric, so only the upper triangle (i <= j) of the square output is
+// computed and each value is stored at (i, j) and (j, i): this holds K_W, K_W~
+// and, in the upper-right block, K_C^T.  float64 runs at 1/58 of the float32
+// rate on this part, which makes this kernel ALU-bound; the triangle halves
+// its flops.
 #include "internal.h"
 
 namespace ssm {
@@ -25,18 +30,31 @@ assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, co
     __shared__ double Cs[TL][TT + 1];
     __shared__ double Xs[TL][TE];
     __shared__ int xoff[TE];
-    const int64_t ne = (int64_t)rows * cols;
+    __shared__ int ooff[2 * TE];
+    const int64_t ne = (int64_t)rows * (rows + 1) / 2;  // rows == cols
+    const int64_t nsq = (int64_t)rows * cols;
     const int64_t t0 = (int64_t)blockIdx.y * TT;
     const int64_t e0 = (int64_t)blockIdx.x * TE;
     const size_t nn = (size_t)n_tot * n_tot;
     if (threadIdx.x < TE) {
         const int64_t e = e0 + threadIdx.x;
-        int off = -1;
+        int off = -1, oij = -1, oji = -1;
         if (e < ne) {
-            const int i = (int)(e / cols), j = (int)(e - (int64_t)i * cols);
+            // packed upper triangle, row-major: e = i*n - i(i-1)/2 + (j - i)
+            const double nn1 = 2.0 * rows + 1.0;
+            int i = (int)((nn1 - sqrt(nn1 * nn1 - 8.0 * (double)e)) * 0.5);
+            if (i < 0) i = 0;
+            if (i > rows - 1) i = rows - 1;
+            while (i > 0 && (int64_t)i * rows - (int64_t)i * (i - 1) / 2 > e) --i;
+            while (i + 1 < rows && (int64_t)(i + 1) * rows - (int64_t)(i + 1) * i / 2 <= e) ++i;
+            const int j = (int)(e - ((int64_t)i * rows - (int64_t)i * (i - 1) / 2)) + i;
             off = i * n_tot + j;
+            oij = i * cols + j;
+            oji = j * cols + i;
         }
         xoff[threadIdx.x] = off;
+        ooff[threadIdx.x] = oij;
+        ooff[TE + threadIdx.x] = oji;
     }
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double acc[4][4];
@@ -79,8 +97,12 @@ assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, co
         if (ti >= n_t) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int64_t e = e0 + tx + 16 * q;
-            if (e < ne) out[ti * ne + e] = acc[p][q];
+            const int ee = tx + 16 * q;
+            const int oij = ooff[ee];
+            if (oij >= 0) {
+                out[ti * nsq + oij] = acc[p][q];
+                out[ti * nsq + ooff[TE + ee]] = acc[p][q];
+            }
         }
     }
 }
@@ -89,7 +111,8 @@ assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, co
 
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X, int n_tot,
                             int rows, int cols, double* out, cudaStream_t s) {
-    const int64_t ne = (int64_t)rows * cols;
+    if (rows != cols) return cudaErrorInvalidValue;
+    const int64_t ne = (int64_t)rows * (rows + 1) / 2;
     dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
     assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
     return cudaGetLastError();

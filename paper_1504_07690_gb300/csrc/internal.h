@@ -51,6 +51,9 @@ struct Plan {
     void* d_V[3] = {nullptr, nullptr, nullptr};
     double* d_part = nullptr;          // Gram partials [n_split][2][n_tot][n_tot]
     int n_split = 0;
+    bool use_tc = false;               // mixed path on tensor cores
+    int tc_ne = 0, tc_no = 0;
+    float* d_part_tc = nullptr;        // [tc_ne + tc_no][n_tot][n_tot]
     double* d_X = nullptr;             // (M+1) x n_tot x n_tot
     bool have_moments = false;
     double x0max = 0;                  // max_i X_0[i][i] over the first n_v probes
@@ -111,6 +114,16 @@ cudaError_t launch_gram_f32(const float* A, const float* B, int ld, int n_tot, i
 cudaError_t launch_reduce_gram_pair(const double* part, int n_split, int n, double* gaa, double* gab,
                                     cudaStream_t s);
 
+// Tensor-core split-bf16 Gram (gram_tc.cu): Ge over n_e slabs, Go over n_o slabs,
+// float32 partials [n_e + n_o][n_tot][n_tot]; status bit 2 on a timed-out wait.
+bool gram_tc_supported(int n_tot, int ld);
+void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o);
+size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot);
+size_t gram_tc_partial_floats_total(int n_e, int n_o, int n_tot);  // + room for the float64 sums
+cudaError_t launch_gram_tc(const float* X, const float* Y, int ld, int n_tot, int64_t n_rows, int n_e, int n_o,
+                           float* part, int* flag, cudaStream_t s);
+cudaError_t launch_reduce_tc(const float* part, int n_e, int n_o, int n_tot, double* X, int step, cudaStream_t s);
+
 // Reduce partials into the moments of step k (see moments.cu).
 cudaError_t launch_reduce_moments(const double* part, int n_split, int n_tot, double* X, int step,
                                   cudaStream_t s);
@@ -136,7 +149,8 @@ size_t solve_workspace_bytes(int n_v);
 // floor(t) = floor_scale * sum_{l<=K} (l+1) |mu[t][l]| (see ssm_params.eps_floor).
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh,
                          double tau, double xlo, double xhi, const double* mu, int ldmu, int K,
-                         double floor_scale, void* work, double* dos, int32_t* rank, cudaStream_t s);
+                         double floor_scale, void* work, double* dos, int32_t* rank, int* flag,
+                         cudaStream_t s);
 
 // Alg. 8 pieces (trace.cu).
 cudaError_t launch_trace_h(const double* tt, const double* fx, int64_t n_t, double fend, double a,

@@ -2,21 +2,26 @@
 //
 // For every sweep point t_i one CTA runs Alg. 4 and the estimate of Alg. 6 /
 // Alg. 7's final loop:
-//   1. K_W = U S U^T                                   (cyclic Jacobi)
+//   1. K_W = U S U^T
 //   2. keep s_j >= max(tau max s, floor(t)) (nothing if max s <= 0); floor(t)
 //      is the rounding error of K_W(t), so that points where K_W(t) is
 //      numerically zero keep no noise directions
-//   3. B = S~^-1/2 U~^T K_Z U~ S~^-1/2 = X Xi X^T      (cyclic Jacobi)
+//   3. B = S~^-1/2 U~^T K_Z U~ S~^-1/2 = X Xi X^T
 //   4. keep xi in [xlo, xhi] (the range of g_sigma with a rounding slack)
 //   5. C~ = U~ S~^-1/2 X~
 //   phi = sum xi~ + (Tr K_W~ - ||K_C C~||_F^2) / N~_v   (second term only if N~_v > 0)
 //
-// The eigensolver is two-sided cyclic Jacobi with the round-robin
-// (tournament) ordering, so the n/2 rotations of one round touch disjoint
-// row/column pairs and run in parallel across the CTA.  A rotation is skipped
-// when |a_pq| <= 1e-16 sqrt(|a_pp a_qq|) or |a_pq| <= 1e-22 ||A||_F; sweeps stop
-// when a whole sweep applies no rotation (at most 40 sweeps).  Matrices live
-// in a per-CTA global workspace (L2 resident); eigenvectors are kept as rows.
+// Symmetric eigensolver (float64 is 1/58 of the float32 rate on this part,
+// so the flop count matters): Householder reduction to tridiagonal form,
+// explicit accumulation of the orthogonal factor, then the implicit-shift QL
+// iteration on the tridiagonal matrix (the Householder/QL method of Martin,
+// Reinsch and Wilkinson, Numer. Math. 11, 1968), ~7.7 n^3 flops with vectors.
+// In each QL sweep one thread computes the chain of plane rotations and the
+// whole CTA then applies it to the eigenvector rows, one column per thread,
+// coalesced.  Eigenvalues of B alone (no hybrid correction) skip the
+// accumulation and the rotations: ~1.3 n^3 flops.
+// Matrices live in a per-CTA global workspace (L2 resident); eigenvectors
+// are kept as rows.  QL sweeps are bounded (60 per eigenvalue).
 #include <float.h>
 
 #include "internal.h"
@@ -27,14 +32,20 @@ namespace {
 
 constexpr int NT = 256;          // threads per CTA
 constexpr int MAXN = 1024;       // largest n_v
-constexpr int MAXP = MAXN / 2;
-constexpr int MAX_SWEEPS = 40;
+constexpr int MAX_QL_ITER = 60;
 
-struct JacobiShared {
-    double c[MAXP], s[MAXP], t[MAXP], app[MAXP], aqq[MAXP], apq[MAXP];
-    int p[MAXP], q[MAXP];
-    int count;
-    double red[NT / 32];
+struct Shared {
+    double* d;     // n: diagonal, then eigenvalues
+    double* off;   // n: off-diagonal T[i][i+1]
+    double* v;     // n: Householder vector
+    double* p;     // n: work vector
+    double* rc;    // n: rotation cosines of one QL sweep
+    double* rs;    // n: rotation sines
+    int* keep;     // n
+    int* sel;      // n
+    double* red;   // NT / 32
+    int* misc;     // [0] nkeep, [1] nsel, [2] QL range lo, [3] hi, [4] continue flag
+    double* beta;  // n: Householder scalars
 };
 
 __device__ double block_sum(double v, double* red) {
@@ -59,187 +70,280 @@ __device__ double block_max(double v, double* red) {
     return s;
 }
 
-// Eigen-decomposition of the symmetric n x n matrix A (row-major, ld n) in
-// place: on return diag(A) holds the eigenvalues and row j of Vt the
-// eigenvector of A[j][j].
-__device__ void jacobi_eigh(double* __restrict__ A, double* __restrict__ Vt, int n, JacobiShared& sh) {
+// Householder reduction of the symmetric n x n matrix A (row-major, ld n) to
+// tridiagonal T = H^T A H: sh.d, sh.off receive T; row k of A (columns k+1..)
+// receives the k-th Householder vector and sh.beta[k] its scalar.
+__device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int L = n - k - 1;
+        const double* x = A + (size_t)k * n + k + 1;  // row k == column k (symmetric)
+        double f = 0.0;
+        for (int i = tid; i < L; i += NT) f = fma(x[i], x[i], f);
+        const double nrm2 = block_sum(f, sh.red);
+        const double x0 = x[0];
+        double beta = 0.0, alpha = x0;
+        if (nrm2 - x0 * x0 > 0.0) {
+            alpha = -copysign(sqrt(nrm2), x0);
+            const double v0 = x0 - alpha;
+            const double vtv = nrm2 - x0 * x0 + v0 * v0;
+            beta = 2.0 / vtv;
+            for (int i = tid; i < L; i += NT) sh.v[i] = (i == 0) ? v0 : x[i];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sh.d[k] = A[(size_t)k * n + k];
+            sh.off[k] = alpha;
+            sh.beta[k] = beta;
+        }
+        if (beta != 0.0) {
+            // p = beta A22 v  (warp per row, lanes along the row)
+            for (int i = warp; i < L; i += NT / 32) {
+                const double* row = A + (size_t)(k + 1 + i) * n + k + 1;
+                double s = 0.0;
+                for (int j = lane; j < L; j += 32) s = fma(row[j], sh.v[j], s);
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) sh.p[i] = beta * s;
+            }
+            __syncthreads();
+            double g = 0.0;
+            for (int i = tid; i < L; i += NT) g = fma(sh.p[i], sh.v[i], g);
+            const double K = 0.5 * beta * block_sum(g, sh.red);
+            for (int i = tid; i < L; i += NT) sh.p[i] -= K * sh.v[i];  // p becomes w
+            __syncthreads();
+            // A22 -= v w^T + w v^T
+            for (int e = tid; e < L * L; e += NT) {
+                const int i = e / L, j = e - i * L;
+                double* a = A + (size_t)(k + 1 + i) * n + k + 1 + j;
+                *a -= sh.v[i] * sh.p[j] + sh.p[i] * sh.v[j];
+            }
+            // keep v in row k for the accumulation
+            for (int i = tid; i < L; i += NT) A[(size_t)k * n + k + 1 + i] = sh.v[i];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (n >= 2) {
+            sh.d[n - 2] = A[(size_t)(n - 2) * n + n - 2];
+            sh.off[n - 2] = A[(size_t)(n - 2) * n + n - 1];
+            sh.beta[n - 2] = 0.0;
+        }
+        sh.d[n - 1] = A[(size_t)(n - 1) * n + n - 1];
+        sh.off[n - 1] = 0.0;
+        if (n >= 2) sh.beta[n - 1] = 0.0;
+    }
+    __syncthreads();
+}
+
+// Zt = H^T (rows of Zt are the columns of H = H_0 H_1 ... H_{n-3}), from the
+// vectors left in A by tridiagonalise.  Backward accumulation on H, written
+// transposed: column j of H ends up in row j of Zt.
+__device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ Zt, int n, Shared& sh) {
     const int tid = threadIdx.x;
+    // Zt holds H^T during the accumulation; H_k acts on rows/columns k+1.. of H,
+    // i.e. columns k+1.. of H^T: H^T <- H^T H_k^T = H^T H_k.
     for (int e = tid; e < n * n; e += NT) {
         const int i = e / n, j = e - i * n;
-        Vt[e] = (i == j) ? 1.0 : 0.0;
+        Zt[e] = (i == j) ? 1.0 : 0.0;
     }
-    double f = 0.0;
-    for (int e = tid; e < n * n; e += NT) f = fma(A[e], A[e], f);
-    const double anorm = sqrt(block_sum(f, sh.red));
-    if (n < 2) return;
-    const int np = n + (n & 1);
-    const int npairs = np / 2;
-    for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-        if (tid == 0) sh.count = 0;
-        __syncthreads();
-        for (int r = 0; r < np - 1; ++r) {
-            for (int k = tid; k < npairs; k += NT) {
-                int p, q;
-                if (k == 0) {
-                    p = np - 1;
-                    q = r;
-                } else {
-                    p = (r + k) % (np - 1);
-                    q = (r - k + (np - 1)) % (np - 1);
-                }
-                if (p > q) {
-                    const int w = p;
-                    p = q;
-                    q = w;
-                }
-                double cc = 1.0, ss = 0.0, tt = 0.0, app = 0.0, aqq = 0.0, apq = 0.0;
-                if (q < n) {
-                    apq = A[p * n + q];
-                    app = A[p * n + p];
-                    aqq = A[q * n + q];
-                    const double aa = fabs(apq);
-                    if (aa > 1e-16 * sqrt(fabs(app)) * sqrt(fabs(aqq)) && aa > 1e-22 * anorm) {
-                        const double theta = (aqq - app) / (2.0 * apq);
-                        double t = 1.0 / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
-                        if (theta < 0.0) t = -t;
-                        cc = 1.0 / sqrt(fma(t, t, 1.0));
-                        ss = t * cc;
-                        tt = t;
-                        atomicAdd(&sh.count, 1);
-                    }
-                }
-                sh.p[k] = p;
-                sh.q[k] = q;
-                sh.c[k] = cc;
-                sh.s[k] = ss;
-                sh.t[k] = tt;
-                sh.app[k] = app;
-                sh.aqq[k] = aqq;
-                sh.apq[k] = apq;
-            }
-            __syncthreads();
-            // rows p, q of A and of Vt: A <- J^T A, Vt <- J^T Vt
-            for (int e = tid; e < npairs * n; e += NT) {
-                const int k = e / n, j = e - k * n;
-                const double ss = sh.s[k];
-                if (ss == 0.0) continue;
-                const double cc = sh.c[k];
-                const int p = sh.p[k], q = sh.q[k];
-                const double ap = A[p * n + j], aq = A[q * n + j];
-                A[p * n + j] = cc * ap - ss * aq;
-                A[q * n + j] = ss * ap + cc * aq;
-                const double vp = Vt[p * n + j], vq = Vt[q * n + j];
-                Vt[p * n + j] = cc * vp - ss * vq;
-                Vt[q * n + j] = ss * vp + cc * vq;
-            }
-            __syncthreads();
-            // columns p, q of A: A <- A J
-            for (int e = tid; e < npairs * n; e += NT) {
-                const int i = e / npairs, k = e - i * npairs;
-                const double ss = sh.s[k];
-                if (ss == 0.0) continue;
-                const double cc = sh.c[k];
-                const int p = sh.p[k], q = sh.q[k];
-                const double ap = A[i * n + p], aq = A[i * n + q];
-                A[i * n + p] = cc * ap - ss * aq;
-                A[i * n + q] = ss * ap + cc * aq;
-            }
-            __syncthreads();
-            // exact pivot values of the rotated 2 x 2 block
-            for (int k = tid; k < npairs; k += NT) {
-                if (sh.s[k] == 0.0) continue;
-                const int p = sh.p[k], q = sh.q[k];
-                const double t = sh.t[k], apq = sh.apq[k];
-                A[p * n + p] = sh.app[k] - t * apq;
-                A[q * n + q] = sh.aqq[k] + t * apq;
-                A[p * n + q] = 0.0;
-                A[q * n + p] = 0.0;
-            }
-            __syncthreads();
+    __syncthreads();
+    for (int k = n - 3; k >= 0; --k) {
+        const double beta = sh.beta[k];
+        if (beta == 0.0) continue;
+        const int L = n - k - 1;
+        const double* v = A + (size_t)k * n + k + 1;
+        // H_sub <- H_k H_sub on rows/cols k+1..: u_j = sum_i v_i H[i][j] = sum_i v_i Zt[j][i]
+        for (int j = tid; j < L; j += NT) {
+            const double* zr = Zt + (size_t)(k + 1 + j) * n + k + 1;
+            double s = 0.0;
+            for (int i = 0; i < L; ++i) s = fma(v[i], zr[i], s);
+            sh.p[j] = beta * s;
         }
-        const int done = (sh.count == 0);
         __syncthreads();
-        if (done) break;
+        for (int e = tid; e < L * L; e += NT) {
+            const int j = e / L, i = e - j * L;  // Zt[j][i] = H[i][j]
+            Zt[(size_t)(k + 1 + j) * n + k + 1 + i] -= v[i] * sh.p[j];
+        }
+        __syncthreads();
     }
 }
 
-struct SolveShared {
-    JacobiShared jac;
-    double ev[MAXN];
-    int keep[MAXN];
-    int sel[MAXN];
-    int nkeep, nsel;
-};
+// Implicit-shift QL on (sh.d, sh.off); eigenvalues -> sh.d.  With vectors,
+// every plane rotation acting on eigenvector columns (i, i+1) is applied to
+// rows i, i+1 of Zt.  Returns false if an eigenvalue needed more than
+// MAX_QL_ITER sweeps.
+__device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared& sh) {
+    const int tid = threadIdx.x;
+    bool converged = true;
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter <= MAX_QL_ITER; ++iter) {
+            if (tid == 0) {
+                int m = l;
+                for (; m < n - 1; ++m) {
+                    const double dd = fabs(sh.d[m]) + fabs(sh.d[m + 1]);
+                    if (fabs(sh.off[m]) <= DBL_EPSILON * dd) break;
+                }
+                int lo = 0, hi = -1;  // rotations to apply: i from hi down to lo
+                if (m != l && iter < MAX_QL_ITER) {
+                    double g = (sh.d[l + 1] - sh.d[l]) / (2.0 * sh.off[l]);
+                    double r = hypot(g, 1.0);
+                    g = sh.d[m] - sh.d[l] + sh.off[l] / (g + copysign(r, g));
+                    double s = 1.0, c = 1.0, p = 0.0;
+                    int i = m - 1;
+                    bool early = false;
+                    for (; i >= l; --i) {
+                        const double f = s * sh.off[i];
+                        const double b = c * sh.off[i];
+                        r = hypot(f, g);
+                        sh.off[i + 1] = r;
+                        if (r == 0.0) {
+                            sh.d[i + 1] -= p;
+                            sh.off[m] = 0.0;
+                            early = true;
+                            break;
+                        }
+                        s = f / r;
+                        c = g / r;
+                        g = sh.d[i + 1] - p;
+                        r = (sh.d[i] - g) * s + 2.0 * c * b;
+                        p = s * r;
+                        sh.d[i + 1] = g + p;
+                        g = c * r - b;
+                        sh.rc[i] = c;
+                        sh.rs[i] = s;
+                    }
+                    hi = m - 1;
+                    lo = early ? i + 1 : l;
+                    if (!early) {
+                        sh.d[l] -= p;
+                        sh.off[l] = g;
+                        sh.off[m] = 0.0;
+                    }
+                    sh.misc[4] = 1;
+                } else {
+                    if (m != l) sh.misc[5] = 1;  // iteration limit reached
+                    sh.misc[4] = 0;
+                }
+                sh.misc[2] = lo;
+                sh.misc[3] = hi;
+            }
+            __syncthreads();
+            const int go = sh.misc[4];
+            if (vectors && go) {
+                const int lo = sh.misc[2], hi = sh.misc[3];
+                for (int col = tid; col < n; col += NT) {
+                    for (int i = hi; i >= lo; --i) {
+                        const double c = sh.rc[i], s = sh.rs[i];
+                        double* z0 = Zt + (size_t)i * n + col;
+                        double* z1 = z0 + n;
+                        const double f = *z1;
+                        *z1 = s * (*z0) + c * f;
+                        *z0 = c * (*z0) - s * f;
+                    }
+                }
+            }
+            __syncthreads();
+            if (!go) break;
+        }
+    }
+    if (sh.misc[5]) converged = false;
+    __syncthreads();
+    return converged;
+}
+
+// Eigen-decomposition of the symmetric n x n matrix A (destroyed): sh.d gets
+// the eigenvalues; with vectors, row j of Zt the eigenvector of sh.d[j].
+__device__ bool eigh(double* __restrict__ A, double* __restrict__ Zt, int n, bool vectors, Shared& sh) {
+    if (threadIdx.x == 0) sh.misc[5] = 0;
+    __syncthreads();
+    if (n == 1) {
+        if (threadIdx.x == 0) sh.d[0] = A[0];
+        if (vectors && threadIdx.x == 0) Zt[0] = 1.0;
+        __syncthreads();
+        return true;
+    }
+    tridiagonalise(A, n, sh);
+    if (vectors) accumulate_q(A, Zt, n, sh);
+    return ql_implicit(Zt, n, vectors, sh);
+}
 
 __global__ void __launch_bounds__(NT)
 solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, int64_t n_t, int nv, int nvh,
              double tau, double xlo, double xhi, const double* __restrict__ mu, int ldmu, int K,
              double floor_scale, double* __restrict__ work, double* __restrict__ dos,
-             int32_t* __restrict__ rank) {
-    __shared__ SolveShared sh;
-    const int tid = threadIdx.x;
+             int32_t* __restrict__ rank, int* __restrict__ flag) {
+    extern __shared__ __align__(16) double dyn[];
     const int n = nv;
+    Shared sh;
+    sh.d = dyn;
+    sh.off = sh.d + n;
+    sh.v = sh.off + n;
+    sh.p = sh.v + n;
+    sh.rc = sh.p + n;
+    sh.rs = sh.rc + n;
+    sh.beta = sh.rs + n;
+    sh.red = sh.beta + n;
+    sh.keep = reinterpret_cast<int*>(sh.red + NT / 32);
+    sh.sel = sh.keep + n;
+    sh.misc = sh.sel + n;
+    const int tid = threadIdx.x;
     const int n_tot = nv + nvh;
     const size_t nn = (size_t)n * n;
     double* A = work + (size_t)blockIdx.x * 4 * nn;
-    double* Vt = A + nn;
-    double* Y = Vt + nn;
-    double* Xt = Y + nn;
+    double* Zt = A + nn;
+    double* Y = Zt + nn;
+    double* T1 = Y + nn;
     for (int64_t it = blockIdx.x; it < n_t; it += gridDim.x) {
         const double* Kt = Kfull + (size_t)it * n_tot * n_tot;
-        const double* Zt = KZ + (size_t)it * nn;
-        // 1. K_W (symmetrised) -> A
+        const double* Zk = KZ + (size_t)it * nn;
+        // 1. K_W (symmetrised) -> A, eigen-decomposition
         for (int e = tid; e < n * n; e += NT) {
             const int i = e / n, j = e - i * n;
             A[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
         }
         __syncthreads();
-        jacobi_eigh(A, Vt, n, sh.jac);
-        __syncthreads();
+        bool ok = eigh(A, Zt, n, true, sh);
         // 2. truncation s_j >= max(tau max s, rounding floor of K_W)
         double m = -DBL_MAX;
-        for (int j = tid; j < n; j += NT) {
-            sh.ev[j] = A[(size_t)j * n + j];
-            m = fmax(m, sh.ev[j]);
-        }
-        const double smax = block_max(m, sh.jac.red);
+        for (int j = tid; j < n; j += NT) m = fmax(m, sh.d[j]);
+        const double smax = block_max(m, sh.red);
         double fs = 0.0;
         if (floor_scale > 0.0)
             for (int l = tid; l <= K; l += NT) fs = fma((double)(l + 1), fabs(mu[it * ldmu + l]), fs);
-        const double floor_t = floor_scale * block_sum(fs, sh.jac.red);
+        const double floor_t = floor_scale * block_sum(fs, sh.red);
         if (tid == 0) {
             int r = 0;
             if (smax > 0.0) {
                 const double thr = fmax(tau * smax, floor_t);
                 for (int j = 0; j < n; ++j)
-                    if (sh.ev[j] >= thr) sh.keep[r++] = j;
+                    if (sh.d[j] >= thr) sh.keep[r++] = j;
             }
-            sh.nkeep = r;
+            sh.misc[0] = r;
         }
         __syncthreads();
-        const int r = sh.nkeep;
+        const int r = sh.misc[0];
         // Y = S~^-1/2 U~^T (rows)
         for (int e = tid; e < r * n; e += NT) {
             const int k = e / n, c = e - k * n;
             const int j = sh.keep[k];
-            Y[(size_t)k * n + c] = Vt[(size_t)j * n + c] / sqrt(sh.ev[j]);
+            Y[(size_t)k * n + c] = Zt[(size_t)j * n + c] / sqrt(sh.d[j]);
         }
         __syncthreads();
-        // T1 = Y K_Z (r x n) into A
+        // T1 = Y K_Z (r x n)
         for (int e = tid; e < r * n; e += NT) {
             const int k = e / n, c = e - k * n;
             const double* y = Y + (size_t)k * n;
             double s = 0.0;
-            for (int mm = 0; mm < n; ++mm) s = fma(y[mm], Zt[(size_t)mm * n + c], s);
-            A[(size_t)k * n + c] = s;
+            for (int mm = 0; mm < n; ++mm) s = fma(y[mm], Zk[(size_t)mm * n + c], s);
+            T1[(size_t)k * n + c] = s;
         }
         __syncthreads();
-        // B = T1 Y^T (r x r, ld r) into Vt, symmetric
+        // B = T1 Y^T (r x r, ld r) into A, symmetrised
         for (int e = tid; e < r * r; e += NT) {
             const int k = e / r, kk = e - k * r;
             if (kk < k) continue;
-            const double* a1 = A + (size_t)k * n;
-            const double* a2 = A + (size_t)kk * n;
+            const double* a1 = T1 + (size_t)k * n;
+            const double* a2 = T1 + (size_t)kk * n;
             const double* y1 = Y + (size_t)k * n;
             const double* y2 = Y + (size_t)kk * n;
             double s1 = 0.0, s2 = 0.0;
@@ -248,53 +352,54 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 s2 = fma(a2[c], y1[c], s2);
             }
             const double v = 0.5 * (s1 + s2);
-            Vt[(size_t)k * r + kk] = v;
-            Vt[(size_t)kk * r + k] = v;
+            A[(size_t)k * r + kk] = v;
+            A[(size_t)kk * r + k] = v;
         }
         __syncthreads();
-        // 3. eigen-decomposition of B
-        jacobi_eigh(Vt, Xt, r, sh.jac);
-        __syncthreads();
+        // 3. eigen-decomposition of B (vectors only for the hybrid correction)
+        const bool need_vec = nvh > 0;
+        if (r > 0) ok = eigh(A, Zt, r, need_vec, sh) && ok;
         // 4. range filter; the sum runs in index order on one thread
         if (tid == 0) {
             int q = 0;
             double phi = 0.0;
             for (int k = 0; k < r; ++k) {
-                const double xi = Vt[(size_t)k * r + k];
+                const double xi = sh.d[k];
                 if (xi >= xlo && xi <= xhi) {
                     sh.sel[q++] = k;
                     phi += xi;
                 }
             }
-            sh.nsel = q;
-            sh.ev[0] = phi;
+            sh.misc[1] = q;
+            sh.p[0] = phi;
         }
         __syncthreads();
-        const int rs = sh.nsel;
-        double phi = sh.ev[0];
+        const int rs = sh.misc[1];
+        double phi = sh.p[0];
+        __syncthreads();
         if (nvh > 0) {
-            // 5. C~^T rows: CtT[m][c] = sum_k Xt[sel_m][k] Y[k][c]  (into A, rs x n)
+            // 5. C~^T rows: CtT[m][c] = sum_k X[k][sel_m] Y[k][c], X = eigenvectors of B
+            //    (row sel_m of Zt)  -> T1 (rs x n)
             for (int e = tid; e < rs * n; e += NT) {
                 const int mq = e / n, c = e - mq * n;
-                const double* x = Xt + (size_t)sh.sel[mq] * r;
+                const double* x = Zt + (size_t)sh.sel[mq] * r;
                 double s = 0.0;
                 for (int k = 0; k < r; ++k) s = fma(x[k], Y[(size_t)k * n + c], s);
-                A[(size_t)mq * n + c] = s;
+                T1[(size_t)mq * n + c] = s;
             }
             __syncthreads();
             double f = 0.0;
             for (int e = tid; e < nvh * rs; e += NT) {
                 const int h = e / rs, mq = e - h * rs;
                 const double* kc = Kt + (size_t)(nv + h) * n_tot;
-                const double* ct = A + (size_t)mq * n;
+                const double* ct = T1 + (size_t)mq * n;
                 double s = 0.0;
                 for (int c = 0; c < n; ++c) s = fma(kc[c], ct[c], s);
                 f = fma(s, s, f);
             }
-            const double kcn = block_sum(f, sh.jac.red);
+            const double kcn = block_sum(f, sh.red);
             double tr = 0.0;
-            if (tid == 0)
-                for (int h = 0; h < nvh; ++h) tr += Kt[(size_t)(nv + h) * n_tot + nv + h];
+            for (int h = 0; h < nvh; ++h) tr += Kt[(size_t)(nv + h) * n_tot + nv + h];
             phi += (tr - kcn) / nvh;
         }
         if (tid == 0) {
@@ -303,36 +408,45 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 rank[2 * it] = r;
                 rank[2 * it + 1] = rs;
             }
+            if (!ok) atomicOr(flag, 4);
         }
         __syncthreads();
     }
 }
 
-int solve_grid(int64_t n_t) {
+// CTAs with a private workspace: 4 per SM to overlap the serial QL chains,
+// fewer when 4 n^2 doubles per CTA would exceed 2 GiB in total.
+int workspace_ctas(int n_v) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t g = 2LL * sms;
-    if (g > n_t) g = n_t;
+    const size_t per = (size_t)4 * n_v * n_v * sizeof(double);
+    size_t cap = ((size_t)2 << 30) / per;
+    size_t g = (size_t)4 * sms;
+    if (g > cap) g = cap;
     return g < 1 ? 1 : (int)g;
 }
+
+size_t solve_smem(int n) { return (size_t)7 * n * sizeof(double) + (NT / 32) * sizeof(double) + (2 * n + 8) * sizeof(int); }
 
 }  // namespace
 
 size_t solve_workspace_bytes(int n_v) {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (size_t)2 * sms * 4 * (size_t)n_v * n_v * sizeof(double);
+    return (size_t)workspace_ctas(n_v) * 4 * (size_t)n_v * n_v * sizeof(double);
 }
 
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh, double tau,
                          double xlo, double xhi, const double* mu, int ldmu, int K, double floor_scale, void* work,
-                         double* dos, int32_t* rank, cudaStream_t s) {
+                         double* dos, int32_t* rank, int* flag, cudaStream_t s) {
     if (n_t <= 0) return cudaSuccess;
     if (n_v > MAXN) return cudaErrorInvalidValue;
-    solve_kernel<<<solve_grid(n_t), NT, 0, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K, floor_scale,
-                                                (double*)work, dos, rank);
+    const size_t smem = solve_smem(n_v);
+    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = workspace_ctas(n_v);
+    if (grid > n_t) grid = n_t;
+    solve_kernel<<<(int)grid, NT, smem, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K,
+                                                   floor_scale, (double*)work, dos, rank, flag);
     return cudaGetLastError();
 }
 

@@ -67,7 +67,7 @@ def test_status_strings(lib):
 def test_parameter_validation_before_any_cuda_call(lib, field, value):
     from paper_1504_07690_gb300 import _native as N
 
-    p = N.ssm_params(n_v=4, n_vh=0, degree=10, precision=0, lo=0, hi=0, tau=0, kappa=-1, n_theta=0)
+    p = N.ssm_params(n_v=4, n_vh=0, degree=10, precision=0, lo=0, hi=0, tau=0, kappa=-1, n_theta=0, options=0)
     setattr(p, field, value)
     diag = (C.c_double * 8)(*([2.0] * 8))
     st = N.ssm_stencil((C.c_int64 * 3)(8, 1, 1), (C.c_int32 * 3)(0, 0, 0), C.cast(diag, C.c_void_p),
@@ -82,7 +82,7 @@ def test_parameter_validation_before_any_cuda_call(lib, field, value):
 def test_both_or_no_operator_is_rejected(lib):
     from paper_1504_07690_gb300 import _native as N
 
-    p = N.ssm_params(n_v=4, n_vh=0, degree=10, precision=0, lo=0, hi=0, tau=0, kappa=-1, n_theta=0)
+    p = N.ssm_params(n_v=4, n_vh=0, degree=10, precision=0, lo=0, hi=0, tau=0, kappa=-1, n_theta=0, options=0)
     h = C.c_void_p()
     assert lib.ssm_plan_create(C.byref(h), None, None, C.byref(p), None) == 1
 

@@ -268,3 +268,29 @@ def test_gram_pair_fp64_matches_definition_and_repeats(S):
     assert torch.equal(gaa, gaa2) and torch.equal(gab, gab2)
     g1, none = S.ssm_gram_pair(Ad[:1])
     assert none is None and np.allclose(g1.cpu().numpy(), np.outer(A[0], A[0]), rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------------------------ tensor-core Gram (mixed path)
+
+@pytest.mark.parametrize("nv,nvh,nx", [(150, 50, 61), (37, 0, 33), (128, 0, 40), (100, 29, 47)])
+def test_mixed_tensor_core_moments(S, nv, nvh, nx):
+    # n_tot = 200 (two M blocks), 37 (ragged, one block), 128 (exactly one), 129 (just over)
+    st = wl.anderson2d(nx, 900 + nx)
+    n_tot = nv + nvh
+    W = wl.random_block(st.n, n_tot, 901 + nx, "rademacher")
+    M = 60
+    plan_tc = S.ssm_plan_create(stencil=st, n_v=nv, n_vh=nvh, degree=M, precision="mixed")
+    plan_cc = S.ssm_plan_create(stencil=st, n_v=nv, n_vh=nvh, degree=M, precision="mixed", options=1)
+    Wd = torch.from_numpy(W).cuda()
+    Xtc = S.ssm_moments(plan_tc, Wd, return_moments=True).cpu().numpy()
+    Xcc = S.ssm_moments(plan_cc, Wd, return_moments=True).cpu().numpy()
+    info = S.ssm_plan_info(plan_tc)
+    A = _csr_A(st)
+    X64 = O.moments_direct(O.transform(A, info["a"], info["b"]), W, M)
+    scale = np.max(np.abs(X64))
+    # float32 recurrence: both mixed variants within 2e-5 of the float64 oracle
+    assert np.max(np.abs(Xcc - X64)) <= 2e-5 * scale
+    assert np.max(np.abs(Xtc - X64)) <= 2e-5 * scale
+    # split-bf16 tensor products vs float32 CUDA-core products on the same blocks
+    assert np.max(np.abs(Xtc - Xcc)) <= 1e-5 * scale
+    assert np.array_equal(Xtc, np.transpose(Xtc, (0, 2, 1)))
