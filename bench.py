@@ -129,6 +129,73 @@ def _traffic(kernel: str):
     return d["dram_bytes_per_launch"]
 
 
+# ----------------------------------------------------------------------------- rooflines
+
+FP64_FMA_PER_SM_CLK = 2   # measured: FMA chains reach 1.20 TFLOP/s on 152 SMs at 2.07 GHz
+
+
+def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks):
+    """Per-kernel algorithmic work / measured launch time against its bound.
+
+    Algorithmic work per launch (stated in the design doc):
+      stencil_step_kernel  bytes = (3 N n_tot + N) e   (read V_k, V_{k-1}, diag; write V_{k+1})
+      gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
+      gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
+      assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step
+      solve_kernel         flops = n_t (14.3 n_v^3)  (eigh with vectors 9 n^3, B 4 n^3, eigvals 1.3 n^3)
+    """
+    N = st.n
+    n_tot = c["n_v"] + c["n_vh"]
+    nv = c["n_v"]
+    M, n_t = c["M"], c["n_t"]
+    steps = args.steps
+    mixed = args.precision == "mixed"
+    e = 4 if mixed else 8
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak = 152 * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    out = []
+    rl = max(1, stats["recurrence_launches"])
+    rec_ms = stats["ms_recurrence"] / rl
+    rec_bytes = (3.0 * N * n_tot + N) * e
+    out.append(dict(kernel="stencil_step_kernel", bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9,
+                    peak=hbm, unit="GB/s", traffic=_traffic("stencil_step_kernel"), work_per_launch=rec_bytes,
+                    launch_ms=rec_ms, ms_per_step=stats["ms_recurrence"] / steps,
+                    peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"))
+    gl = max(1, stats["gram_launches"])
+    g_ms = stats["ms_gram"] / gl
+    pair = n_tot * (n_tot + 1) / 2.0 + n_tot * n_tot
+    if mixed and n_tot <= 256:
+        g_flops = 3.0 * 2.0 * N * pair
+        out.append(dict(kernel="gram_tc_kernel", bound="tensor", achieved=g_flops / (g_ms * 1e-3) / 1e12,
+                        peak=bf16, unit="TFLOP/s", traffic=_traffic("gram_tc_kernel"), work_per_launch=g_flops,
+                        launch_ms=g_ms, ms_per_step=stats["ms_gram"] / steps,
+                        peak_source=f"MEASURED_PEAKS.json bf16_tflops ({peak_kind})"))
+    else:
+        g_flops = 2.0 * N * pair
+        pk = fp32_peak if mixed else fp64_peak
+        out.append(dict(kernel="gram_kernel", bound="alu", achieved=g_flops / (g_ms * 1e-3) / 1e12, peak=pk,
+                        unit="TFLOP/s", traffic=None, work_per_launch=g_flops, launch_ms=g_ms,
+                        ms_per_step=stats["ms_gram"] / steps,
+                        peak_source="%s CUDA-core peak: 152 SMs x %d FMA/clk x 2 x %.0f MHz" % (
+                            "fp32" if mixed else "fp64", 128 if mixed else FP64_FMA_PER_SM_CLK, sm_mhz)))
+    a_flops = 2.0 * n_t * ((M // 2 + 1) * n_tot * (n_tot + 1) / 2.0 + (M + 1) * nv * (nv + 1) / 2.0)
+    a_ms = stats["ms_assemble"] / steps
+    out.append(dict(kernel="assemble_kernel", bound="alu", achieved=a_flops / (a_ms * 1e-3) / 1e12, peak=fp64_peak,
+                    unit="TFLOP/s", traffic=None, work_per_launch=a_flops / 2, launch_ms=a_ms / 2,
+                    ms_per_step=a_ms,
+                    peak_source="fp64 peak: 152 SMs x 2 FMA/clk x 2 x %.0f MHz (FMA-chain probe: 1.20 TFLOP/s)"
+                                % sm_mhz))
+    s_flops = n_t * 14.3 * nv ** 3
+    s_ms = stats["ms_solve"] / steps
+    out.append(dict(kernel="solve_kernel", bound="alu", achieved=s_flops / (s_ms * 1e-3) / 1e12, peak=fp64_peak,
+                    unit="TFLOP/s", traffic=None, work_per_launch=s_flops, launch_ms=s_ms, ms_per_step=s_ms,
+                    peak_source="fp64 peak: 152 SMs x 2 FMA/clk x 2 x %.0f MHz" % sm_mhz))
+    for r in out:
+        r["frac"] = r["achieved"] / r["peak"]
+    return out
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def cpu_oracle_sample(c, st, W, csr, rec_steps: int = 24, points: int = 6):
@@ -262,18 +329,13 @@ def run_gpu(args, c, st, W, csr):
     stats = S.ssm_stats_get(plan)
     value = units * ws / (ms * 1e-3)
 
-    # dominant kernel of the timed region and its roofline
+    # rooflines of the main kernels; "roofline" is the dominant one of the timed region
     hbm, bf16, bf16s, peak_kind = _peaks()
     phases = {k: stats[k] / args.steps for k in ("ms_coeffs", "ms_recurrence", "ms_gram", "ms_reduce",
                                                   "ms_assemble", "ms_solve", "ms_kpm")}
-    esz = 4 if args.precision == "mixed" else 8
-    rec_bytes = 3.0 * st.n * n_tot * esz + st.n * esz
-    rec_launch_ms = stats["ms_recurrence"] / max(1, stats["recurrence_launches"])
-    rec_achieved = rec_bytes / (rec_launch_ms * 1e-3) / 1e9
-    roofline = {"kernel": "stencil_step_kernel", "bound": "hbm", "achieved": rec_achieved, "peak": hbm,
-                "unit": "GB/s", "frac": rec_achieved / hbm, "traffic": _traffic("stencil_step_kernel"),
-                "bytes_per_launch": rec_bytes, "launch_ms": rec_launch_ms,
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    roofs = kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, ck)
+    dominant = max(roofs, key=lambda r: r["ms_per_step"])
+    roofline = dict(dominant)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -320,7 +382,8 @@ def run_gpu(args, c, st, W, csr):
                        "precision": args.precision,
                        "l2": "inputs larger than L2 (3 recurrence blocks of 52 MB + 320 MB of moments)",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": roofline, "phases_ms_per_step": phases, "gpu_launches": int(stats["launches"]),
+            "roofline": roofline, "rooflines": roofs, "phases_ms_per_step": phases,
+            "gpu_launches": int(stats["launches"]),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
         }
         print(json.dumps(line), flush=True)

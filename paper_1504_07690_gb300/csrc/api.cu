@@ -44,7 +44,16 @@ thread_local std::string g_create_error;
 
 enum Phase { PH_COEFFS, PH_REC, PH_GRAM, PH_REDUCE, PH_ASSEMBLE, PH_SOLVE, PH_KPM, PH_TRACE };
 
-constexpr int64_t BATCH_T = 256;     // sweep points per assembly / solve batch
+// Sweep points per assembly / solve batch: all of them when the per-point
+// matrices (K and K_Z, float64) fit in 2 GiB, so that every SM holds several
+// concurrent per-point solves.
+int64_t batch_points(const Plan& P) {
+    const size_t per = sizeof(double) * ((size_t)P.n_tot * P.n_tot + (size_t)P.p.n_v * P.p.n_v);
+    int64_t b = (int64_t)(((size_t)2 << 30) / per);
+    if (b > 4096) b = 4096;
+    if (b < 64) b = 64;
+    return b;
+}
 constexpr double DECONV_CUTOFF = 1e-14;
 
 ssm_status fail(ssm_plan_s* h, ssm_status st, const std::string& msg) {
@@ -190,6 +199,10 @@ void free_plan(ssm_plan_s* h) {
     for (auto& v : P.d_V) dev_free(v);
     dev_free(P.d_part);
     dev_free(P.d_part_tc);
+    dev_free(P.d_ring);
+    dev_free(P.d_ring_sum);
+    dev_free(P.d_panel[0]);
+    dev_free(P.d_panel[1]);
     dev_free(P.d_X);
     dev_free(P.d_flag);
     dev_free(P.d_stage);
@@ -239,7 +252,8 @@ ssm_status ensure_points(ssm_plan_s* h, int64_t n_t) {
         CUDA_OR_FAIL(h, dev_alloc(&h->d_rank, 2 * n_t));
         h->cap_t = n_t;
     }
-    const int64_t nb = n_t < BATCH_T ? n_t : BATCH_T;
+    const int64_t bt = batch_points(P);
+    const int64_t nb = n_t < bt ? n_t : bt;
     if ((size_t)nb > h->cap_batch) {
         dev_free(h->d_mu);
         dev_free(h->d_nu);
@@ -283,8 +297,9 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
     const int nv = P.p.n_v, nvh = P.p.n_vh, n_tot = P.n_tot;
     const double gmax = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
     const double xlo = -P.p.kappa * gmax, xhi = (1.0 + P.p.kappa) * gmax;
-    for (int64_t t0 = 0; t0 < n_t; t0 += BATCH_T) {
-        const int64_t nb = (n_t - t0) < BATCH_T ? (n_t - t0) : BATCH_T;
+    const int64_t bt = batch_points(P);
+    for (int64_t t0 = 0; t0 < n_t; t0 += bt) {
+        const int64_t nb = (n_t - t0) < bt ? (n_t - t0) : bt;
         ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, h->d_nu);
         if (st != SSM_OK) return st;
         {
@@ -518,6 +533,21 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if (P.use_tc) {
         gram_tc_slabs(P.n, &P.tc_ne, &P.tc_no);
         CREATE_CUDA(dev_alloc(&P.d_part_tc, gram_tc_partial_floats_total(P.tc_ne, P.tc_no, P.n_tot) + 2));
+        // partials of up to 64 steps are reduced in one batch (at most 1 GiB of ring)
+        const size_t slot = gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot);
+        int ring = (int)(((size_t)1 << 30) / (slot * sizeof(float)));
+        if (ring > 64) ring = 64;
+        if (ring < 1) ring = 1;
+        P.tc_ring = ring;
+        CREATE_CUDA(dev_alloc(&P.d_ring, slot * ring));
+        CREATE_CUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * ring * P.n_tot * P.n_tot));
+        P.panel_groups = gram_tc_groups(P.n_tot);
+        P.n_panels = (P.n + 31) / 32;
+        const size_t pbytes = (size_t)P.n_panels * 2 * P.panel_groups * 512;
+        for (auto& pb : P.d_panel) {
+            CREATE_CUDA(cudaMalloc((void**)&pb, pbytes));
+            CREATE_CUDA(cudaMemsetAsync(pb, 0, pbytes, P.stream));  // rows past N stay zero
+        }
     } else {
         P.n_split = gram_split_count(P.n, P.n_tot);
         CREATE_CUDA(dev_alloc(&P.d_part, (size_t)P.n_split * 2 * P.n_tot * P.n_tot));
@@ -569,19 +599,29 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     }
     CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, P.stream));
     P.stats.launches++;
-    auto gram = [&](const void* A, const void* B) -> cudaError_t {
-        if (P.use_tc)
-            return launch_gram_tc((const float*)A, (const float*)B, P.ld, P.n_tot, P.n, P.tc_ne, P.tc_no,
-                                  P.d_part_tc, P.d_flag, P.stream);
+    // split-bf16 panels of V_j live in d_panel[j % 2] (tensor-core path)
+    auto gram = [&](const void* A, const void* B, int j) -> cudaError_t {
+        if (P.use_tc) {
+            // steps k = j-1 >= 1 write into the ring; V_0 and step 0 into d_part_tc
+            float* dst = (j >= 2) ? P.d_ring + (size_t)((j - 2) % P.tc_ring) *
+                                                   gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot)
+                                  : P.d_part_tc;
+            return launch_gram_tc(P.d_panel[j & 1], B ? P.d_panel[(j + 1) & 1] : nullptr, P.n_tot, P.n, P.tc_ne,
+                                  P.tc_no, dst, P.d_flag, P.stream);
+        }
         if (P.mixed)
             return launch_gram_f32((const float*)A, (const float*)B, P.ld, P.n_tot, P.n, P.n_split, P.d_part,
                                    P.stream);
         return launch_gram_f64((const double*)A, (const double*)B, P.ld, P.n_tot, P.n, P.n_split, P.d_part,
                                P.stream);
     };
+    if (P.use_tc) {
+        CUDA_OR_FAIL(h, launch_panelize(P, (const float*)P.d_V[0], P.d_panel[0], P.stream));
+        P.stats.launches++;
+    }
     {
         Scope sc(h, PH_GRAM);
-        CUDA_OR_FAIL(h, gram(P.d_V[0], nullptr));
+        CUDA_OR_FAIL(h, gram(P.d_V[0], nullptr, 0));
         P.stats.launches++;
         P.stats.gram_launches++;
     }
@@ -600,10 +640,11 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
             Scope sc(h, PH_REC);
             cudaError_t e;
             if (P.mixed) {
+                uint8_t* pn = P.use_tc ? P.d_panel[(k + 1) & 1] : nullptr;
                 e = P.is_stencil ? launch_stencil_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn,
-                                                           (float)c, (float)d, P.stream)
+                                                           (float)c, (float)d, pn, P.stream)
                                  : launch_csr_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn, (float)c,
-                                                       (float)d, P.stream);
+                                                       (float)d, pn, P.stream);
             } else {
                 e = P.is_stencil ? launch_stencil_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c,
                                                            d, P.stream)
@@ -616,15 +657,24 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         }
         {
             Scope sc(h, PH_GRAM);
-            CUDA_OR_FAIL(h, gram(Vn, Vc));
+            CUDA_OR_FAIL(h, gram(Vn, Vc, k + 1));
             P.stats.launches++;
             P.stats.gram_launches++;
         }
-        {
+        if (!P.use_tc || k == 0) {
             Scope sc(h, PH_REDUCE);
             CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k, P.stream)
                                      : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, k, P.stream));
-            P.stats.launches++;
+            P.stats.launches += P.use_tc ? 2 : 1;
+        } else if ((k % P.tc_ring) == 0 || k == S - 1) {
+            // ring slots hold steps k0..k; reduce them in one batch
+            const int k0 = ((k - 1) / P.tc_ring) * P.tc_ring + 1;
+            const int nk = k - k0 + 1;
+            Scope sc(h, PH_REDUCE);
+            const size_t nn2 = (size_t)P.n_tot * P.n_tot;
+            CUDA_OR_FAIL(h, launch_reduce_tc_batch(P.d_ring, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k0, nk, P.d_ring_sum,
+                                                   P.d_ring_sum + (size_t)P.tc_ring * nn2, P.stream));
+            P.stats.launches += nk + 1;
         }
     }
     CUDA_OR_FAIL(h, launch_check_finite(P.d_X, (int64_t)(M + 1) * nn, P.d_flag, P.stream));

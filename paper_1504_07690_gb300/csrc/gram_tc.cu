@@ -8,18 +8,21 @@
 // accumulated in float32 in TMEM (the dropped lo.lo term is below 2^-16 of
 // the product), so a Gram entry carries ~2^-17 relative error per term.
 //
-// Work split: a CTA owns one row slab and one of the two products ("Ge" or
-// "Go"); Go CTAs read two blocks, so they get half as many rows.  Per chunk
-// (64 rows for Ge, 32 for Go) the CTA loads the rows (float4, coalesced, one
-// chunk ahead into a second register set), converts them to the hi/lo bf16
-// operand tiles in shared
-// memory (MN-major, no swizzle: 8 x 16-byte core matrices; K stride 128 B,
-// MN stride 128 B x chunk/8), and one thread issues M=128 tcgen05.mma.kind::f16 into
-// TMEM.  Operand tiles are double buffered: the conversion of chunk c+1
-// overlaps the MMAs of chunk c, which signal an mbarrier through
-// tcgen05.commit.  At the end the accumulators are read back with
-// tcgen05.ld and written as one float32 partial per slab; partials are
+// Operands: the recurrence kernel writes every block it produces a second
+// time as split-bf16 "panels" (recurrence.cu): 32-row panels, 8-column
+// groups, hi and lo parts, each (panel, part, group) a 512-byte run of four
+// 8 x 16-byte core matrices - exactly the MN-major, no-swizzle shared-memory
+// operand layout of tcgen05 (K stride 128 B, MN stride 512 B).  This kernel
+// therefore does no conversion: one thread streams panels into a shared-
+// memory ring (6 stages of 32 KB for Ge, 3 of 64 KB for Go) with 1-D bulk TMA copies (cp.async.bulk, completion
+// counted in bytes on an mbarrier), one thread issues M=128
+// tcgen05.mma.kind::f16 into TMEM and releases each stage through
+// tcgen05.commit, and at the end all four warps read the accumulators back
+// with tcgen05.ld and write one float32 partial per slab; partials are
 // reduced in slab order in float64.
+//
+// Work split: a CTA owns one slab of panels and one of the two products
+// ("Ge" or "Go"); Go CTAs read two blocks, so their slabs are half as long.
 //
 // TMEM: Ge uses ntp (+ ntp-128) columns, Go ntp (+ ntp) columns, ntp = n_tot
 // rounded up to 16, n_tot <= 256; a CTA allocates all 512 columns and its
@@ -34,11 +37,16 @@ namespace ssm {
 
 namespace {
 
-constexpr int KC = 32;                 // row granularity of the slabs (the smallest chunk)
-constexpr int NTHREADS = 256;
+constexpr int KC = 32;                 // rows per panel (K of one pipeline stage)
+constexpr int KG = KC / 8;             // 8-row core groups per panel
+constexpr int STAGES_E = 6;            // one-source stages (32 KB each)
+constexpr int STAGES_O = 3;            // two-source stages (64 KB each)
+constexpr int STAGES = 6;              // barrier slots
+constexpr int NTHREADS = 128;
+constexpr int PART_BYTES = 32 * KG * 128;  // one part of one stage: 32 column groups
 constexpr int TMEM_COLS = 512;
 constexpr long WAIT_LIMIT = 1L << 26;  // bounded mbarrier polls
-constexpr int SMEM_BYTES = 160 * 1024; // > half of an SM: one CTA per SM
+constexpr int SMEM_BYTES = STAGES_E * 2 * PART_BYTES + 1024;  // > half of an SM: one CTA per SM
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -91,73 +99,93 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 struct TcArgs {
-    const float* X;   // V_{k+1}
-    const float* Y;   // V_k (NULL: Ge only)
-    int ld;           // leading dimension, multiple of 4
+    const uint8_t* PX;  // panels of V_{k+1}
+    const uint8_t* PY;  // panels of V_k (NULL: Ge only)
+    int G;              // column groups of the panels
     int n_tot;
-    int64_t n_rows;
-    int n_e, n_o;     // slabs of the Ge and Go products
-    int64_t rows_e, rows_o;
-    float* part_e;    // [n_e][n_tot][n_tot]
-    float* part_o;    // [n_o][n_tot][n_tot]
+    int64_t n_panels;
+    int n_e, n_o;       // slabs of the Ge and Go products
+    int64_t pan_e, pan_o;  // panels per slab
+    float* part_e;      // [n_e][n_tot][n_tot]
+    float* part_o;      // [n_o][n_tot][n_tot]
     int* flag;
 };
 
-// One 16-byte operand row: 8 consecutive columns of one matrix row, float32.
-struct Row8 {
-    float4 a, b;
-};
-
-__device__ __forceinline__ Row8 load_row8(const float* __restrict__ V, int64_t row, int64_t r1, int col0, int n_tot,
-                                          int ld) {
-    Row8 r;
-    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-    r.b = r.a;
-    if (row < r1) {
-        const float* p = V + row * (int64_t)ld + col0;
-        if (col0 + 8 <= n_tot) {
-            r.a = __ldg(reinterpret_cast<const float4*>(p));
-            r.b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-        } else {
-            float t[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) t[q] = (col0 + q < n_tot) ? __ldg(p + q) : 0.f;
-            r.a = make_float4(t[0], t[1], t[2], t[3]);
-            r.b = make_float4(t[4], t[5], t[6], t[7]);
-        }
-    }
-    return r;
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
 }
 
-__device__ __forceinline__ void split_store(const Row8& r, uint8_t* hi, uint8_t* lo) {
-    const float v[8] = {r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.b.y, r.b.z, r.b.w};
-    __align__(16) __nv_bfloat16 h[8];
-    __align__(16) __nv_bfloat16 l[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        h[q] = __float2bfloat16_rn(v[q]);
-        l[q] = __float2bfloat16_rn(v[q] - __bfloat162float(h[q]));
-    }
-    *reinterpret_cast<uint4*>(hi) = *reinterpret_cast<const uint4*>(h);
-    *reinterpret_cast<uint4*>(lo) = *reinterpret_cast<const uint4*>(l);
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_u32(m)), "r"(bytes)
+                 : "memory");
+    (void)state;
 }
 
-// One slab of rows [r0, r1): chunks of CK rows (CK = 64 for the one-source
-// product, 32 for the two-source one, so that two operand stages fit in
-// shared memory); two register sets let the loads of chunk c+1 fly while
-// chunk c is converted and handed to the tensor cores.
-template <int NSRC, int GROUPS, int CK>
-__device__ void run_slab(const TcArgs& P, bool cross, int64_t r0, int64_t r1, float* out, uint8_t* smem,
-                         uint64_t* mbar, uint32_t tmem) {
-    constexpr int KG = CK / 8;                              // 8-row core groups per chunk
-    constexpr int U = GROUPS * KG * 8 / NTHREADS;           // 16-byte operand rows per thread per source
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(m)) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* m) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(m))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_tot = P.n_tot;
-    const int ntp = (n_tot + 15) / 16 * 16;
-    const uint32_t buf_bytes = (uint32_t)GROUPS * KG * 128;
-    const uint32_t stage_bytes = 2u * NSRC * buf_bytes;     // hi, lo per source
-    const int nchunk = r1 > r0 ? (int)((r1 - r0 + CK - 1) / CK) : 0;
-    // tiles: M block 0 (columns 0..127 of the left operand), M block 1 (128..255)
+    const bool cross = (int)blockIdx.x >= P.n_e;
+    const int slab = cross ? (int)blockIdx.x - P.n_e : (int)blockIdx.x;
+    const int64_t pan = cross ? P.pan_o : P.pan_e;
+    const int64_t p0 = (int64_t)slab * pan;
+    int64_t p1 = p0 + pan;
+    if (p1 > P.n_panels) p1 = P.n_panels;
+    const int nch = p1 > p0 ? (int)(p1 - p0) : 0;
+    const int nsrc = cross ? 2 : 1;
+    const int nstage = cross ? STAGES_O : STAGES_E;
+    const int n_tot = P.n_tot, G = P.G;
+    const int ntp = G * 8;
+    const uint32_t stage_bytes = (uint32_t)nsrc * 2 * PART_BYTES;
+    float* out = cross ? P.part_o + (size_t)slab * n_tot * n_tot : P.part_e + (size_t)slab * n_tot * n_tot;
+
+    // zero the stages once: column groups >= G are never copied and must read as 0
+    for (uint32_t t = tid; t < (uint32_t)nstage * stage_bytes / 16; t += NTHREADS)
+        reinterpret_cast<uint4*>(smem)[t] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // tiles: M block 0 (columns 0..127 of V_{k+1}), M block 1 (128..255)
     int nt = 1;
     int t_ag[2] = {0, 16}, t_bg[2] = {0, 0}, t_n[2] = {ntp, 0}, t_dc[2] = {0, ntp}, t_m0[2] = {0, 128},
         t_n0[2] = {0, 0};
@@ -171,144 +199,89 @@ __device__ void run_slab(const TcArgs& P, bool cross, int64_t r0, int64_t r1, fl
             t_n[1] = ntp;
         }
     }
-    Row8 ra[NSRC][U], rb[NSRC][U];
-    auto load_chunk = [&](int c, Row8 (&regs)[NSRC][U]) {
-        const int64_t kr0 = r0 + (int64_t)c * CK;
-#pragma unroll
-        for (int s = 0; s < NSRC; ++s) {
-            const float* V = (s == 0) ? P.X : P.Y;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int id = tid + NTHREADS * u;
-                const int g = id % GROUPS, rest = id / GROUPS, j = rest & 7, kg = rest >> 3;
-                regs[s][u] = load_row8(V, kr0 + kg * 8 + j, r1, g * 8, n_tot, P.ld);
-            }
-        }
-    };
-    bool ok = true;
-    // convert chunk c (held in regs) into its stage and issue its MMAs
-    auto stage_chunk = [&](int c, Row8 (&regs)[NSRC][U]) -> bool {
-        const int st = c & 1;
-        if (c >= 2) {
-            const bool w = mbar_wait(smem_u32(&mbar[st]), ((c - 2) >> 1) & 1);
-            if (!__syncthreads_and(w)) return false;
-        }
-        uint8_t* sb = smem + st * stage_bytes;
-#pragma unroll
-        for (int s = 0; s < NSRC; ++s) {
-            uint8_t* hi = sb + (2 * s) * buf_bytes;
-            uint8_t* lo = hi + buf_bytes;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int id = tid + NTHREADS * u;
-                const int g = id % GROUPS, rest = id / GROUPS, j = rest & 7, kg = rest >> 3;
-                const uint32_t off = ((uint32_t)(g * KG + kg) * 8 + j) * 16;
-                split_store(regs[s][u], hi + off, lo + off);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t xhi = smem_u32(sb), xlo = xhi + buf_bytes;
-            const uint32_t yhi = (NSRC == 1) ? xhi : xhi + 2 * buf_bytes;
-            const uint32_t ylo = (NSRC == 1) ? xlo : xhi + 3 * buf_bytes;
-            const uint32_t lbo = 128, sbo = KG * 128;
-            for (int t = 0; t < nt; ++t) {
-                const uint32_t idesc = instr_desc(t_n[t]);
-                const uint32_t dt = tmem + (uint32_t)t_dc[t];
-#pragma unroll
-                for (int kk = 0; kk < CK / 16; ++kk) {
-                    const uint32_t ao = (uint32_t)(t_ag[t] * KG + 2 * kk) * 128;
-                    const uint32_t bo = (uint32_t)(t_bg[t] * KG + 2 * kk) * 128;
-                    const uint32_t acc0 = (c == 0 && kk == 0) ? 0u : 1u;
-                    mma_bf16(dt, smem_desc(xhi + ao, lbo, sbo), smem_desc(yhi + bo, lbo, sbo), idesc, acc0);
-                    mma_bf16(dt, smem_desc(xhi + ao, lbo, sbo), smem_desc(ylo + bo, lbo, sbo), idesc, 1u);
-                    mma_bf16(dt, smem_desc(xlo + ao, lbo, sbo), smem_desc(yhi + bo, lbo, sbo), idesc, 1u);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar[st]))
-                         : "memory");
-        }
-        return true;
-    };
-    if (nchunk > 0) load_chunk(0, ra);
-    for (int c = 0; c < nchunk && ok; c += 2) {
-        if (c + 1 < nchunk) load_chunk(c + 1, rb);
-        ok = stage_chunk(c, ra);
-        if (!ok || c + 1 >= nchunk) break;
-        if (c + 2 < nchunk) load_chunk(c + 2, ra);
-        ok = stage_chunk(c + 1, rb);
-    }
-    if (ok && nchunk > 0) ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[(nchunk - 1) & 1]), ((nchunk - 1) >> 1) & 1));
-    if (!ok) {
-        if (tid == 0) atomicOr(P.flag, 2);
-        // give in-flight MMAs one more bounded chance before TMEM is released
-        if (nchunk > 0) mbar_wait(smem_u32(&mbar[(nchunk - 1) & 1]), ((nchunk - 1) >> 1) & 1);
-        return;
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int q = warp & 3, half = warp >> 2;
-    for (int t = 0; t < nt; ++t) {
-        for (int cc = half * 16; cc < t_n[t]; cc += 32) {
-            float v[16];
-            if (nchunk > 0) {
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t_dc[t] + cc), v);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
-            }
-            const int m = t_m0[t] + 32 * q + lane;
-            if (m < n_tot) {
-                float* o = out + (size_t)m * n_tot + t_n0[t] + cc;
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (t_n0[t] + cc + j < n_tot) o[j] = v[j];
-            }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar[2];
-    __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const bool cross = (int)blockIdx.x >= P.n_e;
-    const int slab = cross ? (int)blockIdx.x - P.n_e : (int)blockIdx.x;
-    const int64_t rows = cross ? P.rows_o : P.rows_e;
-    const int64_t r0 = (int64_t)slab * rows;
-    int64_t r1 = r0 + rows;
-    if (r1 > P.n_rows) r1 = P.n_rows;
-    float* out = cross ? P.part_o + (size_t)slab * P.n_tot * P.n_tot : P.part_e + (size_t)slab * P.n_tot * P.n_tot;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        if (lane == 0) {  // producer: bulk copies of panels into the ring
+            const uint32_t copy = (uint32_t)G * 512;
+            for (int c = 0; c < nch; ++c) {
+                const int s = c % nstage;
+                if (c >= nstage && !mbar_wait(smem_u32(&empty[s]), ((c / nstage) - 1) & 1)) {
+                    atomicOr(&fail, 1);
+                    break;
+                }
+                const uint32_t dst = smem_u32(smem + s * stage_bytes);
+                mbar_expect_tx(&full[s], (uint32_t)nsrc * 2 * copy);
+                const int64_t pnl = p0 + c;
+                for (int src = 0; src < nsrc; ++src) {
+                    const uint8_t* base = (src == 0 ? P.PX : P.PY) + (size_t)pnl * 2 * G * 512;
+                    bulk_copy(dst + (2 * src) * PART_BYTES, base, copy, &full[s]);
+                    bulk_copy(dst + (2 * src + 1) * PART_BYTES, base + (size_t)G * 512, copy, &full[s]);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            const uint32_t lbo = 128, sbo = KG * 128;
+            bool ok = true;
+            for (int c = 0; c < nch; ++c) {
+                const int s = c % nstage;
+                if (!mbar_wait(smem_u32(&full[s]), (c / nstage) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t xhi = smem_u32(smem + s * stage_bytes), xlo = xhi + PART_BYTES;
+                const uint32_t yhi = cross ? xhi + 2 * PART_BYTES : xhi;
+                const uint32_t ylo = cross ? xhi + 3 * PART_BYTES : xlo;
+                for (int t = 0; t < nt; ++t) {
+                    const uint32_t idesc = instr_desc(t_n[t]);
+                    const uint32_t dt = tmem + (uint32_t)t_dc[t];
+#pragma unroll
+                    for (int kk = 0; kk < KC / 16; ++kk) {
+                        const uint32_t ao = (uint32_t)(t_ag[t] * KG + 2 * kk) * 128;
+                        const uint32_t bo = (uint32_t)(t_bg[t] * KG + 2 * kk) * 128;
+                        const uint32_t acc0 = (c == 0 && kk == 0) ? 0u : 1u;
+                        mma_bf16(dt, smem_desc(xhi + ao, lbo, sbo), smem_desc(yhi + bo, lbo, sbo), idesc, acc0);
+                        mma_bf16(dt, smem_desc(xhi + ao, lbo, sbo), smem_desc(ylo + bo, lbo, sbo), idesc, 1u);
+                        mma_bf16(dt, smem_desc(xlo + ao, lbo, sbo), smem_desc(yhi + bo, lbo, sbo), idesc, 1u);
+                    }
+                }
+                umma_commit(&empty[s]);
+            }
+            if (!ok) atomicOr(&fail, 1);
+            if (nch > 0 && ok)
+                umma_commit(&done);  // arrives once every MMA issued above has completed
+            else
+                mbar_arrive(&done);
+        }
+        __syncwarp();
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool dn = mbar_wait(smem_u32(&done), 0);
     __syncthreads();
+    const bool ok = dn && fail == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_slot;
-    const bool wide = P.n_tot > 128;
-    if (cross) {
-        if (wide)
-            run_slab<2, 32, 32>(P, true, r0, r1, out, smem, mbar, tmem);
-        else
-            run_slab<2, 16, 32>(P, true, r0, r1, out, smem, mbar, tmem);
-    } else {
-        if (wide)
-            run_slab<1, 32, 64>(P, false, r0, r1, out, smem, mbar, tmem);
-        else
-            run_slab<1, 16, 64>(P, false, r0, r1, out, smem, mbar, tmem);
+    if (ok) {
+        for (int t = 0; t < nt; ++t) {
+            for (int cc = 0; cc < t_n[t]; cc += 16) {
+                float v[16];
+                if (nch > 0) {
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t_dc[t] + cc), v);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                }
+                const int m = t_m0[t] + 32 * warp + lane;
+                if (m < n_tot) {
+                    float* o = out + (size_t)m * n_tot + t_n0[t] + cc;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (t_n0[t] + cc + j < n_tot) o[j] = v[j];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(P.flag, 2);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -318,18 +291,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
 
 // Slab sums in float64, coalesced: ge[e] = sum_s pe[s][lo][hi] (upper element of
 // the pair), go[e] = sum_s po[s][e]; the symmetrisation of go reads it transposed
-// from this small float64 buffer in a second pass.
-__global__ void sum_tc_kernel(const float* __restrict__ pe, int n_e, const float* __restrict__ po, int n_o,
-                              int n_tot, double* __restrict__ ge, double* __restrict__ go) {
+// from this small float64 buffer in a second pass.  A block covers 32
+// consecutive elements; its 8 warps take every 8th slab and their partial
+// sums are added in warp order, so the result is independent of timing.
+__global__ void __launch_bounds__(256)
+sum_tc_kernel(const float* __restrict__ pe, int n_e, const float* __restrict__ po, int n_o, int n_tot,
+              double* __restrict__ ge, double* __restrict__ go) {
+    __shared__ double se[8][32], so[8][32];
     const size_t nn = (size_t)n_tot * n_tot;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
-        double a = 0.0, b = 0.0;
-        if (i <= j)
-            for (int s = 0; s < n_e; ++s) a += (double)pe[(size_t)s * nn + e];
-        for (int s = 0; s < n_o; ++s) b += (double)po[(size_t)s * nn + e];
-        ge[e] = a;
-        go[e] = b;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
+        const size_t e = e0 + lane;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        if (e < nn) {
+            const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
+            if (i <= j) {
+                int s = w;
+                for (; s + 8 < n_e; s += 16) {
+                    a0 += (double)pe[(size_t)s * nn + e];
+                    a1 += (double)pe[(size_t)(s + 8) * nn + e];
+                }
+                for (; s < n_e; s += 8) a0 += (double)pe[(size_t)s * nn + e];
+            }
+            int s = w;
+            for (; s + 8 < n_o; s += 16) {
+                b0 += (double)po[(size_t)s * nn + e];
+                b1 += (double)po[(size_t)(s + 8) * nn + e];
+            }
+            for (; s < n_o; s += 8) b0 += (double)po[(size_t)s * nn + e];
+        }
+        se[w][lane] = a0 + a1;
+        so[w][lane] = b0 + b1;
+        __syncthreads();
+        if (w == 0 && e < nn) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                a += se[k][lane];
+                b += so[k][lane];
+            }
+            ge[e] = a;
+            go[e] = b;
+        }
+        __syncthreads();
     }
 }
 
@@ -352,15 +355,32 @@ __global__ void moments_tc_kernel(const double* __restrict__ ge, const double* _
     }
 }
 
+__global__ void moments_tc_batch_kernel(const double* __restrict__ ge, const double* __restrict__ go, int n_tot,
+                                        double* __restrict__ X, int k0) {
+    const size_t nn = (size_t)n_tot * n_tot;
+    const int q = blockIdx.y, step = k0 + q;
+    const double* gq = ge + (size_t)q * nn;
+    const double* oq = go + (size_t)q * nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
+        const double gs = (i <= j) ? gq[e] : gq[(size_t)j * n_tot + i];
+        const double gc = 0.5 * (oq[e] + oq[(size_t)j * n_tot + i]);
+        X[(size_t)(2 * step + 1) * nn + e] = 2.0 * gc - X[nn + e];
+        X[(size_t)(2 * step + 2) * nn + e] = 2.0 * gs - X[e];
+    }
+}
+
 }  // namespace
 
 bool gram_tc_supported(int n_tot, int ld) { return n_tot >= 1 && n_tot <= 256 && (ld % 4) == 0; }
+
+int gram_tc_groups(int n_tot) { return (n_tot + 15) / 16 * 2; }
 
 void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // Go CTAs read two blocks: give them half the rows (a third of the SMs each way round)
+    // Go CTAs read two blocks: give them half the panels (a third of the SMs each way round)
     int e = sms / 3, o = sms - e;
     const int64_t cap = (n_rows + KC - 1) / KC;
     if (e > cap) e = (int)cap;
@@ -371,22 +391,20 @@ void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o) {
 
 size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot) { return (size_t)(n_e + n_o) * n_tot * n_tot; }
 
-cudaError_t launch_gram_tc(const float* X, const float* Y, int ld, int n_tot, int64_t n_rows, int n_e, int n_o,
+cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int64_t n_rows, int n_e, int n_o,
                            float* part, int* flag, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     TcArgs a;
-    a.X = X;
-    a.Y = Y;
-    a.ld = ld;
+    a.PX = PX;
+    a.PY = PY;
+    a.G = gram_tc_groups(n_tot);
     a.n_tot = n_tot;
-    a.n_rows = n_rows;
+    a.n_panels = (n_rows + KC - 1) / KC;
     a.n_e = n_e;
-    a.n_o = Y ? n_o : 0;
-    int64_t re = (n_rows + n_e - 1) / n_e;
-    int64_t ro = (n_rows + n_o - 1) / n_o;
-    a.rows_e = (re + 2 * KC - 1) / (2 * KC) * (2 * KC);  // whole 64-row chunks
-    a.rows_o = (ro + KC - 1) / KC * KC;
+    a.n_o = PY ? n_o : 0;
+    a.pan_e = (a.n_panels + n_e - 1) / n_e;
+    a.pan_o = (a.n_panels + n_o - 1) / n_o;
     a.part_e = part;
     a.part_o = part + (size_t)n_e * n_tot * n_tot;
     a.flag = flag;
@@ -408,10 +426,32 @@ cudaError_t launch_reduce_tc(const float* part, int n_e, int n_o, int n_tot, dou
     // the float64 sums live after the float32 partials (8-byte aligned: pf is even)
     double* ge = reinterpret_cast<double*>(const_cast<float*>(part) + ((pf + 1) & ~(size_t)1));
     double* go = ge + nn;
-    sum_tc_kernel<<<(int)b, 256, 0, s>>>(part, n_e, part + (size_t)n_e * nn, step >= 0 ? n_o : 0, n_tot, ge, go);
+    int64_t sb = (nn + 31) / 32;
+    if (sb > 152 * 8) sb = 152 * 8;
+    sum_tc_kernel<<<(int)sb, 256, 0, s>>>(part, n_e, part + (size_t)n_e * nn, step >= 0 ? n_o : 0, n_tot, ge, go);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     moments_tc_kernel<<<(int)b, 256, 0, s>>>(ge, go, n_tot, X, step);
+    return cudaGetLastError();
+}
+
+// Steps k0 .. k0+nk-1 (k0 >= 1) whose partials sit in ring slots
+// (k - k0) of `ring` (each slot [n_e + n_o][n_tot][n_tot] float32); ge/go
+// scratch [nk][n_tot][n_tot] float64.
+cudaError_t launch_reduce_tc_batch(const float* ring, int n_e, int n_o, int n_tot, double* X, int k0, int nk,
+                                   double* ge, double* go, cudaStream_t s) {
+    const int64_t nn = (int64_t)n_tot * n_tot;
+    const size_t slot = gram_tc_partial_floats(n_e, n_o, n_tot);
+    int64_t sb = (nn + 31) / 32;
+    if (sb > 152 * 8) sb = 152 * 8;
+    for (int q = 0; q < nk; ++q) {
+        const float* p = ring + (size_t)q * slot;
+        sum_tc_kernel<<<(int)sb, 256, 0, s>>>(p, n_e, p + (size_t)n_e * nn, n_o, n_tot, ge + q * nn, go + q * nn);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((nn + 255) / 256 > 512 ? 512 : (nn + 255) / 256), (unsigned)nk);
+    moments_tc_batch_kernel<<<grid, 256, 0, s>>>(ge, go, n_tot, X, k0);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,12 @@ struct Plan {
     bool use_tc = false;               // mixed path on tensor cores
     int tc_ne = 0, tc_no = 0;
     float* d_part_tc = nullptr;        // [tc_ne + tc_no][n_tot][n_tot]
+    float* d_ring = nullptr;           // ring of tc_ring partial slots (steps >= 1)
+    double* d_ring_sum = nullptr;      // 2 x tc_ring x n_tot^2 float64 slab sums
+    int tc_ring = 0;
+    int panel_groups = 0;              // split-bf16 panels: column groups of 8
+    int64_t n_panels = 0;              // panels of 32 rows
+    uint8_t* d_panel[2] = {nullptr, nullptr};  // panels of V_j for j even / odd
     double* d_X = nullptr;             // (M+1) x n_tot x n_tot
     bool have_moments = false;
     double x0max = 0;                  // max_i X_0[i][i] over the first n_v probes
@@ -87,12 +93,15 @@ void set_global_error(const char* msg);
 // Recurrence: Vn = c (2 A~ Vc) - d Vp, row-major blocks with leading dim ld.
 cudaError_t launch_stencil_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
                                     double c, double d, cudaStream_t s);
+// The float32 steps also write V_{k+1} as split-bf16 panels when `panel` is
+// non-NULL (layout in recurrence.cu / gram_tc.cu).
 cudaError_t launch_stencil_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
-                                    float c, float d, cudaStream_t s);
+                                    float c, float d, uint8_t* panel, cudaStream_t s);
 cudaError_t launch_csr_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
                                 double c, double d, cudaStream_t s);
 cudaError_t launch_csr_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
-                                float c, float d, cudaStream_t s);
+                                float c, float d, uint8_t* panel, cudaStream_t s);
+cudaError_t launch_panelize(const Plan& P, const float* V, uint8_t* panel, cudaStream_t s);
 
 // Operator set-up (operator.cu).
 int operator_bound_blocks(int64_t n);
@@ -114,15 +123,20 @@ cudaError_t launch_gram_f32(const float* A, const float* B, int ld, int n_tot, i
 cudaError_t launch_reduce_gram_pair(const double* part, int n_split, int n, double* gaa, double* gab,
                                     cudaStream_t s);
 
-// Tensor-core split-bf16 Gram (gram_tc.cu): Ge over n_e slabs, Go over n_o slabs,
-// float32 partials [n_e + n_o][n_tot][n_tot]; status bit 2 on a timed-out wait.
+// Tensor-core split-bf16 Gram (gram_tc.cu) on the panels of V_{k+1} (PX) and
+// V_k (PY): Ge over n_e slabs, Go over n_o slabs, float32 partials
+// [n_e + n_o][n_tot][n_tot]; status bit 2 on a timed-out wait.
 bool gram_tc_supported(int n_tot, int ld);
 void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o);
 size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot);
 size_t gram_tc_partial_floats_total(int n_e, int n_o, int n_tot);  // + room for the float64 sums
-cudaError_t launch_gram_tc(const float* X, const float* Y, int ld, int n_tot, int64_t n_rows, int n_e, int n_o,
+int gram_tc_groups(int n_tot);  // 8-column groups of a panel (n_tot rounded up to 16)
+cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int64_t n_rows, int n_e, int n_o,
                            float* part, int* flag, cudaStream_t s);
 cudaError_t launch_reduce_tc(const float* part, int n_e, int n_o, int n_tot, double* X, int step, cudaStream_t s);
+// Moments of steps k0..k0+nk-1 from a ring of nk partial slots (float64 scratch ge, go: nk x n_tot^2 each).
+cudaError_t launch_reduce_tc_batch(const float* ring, int n_e, int n_o, int n_tot, double* X, int k0, int nk,
+                                   double* ge, double* go, cudaStream_t s);
 
 // Reduce partials into the moments of step k (see moments.cu).
 cudaError_t launch_reduce_moments(const double* part, int n_split, int n_tot, double* X, int step,

@@ -7,11 +7,13 @@
 // (2A - (a+b)I)/(b-a) is folded into the operator coefficients).
 //
 // Blocks are row-major, n rows x ld columns, ld a multiple of the 16-byte
-// vector width.  One thread produces one 16-byte vector of one output row:
-// consecutive threads walk consecutive vectors of the same row and then the
-// next row, so every load and store of the streamed blocks is coalesced.
-// Neighbour rows along the fastest grid axis are adjacent in memory and the
-// rows one plane away are reused from L2 by the CTAs working next to them.
+// vector width.  The stencil kernel gives each output row to one warp whose
+// lanes walk the row's 16-byte vectors (coalesced); the CSR kernel gives
+// each thread one vector of one row.  Neighbour rows along the fastest grid
+// axis are adjacent in memory and the rows one plane away are reused from L2
+// by the warps working next to them.
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace ssm {
@@ -38,126 +40,261 @@ __device__ __forceinline__ double2 vzero(double) { return make_double2(0.0, 0.0)
 template <typename VT>
 __device__ __forceinline__ VT ldg_stream(const VT* p) { return __ldg(p); }
 
-// Neighbour sum along one axis: v_{i-s} + v_{i+s} with wrap / Dirichlet edge.
-template <typename T, typename VT>
-__device__ __forceinline__ VT axis_pair(const VT* __restrict__ vc, uint32_t i, uint32_t coord, uint32_t ext,
-                                        uint32_t stride, uint32_t per, uint32_t ldv, uint32_t cc) {
-    VT s = vzero(T(0));
-    if (coord > 0) {
-        s = vadd(s, ldg_stream(vc + (size_t)(i - stride) * ldv + cc));
-    } else if (per) {
-        s = vadd(s, ldg_stream(vc + (size_t)(i + (ext - 1) * stride) * ldv + cc));
-    }
-    if (coord + 1 < ext) {
-        s = vadd(s, ldg_stream(vc + (size_t)(i + stride) * ldv + cc));
-    } else if (per) {
-        s = vadd(s, ldg_stream(vc + (size_t)(i - (ext - 1) * stride) * ldv + cc));
-    }
-    return s;
+// Split-bf16 panel of a float32 block for the tensor-core Gram (see
+// gram_tc.cu): rows in panels of 32, columns in groups of 8 (G groups,
+// n_tot rounded up to 16), each (panel, part, group) a 512-byte run of four
+// 8 x 16-byte core matrices (8 rows x 8 bf16 each); part 0 = hi = rn(v),
+// part 1 = lo = rn(v - hi).  The CTA of 8 warps that writes 8 consecutive
+// rows stages their hi/lo values in shared memory and writes whole 128-byte
+// core matrices.
+struct PanelOut {
+    uint8_t* base;   // NULL: no panel output
+    uint32_t G;      // column groups
+};
+
+// Shared-memory stage of one 32-row panel: [part][row 0..31][group, padded to
+// G+1][16 B].  Consecutive columns of a row are adjacent (the split stores of
+// consecutive threads do not conflict) and the one-chunk pad makes the 8
+// rows read together by the flush fall in distinct banks.
+__device__ __forceinline__ uint32_t stage_off(uint32_t G, uint32_t part, uint32_t row, uint32_t g) {
+    return ((part * 32 + row) * (G + 1) + g) * 16;
 }
 
-template <typename T>
+// Write the staged panel as 512-byte runs (panel, part, group) in core-matrix
+// order [kg][row8][16 B] (row = kg*8 + row8).
+__device__ __forceinline__ void flush_panel(const uint8_t* stage, PanelOut po, uint32_t panel) {
+    const uint32_t n16 = 2 * po.G * 32;  // 16-byte pieces: part x group x row
+    for (uint32_t t = threadIdx.x; t < n16; t += blockDim.x) {
+        const uint32_t row = t & 31, g = (t >> 5) % po.G, part = (t >> 5) / po.G;
+        const uint4 v = *reinterpret_cast<const uint4*>(stage + stage_off(po.G, part, row, g));
+        uint8_t* dst = po.base + (((size_t)panel * 2 + part) * po.G + g) * 512 + row * 16;
+        *reinterpret_cast<uint4*>(dst) = v;
+    }
+}
+
+// Split 4 consecutive columns of staged row `row` (0..31) of a panel stage.
+__device__ __forceinline__ void stage_split4p(uint8_t* stage, int G, int row, int col0, float4 v) {
+    __align__(8) __nv_bfloat16 h[4];
+    __align__(8) __nv_bfloat16 l[4];
+    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h[q] = __float2bfloat16_rn(x[q]);
+        l[q] = __float2bfloat16_rn(x[q] - __bfloat162float(h[q]));
+    }
+    const uint32_t g = (uint32_t)col0 >> 3, half = ((uint32_t)col0 >> 2) & 1;
+    *reinterpret_cast<uint2*>(stage + stage_off(G, 0, row, g) + half * 8) = *reinterpret_cast<const uint2*>(h);
+    *reinterpret_cast<uint2*>(stage + stage_off(G, 1, row, g) + half * 8) = *reinterpret_cast<const uint2*>(l);
+}
+__device__ __forceinline__ void stage_split4p(uint8_t*, int, int, int, double2) {}
+
+// Per-row neighbour table of a 32-row panel.
+struct RowInfo {
+    uint32_t nb[6];
+    uint32_t has;  // bit a: neighbour a present; bit 31: row exists
+};
+
+// A CTA owns one 32-row panel at a time (grid-stride over panels): the first
+// 32 threads tabulate the rows' neighbour rows, then all 256 threads walk the
+// panel's (row, 16-byte chunk) items, so loads and stores are coalesced and
+// every lane is busy; with PANEL the split-bf16 copy of the panel is staged
+// in shared memory and written as whole 512-byte runs.
+template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                     const T* __restrict__ diag2, StencilGeom g, T o0, T o1, T o2, T c, T d,
-                    uint32_t nchunk, uint32_t n_rows) {
+                    uint32_t nchunk, uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
+    __shared__ __align__(16) uint8_t stage[PANEL ? 2 * 32 * 33 * 16 : 16];
+    __shared__ RowInfo info[32];
+    const uint32_t mdiv = ((1u << 20) + nchunk - 1) / nchunk;  // it / nchunk for it < 32 nchunk
     const VT* vc = reinterpret_cast<const VT*>(Vc);
     const VT* vp = reinterpret_cast<const VT*>(Vp);
     VT* vn = reinterpret_cast<VT*>(Vn);
-    const uint32_t total = n_rows * nchunk;
     const uint32_t s1 = g.d2, s0 = g.d1 * g.d2;
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const uint32_t i = idx / nchunk;
-        const uint32_t cc = idx - i * nchunk;
-        const uint32_t i2 = i % g.d2;
-        const uint32_t q = i / g.d2;
-        const uint32_t i1 = q % g.d1;
-        const uint32_t i0 = q / g.d1;
-        const VT x = ldg_stream(vc + (size_t)i * nchunk + cc);
-        VT acc = vscale(__ldg(diag2 + i), x);
-        if (g.active[0]) acc = vfma(o0, axis_pair<T, VT>(vc, i, i0, g.d0, s0, g.per[0], nchunk, cc), acc);
-        if (g.active[1]) acc = vfma(o1, axis_pair<T, VT>(vc, i, i1, g.d1, s1, g.per[1], nchunk, cc), acc);
-        if (g.active[2]) acc = vfma(o2, axis_pair<T, VT>(vc, i, i2, g.d2, 1u, g.per[2], nchunk, cc), acc);
-        VT out = vscale(c, acc);
-        if (d != T(0)) out = vfma(-d, ldg_stream(vp + (size_t)i * nchunk + cc), out);
-        vn[(size_t)i * nchunk + cc] = out;
+    const T w[3] = {g.active[0] ? o0 : T(0), g.active[1] ? o1 : T(0), g.active[2] ? o2 : T(0)};
+    if (PANEL)
+        for (uint32_t t = threadIdx.x; t < 2 * 32 * 33; t += blockDim.x)
+            reinterpret_cast<uint4*>(stage)[t] = make_uint4(0, 0, 0, 0);
+    const uint32_t n_pan = (n_rows + 31) / 32;
+    const uint32_t items = 32 * nchunk;
+    for (uint32_t pnl = blockIdx.x; pnl < n_pan; pnl += gridDim.x) {
+        __syncthreads();  // info / stage free
+        if (threadIdx.x < 32) {
+            const uint32_t i = pnl * 32 + threadIdx.x;
+            RowInfo ri;
+            ri.has = 0;
+            if (i < n_rows) {
+                ri.has = 1u << 31;
+                const uint32_t i2 = i % g.d2, q = i / g.d2, i1 = q % g.d1, i0 = q / g.d1;
+                const uint32_t co[3] = {i0, i1, i2}, ex[3] = {g.d0, g.d1, g.d2}, sd[3] = {s0, s1, 1u};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const uint32_t cm = co[a], e = ex[a], st = sd[a];
+                    const bool act = g.active[a] != 0;
+                    if (act && (cm > 0 || g.per[a])) ri.has |= 1u << (2 * a);
+                    if (act && (cm + 1 < e || g.per[a])) ri.has |= 1u << (2 * a + 1);
+                    ri.nb[2 * a] = cm > 0 ? i - st : i + (e - 1) * st;
+                    ri.nb[2 * a + 1] = cm + 1 < e ? i + st : i - (e - 1) * st;
+                }
+            }
+            info[threadIdx.x] = ri;
+        }
+        __syncthreads();
+        for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+            const uint32_t r = (it * mdiv) >> 20, cc = it - r * nchunk;
+            const RowInfo& ri = info[r];
+            VT out = vzero(T(0));
+            if (ri.has >> 31) {
+                const uint32_t i = pnl * 32 + r;
+                const size_t base = (size_t)i * nchunk;
+                const VT x = ldg_stream(vc + base + cc);
+                VT acc = vscale(__ldg(diag2 + i), x);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const bool lo = (ri.has >> (2 * a)) & 1u, hi = (ri.has >> (2 * a + 1)) & 1u;
+                    if (lo || hi) {
+                        VT sacc = vzero(T(0));
+                        if (lo) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a] * nchunk + cc));
+                        if (hi) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a + 1] * nchunk + cc));
+                        acc = vfma(w[a], sacc, acc);
+                    }
+                }
+                out = vscale(c, acc);
+                if (d != T(0)) out = vfma(-d, ldg_stream(vp + base + cc), out);
+                vn[base + cc] = out;
+            }
+            if constexpr (PANEL) stage_split4p(stage, po.G, r, 4 * cc, out);
+        }
+        if constexpr (PANEL) {
+            __syncthreads();
+            flush_panel(stage, po, pnl);
+        }
     }
 }
 
-template <typename T>
+template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                 const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                const T* __restrict__ val2, T beta, T c, T d, uint32_t nchunk, uint32_t n_rows) {
+                const T* __restrict__ val2, T beta, T c, T d, uint32_t nchunk, uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
+    __shared__ __align__(16) uint8_t stage[PANEL ? 2 * 32 * 33 * 16 : 16];
     const VT* vc = reinterpret_cast<const VT*>(Vc);
     const VT* vp = reinterpret_cast<const VT*>(Vp);
     VT* vn = reinterpret_cast<VT*>(Vn);
-    const uint32_t total = n_rows * nchunk;
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const uint32_t i = idx / nchunk;
-        const uint32_t cc = idx - i * nchunk;
-        VT acc = vscale(beta, ldg_stream(vc + (size_t)i * nchunk + cc));
-        const int64_t e1 = __ldg(rowptr + i + 1);
-        for (int64_t e = __ldg(rowptr + i); e < e1; ++e) {
-            const uint32_t j = (uint32_t)__ldg(colind + e);
-            acc = vfma(__ldg(val2 + e), ldg_stream(vc + (size_t)j * nchunk + cc), acc);
+    if (PANEL)
+        for (uint32_t t = threadIdx.x; t < 2 * 32 * 33; t += blockDim.x)
+            reinterpret_cast<uint4*>(stage)[t] = make_uint4(0, 0, 0, 0);
+    const uint32_t n_pan = (n_rows + 31) / 32;
+    const uint32_t items = 32 * nchunk;
+    for (uint32_t pnl = blockIdx.x; pnl < n_pan; pnl += gridDim.x) {
+        if (PANEL) __syncthreads();
+        for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+            const uint32_t r = it / nchunk, cc = it - r * nchunk;
+            const uint32_t i = pnl * 32 + r;
+            VT out = vzero(T(0));
+            if (i < n_rows) {
+                const size_t base = (size_t)i * nchunk;
+                VT acc = vscale(beta, ldg_stream(vc + base + cc));
+                const int64_t e1 = __ldg(rowptr + i + 1);
+                for (int64_t e = __ldg(rowptr + i); e < e1; ++e) {
+                    const uint32_t j = (uint32_t)__ldg(colind + e);
+                    acc = vfma(__ldg(val2 + e), ldg_stream(vc + (size_t)j * nchunk + cc), acc);
+                }
+                out = vscale(c, acc);
+                if (d != T(0)) out = vfma(-d, ldg_stream(vp + base + cc), out);
+                vn[base + cc] = out;
+            }
+            if constexpr (PANEL) stage_split4p(stage, po.G, r, 4 * cc, out);
         }
-        VT out = vscale(c, acc);
-        if (d != T(0)) out = vfma(-d, ldg_stream(vp + (size_t)i * nchunk + cc), out);
-        vn[(size_t)i * nchunk + cc] = out;
+        if constexpr (PANEL) {
+            __syncthreads();
+            flush_panel(stage, po, pnl);
+        }
     }
 }
 
-int grid_for(uint64_t total) {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    uint64_t blocks = (total + 255) / 256;
-    uint64_t cap = (uint64_t)sms * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    return (int)blocks;
+// Panels of an existing float32 block (the probe block V_0).
+__global__ void __launch_bounds__(256)
+panelize_kernel(const float* __restrict__ V, uint32_t nchunk, uint32_t n_rows, PanelOut po) {
+    __shared__ __align__(16) uint8_t stage[2 * 32 * 33 * 16];
+    const float4* v = reinterpret_cast<const float4*>(V);
+    for (uint32_t t = threadIdx.x; t < 2 * 32 * 33; t += blockDim.x)
+        reinterpret_cast<uint4*>(stage)[t] = make_uint4(0, 0, 0, 0);
+    const uint32_t n_pan = (n_rows + 31) / 32;
+    for (uint32_t pnl = blockIdx.x; pnl < n_pan; pnl += gridDim.x) {
+        __syncthreads();
+        for (uint32_t it = threadIdx.x; it < 32 * nchunk; it += blockDim.x) {
+            const uint32_t r = it / nchunk, cc = it - r * nchunk;
+            const uint32_t i = pnl * 32 + r;
+            stage_split4p(stage, po.G, r, 4 * cc,
+                          i < n_rows ? __ldg(v + (size_t)i * nchunk + cc) : make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+        __syncthreads();
+        flush_panel(stage, po, pnl);
+    }
+}
+
+// One CTA per 32-row panel (grid-stride beyond 2^20 panels).
+int panel_grid(uint64_t n_rows) {
+    uint64_t blocks = (n_rows + 31) / 32;
+    if (blocks > (1u << 20)) blocks = 1u << 20;
+    return blocks < 1 ? 1 : (int)blocks;
 }
 
 }  // namespace
 
 template <typename T>
 static cudaError_t stencil_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, const T* diag2,
-                                T o0, T o1, T o2, T c, T d, cudaStream_t s) {
+                                T o0, T o1, T o2, T c, T d, uint8_t* panel, cudaStream_t s) {
     const uint32_t nchunk = (uint32_t)(P.ld / Vec16<T>::W);
-    const uint64_t total = (uint64_t)P.n * nchunk;
-    stencil_step_kernel<T><<<grid_for(total), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0, o1, o2,
-                                                          c, d, nchunk, (uint32_t)P.n);
+    const PanelOut po{panel, (uint32_t)P.panel_groups};
+    if (panel)
+        stencil_step_kernel<T, true><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
+                                                                        o1, o2, c, d, nchunk, (uint32_t)P.n, po);
+    else
+        stencil_step_kernel<T, false><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
+                                                                         o1, o2, c, d, nchunk, (uint32_t)P.n, po);
     return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t csr_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, const T* val2, T beta,
-                            T c, T d, cudaStream_t s) {
+                            T c, T d, uint8_t* panel, cudaStream_t s) {
     const uint32_t nchunk = (uint32_t)(P.ld / Vec16<T>::W);
-    const uint64_t total = (uint64_t)P.n * nchunk;
-    csr_step_kernel<T><<<grid_for(total), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr, P.d_colind, val2,
-                                                      beta, c, d, nchunk, (uint32_t)P.n);
+    const PanelOut po{panel, (uint32_t)P.panel_groups};
+    if (panel)
+        csr_step_kernel<T, true><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr, P.d_colind,
+                                                                    val2, beta, c, d, nchunk, (uint32_t)P.n, po);
+    else
+        csr_step_kernel<T, false><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr,
+                                                                     P.d_colind, val2, beta, c, d, nchunk,
+                                                                     (uint32_t)P.n, po);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stencil_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
                                     double c, double d, cudaStream_t s) {
-    return stencil_step<double>(P, Vc, Vp, Vn, P.d_diag64, P.off64[0], P.off64[1], P.off64[2], c, d, s);
+    return stencil_step<double>(P, Vc, Vp, Vn, P.d_diag64, P.off64[0], P.off64[1], P.off64[2], c, d, nullptr, s);
 }
 cudaError_t launch_stencil_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
-                                    float c, float d, cudaStream_t s) {
-    return stencil_step<float>(P, Vc, Vp, Vn, P.d_diag32, P.off32[0], P.off32[1], P.off32[2], c, d, s);
+                                    float c, float d, uint8_t* panel, cudaStream_t s) {
+    return stencil_step<float>(P, Vc, Vp, Vn, P.d_diag32, P.off32[0], P.off32[1], P.off32[2], c, d, panel, s);
 }
 cudaError_t launch_csr_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
                                 double c, double d, cudaStream_t s) {
-    return csr_step<double>(P, Vc, Vp, Vn, P.d_val64, P.beta, c, d, s);
+    return csr_step<double>(P, Vc, Vp, Vn, P.d_val64, P.beta, c, d, nullptr, s);
 }
 cudaError_t launch_csr_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
-                                float c, float d, cudaStream_t s) {
-    return csr_step<float>(P, Vc, Vp, Vn, P.d_val32, (float)P.beta, c, d, s);
+                                float c, float d, uint8_t* panel, cudaStream_t s) {
+    return csr_step<float>(P, Vc, Vp, Vn, P.d_val32, (float)P.beta, c, d, panel, s);
+}
+
+cudaError_t launch_panelize(const Plan& P, const float* V, uint8_t* panel, cudaStream_t s) {
+    const PanelOut po{panel, (uint32_t)P.panel_groups};
+    panelize_kernel<<<panel_grid(P.n), 256, 0, s>>>(V, (uint32_t)(P.ld / 4), (uint32_t)P.n, po);
+    return cudaGetLastError();
 }
 
 }  // namespace ssm

@@ -19,7 +19,8 @@
 // In each QL sweep one thread computes the chain of plane rotations and the
 // whole CTA then applies it to the eigenvector rows, one column per thread,
 // coalesced.  Eigenvalues of B alone (no hybrid correction) skip the
-// accumulation and the rotations: ~1.3 n^3 flops.
+// accumulation and the QL sweeps: they come from bisection on Sturm counts,
+// one thread per eigenvalue (~0.7 n^3 flops for the reduction).
 // Matrices live in a per-CTA global workspace (L2 resident); eigenvectors
 // are kept as rows.  QL sweeps are bounded (60 per eigenvalue).
 #include <float.h>
@@ -111,11 +112,26 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             const double K = 0.5 * beta * block_sum(g, sh.red);
             for (int i = tid; i < L; i += NT) sh.p[i] -= K * sh.v[i];  // p becomes w
             __syncthreads();
-            // A22 -= v w^T + w v^T
-            for (int e = tid; e < L * L; e += NT) {
-                const int i = e / L, j = e - i * L;
-                double* a = A + (size_t)(k + 1 + i) * n + k + 1 + j;
-                *a -= sh.v[i] * sh.p[j] + sh.p[i] * sh.v[j];
+            // A22 -= v w^T + w v^T  (4 independent elements per thread per pass)
+            const int LL = L * L;
+            for (int e0 = tid; e0 < LL; e0 += 4 * NT) {
+                double a[4];
+                double* ap[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * NT;
+                    const int i = e / L, j = e - (e / L) * L;
+                    ap[u] = A + (size_t)(k + 1 + i) * n + k + 1 + j;
+                    if (e < LL) a[u] = *ap[u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * NT;
+                    if (e < LL) {
+                        const int i = e / L, j = e - i * L;
+                        *ap[u] = a[u] - (sh.v[i] * sh.p[j] + sh.p[i] * sh.v[j]);
+                    }
+                }
             }
             // keep v in row k for the accumulation
             for (int i = tid; i < L; i += NT) A[(size_t)k * n + k + 1 + i] = sh.v[i];
@@ -160,9 +176,25 @@ __device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ 
             sh.p[j] = beta * s;
         }
         __syncthreads();
-        for (int e = tid; e < L * L; e += NT) {
-            const int j = e / L, i = e - j * L;  // Zt[j][i] = H[i][j]
-            Zt[(size_t)(k + 1 + j) * n + k + 1 + i] -= v[i] * sh.p[j];
+        const int LL = L * L;
+        for (int e0 = tid; e0 < LL; e0 += 4 * NT) {  // Zt[j][i] = H[i][j]
+            double z[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * NT;
+                if (e < LL) {
+                    const int j = e / L, i = e - j * L;
+                    z[u] = Zt[(size_t)(k + 1 + j) * n + k + 1 + i];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * NT;
+                if (e < LL) {
+                    const int j = e / L, i = e - j * L;
+                    Zt[(size_t)(k + 1 + j) * n + k + 1 + i] = z[u] - v[i] * sh.p[j];
+                }
+            }
         }
         __syncthreads();
     }
@@ -186,7 +218,7 @@ __device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared
                 int lo = 0, hi = -1;  // rotations to apply: i from hi down to lo
                 if (m != l && iter < MAX_QL_ITER) {
                     double g = (sh.d[l + 1] - sh.d[l]) / (2.0 * sh.off[l]);
-                    double r = hypot(g, 1.0);
+                    double r = sqrt(fma(g, g, 1.0));
                     g = sh.d[m] - sh.d[l] + sh.off[l] / (g + copysign(r, g));
                     double s = 1.0, c = 1.0, p = 0.0;
                     int i = m - 1;
@@ -194,16 +226,30 @@ __device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared
                     for (; i >= l; --i) {
                         const double f = s * sh.off[i];
                         const double b = c * sh.off[i];
-                        r = hypot(f, g);
-                        sh.off[i + 1] = r;
-                        if (r == 0.0) {
+                        // r = |(f, g)|, s = f / r, c = g / r with one reciprocal square root
+                        // (|f|, |g| are far from the float64 over/underflow range here; a
+                        // pair below 2^-500 is rescaled first)
+                        double fs = f, gs = g, scale = 1.0;
+                        if (fmax(fabs(f), fabs(g)) < 0x1p-500) {
+                            fs = f * 0x1p+500;
+                            gs = g * 0x1p+500;
+                            scale = 0x1p-500;
+                        }
+                        const double q = fma(fs, fs, gs * gs);
+                        if (q == 0.0) {
+                            sh.off[i + 1] = 0.0;
                             sh.d[i + 1] -= p;
                             sh.off[m] = 0.0;
                             early = true;
                             break;
                         }
-                        s = f / r;
-                        c = g / r;
+                        const double rin = rsqrt(q);
+                        // one Newton step on 1/sqrt(q) keeps the rotation orthogonal to rounding
+                        const double rinv = rin * fma(-0.5 * q * rin, rin, 1.5);
+                        r = q * rinv * scale;
+                        sh.off[i + 1] = r;
+                        s = fs * rinv;
+                        c = gs * rinv;
                         g = sh.d[i + 1] - p;
                         r = (sh.d[i] - g) * s + 2.0 * c * b;
                         p = s * r;
@@ -230,15 +276,29 @@ __device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared
             __syncthreads();
             const int go = sh.misc[4];
             if (vectors && go) {
+                // Rotation i maps (z_i, z_{i+1}) to (c z_i - s z_{i+1}, s z_i + c z_{i+1}); the new
+                // z_i is the z_{i+1} of rotation i-1, so it is carried in a register and every
+                // row is read and written once, with the reads issued 8 rotations ahead.
                 const int lo = sh.misc[2], hi = sh.misc[3];
-                for (int col = tid; col < n; col += NT) {
-                    for (int i = hi; i >= lo; --i) {
-                        const double c = sh.rc[i], s = sh.rs[i];
-                        double* z0 = Zt + (size_t)i * n + col;
-                        double* z1 = z0 + n;
-                        const double f = *z1;
-                        *z1 = s * (*z0) + c * f;
-                        *z0 = c * (*z0) - s * f;
+                if (hi >= lo) {
+                    for (int col = tid; col < n; col += NT) {
+                        double carry = Zt[(size_t)(hi + 1) * n + col];
+                        for (int i = hi; i >= lo; i -= 8) {
+                            const int cnt = (i - lo + 1) < 8 ? (i - lo + 1) : 8;
+                            double z[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (u < cnt) z[u] = Zt[(size_t)(i - u) * n + col];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                if (u < cnt) {
+                                    const double c = sh.rc[i - u], s = sh.rs[i - u];
+                                    Zt[(size_t)(i - u + 1) * n + col] = s * z[u] + c * carry;
+                                    carry = c * z[u] - s * carry;
+                                }
+                            }
+                        }
+                        Zt[(size_t)lo * n + col] = carry;
                     }
                 }
             }
@@ -251,8 +311,73 @@ __device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared
     return converged;
 }
 
+// Number of eigenvalues of the tridiagonal (d, off) below x: the sign changes
+// of the Sturm sequence p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i -
+// off_{i-1}^2 p_{i-1} (no divisions; a pair is rescaled by 2^-600 / 2^600 when
+// it leaves [2^-600, 2^600]; a zero p_i takes the opposite sign of p_{i-1}).
+__device__ int sturm_below(const double* __restrict__ d, const double* __restrict__ e2, int n, double x) {
+    double pm = 1.0, pc = d[0] - x;
+    int neg_prev = 0, count = 0;
+    int neg = pc < 0.0 || (pc == 0.0 && !neg_prev);
+    count += (neg != neg_prev);
+    neg_prev = neg;
+    for (int i = 1; i < n; ++i) {
+        const double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
+        pm = pc;
+        pc = pn;
+        const double a = fabs(pc);
+        if (a > 0x1p+600 || (a < 0x1p-600 && a > 0.0)) {
+            const double sc = a > 1.0 ? 0x1p-600 : 0x1p+600;
+            pc *= sc;
+            pm *= sc;
+        }
+        neg = pc < 0.0 || (pc == 0.0 && !neg_prev);
+        count += (neg != neg_prev);
+        neg_prev = neg;
+    }
+    return count;
+}
+
+// Eigenvalues of the tridiagonal (sh.d, sh.off) by bisection, one thread per
+// eigenvalue (the j-th smallest), into sh.v (ascending).  e2 = off^2 is kept
+// in sh.p.
+__device__ void bisect_all(int n, Shared& sh) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += NT) sh.p[i] = (i + 1 < n) ? sh.off[i] * sh.off[i] : 0.0;
+    __syncthreads();
+    if (tid == 0) {
+        double lo = sh.d[0], hi = sh.d[0];
+        for (int i = 0; i < n; ++i) {
+            const double r = (i > 0 ? fabs(sh.off[i - 1]) : 0.0) + (i + 1 < n ? fabs(sh.off[i]) : 0.0);
+            lo = fmin(lo, sh.d[i] - r);
+            hi = fmax(hi, sh.d[i] + r);
+        }
+        const double w = fmax(hi - lo, fmax(fabs(lo), fabs(hi))) * DBL_EPSILON * 4 + DBL_MIN;
+        sh.rc[0] = lo - w;
+        sh.rc[1] = hi + w;
+    }
+    __syncthreads();
+    const double glo = sh.rc[0], ghi = sh.rc[1];
+    __syncthreads();
+    for (int j = tid; j < n; j += NT) {
+        double lo = glo, hi = ghi;
+        for (int it = 0; it < 80; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (sturm_below(sh.d, sh.p, n, mid) > j)
+                hi = mid;
+            else
+                lo = mid;
+        }
+        sh.v[j] = 0.5 * (lo + hi);
+    }
+    __syncthreads();
+}
+
 // Eigen-decomposition of the symmetric n x n matrix A (destroyed): sh.d gets
 // the eigenvalues; with vectors, row j of Zt the eigenvector of sh.d[j].
+// Without vectors the eigenvalues come from bisection (parallel) instead of
+// the serial QL sweeps.
 __device__ bool eigh(double* __restrict__ A, double* __restrict__ Zt, int n, bool vectors, Shared& sh) {
     if (threadIdx.x == 0) sh.misc[5] = 0;
     __syncthreads();
@@ -263,11 +388,17 @@ __device__ bool eigh(double* __restrict__ A, double* __restrict__ Zt, int n, boo
         return true;
     }
     tridiagonalise(A, n, sh);
-    if (vectors) accumulate_q(A, Zt, n, sh);
+    if (!vectors) {
+        bisect_all(n, sh);
+        for (int j = threadIdx.x; j < n; j += NT) sh.d[j] = sh.v[j];
+        __syncthreads();
+        return true;
+    }
+    accumulate_q(A, Zt, n, sh);
     return ql_implicit(Zt, n, vectors, sh);
 }
 
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 3)
 solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, int64_t n_t, int nv, int nvh,
              double tau, double xlo, double xhi, const double* __restrict__ mu, int ldmu, int K,
              double floor_scale, double* __restrict__ work, double* __restrict__ dos,
@@ -338,20 +469,26 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             T1[(size_t)k * n + c] = s;
         }
         __syncthreads();
-        // B = T1 Y^T (r x r, ld r) into A, symmetrised
-        for (int e = tid; e < r * r; e += NT) {
-            const int k = e / r, kk = e - k * r;
-            if (kk < k) continue;
+        // B = T1 Y^T (r x r, ld r) into A: symmetric (K_Z is), upper triangle
+        // computed and mirrored
+        const int npair = r * (r + 1) / 2;
+        for (int e = tid; e < npair; e += NT) {
+            // packed upper triangle index -> (k, kk), k <= kk
+            int k = (int)((2.0 * r + 1.0 - sqrt((2.0 * r + 1.0) * (2.0 * r + 1.0) - 8.0 * e)) * 0.5);
+            if (k < 0) k = 0;
+            if (k > r - 1) k = r - 1;
+            while (k > 0 && k * r - k * (k - 1) / 2 > e) --k;
+            while (k + 1 < r && (k + 1) * r - (k + 1) * k / 2 <= e) ++k;
+            const int kk = e - (k * r - k * (k - 1) / 2) + k;
             const double* a1 = T1 + (size_t)k * n;
-            const double* a2 = T1 + (size_t)kk * n;
-            const double* y1 = Y + (size_t)k * n;
             const double* y2 = Y + (size_t)kk * n;
             double s1 = 0.0, s2 = 0.0;
-            for (int c = 0; c < n; ++c) {
+            for (int c = 0; c + 1 < n; c += 2) {
                 s1 = fma(a1[c], y2[c], s1);
-                s2 = fma(a2[c], y1[c], s2);
+                s2 = fma(a1[c + 1], y2[c + 1], s2);
             }
-            const double v = 0.5 * (s1 + s2);
+            if (n & 1) s1 = fma(a1[n - 1], y2[n - 1], s1);
+            const double v = s1 + s2;
             A[(size_t)k * r + kk] = v;
             A[(size_t)kk * r + k] = v;
         }
