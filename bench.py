@@ -314,11 +314,13 @@ def run_gpu(args, c, st, W, csr):
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("ssm_timed")  # ncu --nvtx --nvtx-include ssm_timed/ profiles this region
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     if dist is not None:

@@ -674,7 +674,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
             const size_t nn2 = (size_t)P.n_tot * P.n_tot;
             CUDA_OR_FAIL(h, launch_reduce_tc_batch(P.d_ring, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k0, nk, P.d_ring_sum,
                                                    P.d_ring_sum + (size_t)P.tc_ring * nn2, P.stream));
-            P.stats.launches += nk + 1;
+            P.stats.launches += 2;
         }
     }
     CUDA_OR_FAIL(h, launch_check_finite(P.d_X, (int64_t)(M + 1) * nn, P.d_flag, P.stream));

@@ -336,6 +336,53 @@ sum_tc_kernel(const float* __restrict__ pe, int n_e, const float* __restrict__ p
     }
 }
 
+// One launch for a whole ring batch: blockIdx.y selects the step.
+__global__ void __launch_bounds__(256)
+sum_tc_batch_kernel(const float* __restrict__ ring, size_t slot, int n_e, int n_o, int n_tot,
+                    double* __restrict__ ge, double* __restrict__ go) {
+    __shared__ double se[8][32], so[8][32];
+    const size_t nn = (size_t)n_tot * n_tot;
+    const float* pe = ring + (size_t)blockIdx.y * slot;
+    const float* po = pe + (size_t)n_e * nn;
+    double* gq = ge + (size_t)blockIdx.y * nn;
+    double* oq = go + (size_t)blockIdx.y * nn;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
+        const size_t e = e0 + lane;
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        if (e < nn) {
+            const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
+            if (i <= j) {
+                int s = w;
+                for (; s + 8 < n_e; s += 16) {
+                    a0 += (double)pe[(size_t)s * nn + e];
+                    a1 += (double)pe[(size_t)(s + 8) * nn + e];
+                }
+                for (; s < n_e; s += 8) a0 += (double)pe[(size_t)s * nn + e];
+            }
+            int s = w;
+            for (; s + 8 < n_o; s += 16) {
+                b0 += (double)po[(size_t)s * nn + e];
+                b1 += (double)po[(size_t)(s + 8) * nn + e];
+            }
+            for (; s < n_o; s += 8) b0 += (double)po[(size_t)s * nn + e];
+        }
+        se[w][lane] = a0 + a1;
+        so[w][lane] = b0 + b1;
+        __syncthreads();
+        if (w == 0 && e < nn) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                a += se[k][lane];
+                b += so[k][lane];
+            }
+            gq[e] = a;
+            oq[e] = b;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void moments_tc_kernel(const double* __restrict__ ge, const double* __restrict__ go, int n_tot,
                                   double* __restrict__ X, int step) {
     const size_t nn = (size_t)n_tot * n_tot;
@@ -443,11 +490,9 @@ cudaError_t launch_reduce_tc_batch(const float* ring, int n_e, int n_o, int n_to
     const int64_t nn = (int64_t)n_tot * n_tot;
     const size_t slot = gram_tc_partial_floats(n_e, n_o, n_tot);
     int64_t sb = (nn + 31) / 32;
-    if (sb > 152 * 8) sb = 152 * 8;
-    for (int q = 0; q < nk; ++q) {
-        const float* p = ring + (size_t)q * slot;
-        sum_tc_kernel<<<(int)sb, 256, 0, s>>>(p, n_e, p + (size_t)n_e * nn, n_o, n_tot, ge + q * nn, go + q * nn);
-    }
+    if (sb > 1024) sb = 1024;
+    dim3 sgrid((unsigned)sb, (unsigned)nk);
+    sum_tc_batch_kernel<<<sgrid, 256, 0, s>>>(ring, slot, n_e, n_o, n_tot, ge, go);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((nn + 255) / 256 > 512 ? 512 : (nn + 255) / 256), (unsigned)nk);

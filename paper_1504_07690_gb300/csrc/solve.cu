@@ -313,37 +313,75 @@ __device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared
 
 // Number of eigenvalues of the tridiagonal (d, off) below x: the sign changes
 // of the Sturm sequence p_0 = 1, p_1 = d_0 - x, p_{i+1} = (d_i - x) p_i -
-// off_{i-1}^2 p_{i-1} (no divisions; a pair is rescaled by 2^-600 / 2^600 when
-// it leaves [2^-600, 2^600]; a zero p_i takes the opposite sign of p_{i-1}).
+// off_{i-1}^2 p_{i-1} (no divisions; a zero p_i takes the opposite sign of
+// p_{i-1}).  The pair (p_i, p_{i-1}) is rescaled by 2^-/+600 when p_i leaves
+// [2^-600, 2^600].  Signs and exponent tests use the integer pipe (the
+// float64 pipe runs at 1/58 of the float32 rate on this part).
 __device__ int sturm_below(const double* __restrict__ d, const double* __restrict__ e2, int n, double x) {
     double pm = 1.0, pc = d[0] - x;
     int neg_prev = 0, count = 0;
-    int neg = pc < 0.0 || (pc == 0.0 && !neg_prev);
-    count += (neg != neg_prev);
-    neg_prev = neg;
-    for (int i = 1; i < n; ++i) {
-        const double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
-        pm = pc;
-        pc = pn;
-        const double a = fabs(pc);
-        if (a > 0x1p+600 || (a < 0x1p-600 && a > 0.0)) {
-            const double sc = a > 1.0 ? 0x1p-600 : 0x1p+600;
+    for (int i = 0;; ++i) {
+        const int hi = __double2hiint(pc);
+        const int zero = ((hi & 0x7fffffff) | __double2loint(pc)) == 0;
+        const int neg = zero ? !neg_prev : (hi < 0);
+        count += (neg != neg_prev);
+        neg_prev = neg;
+        if (i + 1 >= n) break;
+        const int ex = (hi >> 20) & 0x7ff;  // biased exponent of p_i
+        if (ex > 1023 + 600 || (ex < 1023 - 600 && !zero)) {
+            const double sc = ex > 1023 ? 0x1p-600 : 0x1p+600;
             pc *= sc;
             pm *= sc;
         }
-        neg = pc < 0.0 || (pc == 0.0 && !neg_prev);
+        const double pn = fma(d[i + 1] - x, pc, -e2[i] * pm);
+        pm = pc;
+        pc = pn;
+    }
+    return count;
+}
+
+// Same count in float32 for the coarse part of the bisection (the sequence
+// is rescaled by 2^-/+60 to stay inside the float32 range).
+__device__ int sturm_below_f32(const float* __restrict__ d, const float* __restrict__ e2, int n, float x) {
+    float pm = 1.f, pc = d[0] - x;
+    int neg_prev = 0, count = 0;
+    for (int i = 0;; ++i) {
+        const int bits = __float_as_int(pc);
+        const int zero = (bits & 0x7fffffff) == 0;
+        const int neg = zero ? !neg_prev : (bits < 0);
         count += (neg != neg_prev);
         neg_prev = neg;
+        if (i + 1 >= n) break;
+        const int ex = (bits >> 23) & 0xff;
+        if (ex > 127 + 60 || (ex < 127 - 60 && !zero)) {
+            const float sc = ex > 127 ? 0x1p-60f : 0x1p+60f;
+            pc *= sc;
+            pm *= sc;
+        }
+        const float pn = fmaf(d[i + 1] - x, pc, -e2[i] * pm);
+        pm = pc;
+        pc = pn;
     }
     return count;
 }
 
 // Eigenvalues of the tridiagonal (sh.d, sh.off) by bisection, one thread per
-// eigenvalue (the j-th smallest), into sh.v (ascending).  e2 = off^2 is kept
-// in sh.p.
+// eigenvalue (the j-th smallest), into sh.v (ascending).  The interval is
+// first narrowed in float32 (with a float32 count the j-th eigenvalue is
+// certain to lie within a few float32 ulps of the float32 bracket, so the
+// bracket is widened by 8 ulps of its magnitude before the float64 pass),
+// then refined in float64.  e2 = off^2 is kept in sh.p (float64) and
+// sh.rs (float32 copies of d and e2).
 __device__ void bisect_all(int n, Shared& sh) {
     const int tid = threadIdx.x;
-    for (int i = tid; i < n; i += NT) sh.p[i] = (i + 1 < n) ? sh.off[i] * sh.off[i] : 0.0;
+    float* d32 = reinterpret_cast<float*>(sh.rs);
+    float* e32 = d32 + n;
+    for (int i = tid; i < n; i += NT) {
+        const double e2 = (i + 1 < n) ? sh.off[i] * sh.off[i] : 0.0;
+        sh.p[i] = e2;
+        d32[i] = (float)sh.d[i];
+        e32[i] = (float)e2;
+    }
     __syncthreads();
     if (tid == 0) {
         double lo = sh.d[0], hi = sh.d[0];
@@ -358,9 +396,27 @@ __device__ void bisect_all(int n, Shared& sh) {
     }
     __syncthreads();
     const double glo = sh.rc[0], ghi = sh.rc[1];
+    const double scale = fmax(fabs(glo), fabs(ghi));
     __syncthreads();
     for (int j = tid; j < n; j += NT) {
-        double lo = glo, hi = ghi;
+        // coarse float32 pass
+        float flo = (float)glo, fhi = (float)ghi;
+        for (int it = 0; it < 28; ++it) {
+            const float mid = 0.5f * (flo + fhi);
+            if (mid <= flo || mid >= fhi) break;
+            if (sturm_below_f32(d32, e32, n, mid) > j)
+                fhi = mid;
+            else
+                flo = mid;
+        }
+        // float32 rounding of T moves eigenvalues by up to ~n ulp(|T|): widen
+        const double pad = scale * (4e-7 * n + 1e-6) + DBL_MIN;
+        double lo = fmax(glo, (double)flo - pad), hi = fmin(ghi, (double)fhi + pad);
+        // the widened bracket must still contain the j-th eigenvalue; fall back if not
+        if (!(sturm_below(sh.d, sh.p, n, lo) <= j && sturm_below(sh.d, sh.p, n, hi) > j)) {
+            lo = glo;
+            hi = ghi;
+        }
         for (int it = 0; it < 80; ++it) {
             const double mid = 0.5 * (lo + hi);
             if (mid <= lo || mid >= hi) break;
@@ -454,10 +510,11 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
         __syncthreads();
         const int r = sh.misc[0];
         // Y = S~^-1/2 U~^T (rows)
+        for (int k = tid; k < r; k += NT) sh.v[k] = 1.0 / sqrt(sh.d[sh.keep[k]]);
+        __syncthreads();
         for (int e = tid; e < r * n; e += NT) {
             const int k = e / n, c = e - k * n;
-            const int j = sh.keep[k];
-            Y[(size_t)k * n + c] = Zt[(size_t)j * n + c] / sqrt(sh.d[j]);
+            Y[(size_t)k * n + c] = Zt[(size_t)sh.keep[k] * n + c] * sh.v[k];
         }
         __syncthreads();
         // T1 = Y K_Z (r x n)
