@@ -543,7 +543,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         CREATE_CUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * ring * P.n_tot * P.n_tot));
         P.panel_groups = gram_tc_groups(P.n_tot);
         P.n_panels = (P.n + 31) / 32;
-        const size_t pbytes = (size_t)P.n_panels * 2 * P.panel_groups * 512;
+        const size_t pbytes = (size_t)P.n_panels * 2 * P.panel_groups * 528;
         for (auto& pb : P.d_panel) {
             CREATE_CUDA(cudaMalloc((void**)&pb, pbytes));
             CREATE_CUDA(cudaMemsetAsync(pb, 0, pbytes, P.stream));  // rows past N stay zero

@@ -11,8 +11,9 @@
 // Operands: the recurrence kernel writes every block it produces a second
 // time as split-bf16 "panels" (recurrence.cu): 32-row panels, 8-column
 // groups, hi and lo parts, each (panel, part, group) a 512-byte run of four
-// 8 x 16-byte core matrices - exactly the MN-major, no-swizzle shared-memory
-// operand layout of tcgen05 (K stride 128 B, MN stride 512 B).  This kernel
+// 8 x 16-byte core matrices plus a 16-byte pad - exactly the MN-major,
+// no-swizzle shared-memory operand layout of tcgen05 (K stride 128 B, MN
+// stride 528 B).  This kernel
 // therefore does no conversion: one thread streams panels into a shared-
 // memory ring (6 stages of 32 KB for Ge, 3 of 64 KB for Go) with 1-D bulk TMA copies (cp.async.bulk, completion
 // counted in bytes on an mbarrier), one thread issues M=128
@@ -43,7 +44,11 @@ constexpr int STAGES_E = 6;            // one-source stages (32 KB each)
 constexpr int STAGES_O = 3;            // two-source stages (64 KB each)
 constexpr int STAGES = 6;              // barrier slots
 constexpr int NTHREADS = 128;
-constexpr int PART_BYTES = 32 * KG * 128;  // one part of one stage: 32 column groups
+// A column group of a panel is 4 core matrices (512 B) plus a 16-byte pad:
+// with a 528-byte group stride the M/N groups of an MMA operand start on
+// rotating shared-memory banks instead of all on bank 0.
+constexpr int GROUP_BYTES = KG * 128 + 16;
+constexpr int PART_BYTES = 32 * GROUP_BYTES;  // one part of one stage: 32 column groups
 constexpr int TMEM_COLS = 512;
 constexpr long WAIT_LIMIT = 1L << 26;  // bounded mbarrier polls
 constexpr int SMEM_BYTES = STAGES_E * 2 * PART_BYTES + 1024;  // > half of an SM: one CTA per SM
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
 
     if (warp == 0) {
         if (lane == 0) {  // producer: bulk copies of panels into the ring
-            const uint32_t copy = (uint32_t)G * 512;
+            const uint32_t copy = (uint32_t)G * GROUP_BYTES;
             for (int c = 0; c < nch; ++c) {
                 const int s = c % nstage;
                 if (c >= nstage && !mbar_wait(smem_u32(&empty[s]), ((c / nstage) - 1) & 1)) {
@@ -213,16 +218,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
                 mbar_expect_tx(&full[s], (uint32_t)nsrc * 2 * copy);
                 const int64_t pnl = p0 + c;
                 for (int src = 0; src < nsrc; ++src) {
-                    const uint8_t* base = (src == 0 ? P.PX : P.PY) + (size_t)pnl * 2 * G * 512;
+                    const uint8_t* base = (src == 0 ? P.PX : P.PY) + (size_t)pnl * 2 * G * GROUP_BYTES;
                     bulk_copy(dst + (2 * src) * PART_BYTES, base, copy, &full[s]);
-                    bulk_copy(dst + (2 * src + 1) * PART_BYTES, base + (size_t)G * 512, copy, &full[s]);
+                    bulk_copy(dst + (2 * src + 1) * PART_BYTES, base + (size_t)G * GROUP_BYTES, copy, &full[s]);
                 }
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            const uint32_t lbo = 128, sbo = KG * 128;
+            const uint32_t lbo = 128, sbo = GROUP_BYTES;
             bool ok = true;
             for (int c = 0; c < nch; ++c) {
                 const int s = c % nstage;
@@ -239,8 +244,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
                     const uint32_t dt = tmem + (uint32_t)t_dc[t];
 #pragma unroll
                     for (int kk = 0; kk < KC / 16; ++kk) {
-                        const uint32_t ao = (uint32_t)(t_ag[t] * KG + 2 * kk) * 128;
-                        const uint32_t bo = (uint32_t)(t_bg[t] * KG + 2 * kk) * 128;
+                        const uint32_t ao = (uint32_t)t_ag[t] * GROUP_BYTES + 2 * kk * 128;
+                        const uint32_t bo = (uint32_t)t_bg[t] * GROUP_BYTES + 2 * kk * 128;
                         const uint32_t acc0 = (c == 0 && kk == 0) ? 0u : 1u;
                         mma_bf16(dt, smem_desc(xhi + ao, lbo, sbo), smem_desc(yhi + bo, lbo, sbo), idesc, acc0);
                         mma_bf16(dt, smem_desc(xhi + ao, lbo, sbo), smem_desc(ylo + bo, lbo, sbo), idesc, 1u);

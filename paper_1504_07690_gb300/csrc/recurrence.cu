@@ -43,7 +43,8 @@ __device__ __forceinline__ VT ldg_stream(const VT* p) { return __ldg(p); }
 // Split-bf16 panel of a float32 block for the tensor-core Gram (see
 // gram_tc.cu): rows in panels of 32, columns in groups of 8 (G groups,
 // n_tot rounded up to 16), each (panel, part, group) a 512-byte run of four
-// 8 x 16-byte core matrices (8 rows x 8 bf16 each); part 0 = hi = rn(v),
+// 8 x 16-byte core matrices (8 rows x 8 bf16 each) and a 16-byte pad (a
+// 528-byte group stride); part 0 = hi = rn(v),
 // part 1 = lo = rn(v - hi).  The CTA of 8 warps that writes 8 consecutive
 // rows stages their hi/lo values in shared memory and writes whole 128-byte
 // core matrices.
@@ -60,14 +61,15 @@ __device__ __forceinline__ uint32_t stage_off(uint32_t G, uint32_t part, uint32_
     return ((part * 32 + row) * (G + 1) + g) * 16;
 }
 
-// Write the staged panel as 512-byte runs (panel, part, group) in core-matrix
-// order [kg][row8][16 B] (row = kg*8 + row8).
+// Write the staged panel as 512-byte runs (panel, part, group), 528 bytes
+// apart (a 16-byte pad per group), in core-matrix order [kg][row8][16 B]
+// (row = kg*8 + row8).
 __device__ __forceinline__ void flush_panel(const uint8_t* stage, PanelOut po, uint32_t panel) {
     const uint32_t n16 = 2 * po.G * 32;  // 16-byte pieces: part x group x row
     for (uint32_t t = threadIdx.x; t < n16; t += blockDim.x) {
         const uint32_t row = t & 31, g = (t >> 5) % po.G, part = (t >> 5) / po.G;
         const uint4 v = *reinterpret_cast<const uint4*>(stage + stage_off(po.G, part, row, g));
-        uint8_t* dst = po.base + (((size_t)panel * 2 + part) * po.G + g) * 512 + row * 16;
+        uint8_t* dst = po.base + (((size_t)panel * 2 + part) * po.G + g) * 528 + row * 16;
         *reinterpret_cast<uint4*>(dst) = v;
     }
 }
