@@ -365,14 +365,15 @@ __device__ int sturm_below_f32(const float* __restrict__ d, const float* __restr
     return count;
 }
 
-// Eigenvalues of the tridiagonal (sh.d, sh.off) by bisection, one thread per
-// eigenvalue (the j-th smallest), into sh.v (ascending).  The interval is
-// first narrowed in float32 (with a float32 count the j-th eigenvalue is
-// certain to lie within a few float32 ulps of the float32 bracket, so the
-// bracket is widened by 8 ulps of its magnitude before the float64 pass),
-// then refined in float64.  e2 = off^2 is kept in sh.p (float64) and
-// sh.rs (float32 copies of d and e2).
-__device__ void bisect_all(int n, Shared& sh) {
+// Bisection on Sturm counts for eigenvalues of the tridiagonal (sh.d,
+// sh.off).  bisect_prepare stores e2 = off^2 in sh.p (float64), float32
+// copies of d and e2 in sh.rs, and a Gershgorin bracket of the spectrum in
+// sh.rc[0..1]; bisect_one then returns the j-th smallest eigenvalue.  The
+// interval is first narrowed in float32 (with a float32 count the j-th
+// eigenvalue is certain to lie within a few float32 ulps of the float32
+// bracket, so the bracket is widened by 8 ulps of its magnitude before the
+// float64 pass), then refined in float64.
+__device__ void bisect_prepare(int n, Shared& sh) {
     const int tid = threadIdx.x;
     float* d32 = reinterpret_cast<float*>(sh.rs);
     float* e32 = d32 + n;
@@ -395,37 +396,122 @@ __device__ void bisect_all(int n, Shared& sh) {
         sh.rc[1] = hi + w;
     }
     __syncthreads();
+}
+
+__device__ double bisect_one(int j, int n, const Shared& sh) {
+    const float* d32 = reinterpret_cast<const float*>(sh.rs);
+    const float* e32 = d32 + n;
     const double glo = sh.rc[0], ghi = sh.rc[1];
     const double scale = fmax(fabs(glo), fabs(ghi));
+    // coarse float32 pass
+    float flo = (float)glo, fhi = (float)ghi;
+    for (int it = 0; it < 28; ++it) {
+        const float mid = 0.5f * (flo + fhi);
+        if (mid <= flo || mid >= fhi) break;
+        if (sturm_below_f32(d32, e32, n, mid) > j)
+            fhi = mid;
+        else
+            flo = mid;
+    }
+    // float32 rounding of T moves eigenvalues by up to ~n ulp(|T|): widen
+    const double pad = scale * (4e-7 * n + 1e-6) + DBL_MIN;
+    double lo = fmax(glo, (double)flo - pad), hi = fmin(ghi, (double)fhi + pad);
+    // the widened bracket must still contain the j-th eigenvalue; fall back if not
+    if (!(sturm_below(sh.d, sh.p, n, lo) <= j && sturm_below(sh.d, sh.p, n, hi) > j)) {
+        lo = glo;
+        hi = ghi;
+    }
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_below(sh.d, sh.p, n, mid) > j)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// All eigenvalues, one thread per eigenvalue, into sh.v (ascending).
+__device__ void bisect_all(int n, Shared& sh) {
+    bisect_prepare(n, sh);
+    for (int j = threadIdx.x; j < n; j += NT) sh.v[j] = bisect_one(j, n, sh);
     __syncthreads();
-    for (int j = tid; j < n; j += NT) {
-        // coarse float32 pass
-        float flo = (float)glo, fhi = (float)ghi;
-        for (int it = 0; it < 28; ++it) {
-            const float mid = 0.5f * (flo + fhi);
-            if (mid <= flo || mid >= fhi) break;
-            if (sturm_below_f32(d32, e32, n, mid) > j)
-                fhi = mid;
-            else
-                flo = mid;
+}
+
+// Cholesky factor of the symmetric positive definite n x n matrix A
+// (row-major), right-looking: the lower triangle of A receives L (A = L L^T)
+// and sh.v[k] = 1 / L[k][k].  Returns false (on every thread) at the first
+// pivot that is not positive.
+__device__ bool cholesky_lower(double* __restrict__ A, int n, Shared& sh) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = 0; k < n; ++k) {
+        if (tid == 0) {
+            const double piv = A[(size_t)k * n + k];
+            const bool pos = piv > 0.0;
+            const double r = pos ? rsqrt(piv) : 0.0;
+            // one Newton step on 1/sqrt(piv)
+            const double rr = pos ? r * fma(-0.5 * piv * r, r, 1.5) : 0.0;
+            sh.v[k] = rr;
+            A[(size_t)k * n + k] = piv * rr;
+            sh.misc[6] = pos;
         }
-        // float32 rounding of T moves eigenvalues by up to ~n ulp(|T|): widen
-        const double pad = scale * (4e-7 * n + 1e-6) + DBL_MIN;
-        double lo = fmax(glo, (double)flo - pad), hi = fmin(ghi, (double)fhi + pad);
-        // the widened bracket must still contain the j-th eigenvalue; fall back if not
-        if (!(sturm_below(sh.d, sh.p, n, lo) <= j && sturm_below(sh.d, sh.p, n, hi) > j)) {
-            lo = glo;
-            hi = ghi;
+        __syncthreads();
+        if (!sh.misc[6]) return false;
+        const double rk = sh.v[k];
+        for (int i = k + 1 + tid; i < n; i += NT) {
+            const double v = A[(size_t)i * n + k] * rk;
+            A[(size_t)i * n + k] = v;
+            sh.p[i] = v;
         }
-        for (int it = 0; it < 80; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            if (sturm_below(sh.d, sh.p, n, mid) > j)
-                hi = mid;
-            else
-                lo = mid;
+        __syncthreads();
+        // A[i][j] -= l_i l_j for k < j <= i (warp per row, lanes along the row)
+        for (int i = k + 1 + warp; i < n; i += NT / 32) {
+            const double li = sh.p[i];
+            double* row = A + (size_t)i * n;
+            for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fma(-li, sh.p[j], row[j]);
         }
-        sh.v[j] = 0.5 * (lo + hi);
+        __syncthreads();
+    }
+    return true;
+}
+
+// X <- L^{-1} X for the n x n row-major X, L from cholesky_lower (rdiag =
+// sh.v): forward substitution, one column of X per thread.
+__device__ void trsm_lower(const double* __restrict__ L, double* __restrict__ X, int n, const Shared& sh) {
+    for (int c = threadIdx.x; c < n; c += NT) {
+        for (int i = 0; i < n; ++i) {
+            const double* li = L + (size_t)i * n;
+            double s0 = X[(size_t)i * n + c], s1 = 0.0;
+            int k = 0;
+            for (; k + 1 < i; k += 2) {
+                s0 = fma(-li[k], X[(size_t)k * n + c], s0);
+                s1 = fma(-li[k + 1], X[(size_t)(k + 1) * n + c], s1);
+            }
+            if (k < i) s0 = fma(-li[k], X[(size_t)k * n + c], s0);
+            X[(size_t)i * n + c] = (s0 + s1) * sh.v[i];
+        }
+    }
+    __syncthreads();
+}
+
+// Y <- L^{-1} X^T (X, Y distinct, n x n row-major): forward substitution on
+// the rows of X, one row per thread; row r of X gives column r of Y.
+__device__ void trsm_lower_t(const double* __restrict__ L, const double* __restrict__ X, double* __restrict__ Y,
+                             int n, const Shared& sh) {
+    for (int r = threadIdx.x; r < n; r += NT) {
+        const double* xr = X + (size_t)r * n;
+        for (int i = 0; i < n; ++i) {
+            const double* li = L + (size_t)i * n;
+            double s0 = xr[i], s1 = 0.0;
+            int k = 0;
+            for (; k + 1 < i; k += 2) {
+                s0 = fma(-li[k], Y[(size_t)k * n + r], s0);
+                s1 = fma(-li[k + 1], Y[(size_t)(k + 1) * n + r], s1);
+            }
+            if (k < i) s0 = fma(-li[k], Y[(size_t)k * n + r], s0);
+            Y[(size_t)i * n + r] = (s0 + s1) * sh.v[i];
+        }
     }
     __syncthreads();
 }
@@ -483,105 +569,190 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
     for (int64_t it = blockIdx.x; it < n_t; it += gridDim.x) {
         const double* Kt = Kfull + (size_t)it * n_tot * n_tot;
         const double* Zk = KZ + (size_t)it * nn;
-        // 1. K_W (symmetrised) -> A, eigen-decomposition
+        // rounding floor of K_W(t)
+        double fs = 0.0;
+        if (floor_scale > 0.0)
+            for (int l = tid; l <= K; l += NT) fs = fma((double)(l + 1), fabs(mu[it * ldmu + l]), fs);
+        const double floor_t = floor_scale * block_sum(fs, sh.red);
+        // 1. K_W (symmetrised) -> A, tridiagonal form; the largest eigenvalue and
+        //    the number r of eigenvalues >= max(tau smax, floor) from Sturm counts
         for (int e = tid; e < n * n; e += NT) {
             const int i = e / n, j = e - i * n;
             A[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
         }
         __syncthreads();
-        bool ok = eigh(A, Zt, n, true, sh);
-        // 2. truncation s_j >= max(tau max s, rounding floor of K_W)
-        double m = -DBL_MAX;
-        for (int j = tid; j < n; j += NT) m = fmax(m, sh.d[j]);
-        const double smax = block_max(m, sh.red);
-        double fs = 0.0;
-        if (floor_scale > 0.0)
-            for (int l = tid; l <= K; l += NT) fs = fma((double)(l + 1), fabs(mu[it * ldmu + l]), fs);
-        const double floor_t = floor_scale * block_sum(fs, sh.red);
+        tridiagonalise(A, n, sh);
+        bisect_prepare(n, sh);
         if (tid == 0) {
-            int r = 0;
-            if (smax > 0.0) {
-                const double thr = fmax(tau * smax, floor_t);
-                for (int j = 0; j < n; ++j)
-                    if (sh.d[j] >= thr) sh.keep[r++] = j;
-            }
-            sh.misc[0] = r;
+            const double smax = bisect_one(n - 1, n, sh);
+            sh.misc[7] = smax > 0.0 ? n - sturm_below(sh.d, sh.p, n, fmax(tau * smax, floor_t)) : 0;
         }
         __syncthreads();
-        const int r = sh.misc[0];
-        // Y = S~^-1/2 U~^T (rows)
-        for (int k = tid; k < r; k += NT) sh.v[k] = 1.0 / sqrt(sh.d[sh.keep[k]]);
-        __syncthreads();
-        for (int e = tid; e < r * n; e += NT) {
-            const int k = e / n, c = e - k * n;
-            Y[(size_t)k * n + c] = Zt[(size_t)sh.keep[k] * n + c] * sh.v[k];
-        }
-        __syncthreads();
-        // T1 = Y K_Z (r x n)
-        for (int e = tid; e < r * n; e += NT) {
-            const int k = e / n, c = e - k * n;
-            const double* y = Y + (size_t)k * n;
-            double s = 0.0;
-            for (int mm = 0; mm < n; ++mm) s = fma(y[mm], Zk[(size_t)mm * n + c], s);
-            T1[(size_t)k * n + c] = s;
-        }
-        __syncthreads();
-        // B = T1 Y^T (r x r, ld r) into A: symmetric (K_Z is), upper triangle
-        // computed and mirrored
-        const int npair = r * (r + 1) / 2;
-        for (int e = tid; e < npair; e += NT) {
-            // packed upper triangle index -> (k, kk), k <= kk
-            int k = (int)((2.0 * r + 1.0 - sqrt((2.0 * r + 1.0) * (2.0 * r + 1.0) - 8.0 * e)) * 0.5);
-            if (k < 0) k = 0;
-            if (k > r - 1) k = r - 1;
-            while (k > 0 && k * r - k * (k - 1) / 2 > e) --k;
-            while (k + 1 < r && (k + 1) * r - (k + 1) * k / 2 <= e) ++k;
-            const int kk = e - (k * r - k * (k - 1) / 2) + k;
-            const double* a1 = T1 + (size_t)k * n;
-            const double* y2 = Y + (size_t)kk * n;
-            double s1 = 0.0, s2 = 0.0;
-            for (int c = 0; c + 1 < n; c += 2) {
-                s1 = fma(a1[c], y2[c], s1);
-                s2 = fma(a1[c + 1], y2[c + 1], s2);
-            }
-            if (n & 1) s1 = fma(a1[n - 1], y2[n - 1], s1);
-            const double v = s1 + s2;
-            A[(size_t)k * r + kk] = v;
-            A[(size_t)kk * r + k] = v;
-        }
-        __syncthreads();
-        // 3. eigen-decomposition of B (vectors only for the hybrid correction)
-        const bool need_vec = nvh > 0;
-        if (r > 0) ok = eigh(A, Zt, r, need_vec, sh) && ok;
-        // 4. range filter; the sum runs in index order on one thread
-        if (tid == 0) {
-            int q = 0;
-            double phi = 0.0;
-            for (int k = 0; k < r; ++k) {
-                const double xi = sh.d[k];
-                if (xi >= xlo && xi <= xhi) {
-                    sh.sel[q++] = k;
-                    phi += xi;
-                }
-            }
-            sh.misc[1] = q;
-            sh.p[0] = phi;
-        }
-        __syncthreads();
-        const int rs = sh.misc[1];
-        double phi = sh.p[0];
-        __syncthreads();
-        if (nvh > 0) {
-            // 5. C~^T rows: CtT[m][c] = sum_k X[k][sel_m] Y[k][c], X = eigenvectors of B
-            //    (row sel_m of Zt)  -> T1 (rs x n)
-            for (int e = tid; e < rs * n; e += NT) {
-                const int mq = e / n, c = e - mq * n;
-                const double* x = Zt + (size_t)sh.sel[mq] * r;
-                double s = 0.0;
-                for (int k = 0; k < r; ++k) s = fma(x[k], Y[(size_t)k * n + c], s);
-                T1[(size_t)mq * n + c] = s;
+        const int r_est = sh.misc[7];
+        double phi = 0.0;
+        int r = 0, rs = 0;
+        bool ok = true, done = false;
+        if (r_est == 0) {
+            done = true;  // K_W(t) is numerically zero: no direction is kept
+        } else if (r_est == n && nvh == 0) {
+            // 2'. Nothing is truncated, so S~^-1/2 U~^T = S^-1/2 U^T and B = F^-1 K_Z F^-T
+            //     with F = U S^1/2 (K_W = F F^T).  For any other factor G = F Q (Q
+            //     orthogonal) of K_W, G^-1 K_Z G^-T = Q^T B Q has the same eigenvalues,
+            //     so B's eigenvalues come from the Cholesky factor L instead:
+            //     C = L^-1 K_Z L^-T, without the eigenvectors of K_W.
+            for (int e = tid; e < n * n; e += NT) {
+                const int i = e / n, j = e - i * n;
+                Zt[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
             }
             __syncthreads();
+            if (cholesky_lower(Zt, n, sh)) {
+                for (int e = tid; e < n * n; e += NT) {
+                    const int i = e / n, j = e - i * n;
+                    Y[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
+                }
+                __syncthreads();
+                trsm_lower(Zt, Y, n, sh);         // Y = L^-1 K_Z
+                trsm_lower_t(Zt, Y, A, n, sh);    // A = L^-1 Y^T = L^-1 K_Z L^-T
+                for (int e = tid; e < n * n; e += NT) {  // symmetrise (upper from lower)
+                    const int i = e / n, j = e - i * n;
+                    if (i < j) {
+                        const double v = 0.5 * (A[e] + A[(size_t)j * n + i]);
+                        A[e] = v;
+                        A[(size_t)j * n + i] = v;
+                    }
+                }
+                __syncthreads();
+                tridiagonalise(A, n, sh);
+                bisect_prepare(n, sh);
+                // only the eigenvalues near or inside [xlo, xhi] are needed
+                if (tid == 0) {
+                    sh.misc[0] = max(0, sturm_below(sh.d, sh.p, n, xlo) - 1);
+                    sh.misc[1] = min(n, sturm_below(sh.d, sh.p, n, xhi) + 1);
+                }
+                __syncthreads();
+                const int jlo = sh.misc[0], jhi = sh.misc[1];
+                for (int j = jlo + tid; j < jhi; j += NT) sh.v[j] = bisect_one(j, n, sh);
+                __syncthreads();
+                if (tid == 0) {  // range filter; the sum runs in index order on one thread
+                    int q = 0;
+                    double f = 0.0;
+                    for (int j = jlo; j < jhi; ++j) {
+                        const double xi = sh.v[j];
+                        if (xi >= xlo && xi <= xhi) {
+                            ++q;
+                            f += xi;
+                        }
+                    }
+                    sh.misc[1] = q;
+                    sh.p[0] = f;
+                }
+                __syncthreads();
+                r = n;
+                rs = sh.misc[1];
+                phi = sh.p[0];
+                done = true;
+                __syncthreads();
+            }
+        }
+        if (!done) {
+            // 2. eigenvectors of K_W: accumulate the Householder factor (A holds the
+            //    reflectors, sh.d / sh.off the tridiagonal form) and run QL on it
+            accumulate_q(A, Zt, n, sh);
+            if (tid == 0) sh.misc[5] = 0;
+            __syncthreads();
+            ok = ql_implicit(Zt, n, true, sh);
+            // truncation s_j >= max(tau max s, rounding floor of K_W)
+            double m = -DBL_MAX;
+            for (int j = tid; j < n; j += NT) m = fmax(m, sh.d[j]);
+            const double smax = block_max(m, sh.red);
+            if (tid == 0) {
+                int rr = 0;
+                if (smax > 0.0) {
+                    const double thr = fmax(tau * smax, floor_t);
+                    for (int j = 0; j < n; ++j)
+                        if (sh.d[j] >= thr) sh.keep[rr++] = j;
+                }
+                sh.misc[0] = rr;
+            }
+            __syncthreads();
+            r = sh.misc[0];
+            // Y = S~^-1/2 U~^T (rows)
+            for (int k = tid; k < r; k += NT) sh.v[k] = 1.0 / sqrt(sh.d[sh.keep[k]]);
+            __syncthreads();
+            for (int e = tid; e < r * n; e += NT) {
+                const int k = e / n, c = e - k * n;
+                Y[(size_t)k * n + c] = Zt[(size_t)sh.keep[k] * n + c] * sh.v[k];
+            }
+            __syncthreads();
+            // T1 = Y K_Z (r x n)
+            for (int e = tid; e < r * n; e += NT) {
+                const int k = e / n, c = e - k * n;
+                const double* y = Y + (size_t)k * n;
+                double s = 0.0;
+                for (int mm = 0; mm < n; ++mm) s = fma(y[mm], Zk[(size_t)mm * n + c], s);
+                T1[(size_t)k * n + c] = s;
+            }
+            __syncthreads();
+            // B = T1 Y^T (r x r, ld r) into A: symmetric (K_Z is), upper triangle
+            // computed and mirrored
+            const int npair = r * (r + 1) / 2;
+            for (int e = tid; e < npair; e += NT) {
+                // packed upper triangle index -> (k, kk), k <= kk
+                int k = (int)((2.0 * r + 1.0 - sqrt((2.0 * r + 1.0) * (2.0 * r + 1.0) - 8.0 * e)) * 0.5);
+                if (k < 0) k = 0;
+                if (k > r - 1) k = r - 1;
+                while (k > 0 && k * r - k * (k - 1) / 2 > e) --k;
+                while (k + 1 < r && (k + 1) * r - (k + 1) * k / 2 <= e) ++k;
+                const int kk = e - (k * r - k * (k - 1) / 2) + k;
+                const double* a1 = T1 + (size_t)k * n;
+                const double* y2 = Y + (size_t)kk * n;
+                double s1 = 0.0, s2 = 0.0;
+                for (int c = 0; c + 1 < n; c += 2) {
+                    s1 = fma(a1[c], y2[c], s1);
+                    s2 = fma(a1[c + 1], y2[c + 1], s2);
+                }
+                if (n & 1) s1 = fma(a1[n - 1], y2[n - 1], s1);
+                const double v = s1 + s2;
+                A[(size_t)k * r + kk] = v;
+                A[(size_t)kk * r + k] = v;
+            }
+            __syncthreads();
+            // 3. eigen-decomposition of B (vectors only for the hybrid correction)
+            const bool need_vec = nvh > 0;
+            if (r > 0) ok = eigh(A, Zt, r, need_vec, sh) && ok;
+            // 4. range filter; the sum runs in index order on one thread
+            if (tid == 0) {
+                int q = 0;
+                double f = 0.0;
+                for (int k = 0; k < r; ++k) {
+                    const double xi = sh.d[k];
+                    if (xi >= xlo && xi <= xhi) {
+                        sh.sel[q++] = k;
+                        f += xi;
+                    }
+                }
+                sh.misc[1] = q;
+                sh.p[0] = f;
+            }
+            __syncthreads();
+            rs = sh.misc[1];
+            phi = sh.p[0];
+            __syncthreads();
+            if (nvh > 0) {
+                // 5. C~^T rows: CtT[m][c] = sum_k X[k][sel_m] Y[k][c], X = eigenvectors of B
+                //    (row sel_m of Zt)  -> T1 (rs x n)
+                for (int e = tid; e < rs * n; e += NT) {
+                    const int mq = e / n, c = e - mq * n;
+                    const double* x = Zt + (size_t)sh.sel[mq] * r;
+                    double s = 0.0;
+                    for (int k = 0; k < r; ++k) s = fma(x[k], Y[(size_t)k * n + c], s);
+                    T1[(size_t)mq * n + c] = s;
+                }
+                __syncthreads();
+            }
+        }
+        if (nvh > 0) {
+            // hybrid correction (Tr K_W~ - ||K_C C~||_F^2) / N~_v; C~ has rs columns (rows of T1)
             double f = 0.0;
             for (int e = tid; e < nvh * rs; e += NT) {
                 const int h = e / rs, mq = e - h * rs;
