@@ -100,14 +100,21 @@ typedef struct {
     int32_t n_theta;    /* quadrature size N_theta of Alg. 1 (> M); 0 selects 2M */
     int32_t options;    /* bit 0: the SSM_MIXED path forms its Gram products on CUDA cores
                            (float32) instead of the tensor cores (split bf16); used for
-                           cross-checks.  Other bits must be 0. */
+                           cross-checks.  bit 1 (SSM_OPT_ADJOINT): ssm_moments keeps
+                           checkpoints of the recurrence (2 ceil(S / ceil(sqrt(S))) blocks
+                           of N x n_tot, S = M/2) for ssm_moments_adjoint.  Other bits
+                           must be 0 (SSM_EINVAL otherwise). */
     double eps_floor;   /* rounding unit of the floor of Alg. 4's truncation: an eigenvalue
                            of K_W(t) is also dropped below
                            8 n_v eps_floor max_i X_0[i][i] sum_{l<=M/2} (l+1)|mu_l(t)|,
                            the size of the rounding error of K_W(t), so that points where
-                           K_W(t) is numerically zero give no spurious terms; 0 selects the
-                           working precision (2^-52 for SSM_FP64, 2^-23 for SSM_MIXED),
-                           a negative value disables the floor */
+                           K_W(t) is numerically zero give no spurious terms; 0 selects
+                           2^-52 for SSM_FP64 (the float64 unit) and 2^-36 for SSM_MIXED
+                           (the float32 recurrence and split-bf16 Gram products leave
+                           moment errors far below the float32 unit times this worst-case
+                           bound; 2^-36 was the best of 2^-30..2^-40 against the float64
+                           path on a 65536-row Anderson model), a negative value disables
+                           the floor */
 } ssm_params;
 
 typedef struct ssm_plan_s* ssm_plan_t;
@@ -122,6 +129,32 @@ typedef struct ssm_plan_s* ssm_plan_t;
  * SSM_ENONFINITE, SSM_ENOMEM or SSM_ECUDA on failure, with *out = NULL. */
 ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr* csr,
                            const ssm_params* params, void* stream);
+
+/* Batched plan for B operators of uneven size (the paper treats one matrix at a
+ * time; this runs Alg. 7 for all of them at once).  csrs: B CSR operators
+ * (host or device arrays), each checked as in ssm_plan_create, each with its
+ * own interval (a_b, b_b) (Gershgorin + 1e-3 pad, or the caller's lo/hi for
+ * all).  They are laid side by side in one block-diagonal operator, each
+ * starting on a 32-row boundary.  On such a plan:
+ *   ssm_moments: W holds the B probe blocks stacked (sum_b N_b rows x n_tot,
+ *     leading dimension ldw); the recurrence, the Gram products and the
+ *     moment reductions of all matrices run as one CUDA graph (captured on
+ *     the first call, one graph launch per call after); moments (nullable)
+ *     receives B x (M+1) x n_tot x n_tot.  The CSR step's CTA size is picked
+ *     on the first call by timing 64/128/256 threads (autotuner).
+ *   ssm_dos: t holds B blocks of n_t/B points (block b for matrix b, in the
+ *     units of that matrix); outputs are laid out the same way.
+ * ssm_trace_f, ssm_trace_weights, ssm_coefficients, ssm_kpm_adjoint and the
+ * adjoint option are not available (SSM_EINVAL).  Same errors as
+ * ssm_plan_create. */
+ssm_status ssm_plan_create_batched(ssm_plan_t* out, int32_t B, const ssm_csr* csrs, const ssm_params* params,
+                                   void* stream);
+
+/* Interval (a, b), spectral bounds [lo, hi] and size N of matrix b of a
+ * batched plan.  Outputs may be NULL.  SSM_EINVAL for other plans or b out of
+ * range. */
+ssm_status ssm_batch_info(ssm_plan_t plan, int32_t b, double* a, double* bb, double* lo, double* hi,
+                          int64_t* n);
 
 /* The plan's Chebyshev interval (a, b), its spectral bounds [lo, hi] (the
  * unpadded Gershgorin interval, or the caller's interval), and the problem
@@ -163,6 +196,60 @@ ssm_status ssm_dos(ssm_plan_t plan, const double* t, int64_t n_t, double sigma,
 ssm_status ssm_trace_f(ssm_plan_t plan, double (*f)(double x, void* ctx), void* ctx,
                        int64_t n_t, double sigma, double sigma_tilde, double a,
                        double* tr_ss, double* tr_kpm);
+
+/* Trace weights of Alg. 8: the periodic grid x (n_t points, as in
+ * ssm_trace_f) and w_i = N dx f~(x_i), so that the KPM estimate of Tr f(A) is
+ * sum_i w_i phi_KPM(x_i) (the same number ssm_trace_f returns as tr_kpm).
+ * The weights depend on f, the grid and sigma only, not on the moments, so
+ * they turn Tr f(A) into a KPM-line loss for ssm_kpm_adjoint.  x and w are
+ * n_t doubles each (host or device).  Errors as ssm_trace_f. */
+ssm_status ssm_trace_weights(ssm_plan_t plan, double (*f)(double x, void* ctx), void* ctx,
+                             int64_t n_t, double sigma, double sigma_tilde, double a,
+                             double* x, double* w);
+
+/* Replace the diagonal of a stencil plan's operator (diag: N doubles, host or
+ * device), e.g. a potential being optimised.  The plan's interval (a, b) and
+ * spectral bounds stay those of ssm_plan_create: if the Gershgorin interval
+ * of the new operator leaves (a, b) the call returns SSM_EDOMAIN and the
+ * operator is unchanged.  SSM_ENONFINITE for NaN/Inf, SSM_EINVAL for a CSR
+ * plan.  Invalidates the moments (call ssm_moments again). */
+ssm_status ssm_plan_set_diag(ssm_plan_t plan, const double* diag);
+
+/* Gradient of a loss of the KPM line (Alg. 2) with respect to the moments:
+ * for phi(t_i) = sum_{l<=M} mu_l(t_i) Tr X_l / n_tot at n_t points t (host or
+ * device) and weights w_i = dL/dphi(t_i) (host or device), writes
+ * g_l = sum_i w_i mu_l(t_i) / n_tot, l = 0..M (M+1 doubles, host or device), so
+ * that dL/dX_l = g_l I.  Needs no moments. */
+ssm_status ssm_kpm_adjoint(ssm_plan_t plan, const double* t, int64_t n_t, double sigma, const double* w,
+                           double* g);
+
+/* Adjoint of the moment recurrence (the paper has no gradients; this is the
+ * reverse of Alg. 7's loop as ssm_moments runs it, by the doubling identities
+ * above): given G_l = dL/dX_l for a loss L that depends on A only through the
+ * moments of the last ssm_moments call, returns dL/dA with the interval (a, b)
+ * held fixed.
+ *   kind 0: dL_dX holds (M+1) x n_tot x n_tot matrices G_l (only their
+ *           symmetric parts matter);
+ *   kind 1: dL_dX holds M+1 scalars g_l meaning G_l = g_l I (the KPM line and
+ *           Tr f(A), see ssm_kpm_adjoint and ssm_trace_weights).
+ * Outputs (either may be NULL; host or device):
+ *   dL_ddiag: N doubles, dL/dA_ii;
+ *   dL_doff:  stencil plans: 3 doubles, dL/d offdiag[axis] (every coupling of
+ *             the axis moves together); CSR plans: nnz doubles, the gradient
+ *             with respect to the symmetric operator split evenly over the two
+ *             stored entries (i, j) and (j, i), i.e. (dL/dA_ij + dL/dA_ji) / 2:
+ *             a symmetric pair tied to one weight gets the sum of its two
+ *             entries (only this symmetric part is defined: the moments are
+ *             symmetric functions of A).
+ * Needs a plan created with options bit 1 and a completed ssm_moments.  The
+ * recurrence is recomputed segment by segment from the checkpoints; memory
+ * beyond them: ceil(sqrt(M/2)) + 3 blocks of N x n_tot in the working
+ * precision, plus (kind 0) one more block and (M+1) n_tot^2 doubles.  Row and
+ * entry sums are formed in a fixed order (repeatable results).  SSM_ESTATE
+ * without the option or the moments, SSM_EINVAL for a bad kind, SSM_ENONFINITE
+ * for NaN/Inf in dL_dX. */
+ssm_status ssm_moments_adjoint(ssm_plan_t plan, const double* dL_dX, int32_t kind, double* dL_ddiag,
+                               double* dL_doff);
 
 /* Gram pair of two row-major device blocks (float64): G_aa = A^T A and
  * G_ab = A^T B, the products behind the doubling identities
@@ -224,6 +311,7 @@ typedef struct {
     double ms_solve;        /* Alg. 4 + Alg. 6 per sweep point */
     double ms_kpm;          /* Alg. 2 line */
     double ms_trace;        /* Alg. 8 deconvolution and quadrature */
+    double ms_adjoint;      /* reverse recurrence of ssm_moments_adjoint */
     int64_t recurrence_launches;
     int64_t gram_launches;
     int64_t launches;       /* every kernel launch of the library */

@@ -17,8 +17,9 @@ Readings taken (none is in the paper):
   a function of A, so dL/dA = (2/(b-a)) dL/dA~.
 * Only sym(G_l) matters, because X_l is symmetrised.
 * dL/dA_ij is the derivative for a perturbation of the single stored entry
-  (i, j); a symmetric pair (i, j), (j, i) tied to one weight receives the sum
-  of both entries.  A stencil's per-axis coupling offdiag[d] and its diagonal
+  (i, j) of this loop; only its symmetric part (symmetric_part) is a property
+  of the loss, and a symmetric pair (i, j), (j, i) tied to one weight
+  receives the sum of both entries of it.  A stencil's per-axis coupling offdiag[d] and its diagonal
   receive the directional derivative along d A / d offdiag[d], d A / d A_ii.
 
 The adjoint is written out in the loop's own notation: with
@@ -37,7 +38,7 @@ from typing import Tuple
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["moments_forward_blocks", "moments_adjoint_direct", "grad_wrt_a",
+__all__ = ["moments_forward_blocks", "moments_adjoint_direct", "grad_wrt_a", "symmetric_part",
            "stencil_parameter_grad", "kpm_loss_weights", "moments_linear_loss"]
 
 
@@ -96,6 +97,22 @@ def moments_adjoint_direct(At: sp.spmatrix, W: np.ndarray, M: int, G: np.ndarray
         diag += c * np.einsum("ik,ik->i", U[l + 1], V[l])
     d_pat = sp.csr_matrix((vals, P.indices.copy(), P.indptr.copy()), shape=P.shape)
     return diag, d_pat
+
+
+def symmetric_part(d_pat: sp.csr_matrix) -> sp.csr_matrix:
+    """(G + G^T)/2 on a symmetric pattern: the gradient with respect to a symmetric A.
+
+    For a symmetric A~ the moments do not change under a perturbation E - E^T,
+    so only the symmetric part of dL/dA~ is a property of the loss; the reverse
+    of a different but equivalent loop (e.g. by the doubling identities, which
+    hold for symmetric A~ only) may differ in the antisymmetric part.
+    """
+    P = sp.csr_matrix(d_pat)
+    S = 0.5 * (P + P.T)
+    # read back on P's own pattern and order
+    rows = np.repeat(np.arange(P.shape[0]), np.diff(P.indptr))
+    vals = np.asarray(S[rows, P.indices]).ravel()
+    return sp.csr_matrix((vals, P.indices.copy(), P.indptr.copy()), shape=P.shape)
 
 
 def grad_wrt_a(d_tilde, a: float, b: float):

@@ -13,6 +13,8 @@ STATUS_NAMES = {0: "SSM_OK", 1: "SSM_EINVAL", 2: "SSM_ENOMEM", 3: "SSM_ECUDA", 4
                 9: "SSM_ENOCONV"}
 SSM_FP64 = 0
 SSM_MIXED = 1
+SSM_OPT_CUDA_CORE_GRAM = 1
+SSM_OPT_ADJOINT = 2
 
 
 class ssm_stencil(C.Structure):
@@ -34,7 +36,8 @@ class ssm_params(C.Structure):
 class ssm_stats(C.Structure):
     _fields_ = [("ms_coeffs", C.c_double), ("ms_recurrence", C.c_double), ("ms_gram", C.c_double),
                 ("ms_reduce", C.c_double), ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
-                ("ms_kpm", C.c_double), ("ms_trace", C.c_double), ("recurrence_launches", C.c_int64),
+                ("ms_kpm", C.c_double), ("ms_trace", C.c_double), ("ms_adjoint", C.c_double),
+                ("recurrence_launches", C.c_int64),
                 ("gram_launches", C.c_int64), ("launches", C.c_int64)]
 
 
@@ -44,6 +47,10 @@ TRACE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
 SIGNATURES = {
     "ssm_plan_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(ssm_stencil), C.POINTER(ssm_csr),
                                   C.POINTER(ssm_params), C.c_void_p]),
+    "ssm_plan_create_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ssm_csr),
+                                          C.POINTER(ssm_params), C.c_void_p]),
+    "ssm_batch_info": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "ssm_plan_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
@@ -52,6 +59,11 @@ SIGNATURES = {
                           C.c_void_p]),
     "ssm_trace_f": (C.c_int, [C.c_void_p, TRACE_FN, C.c_void_p, C.c_int64, C.c_double, C.c_double,
                               C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ssm_trace_weights": (C.c_int, [C.c_void_p, TRACE_FN, C.c_void_p, C.c_int64, C.c_double, C.c_double,
+                                    C.c_double, C.c_void_p, C.c_void_p]),
+    "ssm_plan_set_diag": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ssm_kpm_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
+    "ssm_moments_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ssm_coefficients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                    C.c_void_p]),
     "ssm_gram_pair": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int64, C.c_void_p,

@@ -61,10 +61,15 @@ def _check(lib, status: int, handle):
 class Plan:
     """Owns one ssm_plan_t (destroyed with the object)."""
 
-    def __init__(self, handle, params: N.ssm_params):
+    def __init__(self, handle, params: N.ssm_params, is_stencil: bool = True):
         self.handle = handle
         self.params = params
+        self.is_stencil = is_stencil
         self._lib = N.load()
+        n, nnz = C.c_int64(), C.c_int64()
+        self._lib.ssm_plan_info(handle, None, None, None, None, C.byref(n), C.byref(nnz))
+        self.n = n.value
+        self.nnz = nnz.value
 
     @property
     def n_v(self) -> int:
@@ -125,7 +130,39 @@ def ssm_plan_create(stencil=None, csr=None, *, n_v: int, degree: int, n_vh: int 
     h = C.c_void_p()
     status = lib.ssm_plan_create(C.byref(h), st_p, csr_p, C.byref(p), _stream(stream))
     _check(lib, status, None)
-    return Plan(h, p)
+    return Plan(h, p, is_stencil=stencil is not None)
+
+
+def ssm_plan_create_batched(csrs, *, n_v: int, degree: int, n_vh: int = 0, precision: str = "mixed",
+                            lo: float = 0.0, hi: float = 0.0, tau: float = 0.0, kappa: float = -1.0,
+                            n_theta: int = 0, eps_floor: float = 0.0, options: int = 0, stream=None) -> Plan:
+    """ssm_plan_create_batched: B CSR operators of uneven size in one plan."""
+    lib = N.load()
+    p = N.ssm_params(n_v=n_v, n_vh=n_vh, degree=degree,
+                     precision={"fp64": N.SSM_FP64, "mixed": N.SSM_MIXED}[precision],
+                     lo=lo, hi=hi, tau=tau, kappa=kappa, n_theta=n_theta, options=options, eps_floor=eps_floor)
+    keep = []
+    arr = (N.ssm_csr * len(csrs))()
+    for k, c in enumerate(csrs):
+        rp, rpp = _as_buffer(c.rowptr, np.int64)
+        ci, cip = _as_buffer(c.colind, np.int32)
+        va, vap = _as_buffer(c.val, np.float64)
+        keep += [rp, ci, va]
+        arr[k] = N.ssm_csr(int(c.n), int(len(c.val)), rpp, cip, vap)
+    h = C.c_void_p()
+    _check(lib, lib.ssm_plan_create_batched(C.byref(h), len(csrs), arr, C.byref(p), _stream(stream)), None)
+    plan = Plan(h, p, is_stencil=False)
+    plan.batch = len(csrs)
+    return plan
+
+
+def ssm_batch_info(plan: Plan, b: int) -> dict:
+    lib = N.load()
+    a, bb, lo, hi = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    n = C.c_int64()
+    _check(lib, lib.ssm_batch_info(plan.handle, int(b), C.byref(a), C.byref(bb), C.byref(lo), C.byref(hi),
+                                   C.byref(n)), plan.handle)
+    return dict(a=a.value, b=bb.value, lo=lo.value, hi=hi.value, n=n.value)
 
 
 def ssm_plan_info(plan: Plan) -> dict:
@@ -145,7 +182,10 @@ def ssm_moments(plan: Plan, W, return_moments: bool = False):
     out = None
     optr = None
     if return_moments:
-        out, optr = _empty_like_input(W, (plan.degree + 1, plan.n_tot, plan.n_tot), np.float64)
+        shp = (plan.degree + 1, plan.n_tot, plan.n_tot)
+        if getattr(plan, "batch", 0):
+            shp = (plan.batch,) + shp
+        out, optr = _empty_like_input(W, shp, np.float64)
     _check(lib, lib.ssm_moments(plan.handle, Wp, ldw, optr), plan.handle)
     return out
 
@@ -183,6 +223,62 @@ def ssm_trace_f(plan: Plan, f: Callable[[float], float], n_t: int, sigma: float,
     _check(lib, lib.ssm_trace_f(plan.handle, cb, None, int(n_t), float(sigma), float(sigma_tilde), float(a),
                                 C.byref(tr_ss), C.byref(tr_kpm)), plan.handle)
     return tr_ss.value, tr_kpm.value
+
+
+def ssm_trace_weights(plan: Plan, f: Callable[[float], float], n_t: int, sigma: float,
+                      sigma_tilde: float = 0.016, a: float = 0.93, device=None):
+    """ssm_trace_weights: (x, w) with Tr f(A) ~= sum_i w_i phi_KPM(x_i) (Alg. 8's quadrature)."""
+    lib = N.load()
+    cb = N.TRACE_FN(lambda x, ctx: float(f(x)))
+    ref = torch.empty(0, device=device) if (device is not None and torch is not None) else None
+    x, xp = _empty_like_input(ref, (int(n_t),), np.float64)
+    w, wp = _empty_like_input(ref, (int(n_t),), np.float64)
+    _check(lib, lib.ssm_trace_weights(plan.handle, cb, None, int(n_t), float(sigma), float(sigma_tilde), float(a),
+                                      xp, wp), plan.handle)
+    return x, w
+
+
+def ssm_plan_set_diag(plan: Plan, diag):
+    """ssm_plan_set_diag: replace a stencil operator's diagonal (the interval (a, b) stays)."""
+    lib = N.load()
+    db, dp = _as_buffer(diag, np.float64)
+    _check(lib, lib.ssm_plan_set_diag(plan.handle, dp), plan.handle)
+
+
+def ssm_kpm_adjoint(plan: Plan, t, sigma: float, w):
+    """ssm_kpm_adjoint: g_l = sum_i w_i mu_l(t_i) / n_tot (dL/dX_l = g_l I), M+1 values."""
+    lib = N.load()
+    tb, tp = _as_buffer(t, np.float64)
+    wb, wp = _as_buffer(w, np.float64)
+    n_t = int(tb.shape[0])
+    if int(wb.shape[0]) != n_t:
+        raise ValueError("t and w must have the same length")
+    g, gp = _empty_like_input(t, (plan.degree + 1,), np.float64)
+    _check(lib, lib.ssm_kpm_adjoint(plan.handle, tp, n_t, float(sigma), wp, gp), plan.handle)
+    return g
+
+
+def ssm_moments_adjoint(plan: Plan, dL_dX):
+    """ssm_moments_adjoint: (dL/d diag, dL/d offdiag) from dL/dX_l.
+
+    dL_dX of shape (M+1,) means G_l = dL_dX[l] I (kind 1); shape (M+1, n_tot, n_tot)
+    gives the matrices (kind 0).  dL/d offdiag has 3 entries for a stencil plan
+    (per axis) and nnz entries for a CSR plan (per stored entry).
+    """
+    lib = N.load()
+    gb, gp = _as_buffer(dL_dX, np.float64)
+    shp = tuple(gb.shape)
+    if shp == (plan.degree + 1,):
+        kind = 1
+    elif shp == (plan.degree + 1, plan.n_tot, plan.n_tot):
+        kind = 0
+    else:
+        raise ValueError(f"dL_dX must have shape ({plan.degree + 1},) or "
+                         f"({plan.degree + 1}, {plan.n_tot}, {plan.n_tot}), got {shp}")
+    dd, ddp = _empty_like_input(dL_dX, (plan.n,), np.float64)
+    do, dop = _empty_like_input(dL_dX, (3 if plan.is_stencil else plan.nnz,), np.float64)
+    _check(lib, lib.ssm_moments_adjoint(plan.handle, gp, kind, ddp, dop), plan.handle)
+    return dd, do
 
 
 def ssm_gram_pair(A, B=None, stream=None):

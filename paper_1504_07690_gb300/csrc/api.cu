@@ -36,13 +36,16 @@ struct ssm_plan_s {
     // trace buffers
     double* d_tr = nullptr;
     size_t cap_tr = 0;
+    // batched plans: per-point floor scale
+    double* d_fpt = nullptr;
+    size_t cap_fpt = 0;
 };
 
 namespace {
 
 thread_local std::string g_create_error;
 
-enum Phase { PH_COEFFS, PH_REC, PH_GRAM, PH_REDUCE, PH_ASSEMBLE, PH_SOLVE, PH_KPM, PH_TRACE };
+enum Phase { PH_COEFFS, PH_REC, PH_GRAM, PH_REDUCE, PH_ASSEMBLE, PH_SOLVE, PH_KPM, PH_TRACE, PH_ADJOINT };
 
 // Sweep points per assembly / solve batch: all of them when the per-point
 // matrices (K and K_Z, float64) fit in 2 GiB, so that every SM holds several
@@ -50,7 +53,7 @@ enum Phase { PH_COEFFS, PH_REC, PH_GRAM, PH_REDUCE, PH_ASSEMBLE, PH_SOLVE, PH_KP
 int64_t batch_points(const Plan& P) {
     const size_t per = sizeof(double) * ((size_t)P.n_tot * P.n_tot + (size_t)P.p.n_v * P.p.n_v);
     int64_t b = (int64_t)(((size_t)2 << 30) / per);
-    if (b > 4096) b = 4096;
+    if (b > (1 << 20)) b = 1 << 20;
     if (b < 64) b = 64;
     return b;
 }
@@ -156,6 +159,7 @@ void settle_marks(ssm_plan_s* h) {
             case PH_REDUCE: s.ms_reduce += ms; break;
             case PH_ASSEMBLE: s.ms_assemble += ms; break;
             case PH_SOLVE: s.ms_solve += ms; break;
+            case PH_ADJOINT: s.ms_adjoint += ms; break;
             case PH_KPM: s.ms_kpm += ms; break;
             case PH_TRACE: s.ms_trace += ms; break;
         }
@@ -208,6 +212,28 @@ void free_plan(ssm_plan_s* h) {
     dev_free(P.d_stage);
     dev_free(P.d_ctab);
     dev_free(P.d_work);
+    dev_free(P.d_ck);
+    dev_free(P.d_seg);
+    for (auto& u : P.d_U) dev_free(u);
+    dev_free(P.d_Gb);
+    dev_free(P.d_Bm);
+    dev_free(P.d_G);
+    dev_free(P.d_G1p);
+    dev_free(P.d_D);
+    dev_free(P.d_EF);
+    dev_free(P.d_adjsum);
+    dev_free(P.d_rawdiag);
+    dev_free(P.d_beta_row64);
+    dev_free(P.d_beta_row32);
+    dev_free(P.d_slabs);
+    dev_free(P.d_slabseg);
+    dev_free(P.d_x0max);
+    delete[] P.h_row_off;
+    delete[] P.h_nb;
+    delete[] P.h_ab;
+    if (P.graph) cudaGraphExecDestroy(P.graph);
+    if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
+    dev_free(h->d_fpt);
     dev_free(h->d_t);
     dev_free(h->d_mu);
     dev_free(h->d_nu);
@@ -276,12 +302,15 @@ ssm_status ensure_points(ssm_plan_s* h, int64_t n_t) {
 
 // Coefficient tables for n points at d_tpts (device): mu -> dmu, nu -> dnu (ld M+1).
 ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, double sigma, double* dmu,
-                            double* dnu) {
+                            double* dnu, int mat = -1) {
     Plan& P = h->P;
     const int M = P.p.degree;
-    const double inv_norm = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
+    // batched plans: the interval and size of matrix `mat`
+    const double a = mat >= 0 ? P.h_ab[6 * mat] : P.a, b = mat >= 0 ? P.h_ab[6 * mat + 1] : P.b;
+    const double nrows = mat >= 0 ? (double)P.h_nb[mat] : (double)P.n;
+    const double inv_norm = 1.0 / (nrows * sqrt(2.0 * M_PI * sigma * sigma));
     Scope sc(h, PH_COEFFS);
-    CUDA_OR_FAIL(h, launch_mu(d_tpts, n, sigma, inv_norm, P.a, P.b, M, P.n_theta, P.d_ctab, dmu, M + 1, P.stream));
+    CUDA_OR_FAIL(h, launch_mu(d_tpts, n, sigma, inv_norm, a, b, M, P.n_theta, P.d_ctab, dmu, M + 1, P.stream));
     P.stats.launches++;
     if (dnu) {
         CUDA_OR_FAIL(h, launch_nu(dmu, M + 1, n, M, dnu, M + 1, P.stream));
@@ -291,7 +320,7 @@ ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, doub
 }
 
 // DOS at n device points d_tpts into h->d_dos_ss / h->d_dos_kpm (device), ranks into h->d_rank.
-ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigma) {
+ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigma, bool want_ss = true) {
     Plan& P = h->P;
     const int M = P.p.degree, K = M / 2;
     const int nv = P.p.n_v, nvh = P.p.n_vh, n_tot = P.n_tot;
@@ -300,15 +329,15 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
     const int64_t bt = batch_points(P);
     for (int64_t t0 = 0; t0 < n_t; t0 += bt) {
         const int64_t nb = (n_t - t0) < bt ? (n_t - t0) : bt;
-        ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, h->d_nu);
+        ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, want_ss ? h->d_nu : nullptr);
         if (st != SSM_OK) return st;
-        {
+        if (want_ss) {
             Scope sc(h, PH_ASSEMBLE);
             CUDA_OR_FAIL(h, launch_assemble(h->d_mu, M + 1, nb, K + 1, P.d_X, n_tot, n_tot, n_tot, h->d_K, P.stream));
             CUDA_OR_FAIL(h, launch_assemble(h->d_nu, M + 1, nb, M + 1, P.d_X, n_tot, nv, nv, h->d_KZ, P.stream));
             P.stats.launches += 2;
         }
-        {
+        if (want_ss) {
             Scope sc(h, PH_SOLVE);
             const double floor_scale = 8.0 * nv * P.eps_floor * P.x0max;
             CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, h->d_mu, M + 1, K,
@@ -322,6 +351,226 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
             P.stats.launches += 2;
         }
     }
+    return SSM_OK;
+}
+
+// Batched plans: n_t = B n_tp points, block b of n_tp points for matrix b.
+// Coefficients, assembly and the KPM line run per matrix (each has its own
+// interval, size and moments); the per-point solves of all matrices of a
+// batch run in one launch.
+ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigma, bool want_ss) {
+    Plan& P = h->P;
+    const int M = P.p.degree, K = M / 2;
+    const int nv = P.p.n_v, nvh = P.p.n_vh, n_tot = P.n_tot;
+    const int64_t n_tp = n_t / P.B;
+    const size_t xs = (size_t)(M + 1) * n_tot * n_tot;
+    int64_t mb = batch_points(P) / (n_tp > 0 ? n_tp : 1);
+    if (mb < 1) mb = 1;
+    if ((size_t)(3 * n_t) > h->cap_fpt) {
+        dev_free(h->d_fpt);
+        h->d_fpt = nullptr;
+        h->cap_fpt = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_fpt, 3 * n_t));
+        h->cap_fpt = 3 * n_t;
+    }
+    // per point: rounding floor scale and range filter [xlo, xhi] of its matrix
+    std::vector<double> fpt(3 * n_t);
+    std::vector<double> x0(P.B);
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(x0.data(), P.d_x0max, P.B * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    for (int b = 0; b < P.B; ++b) {
+        const double gmax = 1.0 / ((double)P.h_nb[b] * sqrt(2.0 * M_PI * sigma * sigma));
+        for (int64_t i = 0; i < n_tp; ++i) {
+            double* q = &fpt[3 * (b * n_tp + i)];
+            q[0] = 8.0 * nv * P.eps_floor * x0[b];
+            q[1] = -P.p.kappa * gmax;
+            q[2] = (1.0 + P.p.kappa) * gmax;
+        }
+    }
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_fpt, fpt.data(), 3 * n_t * sizeof(double), cudaMemcpyHostToDevice,
+                                    P.stream));
+    for (int64_t b0 = 0; b0 < P.B; b0 += mb) {
+        const int64_t b1 = b0 + mb < P.B ? b0 + mb : P.B;
+        for (int64_t b = b0; b < b1; ++b) {
+            const int64_t off = (b - b0) * n_tp;
+            ssm_status st = coefficients_dev(h, d_tpts + b * n_tp, n_tp, sigma, h->d_mu + off * (M + 1),
+                                             want_ss ? h->d_nu + off * (M + 1) : nullptr, (int)b);
+            if (st != SSM_OK) return st;
+            if (want_ss) {
+                Scope sc(h, PH_ASSEMBLE);
+                CUDA_OR_FAIL(h, launch_assemble(h->d_mu + off * (M + 1), M + 1, n_tp, K + 1, P.d_X + b * xs, n_tot,
+                                                n_tot, n_tot, h->d_K + off * n_tot * n_tot, P.stream));
+                CUDA_OR_FAIL(h, launch_assemble(h->d_nu + off * (M + 1), M + 1, n_tp, M + 1, P.d_X + b * xs, n_tot,
+                                                nv, nv, h->d_KZ + off * nv * nv, P.stream));
+                P.stats.launches += 2;
+            }
+            {
+                Scope sc(h, PH_KPM);
+                CUDA_OR_FAIL(h, launch_kpm(h->d_mu + off * (M + 1), M + 1, n_tp, M, P.d_X + b * xs, n_tot, h->d_zeta,
+                                           h->d_dos_kpm + b * n_tp, P.stream));
+                P.stats.launches += 2;
+            }
+        }
+        if (want_ss) {
+            Scope sc(h, PH_SOLVE);
+            const int64_t nb = (b1 - b0) * n_tp;
+            CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, 0.0, 0.0, h->d_mu, M + 1, K, 0.0,
+                                         h->d_solve, h->d_dos_ss + b0 * n_tp, h->d_rank + 2 * b0 * n_tp, P.d_flag,
+                                         P.stream, h->d_fpt + 3 * b0 * n_tp));
+            P.stats.launches++;
+        }
+    }
+    return SSM_OK;
+}
+
+// Batched plans: the whole recurrence with its Gram products and reductions
+// (a3, a4 for every matrix) is one CUDA graph, captured on the first call and
+// replayed: one launch per ssm_moments, whatever the number of matrices.
+cudaError_t record_batched_moments(Plan& P, cudaStream_t cs) {
+    const int M = P.p.degree, S = M / 2, B = P.B;
+    const size_t nn = (size_t)P.n_tot * P.n_tot, xs = (size_t)(M + 1) * nn;
+    const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
+    cudaError_t e = launch_check_finite(P.d_stage, P.n * (int64_t)P.n_tot, P.d_flag, cs);
+    if (e == cudaSuccess) e = launch_convert_in(P.d_stage, P.n_tot, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, cs);
+    if (e == cudaSuccess && P.use_tc) e = launch_panelize(P, (const float*)P.d_V[0], P.d_panel[0], cs);
+    auto gram_reduce = [&](const void* Vn, const void* Vc, int j, int step) -> cudaError_t {
+        if (P.use_tc) {
+            cudaError_t r = launch_gram_tc(P.d_panel[j & 1], Vc ? P.d_panel[(j + 1) & 1] : nullptr, P.n_tot, P.n,
+                                           P.tc_ne, P.tc_no, P.d_part_tc, P.d_flag, cs, P.d_slabs);
+            if (r != cudaSuccess) return r;
+            return launch_reduce_tc_seg(P.d_part_tc, P.tc_ne, P.n_tot, B, P.d_slabseg, P.d_ring_sum,
+                                        P.d_ring_sum + (size_t)B * nn, P.d_X, xs, step, cs);
+        }
+        for (int b = 0; b < B; ++b) {
+            const size_t off = (size_t)P.h_row_off[b] * P.ld * esz;
+            const void* A = (const uint8_t*)Vn + off;
+            const void* C = Vc ? (const void*)((const uint8_t*)Vc + off) : nullptr;
+            cudaError_t r = P.mixed ? launch_gram_f32((const float*)A, (const float*)C, P.ld, P.n_tot, P.h_nb[b],
+                                                      P.n_split, P.d_part, cs)
+                                    : launch_gram_f64((const double*)A, (const double*)C, P.ld, P.n_tot, P.h_nb[b],
+                                                      P.n_split, P.d_part, cs);
+            if (r == cudaSuccess) r = launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X + b * xs, step, cs);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
+    if (e == cudaSuccess) e = gram_reduce(P.d_V[0], nullptr, 0, -1);
+    for (int k = 0; k < S && e == cudaSuccess; ++k) {
+        void* Vc = P.d_V[k % 3];
+        void* Vp = P.d_V[(k + 2) % 3];
+        void* Vn = P.d_V[(k + 1) % 3];
+        const double c = (k == 0) ? 0.5 : 1.0, d = (k == 0) ? 0.0 : 1.0;
+        if (P.mixed)
+            e = launch_csr_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn, (float)c, (float)d,
+                                    P.use_tc ? P.d_panel[(k + 1) & 1] : nullptr, cs);
+        else
+            e = launch_csr_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d, cs);
+        if (e == cudaSuccess) e = gram_reduce(Vn, Vc, k + 1, k);
+    }
+    if (e == cudaSuccess) e = launch_check_finite(P.d_X, (int64_t)B * (M + 1) * nn, P.d_flag, cs);
+    return e;
+}
+
+// Project autotuner of the batched recurrence: times the CSR step with 64,
+// 128 and 256 threads per 32-row panel on the plan's own operator and keeps
+// the fastest (CUDA events, 2 warm-up and 3 timed launches each).
+cudaError_t autotune_csr(Plan& P) {
+    const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
+    for (auto v : P.d_V) {
+        cudaError_t e = cudaMemsetAsync(v, 0, (size_t)P.n * P.ld * esz, P.stream);
+        if (e != cudaSuccess) return e;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int pick = 256;
+    const int cand[3] = {64, 128, 256};
+    cudaError_t err = cudaSuccess;
+    for (int ci = 0; ci < 3 && err == cudaSuccess; ++ci) {
+        P.csr_threads = cand[ci];
+        float ms = 0.f;
+        for (int r = 0; r < 5 && err == cudaSuccess; ++r) {
+            if (r == 2) cudaEventRecord(e0, P.stream);
+            err = P.mixed ? launch_csr_step_f32(P, (const float*)P.d_V[0], (const float*)P.d_V[1], (float*)P.d_V[2],
+                                                1.f, 1.f, P.use_tc ? P.d_panel[0] : nullptr, P.stream)
+                          : launch_csr_step_f64(P, (const double*)P.d_V[0], (const double*)P.d_V[1],
+                                                (double*)P.d_V[2], 1.0, 1.0, P.stream);
+        }
+        cudaEventRecord(e1, P.stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            pick = cand[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P.csr_threads = pick;
+    return err;
+}
+
+ssm_status moments_batched(ssm_plan_s* h, const double* W, int64_t ldw, double* moments) {
+    Plan& P = h->P;
+    const int M = P.p.degree, B = P.B;
+    const size_t nn = (size_t)P.n_tot * P.n_tot, xs = (size_t)(M + 1) * nn;
+    ssm_status s = ensure_stage(h, (size_t)P.n * P.n_tot * sizeof(double));
+    if (s != SSM_OK) return s;
+    // W (matrices' probe blocks stacked) -> stage with each matrix at its padded row offset
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_stage, 0, (size_t)P.n * P.n_tot * sizeof(double), P.stream));
+    int64_t src = 0;
+    for (int b = 0; b < B; ++b) {
+        CUDA_OR_FAIL(h, cudaMemcpy2DAsync(P.d_stage + (size_t)P.h_row_off[b] * P.n_tot, P.n_tot * sizeof(double),
+                                          W + (size_t)src * ldw, ldw * sizeof(double), P.n_tot * sizeof(double),
+                                          P.h_nb[b], cudaMemcpyDefault, P.stream));
+        src += P.h_nb[b];
+    }
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
+    if (!P.graph) {
+        if (P.csr_threads == 0) CUDA_OR_FAIL(h, autotune_csr(P));
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+        CUDA_OR_FAIL(h, cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = record_batched_moments(P, P.cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(P.cap_stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P.graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            P.graph = nullptr;
+            return fail(h, SSM_ECUDA, std::string("capturing the batched recurrence: ") + cudaGetErrorString(e));
+        }
+    }
+    {
+        Scope sc(h, PH_REC);
+        CUDA_OR_FAIL(h, cudaGraphLaunch(P.graph, P.stream));
+        P.stats.launches++;
+        P.stats.recurrence_launches += P.p.degree / 2;
+    }
+    if (moments) CUDA_OR_FAIL(h, from_device(moments, P.d_X, (size_t)B * xs * sizeof(double), P.stream));
+    s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    int flag = 0;
+    s = read_flag(h, &flag);
+    if (s != SSM_OK) return s;
+    if (flag & 2) return fail(h, SSM_ETIMEOUT, "a tensor-core Gram wait gave up (bounded mbarrier wait)");
+    if (flag) return fail(h, SSM_ENONFINITE, "W or the moments contain NaN/Inf");
+    std::vector<double> d0((size_t)B * P.p.n_v), x0(B);
+    for (int b = 0; b < B; ++b)
+        CUDA_OR_FAIL(h, cudaMemcpy2DAsync(d0.data() + (size_t)b * P.p.n_v, sizeof(double), P.d_X + b * xs,
+                                          (P.n_tot + 1) * sizeof(double), sizeof(double), P.p.n_v,
+                                          cudaMemcpyDeviceToHost, P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    for (int b = 0; b < B; ++b) {
+        double m = 0.0;
+        for (int i = 0; i < P.p.n_v; ++i) m = fmax(m, d0[(size_t)b * P.p.n_v + i]);
+        x0[b] = m;
+    }
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(P.d_x0max, x0.data(), B * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    P.x0max = x0[0];
+    P.have_moments = true;
     return SSM_OK;
 }
 
@@ -370,14 +619,15 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if (p.precision != SSM_FP64 && p.precision != SSM_MIXED) return fail(nullptr, SSM_EINVAL, "unknown precision");
     if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
     if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
+    if (p.options & ~3) return fail(nullptr, SSM_EINVAL, "unknown option bits");
 
     ssm_plan_s* h = new ssm_plan_s();
     Plan& P = h->P;
     P.p = p;
     if (P.p.tau <= 0.0) P.p.tau = 1e-7;
     if (P.p.kappa < 0.0) P.p.kappa = 1e-6;
-    if (P.p.eps_floor == 0.0)
-        P.eps_floor = (p.precision == SSM_MIXED) ? 1.0 / 8388608.0 : 1.0 / 4503599627370496.0;
+    if (P.p.eps_floor == 0.0)  // 2^-36 (mixed, measured) and 2^-52 (float64)
+        P.eps_floor = (p.precision == SSM_MIXED) ? 1.0 / 68719476736.0 : 1.0 / 4503599627370496.0;
     else
         P.eps_floor = P.p.eps_floor > 0.0 ? P.p.eps_floor : 0.0;
     if (!isfinite(p.eps_floor)) return fail(nullptr, SSM_EINVAL, "eps_floor must be finite");
@@ -507,6 +757,8 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         P.beta = -2.0 * (P.a + P.b) / (P.b - P.a);
     }
     // fold the map into the operator
+    P.extra = extra;
+    for (int a = 0; a < 3; ++a) P.raw_off[a] = raw_off[a];
     if (P.is_stencil) {
         CREATE_CUDA(dev_alloc(&P.d_diag64, P.n));
         CREATE_CUDA(dev_alloc(&P.d_diag32, P.n));
@@ -529,6 +781,16 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if ((uint64_t)P.n * (uint64_t)(P.ld / vec) >= (1ULL << 32)) return bail(SSM_EINVAL, "N x n_tot too large");
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
     for (auto& v : P.d_V) CREATE_CUDA(cudaMalloc(&v, (size_t)P.n * P.ld * esz));
+    if (p.options & 2) {
+        // checkpoints (V_{jc}, V_{jc+1}) every c = ceil(sqrt(S)) steps for the adjoint
+        const int S = p.degree / 2;
+        int c = (int)ceil(sqrt((double)S));
+        if (c < 1) c = 1;
+        P.adjoint = true;
+        P.ck_c = c;
+        P.n_ck = (S + c - 1) / c;
+        CREATE_CUDA(cudaMalloc(&P.d_ck, (size_t)2 * P.n_ck * P.n * P.ld * esz));
+    }
     P.use_tc = P.mixed && !(p.options & 1) && gram_tc_supported(P.n_tot, P.ld);
     if (P.use_tc) {
         gram_tc_slabs(P.n, &P.tc_ne, &P.tc_no);
@@ -561,6 +823,213 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     return SSM_OK;
 }
 
+ssm_status ssm_plan_create_batched(ssm_plan_t* out, int32_t B, const ssm_csr* csrs, const ssm_params* params,
+                                   void* stream) {
+    if (!out) return fail(nullptr, SSM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (B < 1 || B > (1 << 20) || !csrs) return fail(nullptr, SSM_EINVAL, "need 1 <= B <= 2^20 and csrs");
+    if (!params) return fail(nullptr, SSM_EINVAL, "params is NULL");
+    const ssm_params& p = *params;
+    if (p.options & 2) return fail(nullptr, SSM_EINVAL, "the adjoint option is not available for batched plans");
+    // host copies of every operator (the inputs may live on the device)
+    std::vector<int64_t> row_off(B + 1, 0), nb(B), nnz_off(B + 1, 0);
+    for (int b = 0; b < B; ++b) {
+        const ssm_csr& c = csrs[b];
+        if (c.n < 1 || c.nnz < 0 || !c.rowptr || (c.nnz > 0 && (!c.colind || !c.val)))
+            return fail(nullptr, SSM_EINVAL, "batched csr " + std::to_string(b) + ": bad size or NULL arrays");
+        nb[b] = c.n;
+        row_off[b + 1] = row_off[b] + (c.n + 31) / 32 * 32;  // panels never straddle two matrices
+        nnz_off[b + 1] = nnz_off[b] + c.nnz;
+    }
+    const int64_t NR = row_off[B], NNZ = nnz_off[B];
+    if (NR > (1LL << 31) - 1) return fail(nullptr, SSM_EINVAL, "batched operator too large");
+    std::vector<int64_t> rp(NR + 1, 0);
+    std::vector<int32_t> ci(NNZ);
+    std::vector<double> va(NNZ);
+    for (int b = 0; b < B; ++b) {
+        const ssm_csr& c = csrs[b];
+        std::vector<int64_t> r(c.n + 1);
+        if (is_device_ptr(c.rowptr)) {
+            if (cudaMemcpy(r.data(), c.rowptr, (c.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(nullptr, SSM_ECUDA, "copying a batched csr");
+        } else {
+            memcpy(r.data(), c.rowptr, (c.n + 1) * sizeof(int64_t));
+        }
+        if (r[0] != 0 || r[c.n] != c.nnz)
+            return fail(nullptr, SSM_EINVAL, "batched csr " + std::to_string(b) + ": rowptr must run from 0 to nnz");
+        for (int64_t i = 0; i < c.n; ++i)
+            if (r[i + 1] < r[i]) return fail(nullptr, SSM_EINVAL, "batched csr rowptr decreases");
+        const int64_t e0 = nnz_off[b];
+        if (c.nnz > 0) {
+            const bool dc = is_device_ptr(c.colind), dv = is_device_ptr(c.val);
+            if (dc) cudaMemcpy(ci.data() + e0, c.colind, c.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost);
+            else memcpy(ci.data() + e0, c.colind, c.nnz * sizeof(int32_t));
+            if (dv) cudaMemcpy(va.data() + e0, c.val, c.nnz * sizeof(double), cudaMemcpyDeviceToHost);
+            else memcpy(va.data() + e0, c.val, c.nnz * sizeof(double));
+        }
+        for (int64_t e = 0; e < c.nnz; ++e) {
+            const int32_t j = ci[e0 + e];
+            if (j < 0 || j >= c.n) return fail(nullptr, SSM_EINVAL, "batched csr column out of range");
+            ci[e0 + e] = (int32_t)(j + row_off[b]);
+        }
+        for (int64_t i = 0; i < c.n; ++i) rp[row_off[b] + i + 1] = e0 + r[i + 1];
+        for (int64_t i = row_off[b] + c.n; i < row_off[b + 1]; ++i) rp[i + 1] = e0 + c.nnz;  // padding rows
+    }
+    // one block-diagonal operator through the single-operator set-up (validation,
+    // bounds of the whole, folding), then per-matrix intervals and folds below
+    ssm_csr all{NR, NNZ, rp.data(), ci.data(), va.data()};
+    ssm_params q = p;
+    q.lo = q.hi = 0.0;
+    ssm_plan_t hh = nullptr;
+    ssm_status st = ssm_plan_create(&hh, nullptr, &all, &q, stream);
+    if (st != SSM_OK) return st;
+    ssm_plan_s* h = hh;
+    Plan& P = h->P;
+    P.p.lo = p.lo;
+    P.p.hi = p.hi;
+    P.B = B;
+    P.h_row_off = new int64_t[B + 1];
+    P.h_nb = new int64_t[B];
+    P.h_ab = new double[6 * (size_t)B];
+    for (int b = 0; b <= B; ++b) P.h_row_off[b] = row_off[b];
+    for (int b = 0; b < B; ++b) P.h_nb[b] = nb[b];
+    auto bail = [&](ssm_status s2, const std::string& m) {
+        cudaStreamSynchronize(P.stream);
+        free_plan(h);
+        return fail(nullptr, s2, m);
+    };
+#define BCUDA(call)                                                                                           \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess)                                                                                \
+            return bail(e_ == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA,                            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                                  \
+    } while (0)
+    // per-matrix Gershgorin intervals (a1) and the fold of each matrix's map
+    double* d_raw = nullptr;
+    double* d_bnd = nullptr;
+    BCUDA(dev_alloc(&d_raw, NNZ));
+    BCUDA(cudaMemcpyAsync(d_raw, va.data(), NNZ * sizeof(double), cudaMemcpyHostToDevice, P.stream));
+    int64_t maxn = 1;
+    for (int b = 0; b < B; ++b) maxn = nb[b] > maxn ? nb[b] : maxn;
+    const int nbmax = operator_bound_blocks(maxn);
+    BCUDA(dev_alloc(&d_bnd, 2 * (size_t)nbmax * B));
+    for (int b = 0; b < B; ++b)
+        BCUDA(launch_csr_bounds_range(P, d_raw, row_off[b], nb[b], d_bnd + 2 * (size_t)nbmax * b, P.stream));
+    std::vector<double> hb(2 * (size_t)nbmax * B);
+    BCUDA(cudaMemcpyAsync(hb.data(), d_bnd, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    BCUDA(cudaStreamSynchronize(P.stream));
+    std::vector<double> beta_row(NR, 0.0);
+    for (int b = 0; b < B; ++b) {
+        const int nbk = operator_bound_blocks(nb[b]);
+        double lo = hb[2 * (size_t)nbmax * b], hi = hb[2 * (size_t)nbmax * b + 1];
+        for (int i = 1; i < nbk; ++i) {
+            lo = fmin(lo, hb[2 * (size_t)nbmax * b + 2 * i]);
+            hi = fmax(hi, hb[2 * (size_t)nbmax * b + 2 * i + 1]);
+        }
+        double ga = lo, gb = hi, aa, bb;
+        if (p.lo < p.hi) {
+            ga = aa = p.lo;
+            gb = bb = p.hi;
+        } else {
+            double w = hi - lo;
+            if (w <= 0.0) w = fmax(fabs(lo), 1.0);
+            aa = lo - 1e-3 * w;
+            bb = hi + 1e-3 * w;
+        }
+        const double alpha = 4.0 / (bb - aa), beta = -2.0 * (aa + bb) / (bb - aa);
+        double* ab = P.h_ab + 6 * (size_t)b;
+        ab[0] = aa;
+        ab[1] = bb;
+        ab[2] = ga;
+        ab[3] = gb;
+        ab[4] = alpha;
+        ab[5] = beta;
+        BCUDA(launch_fold_csr_range(P, d_raw, alpha, nnz_off[b], nnz_off[b + 1], P.stream));
+        for (int64_t i = row_off[b]; i < row_off[b] + nb[b]; ++i) beta_row[i] = beta;
+    }
+    P.a = P.h_ab[0];
+    P.b = P.h_ab[1];
+    P.glo = P.h_ab[2];
+    P.ghi = P.h_ab[3];
+    P.alpha = P.h_ab[4];
+    P.beta = 0.0;  // per-row beta below
+    BCUDA(dev_alloc(&P.d_beta_row64, NR));
+    BCUDA(dev_alloc(&P.d_beta_row32, NR));
+    {
+        std::vector<float> b32(NR);
+        for (int64_t i = 0; i < NR; ++i) b32[i] = (float)beta_row[i];
+        BCUDA(cudaMemcpyAsync(P.d_beta_row64, beta_row.data(), NR * sizeof(double), cudaMemcpyHostToDevice,
+                              P.stream));
+        BCUDA(cudaMemcpyAsync(P.d_beta_row32, b32.data(), NR * sizeof(float), cudaMemcpyHostToDevice, P.stream));
+        BCUDA(cudaStreamSynchronize(P.stream));
+    }
+    dev_free(d_raw);
+    dev_free(d_bnd);
+    // per-matrix moments and X_0 maxima
+    dev_free(P.d_X);
+    P.d_X = nullptr;
+    const size_t nn = (size_t)P.n_tot * P.n_tot;
+    BCUDA(dev_alloc(&P.d_X, (size_t)B * (p.degree + 1) * nn));
+    BCUDA(dev_alloc(&P.d_x0max, B));
+    // Gram slabs: each matrix's panels in ~equal slabs, Ge slabs first, then Go
+    if (P.use_tc) {
+        dev_free(P.d_part_tc);
+        dev_free(P.d_ring);
+        dev_free(P.d_ring_sum);
+        P.d_part_tc = P.d_ring = nullptr;
+        P.d_ring_sum = nullptr;
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t tot_pan = NR / 32;
+        const int64_t pe = (tot_pan + sms - 1) / sms, po = (tot_pan + 2 * sms - 1) / (2 * sms);
+        std::vector<int2> slabs;
+        std::vector<int> seg(2 * (B + 1), 0);
+        for (int pass = 0; pass < 2; ++pass) {
+            const int64_t per = pass == 0 ? (pe < 1 ? 1 : pe) : (po < 1 ? 1 : po);
+            const int base = (int)slabs.size();
+            for (int b = 0; b < B; ++b) {
+                seg[pass * (B + 1) + b] = (int)slabs.size() - base;
+                const int64_t p0 = row_off[b] / 32, p1 = row_off[b + 1] / 32;
+                const int64_t k = (p1 - p0 + per - 1) / per;
+                for (int64_t j = 0; j < k; ++j) {
+                    const int64_t a0 = p0 + (p1 - p0) * j / k, a1 = p0 + (p1 - p0) * (j + 1) / k;
+                    slabs.push_back(make_int2((int)a0, (int)a1));
+                }
+            }
+            seg[pass * (B + 1) + B] = (int)slabs.size() - base;
+            if (pass == 0) P.tc_ne = (int)slabs.size();
+        }
+        P.tc_no = (int)slabs.size() - P.tc_ne;
+        BCUDA(dev_alloc(&P.d_slabs, slabs.size()));
+        BCUDA(dev_alloc(&P.d_slabseg, seg.size()));
+        BCUDA(cudaMemcpyAsync(P.d_slabs, slabs.data(), slabs.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                              P.stream));
+        BCUDA(cudaMemcpyAsync(P.d_slabseg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, P.stream));
+        BCUDA(dev_alloc(&P.d_part_tc, gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot)));
+        BCUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * B * nn));  // per-matrix float64 slab sums
+    }
+    BCUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+    BCUDA(cudaStreamSynchronize(P.stream));
+#undef BCUDA
+    *out = h;
+    return SSM_OK;
+}
+
+ssm_status ssm_batch_info(ssm_plan_t h, int32_t b, double* a, double* bb, double* lo, double* hi, int64_t* n) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    const Plan& P = h->P;
+    if (P.B < 1 || b < 0 || b >= P.B) return fail(h, SSM_EINVAL, "not a batched plan, or b out of range");
+    const double* ab = P.h_ab + 6 * (size_t)b;
+    if (a) *a = ab[0];
+    if (bb) *bb = ab[1];
+    if (lo) *lo = ab[2];
+    if (hi) *hi = ab[3];
+    if (n) *n = P.h_nb[b];
+    return SSM_OK;
+}
+
 ssm_status ssm_plan_info(ssm_plan_t h, double* a, double* b, double* lo, double* hi, int64_t* n, int64_t* nnz) {
     if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
     if (a) *a = h->P.a;
@@ -579,6 +1048,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     if (ldw < P.n_tot) return fail(h, SSM_EINVAL, "ldw < n_v + n_vh");
     CUDA_OR_FAIL(h, cudaSetDevice(P.device));
     P.have_moments = false;
+    if (P.B > 0) return moments_batched(h, W, ldw, moments);
     const int M = P.p.degree, S = M / 2;
     const size_t nn = (size_t)P.n_tot * P.n_tot;
     // W -> V_0 (working precision, zero-padded to ld)
@@ -655,6 +1125,12 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
             P.stats.launches++;
             P.stats.recurrence_launches++;
         }
+        if (P.adjoint && (k % P.ck_c) == 0) {
+            const size_t bb = (size_t)P.n * P.ld * (P.mixed ? sizeof(float) : sizeof(double));
+            uint8_t* ck = (uint8_t*)P.d_ck + (size_t)(2 * (k / P.ck_c)) * bb;
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(ck, Vc, bb, cudaMemcpyDeviceToDevice, P.stream));
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(ck + bb, Vn, bb, cudaMemcpyDeviceToDevice, P.stream));
+        }
         {
             Scope sc(h, PH_GRAM);
             CUDA_OR_FAIL(h, gram(Vn, Vc, k + 1));
@@ -703,6 +1179,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
 ssm_status ssm_coefficients(ssm_plan_t h, const double* t, int64_t n_t, double sigma, double* mu, double* nu) {
     if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
     Plan& P = h->P;
+    if (P.B > 0) return fail(h, SSM_EINVAL, "not available for batched plans");
     if (n_t < 0 || !(sigma > 0.0) || !isfinite(sigma)) return fail(h, SSM_EINVAL, "need n_t >= 0 and sigma > 0");
     if (n_t == 0) return SSM_OK;
     if (!t) return fail(h, SSM_EINVAL, "t is NULL");
@@ -747,7 +1224,12 @@ ssm_status ssm_dos(ssm_plan_t h, const double* t, int64_t n_t, double sigma, dou
     ssm_status s = ensure_points(h, n_t);
     if (s != SSM_OK) return s;
     CUDA_OR_FAIL(h, to_device(h->d_t, t, n_t * sizeof(double), P.stream));
-    s = dos_dev(h, h->d_t, n_t, sigma);
+    if (P.B > 0) {
+        if (n_t % P.B) return fail(h, SSM_EINVAL, "a batched plan takes B blocks of equally many points");
+        s = dos_dev_batched(h, h->d_t, n_t, sigma, dos_ss != nullptr || rank != nullptr);
+    } else {
+        s = dos_dev(h, h->d_t, n_t, sigma, dos_ss != nullptr || rank != nullptr);
+    }
     if (s != SSM_OK) return s;
     if (dos_ss) CUDA_OR_FAIL(h, from_device(dos_ss, h->d_dos_ss, n_t * sizeof(double), P.stream));
     if (dos_kpm) CUDA_OR_FAIL(h, from_device(dos_kpm, h->d_dos_kpm, n_t * sizeof(double), P.stream));
@@ -757,14 +1239,21 @@ ssm_status ssm_dos(ssm_plan_t h, const double* t, int64_t n_t, double sigma, dou
     return check_solver_flag(h);
 }
 
-ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int64_t n_t, double sigma,
-                       double sigma_tilde, double a, double* tr_ss, double* tr_kpm) {
-    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+}  // extern "C"
+
+namespace {
+
+// Alg. 8 up to the deconvolved f~: periodic grid of n_t points with [lo, hi]
+// mapped onto [-a, a], h (Eq. hform with Eq. pifunc), f~ = h deconvolved by
+// the unit-mass Gaussian.  Device results in h->d_tr: tt, x, fx, h, f~, work;
+// *dx receives the grid spacing in the units of A.
+ssm_status trace_prepare(ssm_plan_s* h, double (*f)(double, void*), void* ctx, int64_t n_t, double sigma,
+                         double sigma_tilde, double a, double* dx_out) {
     Plan& P = h->P;
+    if (P.B > 0) return fail(h, SSM_EINVAL, "Tr f(A) is not available for batched plans");
     if (!f) return fail(h, SSM_EINVAL, "f is NULL");
     if (n_t < 2 || !(sigma > 0.0) || !(sigma_tilde > 0.0) || !(a > 0.0 && a < 1.0))
         return fail(h, SSM_EINVAL, "need n_t >= 2, sigma > 0, sigma_tilde > 0, 0 < a < 1");
-    if (!P.have_moments) return fail(h, SSM_ESTATE, "ssm_trace_f needs ssm_moments first");
     CUDA_OR_FAIL(h, cudaSetDevice(P.device));
     // periodic grid: lo/hi onto [-a, a]
     const double c = 0.5 * (P.glo + P.ghi);
@@ -794,12 +1283,10 @@ ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int6
         h->cap_tr = 10 * n_t + 2;
     }
     double* d_tt = h->d_tr;
-    double* d_x = d_tt + n_t;
-    double* d_fx = d_x + n_t;
+    double* d_fx = d_tt + 2 * n_t;
     double* d_h = d_fx + n_t;
     double* d_ft = d_h + n_t;
     double* d_work = d_ft + n_t;   // 5 n_t
-    double* d_out = h->d_tr + 10 * n_t;
     CUDA_OR_FAIL(h, cudaMemcpyAsync(d_tt, host.data(), 3 * n_t * sizeof(double), cudaMemcpyHostToDevice, P.stream));
     {
         Scope sc(h, PH_TRACE);
@@ -807,12 +1294,52 @@ ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int6
         CUDA_OR_FAIL(h, launch_deconvolve(d_h, n_t, dx, sigma, DECONV_CUTOFF, d_work, d_ft, P.stream));
         P.stats.launches += 4;
     }
-    s = dos_dev(h, d_x, n_t, sigma);
+    *dx_out = dx;
+    return SSM_OK;
+}
+
+// Copy n doubles from a host array to a host or device pointer.
+cudaError_t to_device_or_host(double* dst, const double* src, size_t n) {
+    if (n == 0) return cudaSuccess;
+    if (!is_device_ptr(dst)) {
+        memcpy(dst, src, n * sizeof(double));
+        return cudaSuccess;
+    }
+    return cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyHostToDevice);
+}
+
+// Copy n doubles from a host or device pointer to the host.
+cudaError_t to_host(double* dst, const double* src, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (!is_device_ptr(src)) {
+        memcpy(dst, src, n * sizeof(double));
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
+}  // namespace
+
+extern "C" {
+
+ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int64_t n_t, double sigma,
+                       double sigma_tilde, double a, double* tr_ss, double* tr_kpm) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (!P.have_moments) return fail(h, SSM_ESTATE, "ssm_trace_f needs ssm_moments first");
+    double dx = 0.0;
+    ssm_status s = trace_prepare(h, f, ctx, n_t, sigma, sigma_tilde, a, &dx);
+    if (s != SSM_OK) return s;
+    double* d_x = h->d_tr + n_t;
+    double* d_ft = h->d_tr + 4 * n_t;
+    double* d_out = h->d_tr + 10 * n_t;
+    s = dos_dev(h, d_x, n_t, sigma, tr_ss != nullptr);
     if (s != SSM_OK) return s;
     const double scale = (double)P.n * dx;
     {
         Scope sc(h, PH_TRACE);
-        CUDA_OR_FAIL(h, launch_trace_dot(d_ft, h->d_dos_ss, n_t, scale, d_out, P.stream));
+        if (tr_ss) CUDA_OR_FAIL(h, launch_trace_dot(d_ft, h->d_dos_ss, n_t, scale, d_out, P.stream));
         CUDA_OR_FAIL(h, launch_trace_dot(d_ft, h->d_dos_kpm, n_t, scale, d_out + 1, P.stream));
         P.stats.launches += 2;
     }
@@ -824,6 +1351,230 @@ ssm_status ssm_trace_f(ssm_plan_t h, double (*f)(double, void*), void* ctx, int6
     if (s != SSM_OK) return s;
     if (tr_ss) *tr_ss = res[0];
     if (tr_kpm) *tr_kpm = res[1];
+    return SSM_OK;
+}
+
+ssm_status ssm_trace_weights(ssm_plan_t h, double (*f)(double, void*), void* ctx, int64_t n_t, double sigma,
+                             double sigma_tilde, double a, double* x, double* w) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (!x || !w) return fail(h, SSM_EINVAL, "x and w must not be NULL");
+    double dx = 0.0;
+    ssm_status s = trace_prepare(h, f, ctx, n_t, sigma, sigma_tilde, a, &dx);
+    if (s != SSM_OK) return s;
+    double* d_x = h->d_tr + n_t;
+    double* d_ft = h->d_tr + 4 * n_t;
+    double* d_w = h->d_tr + 6 * n_t;  // work area, free after the deconvolution
+    CUDA_OR_FAIL(h, launch_scale(d_ft, (double)P.n * dx, n_t, d_w, P.stream));
+    P.stats.launches++;
+    CUDA_OR_FAIL(h, from_device(x, d_x, n_t * sizeof(double), P.stream));
+    CUDA_OR_FAIL(h, from_device(w, d_w, n_t * sizeof(double), P.stream));
+    return sync_and_settle(h);
+}
+
+ssm_status ssm_plan_set_diag(ssm_plan_t h, const double* diag) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (!P.is_stencil) return fail(h, SSM_EINVAL, "ssm_plan_set_diag needs a stencil plan");
+    if (!diag) return fail(h, SSM_EINVAL, "diag is NULL");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    P.have_moments = false;
+    ssm_status s = ensure_stage(h, (size_t)P.n * sizeof(double));
+    if (s != SSM_OK) return s;
+    CUDA_OR_FAIL(h, to_device(P.d_stage, diag, P.n * sizeof(double), P.stream));
+    const int nb = operator_bound_blocks(P.n);
+    if (!P.d_rawdiag) CUDA_OR_FAIL(h, dev_alloc(&P.d_rawdiag, 2 * (size_t)nb));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
+    CUDA_OR_FAIL(h, launch_stencil_bounds(P, P.d_stage, P.raw_off, P.extra, P.d_rawdiag, P.d_flag, P.stream));
+    std::vector<double> hb(2 * nb);
+    int flag = 0;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(hb.data(), P.d_rawdiag, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(&flag, P.d_flag, sizeof(int), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    if (flag) return fail(h, SSM_ENONFINITE, "diag not finite");
+    double lo = hb[0], hi = hb[1];
+    for (int i = 1; i < nb; ++i) {
+        lo = fmin(lo, hb[2 * i]);
+        hi = fmax(hi, hb[2 * i + 1]);
+    }
+    if (lo < P.a || hi > P.b)
+        return fail(h, SSM_EDOMAIN, "the new Gershgorin interval leaves the plan's interval (a, b)");
+    CUDA_OR_FAIL(h, launch_fold_stencil(P, P.d_stage, P.extra, P.stream));
+    P.stats.launches += 2;
+    return sync_and_settle(h);
+}
+
+ssm_status ssm_kpm_adjoint(ssm_plan_t h, const double* t, int64_t n_t, double sigma, const double* w, double* g) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (P.B > 0) return fail(h, SSM_EINVAL, "not available for batched plans");
+    if (n_t < 0 || !(sigma > 0.0) || !isfinite(sigma)) return fail(h, SSM_EINVAL, "need n_t >= 0 and sigma > 0");
+    if (!g || (n_t > 0 && (!t || !w))) return fail(h, SSM_EINVAL, "t, w and g must not be NULL");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    const int M = P.p.degree;
+    double *dt = nullptr, *dw = nullptr, *dmu = nullptr, *dg = nullptr;
+    const int64_t nt1 = n_t > 0 ? n_t : 1;
+    cudaError_t e = dev_alloc(&dt, nt1);
+    if (e == cudaSuccess) e = dev_alloc(&dw, nt1);
+    if (e == cudaSuccess) e = dev_alloc(&dmu, (size_t)nt1 * (M + 1));
+    if (e == cudaSuccess) e = dev_alloc(&dg, M + 1);
+    if (e == cudaSuccess && n_t > 0) e = to_device(dt, t, n_t * sizeof(double), P.stream);
+    if (e == cudaSuccess && n_t > 0) e = to_device(dw, w, n_t * sizeof(double), P.stream);
+    ssm_status s = SSM_OK;
+    if (e != cudaSuccess) s = fail(h, e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA, cudaGetErrorString(e));
+    if (s == SSM_OK && n_t > 0) s = coefficients_dev(h, dt, n_t, sigma, dmu, nullptr);
+    if (s == SSM_OK) {
+        e = n_t > 0 ? launch_kpm_adjoint(dmu, M + 1, n_t, M + 1, dw, 1.0 / P.n_tot, dg, P.stream)
+                    : cudaMemsetAsync(dg, 0, (M + 1) * sizeof(double), P.stream);
+        if (e == cudaSuccess) e = from_device(g, dg, (M + 1) * sizeof(double), P.stream);
+        if (e != cudaSuccess) s = fail(h, SSM_ECUDA, cudaGetErrorString(e));
+        P.stats.launches++;
+    }
+    if (s == SSM_OK) s = sync_and_settle(h);
+    cudaStreamSynchronize(P.stream);
+    dev_free(dt);
+    dev_free(dw);
+    dev_free(dmu);
+    dev_free(dg);
+    return s;
+}
+
+ssm_status ssm_moments_adjoint(ssm_plan_t h, const double* dL_dX, int32_t kind, double* dL_ddiag, double* dL_doff) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (!P.adjoint) return fail(h, SSM_ESTATE, "the plan was created without the adjoint option (options bit 1)");
+    if (!P.have_moments) return fail(h, SSM_ESTATE, "ssm_moments_adjoint needs ssm_moments first");
+    if (!dL_dX) return fail(h, SSM_EINVAL, "dL_dX is NULL");
+    if (kind != 0 && kind != 1) return fail(h, SSM_EINVAL, "kind must be 0 (matrices) or 1 (multiples of I)");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    const int M = P.p.degree, S = M / 2, n = P.n_tot, c = P.ck_c;
+    const size_t nn = (size_t)n * n;
+    const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
+    const size_t bb = (size_t)P.n * P.ld * esz;
+    const int64_t nEF = P.is_stencil ? 3 * P.n : P.nnz;
+    if (!P.d_seg) CUDA_OR_FAIL(h, cudaMalloc(&P.d_seg, bb * c));
+    for (auto& u : P.d_U)
+        if (!u) CUDA_OR_FAIL(h, cudaMalloc(&u, bb));
+    if (!P.d_D) CUDA_OR_FAIL(h, dev_alloc(&P.d_D, P.n));
+    if (!P.d_EF) CUDA_OR_FAIL(h, dev_alloc(&P.d_EF, nEF));
+    if (!P.d_adjsum) CUDA_OR_FAIL(h, dev_alloc(&P.d_adjsum, 4));
+    std::vector<double> g;
+    double g1p = 0.0;
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
+    if (kind == 1) {
+        g.resize(M + 1);
+        CUDA_OR_FAIL(h, to_host(g.data(), dL_dX, M + 1, P.stream));
+        for (double v : g)
+            if (!isfinite(v)) return fail(h, SSM_ENONFINITE, "dL_dX is not finite");
+        g1p = g[1];
+        for (int j = 1; j <= S - 1; ++j) g1p -= g[2 * j + 1];
+    } else {
+        if (!P.d_G) CUDA_OR_FAIL(h, dev_alloc(&P.d_G, (M + 1) * nn));
+        if (!P.d_G1p) CUDA_OR_FAIL(h, dev_alloc(&P.d_G1p, nn));
+        if (!P.d_Gb) CUDA_OR_FAIL(h, cudaMalloc(&P.d_Gb, bb));
+        if (!P.d_Bm) CUDA_OR_FAIL(h, cudaMalloc(&P.d_Bm, 3 * nn * esz));
+        CUDA_OR_FAIL(h, to_device(P.d_G, dL_dX, (M + 1) * nn * sizeof(double), P.stream));
+        CUDA_OR_FAIL(h, launch_check_finite(P.d_G, (int64_t)(M + 1) * nn, P.d_flag, P.stream));
+        CUDA_OR_FAIL(h, launch_adj_g1(P.d_G, n, S, P.d_G1p, P.stream));
+        P.stats.launches += 2;
+    }
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_D, 0, P.n * sizeof(double), P.stream));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_EF, 0, nEF * sizeof(double), P.stream));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_U[(S + 1) % 3], 0, bb, P.stream));
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_U[(S + 2) % 3], 0, bb, P.stream));
+    uint8_t* ck = (uint8_t*)P.d_ck;
+    uint8_t* seg = (uint8_t*)P.d_seg;
+    {
+        Scope sc(h, PH_ADJOINT);
+        for (int j = P.n_ck - 1; j >= 0; --j) {
+            const int lo = j * c, hi = (j + 1) * c < S ? (j + 1) * c : S;
+            const int top = hi + 1 < S ? hi + 1 : S;
+            // V_m of this segment: checkpoints for m = lo, lo+1, recomputed blocks after
+            auto V = [&](int m) -> void* {
+                if (m == lo) return ck + (size_t)(2 * j) * bb;
+                if (m == lo + 1) return ck + (size_t)(2 * j + 1) * bb;
+                return seg + (size_t)(m - lo - 2) * bb;
+            };
+            for (int m = lo + 2; m <= top; ++m) {
+                cudaError_t e;
+                if (P.mixed)
+                    e = P.is_stencil ? launch_stencil_step_f32(P, (const float*)V(m - 1), (const float*)V(m - 2),
+                                                               (float*)V(m), 1.f, 1.f, nullptr, P.stream)
+                                     : launch_csr_step_f32(P, (const float*)V(m - 1), (const float*)V(m - 2),
+                                                           (float*)V(m), 1.f, 1.f, nullptr, P.stream);
+                else
+                    e = P.is_stencil ? launch_stencil_step_f64(P, (const double*)V(m - 1), (const double*)V(m - 2),
+                                                               (double*)V(m), 1.0, 1.0, P.stream)
+                                     : launch_csr_step_f64(P, (const double*)V(m - 1), (const double*)V(m - 2),
+                                                           (double*)V(m), 1.0, 1.0, P.stream);
+                CUDA_OR_FAIL(h, e);
+                P.stats.launches++;
+            }
+            for (int k = hi; k >= lo + 1; --k) {
+                const void* Vm = V(k - 1);
+                const void* V0 = V(k);
+                const void* Vp = k < S ? V(k + 1) : V0;
+                double ga = 0.0, gb = 0.0, gc = 0.0;
+                const void* Gb = nullptr;
+                if (kind == 1) {
+                    ga = (k == 1) ? g1p : 2.0 * g[2 * k - 1];
+                    gb = 4.0 * g[2 * k];
+                    gc = (k < S) ? 2.0 * g[2 * k + 1] : 0.0;
+                } else {
+                    CUDA_OR_FAIL(h, launch_adj_gbar(P, P.d_G, P.d_G1p, k, S, P.d_Bm, Vm, V0, Vp, P.d_Gb, P.stream));
+                    Gb = P.d_Gb;
+                    P.stats.launches += 2;
+                }
+                CUDA_OR_FAIL(h, launch_adj_step(P, P.d_U[(k + 1) % 3], P.d_U[(k + 2) % 3], Vm, V0, Vp, Gb,
+                                                P.d_U[k % 3], ga, gb, gc, k < S ? 2.0 : 0.0, P.d_D, P.d_EF,
+                                                P.stream));
+                P.stats.launches++;
+            }
+        }
+        // the pair (U_1, V_0) enters dL/dA~ once (V_1 = A~ V_0)
+        CUDA_OR_FAIL(h, launch_adj_step(P, P.d_U[1], P.d_U[2], ck, ck, ck, nullptr, nullptr, 0.0, 0.0, 0.0, 1.0,
+                                        P.d_D, P.d_EF, P.stream));
+        P.stats.launches++;
+    }
+    // dA~/dA = 2/(b-a) = alpha/2 with (a, b) fixed
+    const double sA = 0.5 * P.alpha;
+    double sums[4] = {0, 0, 0, 0};
+    if (P.is_stencil) {
+        CUDA_OR_FAIL(h, launch_adj_sum(P.d_D, P.d_EF, P.n, P.d_adjsum, P.stream));
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(sums, P.d_adjsum, 4 * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+        P.stats.launches++;
+    } else if (dL_doff) {
+        // the symmetric part, split evenly over (i, j) and (j, i): the reverse of the
+        // doubling loop and of the M-step loop differ in the antisymmetric part only
+        double* tmp = nullptr;
+        CUDA_OR_FAIL(h, dev_alloc(&tmp, P.nnz));
+        cudaError_t e = launch_csr_sym(P, P.d_EF, sA, tmp, P.stream);
+        if (e == cudaSuccess) e = from_device(dL_doff, tmp, P.nnz * sizeof(double), P.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);
+        dev_free(tmp);
+        CUDA_OR_FAIL(h, e);
+        P.stats.launches++;
+    }
+    CUDA_OR_FAIL(h, launch_scale(P.d_D, sA, P.n, P.d_D, P.stream));
+    P.stats.launches++;
+    if (dL_ddiag) CUDA_OR_FAIL(h, from_device(dL_ddiag, P.d_D, P.n * sizeof(double), P.stream));
+    ssm_status s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    int flag = 0;
+    s = read_flag(h, &flag);
+    if (s != SSM_OK) return s;
+    if (flag) return fail(h, SSM_ENONFINITE, "dL_dX is not finite");
+    if (P.is_stencil && dL_doff) {
+        const int64_t ext[3] = {(int64_t)P.geom.d0, (int64_t)P.geom.d1, (int64_t)P.geom.d2};
+        double off[3];
+        for (int a = 0; a < 3; ++a) {
+            if (ext[a] > 1)
+                off[a] = sA * sums[a];
+            else  // a periodic axis of extent one couples each row to itself twice
+                off[a] = P.geom.per[a] ? 2.0 * sA * sums[3] : 0.0;
+        }
+        CUDA_OR_FAIL(h, to_device_or_host(dL_doff, off, 3));
+    }
     return SSM_OK;
 }
 

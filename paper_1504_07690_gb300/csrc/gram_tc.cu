@@ -103,6 +103,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two 16-column loads in flight, one wait.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 16u));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 struct TcArgs {
     const uint8_t* PX;  // panels of V_{k+1}
     const uint8_t* PY;  // panels of V_k (NULL: Ge only)
@@ -114,6 +132,7 @@ struct TcArgs {
     float* part_e;      // [n_e][n_tot][n_tot]
     float* part_o;      // [n_o][n_tot][n_tot]
     int* flag;
+    const int2* slabs;  // NULL: uniform slabs; else panel range [x, y) of every CTA
 };
 
 __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
@@ -156,8 +175,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     const bool cross = (int)blockIdx.x >= P.n_e;
     const int slab = cross ? (int)blockIdx.x - P.n_e : (int)blockIdx.x;
     const int64_t pan = cross ? P.pan_o : P.pan_e;
-    const int64_t p0 = (int64_t)slab * pan;
+    int64_t p0 = (int64_t)slab * pan;
     int64_t p1 = p0 + pan;
+    if (P.slabs) {
+        const int2 r = P.slabs[blockIdx.x];
+        p0 = r.x;
+        p1 = r.y;
+    }
     if (p1 > P.n_panels) p1 = P.n_panels;
     const int nch = p1 > p0 ? (int)(p1 - p0) : 0;
     const int nsrc = cross ? 2 : 1;
@@ -267,21 +291,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     const bool ok = dn && fail == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
+        // each lane owns one row m of a tile: 32 columns per TMEM round trip, written
+        // as whole 128-byte runs (float4) when the row is 16-byte aligned
+        const bool vec = (n_tot & 3) == 0;
         for (int t = 0; t < nt; ++t) {
-            for (int cc = 0; cc < t_n[t]; cc += 16) {
-                float v[16];
+            const int m = t_m0[t] + 32 * warp + lane;
+            float* orow = out + (size_t)m * n_tot + t_n0[t];
+            for (int cc = 0; cc < t_n[t]; cc += 32) {
+                float v[32];
+                const int w = t_n[t] - cc >= 32 ? 32 : 16;
                 if (nch > 0) {
-                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t_dc[t] + cc), v);
+                    const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t_dc[t] + cc);
+                    if (w == 32)
+                        tmem_ld32(ta, v);
+                    else
+                        tmem_ld16(ta, v);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
                 }
-                const int m = t_m0[t] + 32 * warp + lane;
                 if (m < n_tot) {
-                    float* o = out + (size_t)m * n_tot + t_n0[t] + cc;
+                    if (vec && t_n0[t] + cc + w <= n_tot) {
+                        float4* o4 = reinterpret_cast<float4*>(orow + cc);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (t_n0[t] + cc + j < n_tot) o[j] = v[j];
+                        for (int q = 0; q < 8; ++q)
+                            if (4 * q < w) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < w && t_n0[t] + cc + j < n_tot) orow[cc + j] = v[j];
+                    }
                 }
             }
         }
@@ -422,6 +461,67 @@ __global__ void moments_tc_batch_kernel(const double* __restrict__ ge, const dou
     }
 }
 
+// Batched plans: matrix b = blockIdx.y sums its own slabs (Ge slabs [se[b],
+// se[b+1]), Go slabs [so[b], so[b+1])), in the fixed order of sum_tc_kernel.
+__global__ void __launch_bounds__(256)
+sum_tc_seg_kernel(const float* __restrict__ pe, const float* __restrict__ po, const int* __restrict__ seg, int B,
+                  int n_tot, bool odd, double* __restrict__ ge, double* __restrict__ go) {
+    __shared__ double se_[8][32], so_[8][32];
+    const size_t nn = (size_t)n_tot * n_tot;
+    const int b = blockIdx.y;
+    const int e0s = seg[b], e1s = seg[b + 1], o0s = seg[B + 1 + b], o1s = seg[B + 2 + b];
+    double* gq = ge + (size_t)b * nn;
+    double* oq = go + (size_t)b * nn;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
+        const size_t e = e0 + lane;
+        double a0 = 0.0, b0 = 0.0;
+        if (e < nn) {
+            const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
+            if (i <= j)
+                for (int sl = e0s + w; sl < e1s; sl += 8) a0 += (double)pe[(size_t)sl * nn + e];
+            if (odd)
+                for (int sl = o0s + w; sl < o1s; sl += 8) b0 += (double)po[(size_t)sl * nn + e];
+        }
+        se_[w][lane] = a0;
+        so_[w][lane] = b0;
+        __syncthreads();
+        if (w == 0 && e < nn) {
+            double a = 0.0, c = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                a += se_[k][lane];
+                c += so_[k][lane];
+            }
+            gq[e] = a;
+            oq[e] = c;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void moments_tc_seg_kernel(const double* __restrict__ ge, const double* __restrict__ go, int n_tot,
+                                      double* __restrict__ X, size_t xstride, int step) {
+    const size_t nn = (size_t)n_tot * n_tot;
+    const int b = blockIdx.y;
+    const double* gq = ge + (size_t)b * nn;
+    const double* oq = go + (size_t)b * nn;
+    double* Xb = X + (size_t)b * xstride;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
+        const double gs = (i <= j) ? gq[e] : gq[(size_t)j * n_tot + i];
+        const double gc = 0.5 * (oq[e] + oq[(size_t)j * n_tot + i]);
+        if (step < 0) {
+            Xb[e] = gs;
+        } else if (step == 0) {
+            Xb[nn + e] = gc;
+            Xb[2 * nn + e] = 2.0 * gs - Xb[e];
+        } else {
+            Xb[(size_t)(2 * step + 1) * nn + e] = 2.0 * gc - Xb[nn + e];
+            Xb[(size_t)(2 * step + 2) * nn + e] = 2.0 * gs - Xb[e];
+        }
+    }
+}
+
 }  // namespace
 
 bool gram_tc_supported(int n_tot, int ld) { return n_tot >= 1 && n_tot <= 256 && (ld % 4) == 0; }
@@ -444,7 +544,7 @@ void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o) {
 size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot) { return (size_t)(n_e + n_o) * n_tot * n_tot; }
 
 cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int64_t n_rows, int n_e, int n_o,
-                           float* part, int* flag, cudaStream_t s) {
+                           float* part, int* flag, cudaStream_t s, const int2* slabs) {
     cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     TcArgs a;
@@ -460,6 +560,7 @@ cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int6
     a.part_e = part;
     a.part_o = part + (size_t)n_e * n_tot * n_tot;
     a.flag = flag;
+    a.slabs = slabs;
     gram_tc_kernel<<<a.n_e + a.n_o, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
@@ -502,6 +603,22 @@ cudaError_t launch_reduce_tc_batch(const float* ring, int n_e, int n_o, int n_to
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((nn + 255) / 256 > 512 ? 512 : (nn + 255) / 256), (unsigned)nk);
     moments_tc_batch_kernel<<<grid, 256, 0, s>>>(ge, go, n_tot, X, k0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_tc_seg(const float* part, int n_e, int n_tot, int B, const int* seg, double* ge,
+                                 double* go, double* X, size_t xstride, int step, cudaStream_t s) {
+    const int64_t nn = (int64_t)n_tot * n_tot;
+    int64_t sb = (nn + 31) / 32;
+    if (sb > 64) sb = 64;
+    dim3 sg((unsigned)sb, (unsigned)B);
+    sum_tc_seg_kernel<<<sg, 256, 0, s>>>(part, part + (size_t)n_e * nn, seg, B, n_tot, step >= 0, ge, go);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t mb = (nn + 255) / 256;
+    if (mb > 64) mb = 64;
+    dim3 mg((unsigned)mb, (unsigned)B);
+    moments_tc_seg_kernel<<<mg, 256, 0, s>>>(ge, go, n_tot, X, xstride, step);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,40 @@ struct Plan {
     void* d_work = nullptr;
     int64_t work_nt = 0;
 
+    // adjoint (ssm_moments_adjoint): checkpoints (V_{jc}, V_{jc+1}), j < n_ck, written
+    // by ssm_moments; the rest is allocated on the first adjoint call
+    bool adjoint = false;
+    int ck_c = 0, n_ck = 0;
+    void* d_ck = nullptr;              // 2 n_ck blocks
+    void* d_seg = nullptr;             // ck_c recomputed blocks of one segment
+    void* d_U[3] = {nullptr, nullptr, nullptr};
+    void* d_Gb = nullptr;              // Gbar_k block (general G)
+    void* d_Bm = nullptr;              // 3 n_tot x n_tot coefficient matrices (general G)
+    double* d_G = nullptr;             // (M+1) x n_tot^2 (general G)
+    double* d_G1p = nullptr;           // n_tot^2
+    double* d_D = nullptr;             // N
+    double* d_EF = nullptr;            // 3N (stencil) or nnz (CSR)
+    double* d_adjsum = nullptr;        // 4
+    double* d_rawdiag = nullptr;       // unfolded stencil diagonal (N) for ssm_plan_set_diag bounds
+    double raw_off[3] = {0, 0, 0};
+    double extra = 0;                  // self-coupling of periodic extent-1 axes
+
+    // batched plans (ssm_plan_create_batched): B operators side by side in one
+    // block-diagonal CSR, matrix b's rows at [row_off[b], row_off[b] + n_b[b]),
+    // row_off a multiple of 32 (no panel straddles two matrices)
+    int B = 0;
+    int64_t* h_row_off = nullptr;      // B + 1 (host)
+    int64_t* h_nb = nullptr;           // B rows per matrix (host)
+    double* h_ab = nullptr;            // 6 B: a, b, glo, ghi, alpha, beta per matrix (host)
+    double* d_beta_row64 = nullptr;    // per-row beta of the folded map (batched CSR)
+    float* d_beta_row32 = nullptr;
+    int2* d_slabs = nullptr;           // tensor-core Gram slab table [n_e + n_o] (panel ranges)
+    int* d_slabseg = nullptr;          // per-matrix slab ranges: se[B+1], so[B+1]
+    double* d_x0max = nullptr;         // per-matrix max_i X_0[i][i] (B)
+    cudaStream_t cap_stream = nullptr; // capture stream of the batched recurrence graph
+    cudaGraphExec_t graph = nullptr;
+    int csr_threads = 0;               // block size of the CSR step (autotuned for batched plans)
+
     // timing
     bool timing = false;
     ssm_stats stats{};
@@ -111,6 +145,12 @@ cudaError_t launch_csr_bounds(const Plan& P, const double* val, double* out, cud
 cudaError_t launch_csr_validate(const Plan& P, const double* val, int* flag, cudaStream_t s);
 cudaError_t launch_fold_stencil(const Plan& P, const double* diag, double extra, cudaStream_t s);
 cudaError_t launch_fold_csr(const Plan& P, const double* val, cudaStream_t s);
+// Batched plans: bounds of rows [row0, row0+n) (out: 2 operator_bound_blocks(n) values) and
+// the fold val2 = alpha val of entries [e0, e1).
+cudaError_t launch_csr_bounds_range(const Plan& P, const double* val, int64_t row0, int64_t n, double* out,
+                                    cudaStream_t s);
+cudaError_t launch_fold_csr_range(const Plan& P, const double* val, double alpha, int64_t e0, int64_t e1,
+                                  cudaStream_t s);
 
 // Gram partials: part[s][0] = upper tiles of A^T A, part[s][1] = A^T B (if B).
 int gram_split_count(int64_t n_rows, int n_tot);
@@ -132,7 +172,12 @@ size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot);
 size_t gram_tc_partial_floats_total(int n_e, int n_o, int n_tot);  // + room for the float64 sums
 int gram_tc_groups(int n_tot);  // 8-column groups of a panel (n_tot rounded up to 16)
 cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int64_t n_rows, int n_e, int n_o,
-                           float* part, int* flag, cudaStream_t s);
+                           float* part, int* flag, cudaStream_t s, const int2* slabs = nullptr);
+// Batched plans: per-matrix slab sums (matrix b owns Ge slabs [se[b], se[b+1]) and Go
+// slabs [so[b], so[b+1]); seg = se (B+1) followed by so (B+1)) and the moments of step
+// `step` (-1: X_0) into X + b * xstride.
+cudaError_t launch_reduce_tc_seg(const float* part, int n_e, int n_tot, int B, const int* seg, double* ge,
+                                 double* go, double* X, size_t xstride, int step, cudaStream_t s);
 cudaError_t launch_reduce_tc(const float* part, int n_e, int n_o, int n_tot, double* X, int step, cudaStream_t s);
 // Moments of steps k0..k0+nk-1 from a ring of nk partial slots (float64 scratch ge, go: nk x n_tot^2 each).
 cudaError_t launch_reduce_tc_batch(const float* ring, int n_e, int n_o, int n_tot, double* X, int k0, int nk,
@@ -160,11 +205,29 @@ cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, con
 
 // Per-point Alg. 4 + Alg. 6 solve (solve.cu).
 size_t solve_workspace_bytes(int n_v);
-// floor(t) = floor_scale * sum_{l<=K} (l+1) |mu[t][l]| (see ssm_params.eps_floor).
+// floor(t) = floor_scale * sum_{l<=K} (l+1) |mu[t][l]| (see ssm_params.eps_floor).  floor_pt
+// (nullable): per point (floor_scale, xlo, xhi), replacing the scalars (batched plans).
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh,
                          double tau, double xlo, double xhi, const double* mu, int ldmu, int K,
                          double floor_scale, void* work, double* dos, int32_t* rank, int* flag,
-                         cudaStream_t s);
+                         cudaStream_t s, const double* floor_pt = nullptr);
+
+// Adjoint of the recurrence (adjoint.cu).  One backward step: Uo (nullable) =
+// Gbar_k + 2 A~ Un1 - Un2 with Gbar_k = Gb if Gb != NULL, else ga Vm + gb V0 + gc Vp;
+// D[i] += gcoef <Un1[i], V0[i]>; EF: stencil E[3i+d] += gcoef <V0[i], nbr_d(Un1)[i]>,
+// CSR F[e] += gcoef <Un1[i], V0[colind[e]]>.  Blocks in the plan's working precision.
+cudaError_t launch_adj_step(const Plan& P, const void* Un1, const void* Un2, const void* Vm, const void* V0,
+                            const void* Vp, const void* Gb, void* Uo, double ga, double gb, double gc, double gcoef,
+                            double* D, double* EF, cudaStream_t s);
+cudaError_t launch_adj_g1(const double* G, int n, int S, double* G1p, cudaStream_t s);
+cudaError_t launch_adj_gbar(const Plan& P, const double* G, const double* G1p, int k, int S, void* Bm,
+                            const void* Vm, const void* V0, const void* Vp, void* Gb, cudaStream_t s);
+cudaError_t launch_adj_sum(const double* D, const double* E, int64_t n, double* out, cudaStream_t s);
+// out[e] = s (F[e] + F[transpose(e)]) / 2 over the plan's CSR pattern (out may not alias F).
+cudaError_t launch_csr_sym(const Plan& P, const double* F, double s, double* out, cudaStream_t st);
+cudaError_t launch_scale(const double* x, double sc, int64_t n, double* y, cudaStream_t s);
+cudaError_t launch_kpm_adjoint(const double* mu, int ldmu, int64_t n_t, int L, const double* w, double inv_cols,
+                               double* g, cudaStream_t s);
 
 // Alg. 8 pieces (trace.cu).
 cudaError_t launch_trace_h(const double* tt, const double* fx, int64_t n_t, double fend, double a,

@@ -65,13 +65,14 @@ __global__ void stencil_bounds_kernel(const double* __restrict__ diag, StencilGe
     block_minmax_store(lo, hi, out);
 }
 
+// Rows row0 .. row0+n-1 (column indices are global).
 __global__ void csr_bounds_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const double* __restrict__ val, int64_t n, double* __restrict__ out) {
+                                  const double* __restrict__ val, int64_t row0, int64_t n, double* __restrict__ out) {
     double lo = 1e300, hi = -1e300;
     for (int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x; i < n; i += (int64_t)gridDim.x * BT) {
         double d = 0.0, r = 0.0;
-        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-            if (col[e] == i)
+        for (int64_t e = rowptr[row0 + i]; e < rowptr[row0 + i + 1]; ++e) {
+            if (col[e] == row0 + i)
                 d += val[e];
             else
                 r += fabs(val[e]);
@@ -158,7 +159,20 @@ cudaError_t launch_stencil_bounds(const Plan& P, const double* diag, const doubl
 }
 
 cudaError_t launch_csr_bounds(const Plan& P, const double* val, double* out, cudaStream_t s) {
-    csr_bounds_kernel<<<nblk(P.n), BT, 0, s>>>(P.d_rowptr, P.d_colind, val, P.n, out);
+    csr_bounds_kernel<<<nblk(P.n), BT, 0, s>>>(P.d_rowptr, P.d_colind, val, 0, P.n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_bounds_range(const Plan& P, const double* val, int64_t row0, int64_t n, double* out,
+                                    cudaStream_t s) {
+    csr_bounds_kernel<<<nblk(n), BT, 0, s>>>(P.d_rowptr, P.d_colind, val, row0, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_csr_range(const Plan& P, const double* val, double alpha, int64_t e0, int64_t e1,
+                                  cudaStream_t s) {
+    if (e1 <= e0) return cudaSuccess;
+    fold_csr_kernel<<<nblk(e1 - e0), BT, 0, s>>>(val + e0, alpha, e1 - e0, P.d_val64 + e0, P.d_val32 + e0);
     return cudaGetLastError();
 }
 

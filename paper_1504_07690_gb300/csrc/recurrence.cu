@@ -179,7 +179,8 @@ template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                 const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                const T* __restrict__ val2, T beta, T c, T d, uint32_t nchunk, uint32_t n_rows, PanelOut po) {
+                const T* __restrict__ val2, T beta, const T* __restrict__ beta_row, T c, T d, uint32_t nchunk,
+                uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
     __shared__ __align__(16) uint8_t stage[PANEL ? 2 * 32 * 33 * 16 : 16];
     const VT* vc = reinterpret_cast<const VT*>(Vc);
@@ -198,7 +199,7 @@ csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restric
             VT out = vzero(T(0));
             if (i < n_rows) {
                 const size_t base = (size_t)i * nchunk;
-                VT acc = vscale(beta, ldg_stream(vc + base + cc));
+                VT acc = vscale(beta_row ? __ldg(beta_row + i) : beta, ldg_stream(vc + base + cc));
                 const int64_t e1 = __ldg(rowptr + i + 1);
                 for (int64_t e = __ldg(rowptr + i); e < e1; ++e) {
                     const uint32_t j = (uint32_t)__ldg(colind + e);
@@ -263,16 +264,18 @@ static cudaError_t stencil_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, 
 
 template <typename T>
 static cudaError_t csr_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, const T* val2, T beta,
-                            T c, T d, uint8_t* panel, cudaStream_t s) {
+                            const T* beta_row, T c, T d, uint8_t* panel, cudaStream_t s) {
     const uint32_t nchunk = (uint32_t)(P.ld / Vec16<T>::W);
     const PanelOut po{panel, (uint32_t)P.panel_groups};
+    const int nt = P.csr_threads > 0 ? P.csr_threads : 256;
     if (panel)
-        csr_step_kernel<T, true><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr, P.d_colind,
-                                                                    val2, beta, c, d, nchunk, (uint32_t)P.n, po);
+        csr_step_kernel<T, true><<<panel_grid(P.n), nt, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr, P.d_colind,
+                                                                   val2, beta, beta_row, c, d, nchunk,
+                                                                   (uint32_t)P.n, po);
     else
-        csr_step_kernel<T, false><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr,
-                                                                     P.d_colind, val2, beta, c, d, nchunk,
-                                                                     (uint32_t)P.n, po);
+        csr_step_kernel<T, false><<<panel_grid(P.n), nt, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, P.d_rowptr,
+                                                                    P.d_colind, val2, beta, beta_row, c, d,
+                                                                    nchunk, (uint32_t)P.n, po);
     return cudaGetLastError();
 }
 
@@ -286,11 +289,11 @@ cudaError_t launch_stencil_step_f32(const Plan& P, const float* Vc, const float*
 }
 cudaError_t launch_csr_step_f64(const Plan& P, const double* Vc, const double* Vp, double* Vn,
                                 double c, double d, cudaStream_t s) {
-    return csr_step<double>(P, Vc, Vp, Vn, P.d_val64, P.beta, c, d, nullptr, s);
+    return csr_step<double>(P, Vc, Vp, Vn, P.d_val64, P.beta, P.d_beta_row64, c, d, nullptr, s);
 }
 cudaError_t launch_csr_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
                                 float c, float d, uint8_t* panel, cudaStream_t s) {
-    return csr_step<float>(P, Vc, Vp, Vn, P.d_val32, (float)P.beta, c, d, panel, s);
+    return csr_step<float>(P, Vc, Vp, Vn, P.d_val32, (float)P.beta, P.d_beta_row32, c, d, panel, s);
 }
 
 cudaError_t launch_panelize(const Plan& P, const float* V, uint8_t* panel, cudaStream_t s) {

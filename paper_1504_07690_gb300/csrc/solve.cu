@@ -75,7 +75,7 @@ __device__ double block_max(double v, double* red) {
 // tridiagonal T = H^T A H: sh.d, sh.off receive T; row k of A (columns k+1..)
 // receives the k-th Householder vector and sh.beta[k] its scalar.
 __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     for (int k = 0; k + 2 < n; ++k) {
         const int L = n - k - 1;
         const double* x = A + (size_t)k * n + k + 1;  // row k == column k (symmetric)
@@ -98,13 +98,19 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             sh.beta[k] = beta;
         }
         if (beta != 0.0) {
-            // p = beta A22 v  (warp per row, lanes along the row)
-            for (int i = warp; i < L; i += NT / 32) {
-                const double* row = A + (size_t)(k + 1 + i) * n + k + 1;
-                double s = 0.0;
-                for (int j = lane; j < L; j += 32) s = fma(row[j], sh.v[j], s);
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) sh.p[i] = beta * s;
+            // p = beta A22 v: thread i walks column i of the symmetric A22 (row i
+            // transposed), so a warp reads 32 consecutive doubles per step and
+            // every thread has its own independent loads in flight
+            for (int i = tid; i < L; i += NT) {
+                const double* col = A + (size_t)(k + 1) * n + k + 1 + i;
+                double s0 = 0.0, s1 = 0.0;
+                int j = 0;
+                for (; j + 1 < L; j += 2) {
+                    s0 = fma(col[(size_t)j * n], sh.v[j], s0);
+                    s1 = fma(col[(size_t)(j + 1) * n], sh.v[j + 1], s1);
+                }
+                if (j < L) s0 = fma(col[(size_t)j * n], sh.v[j], s0);
+                sh.p[i] = beta * (s0 + s1);
             }
             __syncthreads();
             double g = 0.0;
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(NT, 3)
 solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, int64_t n_t, int nv, int nvh,
              double tau, double xlo, double xhi, const double* __restrict__ mu, int ldmu, int K,
              double floor_scale, double* __restrict__ work, double* __restrict__ dos,
-             int32_t* __restrict__ rank, int* __restrict__ flag) {
+             int32_t* __restrict__ rank, int* __restrict__ flag, const double* __restrict__ floor_pt) {
     extern __shared__ __align__(16) double dyn[];
     const int n = nv;
     Shared sh;
@@ -571,9 +577,10 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
         const double* Zk = KZ + (size_t)it * nn;
         // rounding floor of K_W(t)
         double fs = 0.0;
-        if (floor_scale > 0.0)
+        if (floor_scale > 0.0 || floor_pt)
             for (int l = tid; l <= K; l += NT) fs = fma((double)(l + 1), fabs(mu[it * ldmu + l]), fs);
-        const double floor_t = floor_scale * block_sum(fs, sh.red);
+        const double floor_t = (floor_pt ? floor_pt[3 * it] : floor_scale) * block_sum(fs, sh.red);
+        const double xl = floor_pt ? floor_pt[3 * it + 1] : xlo, xh = floor_pt ? floor_pt[3 * it + 2] : xhi;
         // 1. K_W (symmetrised) -> A, tridiagonal form; the largest eigenvalue and
         //    the number r of eigenvalues >= max(tau smax, floor) from Sturm counts
         for (int e = tid; e < n * n; e += NT) {
@@ -624,10 +631,10 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 __syncthreads();
                 tridiagonalise(A, n, sh);
                 bisect_prepare(n, sh);
-                // only the eigenvalues near or inside [xlo, xhi] are needed
+                // only the eigenvalues near or inside [xl, xh] are needed
                 if (tid == 0) {
-                    sh.misc[0] = max(0, sturm_below(sh.d, sh.p, n, xlo) - 1);
-                    sh.misc[1] = min(n, sturm_below(sh.d, sh.p, n, xhi) + 1);
+                    sh.misc[0] = max(0, sturm_below(sh.d, sh.p, n, xl) - 1);
+                    sh.misc[1] = min(n, sturm_below(sh.d, sh.p, n, xh) + 1);
                 }
                 __syncthreads();
                 const int jlo = sh.misc[0], jhi = sh.misc[1];
@@ -638,7 +645,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     double f = 0.0;
                     for (int j = jlo; j < jhi; ++j) {
                         const double xi = sh.v[j];
-                        if (xi >= xlo && xi <= xhi) {
+                        if (xi >= xl && xi <= xh) {
                             ++q;
                             f += xi;
                         }
@@ -726,7 +733,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 double f = 0.0;
                 for (int k = 0; k < r; ++k) {
                     const double xi = sh.d[k];
-                    if (xi >= xlo && xi <= xhi) {
+                    if (xi >= xl && xi <= xh) {
                         sh.sel[q++] = k;
                         f += xi;
                     }
@@ -802,7 +809,7 @@ size_t solve_workspace_bytes(int n_v) {
 
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh, double tau,
                          double xlo, double xhi, const double* mu, int ldmu, int K, double floor_scale, void* work,
-                         double* dos, int32_t* rank, int* flag, cudaStream_t s) {
+                         double* dos, int32_t* rank, int* flag, cudaStream_t s, const double* floor_pt) {
     if (n_t <= 0) return cudaSuccess;
     if (n_v > MAXN) return cudaErrorInvalidValue;
     const size_t smem = solve_smem(n_v);
@@ -811,7 +818,7 @@ cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int
     int64_t grid = workspace_ctas(n_v);
     if (grid > n_t) grid = n_t;
     solve_kernel<<<(int)grid, NT, smem, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K,
-                                                   floor_scale, (double*)work, dos, rank, flag);
+                                                   floor_scale, (double*)work, dos, rank, flag, floor_pt);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ def test_struct_layouts_match_header_sizes():
     assert C.sizeof(N.ssm_stencil) == 3 * 8 + 3 * 4 + 4 + 8 + 3 * 8
     assert C.sizeof(N.ssm_csr) == 5 * 8
     assert C.sizeof(N.ssm_params) == 4 * 4 + 4 * 8 + 2 * 4 + 8
-    assert C.sizeof(N.ssm_stats) == 8 * 8 + 3 * 8
+    assert C.sizeof(N.ssm_stats) == 9 * 8 + 3 * 8
 
 
 def test_status_strings(lib):
@@ -63,7 +63,7 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("field,value", [("degree", 7), ("degree", 0), ("n_v", 0), ("precision", 5),
-                                         ("n_theta", 3)])
+                                         ("n_theta", 3), ("options", 4)])
 def test_parameter_validation_before_any_cuda_call(lib, field, value):
     from paper_1504_07690_gb300 import _native as N
 
@@ -90,4 +90,7 @@ def test_both_or_no_operator_is_rejected(lib):
 def test_null_plan_calls_fail_cleanly(lib):
     assert lib.ssm_moments(None, None, 0, None) == 1
     assert lib.ssm_dos(None, None, 0, 1.0, None, None, None) == 1
+    assert lib.ssm_moments_adjoint(None, None, 1, None, None) == 1
+    assert lib.ssm_kpm_adjoint(None, None, 0, 1.0, None, None) == 1
+    assert lib.ssm_plan_set_diag(None, None) == 1
     lib.ssm_plan_destroy(None)

@@ -121,3 +121,23 @@ def test_kpm_loss_weights_linear_in_moments():
         Xp[l] += np.eye(k)
         # <g_l I, I> = k g_l; the loss is linear so the difference is exact up to rounding
         assert abs((loss(Xp) - loss(X)) - k * g[l]) <= 1e-12 * max(1.0, abs(k * g[l]))
+
+
+def test_symmetric_part_matches_symmetric_perturbation():
+    c = wl.er_normalized_laplacian(60, 5.0, 3)
+    A = O.csr_matrix(c.n, c.rowptr, c.colind, c.val)
+    a, b = O.spectral_interval(A)
+    At = O.transform(A, a, b)
+    rng = np.random.default_rng(1)
+    W = rng.standard_normal((60, 3))
+    M = 9
+    G = rng.standard_normal((M + 1, 3, 3))
+    _, pat = AO.moments_adjoint_direct(At, W, M, G)
+    Ps = AO.symmetric_part(pat)
+    P = sp.coo_matrix(At)
+    pairs = [(r, q) for r, q in zip(P.row, P.col) if r < q][:5]
+    for (i, j) in pairs:
+        E = sp.csr_matrix(([1.0, 1.0], ([i, j], [j, i])), shape=At.shape)
+        ref = _complex_step(At, W, M, G, E)
+        assert abs(Ps[i, j] + Ps[j, i] - ref) <= 1e-12 * max(1.0, abs(ref))
+        assert abs(Ps[i, j] - Ps[j, i]) <= 1e-14 * max(1.0, abs(ref))

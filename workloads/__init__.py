@@ -41,6 +41,7 @@ __all__ = [
     "CONFIGS",
     "make_operator",
     "sweep_points",
+    "er_batch",
 ]
 
 
@@ -214,7 +215,22 @@ CONFIGS = {
     "lap3d_lognormal_64": dict(
         op="lap3d_lognormal", nx=64, op_seed=1003, n_v=256, n_vh=0, probe="gaussian",
         probe_seed=2003, M=2000, n_t=800, sigma=0.06),
+    # B normalized Laplacians of G(N_b, 8/(N_b-1)), N_b ~ U{2000..60000}
+    "er_batch_128": dict(
+        op="er_batch", B=128, n_lo=2000, n_hi=60000, mean_degree=8.0, op_seed=1004, n_v=64, n_vh=0,
+        probe="gaussian", probe_seed=2004, M=500, n_t=200, sigma=0.05),
+    # trainable N(0, 0.3^2) potential on a 100^3 periodic 7-point Laplacian
+    "lap3d_normal_100": dict(
+        op="lap3d_normal", nx=100, op_seed=1005, n_v=128, n_vh=0, probe="gaussian",
+        probe_seed=2005, M=800, n_t=400, sigma=0.05, target_seed=3005),
 }
+
+
+def er_batch(B: int, n_lo: int, n_hi: int, mean_degree: float, seed: int):
+    """B weighted ER normalized Laplacians with sizes uniform in [n_lo, n_hi]."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_lo, n_hi + 1, size=B)
+    return [er_normalized_laplacian(int(n), mean_degree, seed * 1000 + k) for k, n in enumerate(sizes)]
 
 
 def make_operator(name: str, **over) -> Stencil:
@@ -227,4 +243,8 @@ def make_operator(name: str, **over) -> Stencil:
         return anderson2d(cfg["nx"], cfg["op_seed"])
     if op == "lap3d_lognormal":
         return laplacian3d_lognormal(cfg["nx"], cfg["op_seed"])
+    if op == "lap3d_normal":
+        return laplacian3d_normal_potential(cfg["nx"], cfg["op_seed"])
+    if op == "er_batch":
+        return er_batch(cfg["B"], cfg["n_lo"], cfg["n_hi"], cfg["mean_degree"], cfg["op_seed"])
     raise ValueError(op)
