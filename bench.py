@@ -373,6 +373,12 @@ def run_gpu(args, c, st, W, csr):
         cpu = {"value": units / t_cpu, "unit": "matrix-applies/s", "cores": _blas_threads(), "kind": "oracle",
                "sample": sample}
 
+    batched = adjoint = None
+    if rank == 0 and not args.no_batched:
+        batched = bench_batched(S, hbm)
+    if rank == 0 and not args.no_adjoint:
+        adjoint = bench_adjoint(S, hbm)
+
     if rank == 0:
         line = {
             "metric": "ssm_dos_effective_matrix_applies_per_s", "value": value,
@@ -387,11 +393,119 @@ def run_gpu(args, c, st, W, csr):
             "roofline": roofline, "rooflines": roofs, "phases_ms_per_step": phases,
             "gpu_launches": int(stats["launches"]),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+            "batched": batched, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     plan.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_batched(S, hbm, warmup: int = 1, steps: int = 2):
+    """Row a9: the 128-graph batched workload, recurrence as one captured CUDA graph."""
+    import torch
+    c = dict(wl.CONFIGS["er_batch_128"])
+    graphs = wl.make_operator("er_batch_128")
+    N = sum(g.n for g in graphs)
+    nnz = sum(g.nnz for g in graphs)
+    plan = S.ssm_plan_create_batched(graphs, n_v=c["n_v"], degree=c["M"], precision="mixed")
+    W = torch.from_numpy(wl.random_block(N, c["n_v"], c["probe_seed"], c["probe"])).cuda()
+    t = torch.from_numpy(np.concatenate([np.linspace(0.0, 2.0, c["n_t"]) for _ in graphs])).cuda()
+
+    def step():
+        S.ssm_moments(plan, W)
+        return S.ssm_dos(plan, t, c["sigma"], want_rank=False)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    S.ssm_stats_reset(plan)
+    S.ssm_timing_enable(plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = S.ssm_stats_get(plan)
+    S.ssm_timing_enable(plan, False)
+    M, nv = c["M"], c["n_v"]
+    rec_ms = st["ms_recurrence"] / steps
+    # per recurrence step: read V_k, V_{k-1}, write V_{k+1} (float32), CSR values and columns
+    step_bytes = 3.0 * N * nv * 4 + nnz * 8.0 + 8.0 * N
+    achieved = step_bytes * (M // 2) / (rec_ms * 1e-3) / 1e9
+    out = {"workload": "er_batch_128: 128 weighted ER normalized Laplacians, N_b ~ U{2000..60000} "
+                       "(sum N = %d, nnz = %d), N_v=64 gaussian, M=500, 200 points each, sigma=0.05, mixed" % (N, nnz),
+           "metric": "batched matrix-applies/s (sum_b nnz_b*N_v*M/s)", "value": nnz * nv * M / (ms * 1e-3),
+           "ms_per_step": ms, "phases_ms_per_step": {k: v / steps for k, v in st.items() if k.startswith("ms_")},
+           "csr_threads_autotuned": None, "graph_launches_per_step": 1,
+           "roofline": {"kernel": "recurrence graph (CSR step + tensor-core Gram + reduction), per step",
+                        "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "bytes_per_step": step_bytes}}
+    plan.close()
+    return out
+
+
+def bench_adjoint(S, hbm, warmup: int = 1, steps: int = 2):
+    """Row a10: KPM-DOS + Tr exp(-A) loss on the 100^3 potential workload, gradient by the adjoint."""
+    import torch
+    c = dict(wl.CONFIGS["lap3d_normal_100"])
+    st = wl.make_operator("lap3d_normal_100")
+    plan = S.ssm_plan_create(stencil=st, n_v=c["n_v"], degree=c["M"], precision="mixed", options=2)
+    info = S.ssm_plan_info(plan)
+    W = torch.from_numpy(wl.random_block(st.n, c["n_v"], c["probe_seed"], c["probe"])).cuda()
+    t = torch.linspace(info["lo"], info["hi"], c["n_t"], dtype=torch.float64, device="cuda")
+    dt = float(t[1] - t[0])
+    xw, ww = S.ssm_trace_weights(plan, lambda x: math.exp(-x), 512, 0.05, 0.016, 0.93, device="cuda")
+    tt = torch.cat([t, xw])
+    # target: the KPM DOS of the same stencil with another potential (seed 3005)
+    v_t = np.random.default_rng(c["target_seed"]).normal(0.0, 0.3, st.n) + (st.diag - np.mean(st.diag))
+    v_t = np.clip(v_t, np.min(st.diag), np.max(st.diag))
+    with torch.no_grad():
+        target = S.KPMDensity.apply(torch.from_numpy(v_t).cuda(), plan, W, t, c["sigma"]).clone()
+    v = torch.from_numpy(st.diag.copy()).cuda().requires_grad_(True)
+
+    def step():
+        v.grad = None
+        phi = S.KPMDensity.apply(v, plan, W, tt, c["sigma"])
+        loss = ((phi[: c["n_t"]] - target) ** 2).sum() * dt + (ww * phi[c["n_t"]:]).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    S.ssm_stats_reset(plan)
+    S.ssm_timing_enable(plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stt = S.ssm_stats_get(plan)
+    S.ssm_timing_enable(plan, False)
+    N, nv, M = st.n, c["n_v"], c["M"]
+    S_ = M // 2
+    adj_ms = stt["ms_adjoint"] / steps
+    # per backward step: U_{k+1} (+ neighbours from L2), U_{k+2}, V_{k-1}, V_k, V_{k+1} read, U_k written,
+    # one recomputed V (3 blocks), per-row float64 accumulators (4 read + 4 written)
+    step_bytes = 9.0 * N * nv * 4 + 64.0 * N
+    achieved = step_bytes * S_ / (adj_ms * 1e-3) / 1e9
+    gnorm = float(v.grad.norm()) if v.grad is not None else None
+    out = {"workload": "lap3d_normal_100: 3D 7-point periodic 100^3 (N=1e6) + N(0,0.3^2) potential, N_v=128, "
+                       "M=800, loss = KPM DOS L2 to a target on 400 points + Tr exp(-A) (Alg. 8 weights, 512 points)",
+           "metric": "forward+backward matrix-applies/s (nnz*N_v*M/s, forward counted once)",
+           "value": info["nnz"] * nv * M / (ms * 1e-3), "ms_per_step": ms,
+           "phases_ms_per_step": {k: v_ / steps for k, v_ in stt.items() if k.startswith("ms_")},
+           "grad_norm": gnorm,
+           "roofline": {"kernel": "adjoint steps (adj_stencil_kernel + recomputed stencil steps)", "bound": "hbm",
+                        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                        "bytes_per_step": step_bytes}}
+    plan.close()
+    return out
 
 
 def main():
@@ -404,6 +518,8 @@ def main():
     ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-plan row (128 graphs)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint row (100^3 potential)")
     ap.add_argument("--ref-rec-steps", type=int, default=100)
     ap.add_argument("--ref-points", type=int, default=20)
     args = ap.parse_args()

@@ -31,7 +31,7 @@ namespace ssm {
 
 namespace {
 
-constexpr int NT = 256;          // threads per CTA
+constexpr int NT = 256;          // largest CTA (solve_threads picks the size per n_v)
 constexpr int MAXN = 1024;       // largest n_v
 constexpr int MAX_QL_ITER = 60;
 
@@ -45,7 +45,7 @@ struct Shared {
     int* keep;     // n
     int* sel;      // n
     double* red;   // NT / 32
-    int* misc;     // [0] nkeep, [1] nsel, [2] QL range lo, [3] hi, [4] continue flag
+    int* misc;     // [0] nkeep, [1] nsel, [5] QL limit hit, [6] Cholesky pivot ok, [7] rank, [8..13] QL buffers
     double* beta;  // n: Householder scalars
 };
 
@@ -55,7 +55,7 @@ __device__ double block_sum(double v, double* red) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     __syncthreads();
     return s;
 }
@@ -66,7 +66,7 @@ __device__ double block_max(double v, double* red) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     double s = red[0];
-    for (int w = 1; w < NT / 32; ++w) s = fmax(s, red[w]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
     __syncthreads();
     return s;
 }
@@ -80,7 +80,7 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
         const int L = n - k - 1;
         const double* x = A + (size_t)k * n + k + 1;  // row k == column k (symmetric)
         double f = 0.0;
-        for (int i = tid; i < L; i += NT) f = fma(x[i], x[i], f);
+        for (int i = tid; i < L; i += (int)blockDim.x) f = fma(x[i], x[i], f);
         const double nrm2 = block_sum(f, sh.red);
         const double x0 = x[0];
         double beta = 0.0, alpha = x0;
@@ -89,7 +89,7 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             const double v0 = x0 - alpha;
             const double vtv = nrm2 - x0 * x0 + v0 * v0;
             beta = 2.0 / vtv;
-            for (int i = tid; i < L; i += NT) sh.v[i] = (i == 0) ? v0 : x[i];
+            for (int i = tid; i < L; i += (int)blockDim.x) sh.v[i] = (i == 0) ? v0 : x[i];
         }
         __syncthreads();
         if (tid == 0) {
@@ -101,7 +101,7 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             // p = beta A22 v: thread i walks column i of the symmetric A22 (row i
             // transposed), so a warp reads 32 consecutive doubles per step and
             // every thread has its own independent loads in flight
-            for (int i = tid; i < L; i += NT) {
+            for (int i = tid; i < L; i += (int)blockDim.x) {
                 const double* col = A + (size_t)(k + 1) * n + k + 1 + i;
                 double s0 = 0.0, s1 = 0.0;
                 int j = 0;
@@ -114,25 +114,25 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             }
             __syncthreads();
             double g = 0.0;
-            for (int i = tid; i < L; i += NT) g = fma(sh.p[i], sh.v[i], g);
+            for (int i = tid; i < L; i += (int)blockDim.x) g = fma(sh.p[i], sh.v[i], g);
             const double K = 0.5 * beta * block_sum(g, sh.red);
-            for (int i = tid; i < L; i += NT) sh.p[i] -= K * sh.v[i];  // p becomes w
+            for (int i = tid; i < L; i += (int)blockDim.x) sh.p[i] -= K * sh.v[i];  // p becomes w
             __syncthreads();
             // A22 -= v w^T + w v^T  (4 independent elements per thread per pass)
             const int LL = L * L;
-            for (int e0 = tid; e0 < LL; e0 += 4 * NT) {
+            for (int e0 = tid; e0 < LL; e0 += 4 * (int)blockDim.x) {
                 double a[4];
                 double* ap[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * NT;
+                    const int e = e0 + u * (int)blockDim.x;
                     const int i = e / L, j = e - (e / L) * L;
                     ap[u] = A + (size_t)(k + 1 + i) * n + k + 1 + j;
                     if (e < LL) a[u] = *ap[u];
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * NT;
+                    const int e = e0 + u * (int)blockDim.x;
                     if (e < LL) {
                         const int i = e / L, j = e - i * L;
                         *ap[u] = a[u] - (sh.v[i] * sh.p[j] + sh.p[i] * sh.v[j]);
@@ -140,7 +140,7 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
                 }
             }
             // keep v in row k for the accumulation
-            for (int i = tid; i < L; i += NT) A[(size_t)k * n + k + 1 + i] = sh.v[i];
+            for (int i = tid; i < L; i += (int)blockDim.x) A[(size_t)k * n + k + 1 + i] = sh.v[i];
         }
         __syncthreads();
     }
@@ -164,7 +164,7 @@ __device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ 
     const int tid = threadIdx.x;
     // Zt holds H^T during the accumulation; H_k acts on rows/columns k+1.. of H,
     // i.e. columns k+1.. of H^T: H^T <- H^T H_k^T = H^T H_k.
-    for (int e = tid; e < n * n; e += NT) {
+    for (int e = tid; e < n * n; e += (int)blockDim.x) {
         const int i = e / n, j = e - i * n;
         Zt[e] = (i == j) ? 1.0 : 0.0;
     }
@@ -175,7 +175,7 @@ __device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ 
         const int L = n - k - 1;
         const double* v = A + (size_t)k * n + k + 1;
         // H_sub <- H_k H_sub on rows/cols k+1..: u_j = sum_i v_i H[i][j] = sum_i v_i Zt[j][i]
-        for (int j = tid; j < L; j += NT) {
+        for (int j = tid; j < L; j += (int)blockDim.x) {
             const double* zr = Zt + (size_t)(k + 1 + j) * n + k + 1;
             double s = 0.0;
             for (int i = 0; i < L; ++i) s = fma(v[i], zr[i], s);
@@ -183,11 +183,11 @@ __device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ 
         }
         __syncthreads();
         const int LL = L * L;
-        for (int e0 = tid; e0 < LL; e0 += 4 * NT) {  // Zt[j][i] = H[i][j]
+        for (int e0 = tid; e0 < LL; e0 += 4 * (int)blockDim.x) {  // Zt[j][i] = H[i][j]
             double z[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * NT;
+                const int e = e0 + u * (int)blockDim.x;
                 if (e < LL) {
                     const int j = e / L, i = e - j * L;
                     z[u] = Zt[(size_t)(k + 1 + j) * n + k + 1 + i];
@@ -195,7 +195,7 @@ __device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ 
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * NT;
+                const int e = e0 + u * (int)blockDim.x;
                 if (e < LL) {
                     const int j = e / L, i = e - j * L;
                     Zt[(size_t)(k + 1 + j) * n + k + 1 + i] = z[u] - v[i] * sh.p[j];
@@ -206,115 +206,157 @@ __device__ void accumulate_q(const double* __restrict__ A, double* __restrict__ 
     }
 }
 
-// Implicit-shift QL on (sh.d, sh.off); eigenvalues -> sh.d.  With vectors,
-// every plane rotation acting on eigenvector columns (i, i+1) is applied to
-// rows i, i+1 of Zt.  Returns false if an eigenvalue needed more than
-// MAX_QL_ITER sweeps.
-__device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared& sh) {
-    const int tid = threadIdx.x;
-    bool converged = true;
-    for (int l = 0; l < n; ++l) {
-        for (int iter = 0; iter <= MAX_QL_ITER; ++iter) {
-            if (tid == 0) {
-                int m = l;
-                for (; m < n - 1; ++m) {
-                    const double dd = fabs(sh.d[m]) + fabs(sh.d[m + 1]);
-                    if (fabs(sh.off[m]) <= DBL_EPSILON * dd) break;
-                }
-                int lo = 0, hi = -1;  // rotations to apply: i from hi down to lo
-                if (m != l && iter < MAX_QL_ITER) {
-                    double g = (sh.d[l + 1] - sh.d[l]) / (2.0 * sh.off[l]);
-                    double r = sqrt(fma(g, g, 1.0));
-                    g = sh.d[m] - sh.d[l] + sh.off[l] / (g + copysign(r, g));
-                    double s = 1.0, c = 1.0, p = 0.0;
-                    int i = m - 1;
-                    bool early = false;
-                    for (; i >= l; --i) {
-                        const double f = s * sh.off[i];
-                        const double b = c * sh.off[i];
-                        // r = |(f, g)|, s = f / r, c = g / r with one reciprocal square root
-                        // (|f|, |g| are far from the float64 over/underflow range here; a
-                        // pair below 2^-500 is rescaled first)
-                        double fs = f, gs = g, scale = 1.0;
-                        if (fmax(fabs(f), fabs(g)) < 0x1p-500) {
-                            fs = f * 0x1p+500;
-                            gs = g * 0x1p+500;
-                            scale = 0x1p-500;
-                        }
-                        const double q = fma(fs, fs, gs * gs);
-                        if (q == 0.0) {
-                            sh.off[i + 1] = 0.0;
-                            sh.d[i + 1] -= p;
-                            sh.off[m] = 0.0;
-                            early = true;
-                            break;
-                        }
-                        const double rin = rsqrt(q);
-                        // one Newton step on 1/sqrt(q) keeps the rotation orthogonal to rounding
-                        const double rinv = rin * fma(-0.5 * q * rin, rin, 1.5);
-                        r = q * rinv * scale;
-                        sh.off[i + 1] = r;
-                        s = fs * rinv;
-                        c = gs * rinv;
-                        g = sh.d[i + 1] - p;
-                        r = (sh.d[i] - g) * s + 2.0 * c * b;
-                        p = s * r;
-                        sh.d[i + 1] = g + p;
-                        g = c * r - b;
-                        sh.rc[i] = c;
-                        sh.rs[i] = s;
-                    }
-                    hi = m - 1;
-                    lo = early ? i + 1 : l;
-                    if (!early) {
-                        sh.d[l] -= p;
-                        sh.off[l] = g;
-                        sh.off[m] = 0.0;
-                    }
-                    sh.misc[4] = 1;
-                } else {
-                    if (m != l) sh.misc[5] = 1;  // iteration limit reached
-                    sh.misc[4] = 0;
-                }
-                sh.misc[2] = lo;
-                sh.misc[3] = hi;
-            }
-            __syncthreads();
-            const int go = sh.misc[4];
-            if (vectors && go) {
-                // Rotation i maps (z_i, z_{i+1}) to (c z_i - s z_{i+1}, s z_i + c z_{i+1}); the new
-                // z_i is the z_{i+1} of rotation i-1, so it is carried in a register and every
-                // row is read and written once, with the reads issued 8 rotations ahead.
-                const int lo = sh.misc[2], hi = sh.misc[3];
-                if (hi >= lo) {
-                    for (int col = tid; col < n; col += NT) {
-                        double carry = Zt[(size_t)(hi + 1) * n + col];
-                        for (int i = hi; i >= lo; i -= 8) {
-                            const int cnt = (i - lo + 1) < 8 ? (i - lo + 1) : 8;
-                            double z[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if (u < cnt) z[u] = Zt[(size_t)(i - u) * n + col];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                if (u < cnt) {
-                                    const double c = sh.rc[i - u], s = sh.rs[i - u];
-                                    Zt[(size_t)(i - u + 1) * n + col] = s * z[u] + c * carry;
-                                    carry = c * z[u] - s * carry;
-                                }
-                            }
-                        }
-                        Zt[(size_t)lo * n + col] = carry;
-                    }
-                }
-            }
-            __syncthreads();
-            if (!go) break;
-        }
+// One implicit-shift QL sweep for the eigenvalue l (thread 0 only): finds the
+// unreduced block [l, m], and unless it is already split off (m == l) chases
+// the shifted rotation chain from m-1 down to l, updating (d, off) and
+// storing the rotations (c_i, s_i) in (rc, rs).  Returns m (m == l: converged);
+// [*lo, *hi] receives the rotation range.
+__device__ int ql_sweep(double* __restrict__ d, double* __restrict__ off, int n, int l, double* __restrict__ rc,
+                        double* __restrict__ rs, int* lo_out, int* hi_out) {
+    int m = l;
+    for (; m < n - 1; ++m) {
+        const double dd = fabs(d[m]) + fabs(d[m + 1]);
+        if (fabs(off[m]) <= DBL_EPSILON * dd) break;
     }
-    if (sh.misc[5]) converged = false;
+    if (m == l) return m;
+    double g = (d[l + 1] - d[l]) / (2.0 * off[l]);
+    double r = sqrt(fma(g, g, 1.0));
+    g = d[m] - d[l] + off[l] / (g + copysign(r, g));
+    double s = 1.0, c = 1.0, p = 0.0;
+    int i = m - 1;
+    bool early = false;
+    for (; i >= l; --i) {
+        const double f = s * off[i];
+        const double b = c * off[i];
+        // r = |(f, g)|, s = f / r, c = g / r with one reciprocal square root (|f|, |g|
+        // are far from the float64 over/underflow range here; a pair below 2^-500 is
+        // rescaled first)
+        double fs = f, gs = g, scale = 1.0;
+        if (fmax(fabs(f), fabs(g)) < 0x1p-500) {
+            fs = f * 0x1p+500;
+            gs = g * 0x1p+500;
+            scale = 0x1p-500;
+        }
+        const double q = fma(fs, fs, gs * gs);
+        if (q == 0.0) {
+            off[i + 1] = 0.0;
+            d[i + 1] -= p;
+            off[m] = 0.0;
+            early = true;
+            break;
+        }
+        const double rin = rsqrt(q);
+        // one Newton step on 1/sqrt(q) keeps the rotation orthogonal to rounding
+        const double rinv = rin * fma(-0.5 * q * rin, rin, 1.5);
+        r = q * rinv * scale;
+        off[i + 1] = r;
+        s = fs * rinv;
+        c = gs * rinv;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+        rc[i] = c;
+        rs[i] = s;
+    }
+    *hi_out = m - 1;
+    *lo_out = early ? i + 1 : l;
+    if (!early) {
+        d[l] -= p;
+        off[l] = g;
+        off[m] = 0.0;
+    }
+    return m;
+}
+
+// Implicit-shift QL on (sh.d, sh.off); eigenvalues -> sh.d (the QL method of
+// Martin, Reinsch and Wilkinson).  With vectors, every plane rotation acting
+// on eigenvector columns (i, i+1) is applied to rows i, i+1 of Zt.  The sweeps
+// are pipelined: thread 0 computes the rotation chain of the next sweep (it
+// depends on the tridiagonal only) into one of two buffers while warps 1.. apply
+// the previous sweep's rotations from the other.  Returns false if an
+// eigenvalue needed more than MAX_QL_ITER sweeps.
+__device__ bool ql_implicit(double* __restrict__ Zt, int n, bool vectors, Shared& sh) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // rotation buffers: 0 = (rc, rs), 1 = (v, p); misc[8 + 3 b] = go, lo, hi of buffer b
+    double* bc[2] = {sh.rc, sh.v};
+    double* bs[2] = {sh.rs, sh.p};
+    int l = 0, iter = 0;  // thread 0's position in the eigenvalue sequence
+    auto produce = [&](int b) {
+        int go = 0, lo = 0, hi = -1;
+        while (l < n) {
+            int lo_ = 0, hi_ = -1;
+            if (iter >= MAX_QL_ITER) {
+                // give up on this eigenvalue (reported), move on
+                int m = l;
+                for (; m < n - 1; ++m)
+                    if (fabs(sh.off[m]) <= DBL_EPSILON * (fabs(sh.d[m]) + fabs(sh.d[m + 1]))) break;
+                if (m != l) sh.misc[5] = 1;
+                ++l;
+                iter = 0;
+                continue;
+            }
+            const int m = ql_sweep(sh.d, sh.off, n, l, bc[b], bs[b], &lo_, &hi_);
+            if (m == l) {
+                ++l;
+                iter = 0;
+                continue;
+            }
+            ++iter;
+            go = 1;
+            lo = lo_;
+            hi = hi_;
+            break;
+        }
+        sh.misc[8 + 3 * b] = go;
+        sh.misc[9 + 3 * b] = lo;
+        sh.misc[10 + 3 * b] = hi;
+    };
+    if (!vectors) {
+        if (tid == 0)
+            do produce(0);
+            while (sh.misc[8]);
+        __syncthreads();
+        return sh.misc[5] == 0;
+    }
+    if (tid == 0) produce(0);
     __syncthreads();
-    return converged;
+    const int nap = (int)blockDim.x - 32;  // applying threads (warps 1..)
+    for (int b = 0;; b ^= 1) {
+        if (!sh.misc[8 + 3 * b]) break;
+        if (warp == 0) {
+            if (tid == 0) produce(b ^ 1);
+        } else {
+            // Rotation i maps (z_i, z_{i+1}) to (c z_i - s z_{i+1}, s z_i + c z_{i+1}); the
+            // new z_i is the z_{i+1} of rotation i-1, so it is carried in a register and
+            // every row is read and written once, with the reads issued 8 rotations ahead.
+            const int lo = sh.misc[9 + 3 * b], hi = sh.misc[10 + 3 * b];
+            const double* rc = bc[b];
+            const double* rs = bs[b];
+            for (int col = tid - 32; col < n; col += nap) {
+                double carry = Zt[(size_t)(hi + 1) * n + col];
+                for (int i = hi; i >= lo; i -= 8) {
+                    const int cnt = (i - lo + 1) < 8 ? (i - lo + 1) : 8;
+                    double z[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (u < cnt) z[u] = Zt[(size_t)(i - u) * n + col];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (u < cnt) {
+                            const double c = rc[i - u], s2 = rs[i - u];
+                            Zt[(size_t)(i - u + 1) * n + col] = s2 * z[u] + c * carry;
+                            carry = c * z[u] - s2 * carry;
+                        }
+                    }
+                }
+                Zt[(size_t)lo * n + col] = carry;
+            }
+        }
+        __syncthreads();
+    }
+    return sh.misc[5] == 0;
 }
 
 // Number of eigenvalues of the tridiagonal (d, off) below x: the sign changes
@@ -383,7 +425,7 @@ __device__ void bisect_prepare(int n, Shared& sh) {
     const int tid = threadIdx.x;
     float* d32 = reinterpret_cast<float*>(sh.rs);
     float* e32 = d32 + n;
-    for (int i = tid; i < n; i += NT) {
+    for (int i = tid; i < n; i += (int)blockDim.x) {
         const double e2 = (i + 1 < n) ? sh.off[i] * sh.off[i] : 0.0;
         sh.p[i] = e2;
         d32[i] = (float)sh.d[i];
@@ -441,7 +483,7 @@ __device__ double bisect_one(int j, int n, const Shared& sh) {
 // All eigenvalues, one thread per eigenvalue, into sh.v (ascending).
 __device__ void bisect_all(int n, Shared& sh) {
     bisect_prepare(n, sh);
-    for (int j = threadIdx.x; j < n; j += NT) sh.v[j] = bisect_one(j, n, sh);
+    for (int j = threadIdx.x; j < n; j += (int)blockDim.x) sh.v[j] = bisect_one(j, n, sh);
     __syncthreads();
 }
 
@@ -465,14 +507,14 @@ __device__ bool cholesky_lower(double* __restrict__ A, int n, Shared& sh) {
         __syncthreads();
         if (!sh.misc[6]) return false;
         const double rk = sh.v[k];
-        for (int i = k + 1 + tid; i < n; i += NT) {
+        for (int i = k + 1 + tid; i < n; i += (int)blockDim.x) {
             const double v = A[(size_t)i * n + k] * rk;
             A[(size_t)i * n + k] = v;
             sh.p[i] = v;
         }
         __syncthreads();
         // A[i][j] -= l_i l_j for k < j <= i (warp per row, lanes along the row)
-        for (int i = k + 1 + warp; i < n; i += NT / 32) {
+        for (int i = k + 1 + warp; i < n; i += (int)(blockDim.x >> 5)) {
             const double li = sh.p[i];
             double* row = A + (size_t)i * n;
             for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fma(-li, sh.p[j], row[j]);
@@ -485,7 +527,7 @@ __device__ bool cholesky_lower(double* __restrict__ A, int n, Shared& sh) {
 // X <- L^{-1} X for the n x n row-major X, L from cholesky_lower (rdiag =
 // sh.v): forward substitution, one column of X per thread.
 __device__ void trsm_lower(const double* __restrict__ L, double* __restrict__ X, int n, const Shared& sh) {
-    for (int c = threadIdx.x; c < n; c += NT) {
+    for (int c = threadIdx.x; c < n; c += (int)blockDim.x) {
         for (int i = 0; i < n; ++i) {
             const double* li = L + (size_t)i * n;
             double s0 = X[(size_t)i * n + c], s1 = 0.0;
@@ -505,7 +547,7 @@ __device__ void trsm_lower(const double* __restrict__ L, double* __restrict__ X,
 // the rows of X, one row per thread; row r of X gives column r of Y.
 __device__ void trsm_lower_t(const double* __restrict__ L, const double* __restrict__ X, double* __restrict__ Y,
                              int n, const Shared& sh) {
-    for (int r = threadIdx.x; r < n; r += NT) {
+    for (int r = threadIdx.x; r < n; r += (int)blockDim.x) {
         const double* xr = X + (size_t)r * n;
         for (int i = 0; i < n; ++i) {
             const double* li = L + (size_t)i * n;
@@ -538,7 +580,7 @@ __device__ bool eigh(double* __restrict__ A, double* __restrict__ Zt, int n, boo
     tridiagonalise(A, n, sh);
     if (!vectors) {
         bisect_all(n, sh);
-        for (int j = threadIdx.x; j < n; j += NT) sh.d[j] = sh.v[j];
+        for (int j = threadIdx.x; j < n; j += (int)blockDim.x) sh.d[j] = sh.v[j];
         __syncthreads();
         return true;
     }
@@ -578,12 +620,12 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
         // rounding floor of K_W(t)
         double fs = 0.0;
         if (floor_scale > 0.0 || floor_pt)
-            for (int l = tid; l <= K; l += NT) fs = fma((double)(l + 1), fabs(mu[it * ldmu + l]), fs);
+            for (int l = tid; l <= K; l += (int)blockDim.x) fs = fma((double)(l + 1), fabs(mu[it * ldmu + l]), fs);
         const double floor_t = (floor_pt ? floor_pt[3 * it] : floor_scale) * block_sum(fs, sh.red);
         const double xl = floor_pt ? floor_pt[3 * it + 1] : xlo, xh = floor_pt ? floor_pt[3 * it + 2] : xhi;
         // 1. K_W (symmetrised) -> A, tridiagonal form; the largest eigenvalue and
         //    the number r of eigenvalues >= max(tau smax, floor) from Sturm counts
-        for (int e = tid; e < n * n; e += NT) {
+        for (int e = tid; e < n * n; e += (int)blockDim.x) {
             const int i = e / n, j = e - i * n;
             A[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
         }
@@ -607,20 +649,20 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             //     orthogonal) of K_W, G^-1 K_Z G^-T = Q^T B Q has the same eigenvalues,
             //     so B's eigenvalues come from the Cholesky factor L instead:
             //     C = L^-1 K_Z L^-T, without the eigenvectors of K_W.
-            for (int e = tid; e < n * n; e += NT) {
+            for (int e = tid; e < n * n; e += (int)blockDim.x) {
                 const int i = e / n, j = e - i * n;
                 Zt[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
             }
             __syncthreads();
             if (cholesky_lower(Zt, n, sh)) {
-                for (int e = tid; e < n * n; e += NT) {
+                for (int e = tid; e < n * n; e += (int)blockDim.x) {
                     const int i = e / n, j = e - i * n;
                     Y[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
                 }
                 __syncthreads();
                 trsm_lower(Zt, Y, n, sh);         // Y = L^-1 K_Z
                 trsm_lower_t(Zt, Y, A, n, sh);    // A = L^-1 Y^T = L^-1 K_Z L^-T
-                for (int e = tid; e < n * n; e += NT) {  // symmetrise (upper from lower)
+                for (int e = tid; e < n * n; e += (int)blockDim.x) {  // symmetrise (upper from lower)
                     const int i = e / n, j = e - i * n;
                     if (i < j) {
                         const double v = 0.5 * (A[e] + A[(size_t)j * n + i]);
@@ -638,7 +680,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 }
                 __syncthreads();
                 const int jlo = sh.misc[0], jhi = sh.misc[1];
-                for (int j = jlo + tid; j < jhi; j += NT) sh.v[j] = bisect_one(j, n, sh);
+                for (int j = jlo + tid; j < jhi; j += (int)blockDim.x) sh.v[j] = bisect_one(j, n, sh);
                 __syncthreads();
                 if (tid == 0) {  // range filter; the sum runs in index order on one thread
                     int q = 0;
@@ -670,7 +712,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             ok = ql_implicit(Zt, n, true, sh);
             // truncation s_j >= max(tau max s, rounding floor of K_W)
             double m = -DBL_MAX;
-            for (int j = tid; j < n; j += NT) m = fmax(m, sh.d[j]);
+            for (int j = tid; j < n; j += (int)blockDim.x) m = fmax(m, sh.d[j]);
             const double smax = block_max(m, sh.red);
             if (tid == 0) {
                 int rr = 0;
@@ -684,15 +726,15 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             __syncthreads();
             r = sh.misc[0];
             // Y = S~^-1/2 U~^T (rows)
-            for (int k = tid; k < r; k += NT) sh.v[k] = 1.0 / sqrt(sh.d[sh.keep[k]]);
+            for (int k = tid; k < r; k += (int)blockDim.x) sh.v[k] = 1.0 / sqrt(sh.d[sh.keep[k]]);
             __syncthreads();
-            for (int e = tid; e < r * n; e += NT) {
+            for (int e = tid; e < r * n; e += (int)blockDim.x) {
                 const int k = e / n, c = e - k * n;
                 Y[(size_t)k * n + c] = Zt[(size_t)sh.keep[k] * n + c] * sh.v[k];
             }
             __syncthreads();
             // T1 = Y K_Z (r x n)
-            for (int e = tid; e < r * n; e += NT) {
+            for (int e = tid; e < r * n; e += (int)blockDim.x) {
                 const int k = e / n, c = e - k * n;
                 const double* y = Y + (size_t)k * n;
                 double s = 0.0;
@@ -703,7 +745,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             // B = T1 Y^T (r x r, ld r) into A: symmetric (K_Z is), upper triangle
             // computed and mirrored
             const int npair = r * (r + 1) / 2;
-            for (int e = tid; e < npair; e += NT) {
+            for (int e = tid; e < npair; e += (int)blockDim.x) {
                 // packed upper triangle index -> (k, kk), k <= kk
                 int k = (int)((2.0 * r + 1.0 - sqrt((2.0 * r + 1.0) * (2.0 * r + 1.0) - 8.0 * e)) * 0.5);
                 if (k < 0) k = 0;
@@ -748,7 +790,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             if (nvh > 0) {
                 // 5. C~^T rows: CtT[m][c] = sum_k X[k][sel_m] Y[k][c], X = eigenvectors of B
                 //    (row sel_m of Zt)  -> T1 (rs x n)
-                for (int e = tid; e < rs * n; e += NT) {
+                for (int e = tid; e < rs * n; e += (int)blockDim.x) {
                     const int mq = e / n, c = e - mq * n;
                     const double* x = Zt + (size_t)sh.sel[mq] * r;
                     double s = 0.0;
@@ -761,7 +803,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
         if (nvh > 0) {
             // hybrid correction (Tr K_W~ - ||K_C C~||_F^2) / N~_v; C~ has rs columns (rows of T1)
             double f = 0.0;
-            for (int e = tid; e < nvh * rs; e += NT) {
+            for (int e = tid; e < nvh * rs; e += (int)blockDim.x) {
                 const int h = e / rs, mq = e - h * rs;
                 const double* kc = Kt + (size_t)(nv + h) * n_tot;
                 const double* ct = T1 + (size_t)mq * n;
@@ -786,20 +828,25 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
     }
 }
 
-// CTAs with a private workspace: 4 per SM to overlap the serial QL chains,
-// fewer when 4 n^2 doubles per CTA would exceed 2 GiB in total.
+// Threads per CTA: one per row of the per-point matrices up to 256 (smaller
+// problems, e.g. n_v = 64 in batched plans, get small CTAs and more of them
+// per SM).
+int solve_threads(int n_v) { return n_v <= 64 ? 64 : (n_v <= 128 ? 128 : NT); }
+
+// CTAs with a private workspace: 4 x (256 / threads) per SM to overlap the
+// serial QL chains, fewer when 4 n^2 doubles per CTA would exceed 2 GiB in total.
 int workspace_ctas(int n_v) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t per = (size_t)4 * n_v * n_v * sizeof(double);
     size_t cap = ((size_t)2 << 30) / per;
-    size_t g = (size_t)4 * sms;
+    size_t g = (size_t)4 * sms * (NT / solve_threads(n_v));
     if (g > cap) g = cap;
     return g < 1 ? 1 : (int)g;
 }
 
-size_t solve_smem(int n) { return (size_t)7 * n * sizeof(double) + (NT / 32) * sizeof(double) + (2 * n + 8) * sizeof(int); }
+size_t solve_smem(int n) { return (size_t)7 * n * sizeof(double) + (NT / 32) * sizeof(double) + (2 * n + 16) * sizeof(int); }
 
 }  // namespace
 
@@ -817,7 +864,7 @@ cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int
     if (e != cudaSuccess) return e;
     int64_t grid = workspace_ctas(n_v);
     if (grid > n_t) grid = n_t;
-    solve_kernel<<<(int)grid, NT, smem, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K,
+    solve_kernel<<<(int)grid, solve_threads(n_v), smem, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K,
                                                    floor_scale, (double*)work, dos, rank, flag, floor_pt);
     return cudaGetLastError();
 }
