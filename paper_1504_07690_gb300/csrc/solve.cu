@@ -564,6 +564,150 @@ __device__ void trsm_lower_t(const double* __restrict__ L, const double* __restr
     __syncthreads();
 }
 
+// Sum (and count) of the eigenvalues of the symmetric m x m matrix C (ld m,
+// destroyed) that lie in [xl, xh]: tridiagonal form, then bisection for the
+// eigenvalues near or inside the interval only; the sum runs in index order on
+// one thread.
+__device__ double range_sum(double* __restrict__ C, int m, double xl, double xh, Shared& sh, int* count) {
+    const int tid = threadIdx.x;
+    tridiagonalise(C, m, sh);
+    bisect_prepare(m, sh);
+    if (tid == 0) {
+        sh.misc[0] = max(0, sturm_below(sh.d, sh.p, m, xl) - 1);
+        sh.misc[1] = min(m, sturm_below(sh.d, sh.p, m, xh) + 1);
+    }
+    __syncthreads();
+    const int jlo = sh.misc[0], jhi = sh.misc[1];
+    for (int j = jlo + tid; j < jhi; j += (int)blockDim.x) sh.v[j] = bisect_one(j, m, sh);
+    __syncthreads();
+    if (tid == 0) {
+        int q = 0;
+        double f = 0.0;
+        for (int j = jlo; j < jhi; ++j) {
+            const double xi = sh.v[j];
+            if (xi >= xl && xi <= xh) {
+                ++q;
+                f += xi;
+            }
+        }
+        sh.misc[1] = q;
+        sh.p[0] = f;
+    }
+    __syncthreads();
+    *count = sh.misc[1];
+    const double f = sh.p[0];
+    __syncthreads();
+    return f;
+}
+
+// Eigenvectors of the tridiagonal (sh.d, sh.off) for the r eigenvalues in
+// sh.v[0..r) (accurate, from bisection), one thread each, by the twisted
+// factorization of T - lambda I (Dhillon and Parlett): the top-down pivots
+// D+_i and bottom-up pivots D-_i of T - lambda I = L+ D+ L+^T = U- D- U-^T meet
+// at the index k minimising |gamma_k| = |D+_k + D-_k - (d_k - lambda)|, and the
+// vector is z_k = 1, z_i = -(e_i / D+_i) z_{i+1} above k, z_i = -(e_{i-1} / D-_i)
+// z_{i-1} below, with ||(T - lambda I) z|| = |gamma_k| for z_k = 1.  Column q of
+// Z (ld ldz) receives the normalised vector of sh.v[q]; Dp, Dm (ld ldz) hold the
+// pivots.  Zero pivots are replaced by eps ||T||.  Sets sh.misc[6] = 0 when a
+// vector is not finite, its residual exceeds 1e3 n eps ||T||, or two
+// neighbouring vectors are not orthogonal to 1e-6 (nearly equal eigenvalues):
+// the caller then takes the QL route.
+__device__ void twisted_vectors(int n, int r, double* __restrict__ Z, double* __restrict__ Dp,
+                                double* __restrict__ Dm, int ldz, Shared& sh) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        double tn = 0.0;
+        for (int i = 0; i < n; ++i)
+            tn = fmax(tn, fabs(sh.d[i]) + (i > 0 ? fabs(sh.off[i - 1]) : 0.0) + (i + 1 < n ? fabs(sh.off[i]) : 0.0));
+        sh.red[0] = tn;
+        sh.misc[6] = 1;
+    }
+    __syncthreads();
+    const double tnorm = sh.red[0];
+    const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
+    for (int q = tid; q < r; q += (int)blockDim.x) {
+        const double lam = sh.v[q];
+        double dp = sh.d[0] - lam;
+        if (dp == 0.0) dp = tiny;
+        Dp[q] = dp;
+        for (int i = 0; i + 1 < n; ++i) {
+            const double e = sh.off[i];
+            dp = (sh.d[i + 1] - lam) - e * (e / dp);
+            if (dp == 0.0) dp = tiny;
+            Dp[(size_t)(i + 1) * ldz + q] = dp;
+        }
+        double dm = sh.d[n - 1] - lam;
+        if (dm == 0.0) dm = tiny;
+        Dm[(size_t)(n - 1) * ldz + q] = dm;
+        double gbest = fabs(Dp[(size_t)(n - 1) * ldz + q] + dm - (sh.d[n - 1] - lam));
+        int kbest = n - 1;
+        for (int i = n - 2; i >= 0; --i) {
+            const double e = sh.off[i];
+            dm = (sh.d[i] - lam) - e * (e / dm);
+            if (dm == 0.0) dm = tiny;
+            Dm[(size_t)i * ldz + q] = dm;
+            const double g = fabs(Dp[(size_t)i * ldz + q] + dm - (sh.d[i] - lam));
+            if (g < gbest) {
+                gbest = g;
+                kbest = i;
+            }
+        }
+        Z[(size_t)kbest * ldz + q] = 1.0;
+        double z = 1.0, nrm = 1.0, zmax = 1.0;
+        for (int i = kbest - 1; i >= 0; --i) {
+            z = -(sh.off[i] / Dp[(size_t)i * ldz + q]) * z;
+            Z[(size_t)i * ldz + q] = z;
+            nrm = fma(z, z, nrm);
+            zmax = fmax(zmax, fabs(z));
+        }
+        z = 1.0;
+        for (int i = kbest + 1; i < n; ++i) {
+            z = -(sh.off[i - 1] / Dm[(size_t)i * ldz + q]) * z;
+            Z[(size_t)i * ldz + q] = z;
+            nrm = fma(z, z, nrm);
+            zmax = fmax(zmax, fabs(z));
+        }
+        const bool good = isfinite(nrm) && zmax < 1e150 && gbest <= 1e3 * n * DBL_EPSILON * tnorm * sqrt(nrm);
+        if (!good) sh.misc[6] = 0;
+        const double inv = 1.0 / sqrt(nrm);
+        for (int i = 0; i < n; ++i) Z[(size_t)i * ldz + q] *= inv;
+    }
+    __syncthreads();
+    // neighbouring vectors (close eigenvalues) must come out orthogonal
+    for (int q = tid; q + 1 < r; q += (int)blockDim.x) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c = fma(Z[(size_t)i * ldz + q], Z[(size_t)i * ldz + q + 1], c);
+        if (!(fabs(c) <= 1e-6)) sh.misc[6] = 0;
+    }
+    __syncthreads();
+}
+
+// z <- H z for the r columns of Z (ld ldz), H = H_0 H_1 ... H_{n-3} the
+// Householder factor left by tridiagonalise (vector k in row k of A from column
+// k+1, scalar sh.beta[k]): the eigenvectors of T become those of the matrix it
+// was reduced from.  One thread per column.
+__device__ void back_transform(const double* __restrict__ A, int n, double* __restrict__ Z, int ldz, int r,
+                               const Shared& sh) {
+    for (int q = threadIdx.x; q < r; q += (int)blockDim.x) {
+        for (int k = n - 3; k >= 0; --k) {
+            const double beta = sh.beta[k];
+            if (beta == 0.0) continue;
+            const int L = n - k - 1;
+            const double* v = A + (size_t)k * n + k + 1;
+            double s0 = 0.0, s1 = 0.0;
+            int i = 0;
+            for (; i + 1 < L; i += 2) {
+                s0 = fma(v[i], Z[(size_t)(k + 1 + i) * ldz + q], s0);
+                s1 = fma(v[i + 1], Z[(size_t)(k + 2 + i) * ldz + q], s1);
+            }
+            if (i < L) s0 = fma(v[i], Z[(size_t)(k + 1 + i) * ldz + q], s0);
+            const double f = beta * (s0 + s1);
+            for (int j = 0; j < L; ++j) Z[(size_t)(k + 1 + j) * ldz + q] -= f * v[j];
+        }
+    }
+    __syncthreads();
+}
+
 // Eigen-decomposition of the symmetric n x n matrix A (destroyed): sh.d gets
 // the eigenvalues; with vectors, row j of Zt the eigenvector of sh.d[j].
 // Without vectors the eigenvalues come from bisection (parallel) instead of
@@ -671,39 +815,98 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     }
                 }
                 __syncthreads();
-                tridiagonalise(A, n, sh);
-                bisect_prepare(n, sh);
-                // only the eigenvalues near or inside [xl, xh] are needed
-                if (tid == 0) {
-                    sh.misc[0] = max(0, sturm_below(sh.d, sh.p, n, xl) - 1);
-                    sh.misc[1] = min(n, sturm_below(sh.d, sh.p, n, xh) + 1);
+                phi = range_sum(A, n, xl, xh, sh, &rs);
+                r = n;
+                done = true;
+            }
+        }
+        bool stale = false;  // the tridiagonal form of K_W was overwritten
+        if (!done && r_est > 0 && r_est < n && nvh == 0) {
+            // 2''. Some directions are truncated (the subspace route).  Alg. 4's B is the
+            //     pencil (U~^T K_Z U~, U~^T K_W U~ = S~) on the kept invariant subspace of
+            //     K_W, and its eigenvalues are the same in any basis of that subspace:
+            //     with Y = H Z, Z the twisted-factorization eigenvectors of the kept
+            //     eigenvalues of the tridiagonal T = H^T K_W H, they are those of
+            //     L^-1 (Y^T K_Z Y) L^-T, L L^T = Z^T T Z.  No QL sweeps, no full eigenvector
+            //     matrix; the kept count comes from the same Sturm counts.
+            const int rk = r_est, j0 = n - r_est;
+            for (int q = tid; q < rk; q += (int)blockDim.x) sh.v[q] = bisect_one(j0 + q, n, sh);
+            __syncthreads();
+            twisted_vectors(n, rk, Zt, Y, T1, n, sh);
+            if (sh.misc[6]) {
+                // M_W = Z^T T Z (rk x rk, ld rk) into Y
+                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                    const int pp = e / rk, q = e - pp * rk;
+                    if (pp > q) continue;
+                    double acc = 0.0;
+                    for (int i = 0; i < n; ++i) {
+                        double tz = sh.d[i] * Zt[(size_t)i * n + q];
+                        if (i > 0) tz = fma(sh.off[i - 1], Zt[(size_t)(i - 1) * n + q], tz);
+                        if (i + 1 < n) tz = fma(sh.off[i], Zt[(size_t)(i + 1) * n + q], tz);
+                        acc = fma(Zt[(size_t)i * n + pp], tz, acc);
+                    }
+                    Y[(size_t)pp * rk + q] = acc;
+                    Y[(size_t)q * rk + pp] = acc;
                 }
                 __syncthreads();
-                const int jlo = sh.misc[0], jhi = sh.misc[1];
-                for (int j = jlo + tid; j < jhi; j += (int)blockDim.x) sh.v[j] = bisect_one(j, n, sh);
+                back_transform(A, n, Zt, n, rk, sh);  // columns of Zt: kept eigenvectors of K_W
+                // T1 = K_Z Yc (n x rk, ld rk)
+                for (int e = tid; e < n * rk; e += (int)blockDim.x) {
+                    const int i = e / rk, q = e - i * rk;
+                    const double* zr = Zk + (size_t)i * n;
+                    double s0 = 0.0, s1 = 0.0;
+                    int m = 0;
+                    for (; m + 1 < n; m += 2) {
+                        s0 = fma(zr[m], Zt[(size_t)m * n + q], s0);
+                        s1 = fma(zr[m + 1], Zt[(size_t)(m + 1) * n + q], s1);
+                    }
+                    if (m < n) s0 = fma(zr[m], Zt[(size_t)m * n + q], s0);
+                    T1[(size_t)i * rk + q] = s0 + s1;
+                }
                 __syncthreads();
-                if (tid == 0) {  // range filter; the sum runs in index order on one thread
-                    int q = 0;
-                    double f = 0.0;
-                    for (int j = jlo; j < jhi; ++j) {
-                        const double xi = sh.v[j];
-                        if (xi >= xl && xi <= xh) {
-                            ++q;
-                            f += xi;
+                // M_Z = Yc^T T1 (rk x rk, ld rk) into A (the reflectors are no longer needed)
+                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                    const int pp = e / rk, q = e - pp * rk;
+                    if (pp > q) continue;
+                    double s0 = 0.0, s1 = 0.0;
+                    int i = 0;
+                    for (; i + 1 < n; i += 2) {
+                        s0 = fma(Zt[(size_t)i * n + pp], T1[(size_t)i * rk + q], s0);
+                        s1 = fma(Zt[(size_t)(i + 1) * n + pp], T1[(size_t)(i + 1) * rk + q], s1);
+                    }
+                    if (i < n) s0 = fma(Zt[(size_t)i * n + pp], T1[(size_t)i * rk + q], s0);
+                    A[(size_t)pp * rk + q] = s0 + s1;
+                    A[(size_t)q * rk + pp] = s0 + s1;
+                }
+                __syncthreads();
+                stale = true;
+                if (cholesky_lower(Y, rk, sh)) {
+                    trsm_lower(Y, A, rk, sh);          // A = L^-1 M_Z
+                    trsm_lower_t(Y, A, T1, rk, sh);    // T1 = L^-1 M_Z L^-T
+                    for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                        const int i = e / rk, j = e - i * rk;
+                        if (i < j) {
+                            const double v = 0.5 * (T1[e] + T1[(size_t)j * rk + i]);
+                            T1[e] = v;
+                            T1[(size_t)j * rk + i] = v;
                         }
                     }
-                    sh.misc[1] = q;
-                    sh.p[0] = f;
+                    __syncthreads();
+                    phi = range_sum(T1, rk, xl, xh, sh, &rs);
+                    r = rk;
+                    done = true;
                 }
-                __syncthreads();
-                r = n;
-                rs = sh.misc[1];
-                phi = sh.p[0];
-                done = true;
-                __syncthreads();
             }
         }
         if (!done) {
+            if (stale) {  // start again from K_W
+                for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                    const int i = e / n, j = e - i * n;
+                    A[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
+                }
+                __syncthreads();
+                tridiagonalise(A, n, sh);
+            }
             // 2. eigenvectors of K_W: accumulate the Householder factor (A holds the
             //    reflectors, sh.d / sh.off the tridiagonal form) and run QL on it
             accumulate_q(A, Zt, n, sh);
