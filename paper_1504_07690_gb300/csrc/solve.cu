@@ -47,6 +47,7 @@ struct Shared {
     double* red;   // NT / 32
     int* misc;     // [0] nkeep, [1] nsel, [5] QL limit hit, [6] Cholesky pivot ok, [7] rank, [8..13] QL buffers
     double* beta;  // n: Householder scalars
+    double* gt;    // 2 x 32 x 33: staged tiles of gemm_tn
 };
 
 __device__ double block_sum(double v, double* red) {
@@ -69,6 +70,26 @@ __device__ double block_max(double v, double* red) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
     __syncthreads();
     return s;
+}
+
+// sum_{k < len} a[k sa] b[k sb] with 8 independent partial sums (float64 latency
+// on this part is long: the loads and fmas of 8 terms are in flight at once).
+__device__ __forceinline__ double dot8(const double* __restrict__ a, size_t sa, const double* __restrict__ b,
+                                       size_t sb, int len) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0, s6 = 0.0, s7 = 0.0;
+    int k = 0;
+    for (; k + 8 <= len; k += 8) {
+        s0 = fma(a[(size_t)k * sa], b[(size_t)k * sb], s0);
+        s1 = fma(a[(size_t)(k + 1) * sa], b[(size_t)(k + 1) * sb], s1);
+        s2 = fma(a[(size_t)(k + 2) * sa], b[(size_t)(k + 2) * sb], s2);
+        s3 = fma(a[(size_t)(k + 3) * sa], b[(size_t)(k + 3) * sb], s3);
+        s4 = fma(a[(size_t)(k + 4) * sa], b[(size_t)(k + 4) * sb], s4);
+        s5 = fma(a[(size_t)(k + 5) * sa], b[(size_t)(k + 5) * sb], s5);
+        s6 = fma(a[(size_t)(k + 6) * sa], b[(size_t)(k + 6) * sb], s6);
+        s7 = fma(a[(size_t)(k + 7) * sa], b[(size_t)(k + 7) * sb], s7);
+    }
+    for (; k < len; ++k) s0 = fma(a[(size_t)k * sa], b[(size_t)k * sb], s0);
+    return ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7));
 }
 
 // Householder reduction of the symmetric n x n matrix A (row-major, ld n) to
@@ -101,41 +122,25 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             // p = beta A22 v: thread i walks column i of the symmetric A22 (row i
             // transposed), so a warp reads 32 consecutive doubles per step and
             // every thread has its own independent loads in flight
-            for (int i = tid; i < L; i += (int)blockDim.x) {
-                const double* col = A + (size_t)(k + 1) * n + k + 1 + i;
-                double s0 = 0.0, s1 = 0.0;
-                int j = 0;
-                for (; j + 1 < L; j += 2) {
-                    s0 = fma(col[(size_t)j * n], sh.v[j], s0);
-                    s1 = fma(col[(size_t)(j + 1) * n], sh.v[j + 1], s1);
-                }
-                if (j < L) s0 = fma(col[(size_t)j * n], sh.v[j], s0);
-                sh.p[i] = beta * (s0 + s1);
-            }
+            for (int i = tid; i < L; i += (int)blockDim.x)
+                sh.p[i] = beta * dot8(A + (size_t)(k + 1) * n + k + 1 + i, n, sh.v, 1, L);
             __syncthreads();
             double g = 0.0;
             for (int i = tid; i < L; i += (int)blockDim.x) g = fma(sh.p[i], sh.v[i], g);
             const double K = 0.5 * beta * block_sum(g, sh.red);
             for (int i = tid; i < L; i += (int)blockDim.x) sh.p[i] -= K * sh.v[i];  // p becomes w
             __syncthreads();
-            // A22 -= v w^T + w v^T  (4 independent elements per thread per pass)
-            const int LL = L * L;
-            for (int e0 = tid; e0 < LL; e0 += 4 * (int)blockDim.x) {
-                double a[4];
-                double* ap[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    const int i = e / L, j = e - (e / L) * L;
-                    ap[u] = A + (size_t)(k + 1 + i) * n + k + 1 + j;
-                    if (e < LL) a[u] = *ap[u];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * (int)blockDim.x;
-                    if (e < LL) {
-                        const int i = e / L, j = e - i * L;
-                        *ap[u] = a[u] - (sh.v[i] * sh.p[j] + sh.p[i] * sh.v[j]);
+            // A22 -= v w^T + w v^T on the lower triangle (warp per row, lanes along the
+            // row), mirrored to the upper one: half the float64 work, exact symmetry
+            {
+                const int nw = (int)(blockDim.x >> 5), wp = tid >> 5, ln = tid & 31;
+                for (int i = wp; i < L; i += nw) {
+                    const double vi = sh.v[i], pi = sh.p[i];
+                    double* rowi = A + (size_t)(k + 1 + i) * n + k + 1;
+                    for (int j = ln; j <= i; j += 32) {
+                        const double a = fma(-vi, sh.p[j], fma(-pi, sh.v[j], rowi[j]));
+                        rowi[j] = a;
+                        A[(size_t)(k + 1 + j) * n + k + 1 + i] = a;
                     }
                 }
             }
@@ -528,17 +533,8 @@ __device__ bool cholesky_lower(double* __restrict__ A, int n, Shared& sh) {
 // sh.v): forward substitution, one column of X per thread.
 __device__ void trsm_lower(const double* __restrict__ L, double* __restrict__ X, int n, const Shared& sh) {
     for (int c = threadIdx.x; c < n; c += (int)blockDim.x) {
-        for (int i = 0; i < n; ++i) {
-            const double* li = L + (size_t)i * n;
-            double s0 = X[(size_t)i * n + c], s1 = 0.0;
-            int k = 0;
-            for (; k + 1 < i; k += 2) {
-                s0 = fma(-li[k], X[(size_t)k * n + c], s0);
-                s1 = fma(-li[k + 1], X[(size_t)(k + 1) * n + c], s1);
-            }
-            if (k < i) s0 = fma(-li[k], X[(size_t)k * n + c], s0);
-            X[(size_t)i * n + c] = (s0 + s1) * sh.v[i];
-        }
+        for (int i = 0; i < n; ++i)
+            X[(size_t)i * n + c] = (X[(size_t)i * n + c] - dot8(L + (size_t)i * n, 1, X + c, n, i)) * sh.v[i];
     }
     __syncthreads();
 }
@@ -549,25 +545,20 @@ __device__ void trsm_lower_t(const double* __restrict__ L, const double* __restr
                              int n, const Shared& sh) {
     for (int r = threadIdx.x; r < n; r += (int)blockDim.x) {
         const double* xr = X + (size_t)r * n;
-        for (int i = 0; i < n; ++i) {
-            const double* li = L + (size_t)i * n;
-            double s0 = xr[i], s1 = 0.0;
-            int k = 0;
-            for (; k + 1 < i; k += 2) {
-                s0 = fma(-li[k], Y[(size_t)k * n + r], s0);
-                s1 = fma(-li[k + 1], Y[(size_t)(k + 1) * n + r], s1);
-            }
-            if (k < i) s0 = fma(-li[k], Y[(size_t)k * n + r], s0);
-            Y[(size_t)i * n + r] = (s0 + s1) * sh.v[i];
-        }
+        for (int i = 0; i < n; ++i)
+            Y[(size_t)i * n + r] = (xr[i] - dot8(L + (size_t)i * n, 1, Y + r, n, i)) * sh.v[i];
     }
     __syncthreads();
 }
 
 // Sum (and count) of the eigenvalues of the symmetric m x m matrix C (ld m,
-// destroyed) that lie in [xl, xh]: tridiagonal form, then bisection for the
-// eigenvalues near or inside the interval only; the sum runs in index order on
-// one thread.
+// destroyed) that lie in [xl, xh].  Tridiagonal form; the Sturm counts at xl
+// and xh give how many eigenvalues lie below and above the interval, and only
+// those are found by bisection: the sum over the interval is the trace (sum of
+// the tridiagonal's diagonal, in index order) minus theirs.  When more than
+// half of the eigenvalues lie outside, or one of them is far larger than the
+// interval (the subtraction would cancel), the eigenvalues inside are found
+// and summed in index order instead.
 __device__ double range_sum(double* __restrict__ C, int m, double xl, double xh, Shared& sh, int* count) {
     const int tid = threadIdx.x;
     tridiagonalise(C, m, sh);
@@ -578,26 +569,170 @@ __device__ double range_sum(double* __restrict__ C, int m, double xl, double xh,
     }
     __syncthreads();
     const int jlo = sh.misc[0], jhi = sh.misc[1];
-    for (int j = jlo + tid; j < jhi; j += (int)blockDim.x) sh.v[j] = bisect_one(j, m, sh);
-    __syncthreads();
-    if (tid == 0) {
-        int q = 0;
-        double f = 0.0;
-        for (int j = jlo; j < jhi; ++j) {
-            const double xi = sh.v[j];
-            if (xi >= xl && xi <= xh) {
-                ++q;
-                f += xi;
-            }
+    const int nout = jlo + (m - jhi);
+    const double big = 1e4 * fmax(fabs(xl), fabs(xh)) * m;
+    const bool by_trace = 2 * nout <= m && fmax(fabs(sh.rc[0]), fabs(sh.rc[1])) <= big;
+    if (by_trace) {
+        // the outside eigenvalues, and the two next to the interval's edges (their side
+        // is decided by value, as in the direct sum)
+        for (int q = tid; q < nout + 2 * (jhi > jlo); q += (int)blockDim.x) {
+            int j;
+            if (q < jlo) j = q;
+            else if (q < nout) j = jhi + (q - jlo);
+            else j = (q == nout) ? jlo : jhi - 1;
+            sh.v[j] = bisect_one(j, m, sh);
         }
-        sh.misc[1] = q;
-        sh.p[0] = f;
+        __syncthreads();
+        if (tid == 0) {
+            double tr = 0.0;
+            for (int i = 0; i < m; ++i) tr += sh.d[i];
+            int cnt = jhi - jlo;
+            double out = 0.0;
+            for (int j = 0; j < jlo; ++j) out += sh.v[j];
+            for (int j = jhi; j < m; ++j) out += sh.v[j];
+            if (jhi > jlo) {  // edge eigenvalues that rounding puts outside
+                const double a0 = sh.v[jlo], a1 = sh.v[jhi - 1];
+                if (!(a0 >= xl && a0 <= xh)) {
+                    out += a0;
+                    --cnt;
+                }
+                if (jhi - 1 > jlo && !(a1 >= xl && a1 <= xh)) {
+                    out += a1;
+                    --cnt;
+                }
+            }
+            sh.misc[1] = cnt;
+            sh.p[0] = tr - out;
+        }
+    } else {
+        for (int j = jlo + tid; j < jhi; j += (int)blockDim.x) sh.v[j] = bisect_one(j, m, sh);
+        __syncthreads();
+        if (tid == 0) {
+            int q = 0;
+            double f = 0.0;
+            for (int j = jlo; j < jhi; ++j) {
+                const double xi = sh.v[j];
+                if (xi >= xl && xi <= xh) {
+                    ++q;
+                    f += xi;
+                }
+            }
+            sh.misc[1] = q;
+            sh.p[0] = f;
+        }
     }
     __syncthreads();
     *count = sh.misc[1];
     const double f = sh.p[0];
     __syncthreads();
     return f;
+}
+
+// Largest eigenvalue of the tridiagonal by multisection on warp 0 (after
+// bisect_prepare): each round every lane counts the eigenvalues below its own
+// point of the bracket, which shrinks 33-fold; float32 counts first, then the
+// widened bracket is checked and refined with float64 counts.  Result in
+// sh.red[0] (read after a barrier).
+__device__ void max_eig_warp(int n, Shared& sh) {
+    const int lane = threadIdx.x & 31;
+    const float* d32 = reinterpret_cast<const float*>(sh.rs);
+    const float* e32 = d32 + n;
+    const double glo = sh.rc[0], ghi = sh.rc[1];
+    const double scale = fmax(fabs(glo), fabs(ghi));
+    float flo = (float)glo, fhi = (float)ghi;
+    for (int round = 0; round < 12; ++round) {
+        const float x = flo + (fhi - flo) * (float)(lane + 1) / 33.f;
+        const unsigned m = __ballot_sync(0xffffffffu, sturm_below_f32(d32, e32, n, x) >= n);
+        const int f = m ? __ffs(m) - 1 : 32;  // first point above every eigenvalue
+        const float xf = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
+        const float xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+        const float nlo = f > 0 ? xp : flo, nhi = f < 32 ? xf : fhi;
+        if (!(nhi - nlo < fhi - flo)) break;
+        flo = nlo;
+        fhi = nhi;
+    }
+    const double pad = scale * (4e-7 * n + 1e-6) + DBL_MIN;
+    double lo = fmax(glo, (double)flo - pad), hi = fmin(ghi, (double)fhi + pad);
+    if (!(sturm_below(sh.d, sh.p, n, lo) <= n - 1 && sturm_below(sh.d, sh.p, n, hi) >= n)) {
+        lo = glo;
+        hi = ghi;
+    }
+    for (int round = 0; round < 40; ++round) {
+        const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        const unsigned m = __ballot_sync(0xffffffffu, sturm_below(sh.d, sh.p, n, x) >= n);
+        const int f = m ? __ffs(m) - 1 : 32;
+        const double xf = __shfl_sync(0xffffffffu, x, f < 32 ? f : 31);
+        const double xp = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+        const double nlo = f > 0 ? xp : lo, nhi = f < 32 ? xf : hi;
+        if (!(nhi - nlo < hi - lo)) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) sh.red[0] = 0.5 * (lo + hi);
+}
+
+// C = A^T B for A (K x P, ld lda) and B (K x Q, ld ldb), C (P x Q, ld ldc):
+// 32 x 32 output tiles, the K dimension staged through shared memory in slabs
+// of 32 rows, each thread a 2 x 2 block of outputs with independent
+// accumulators.  With `upper` only tiles on or above the diagonal are formed and
+// every value is also stored at (q, p) (A^T B symmetric, e.g. Z^T T Z).
+__device__ void gemm_tn(const double* __restrict__ Am, int lda, const double* __restrict__ Bm, int ldb, int K,
+                        int P, int Q, double* __restrict__ C, int ldc, bool upper, Shared& sh) {
+    double* ta = sh.gt;            // [32 k][33]
+    double* tb = sh.gt + 32 * 33;  // [32 k][33]
+    const int tid = threadIdx.x, nt = (int)blockDim.x;
+    const int tp = P > 0 ? (P + 31) / 32 : 0, tq = (Q + 31) / 32;
+    for (int tile = 0; tile < tp * tq; ++tile) {
+        const int bp = tile / tq, bq = tile - bp * tq;
+        if (upper && bq < bp) continue;
+        const int p0 = bp * 32, q0 = bq * 32;
+        // thread -> 2 x 2 outputs (rows p0 + 2 (t / 16) .., cols q0 + 2 (t % 16) ..); 256 threads
+        // cover the tile, fewer threads loop over it
+        double acc[4][2][2] = {};  // [pass]: CTAs of 64 / 128 threads take 4 / 2 passes
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            __syncthreads();
+            for (int e = tid; e < 32 * 32; e += nt) {
+                const int kk = e >> 5, c = e & 31;
+                const int k = k0 + kk;
+                ta[kk * 33 + c] = (k < K && p0 + c < P) ? Am[(size_t)k * lda + p0 + c] : 0.0;
+                tb[kk * 33 + c] = (k < K && q0 + c < Q) ? Bm[(size_t)k * ldb + q0 + c] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int pass = 0; pass < 4; ++pass) {
+                const int t = tid + pass * nt;
+                if (t < 256) {
+                    const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+#pragma unroll 8
+                    for (int kk = 0; kk < 32; ++kk) {
+                        const double a0 = ta[kk * 33 + pi], a1 = ta[kk * 33 + pi + 1];
+                        const double b0 = tb[kk * 33 + qj], b1 = tb[kk * 33 + qj + 1];
+                        acc[pass][0][0] = fma(a0, b0, acc[pass][0][0]);
+                        acc[pass][0][1] = fma(a0, b1, acc[pass][0][1]);
+                        acc[pass][1][0] = fma(a1, b0, acc[pass][1][0]);
+                        acc[pass][1][1] = fma(a1, b1, acc[pass][1][1]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+            const int t = tid + pass * nt;
+            if (t < 256) {
+                const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) {
+                        const int pp = p0 + pi + i, q = q0 + qj + j;
+                        if (pp < P && q < Q && (!upper || q >= pp)) {
+                            const double v = acc[pass][i][j];
+                            C[(size_t)pp * ldc + q] = v;
+                            if (upper) C[(size_t)q * ldc + pp] = v;
+                        }
+                    }
+            }
+        }
+    }
+    __syncthreads();
 }
 
 // Eigenvectors of the tridiagonal (sh.d, sh.off) for the r eigenvalues in
@@ -694,14 +829,7 @@ __device__ void back_transform(const double* __restrict__ A, int n, double* __re
             if (beta == 0.0) continue;
             const int L = n - k - 1;
             const double* v = A + (size_t)k * n + k + 1;
-            double s0 = 0.0, s1 = 0.0;
-            int i = 0;
-            for (; i + 1 < L; i += 2) {
-                s0 = fma(v[i], Z[(size_t)(k + 1 + i) * ldz + q], s0);
-                s1 = fma(v[i + 1], Z[(size_t)(k + 2 + i) * ldz + q], s1);
-            }
-            if (i < L) s0 = fma(v[i], Z[(size_t)(k + 1 + i) * ldz + q], s0);
-            const double f = beta * (s0 + s1);
+            const double f = beta * dot8(v, 1, Z + (size_t)(k + 1) * ldz + q, ldz, L);
             for (int j = 0; j < L; ++j) Z[(size_t)(k + 1 + j) * ldz + q] -= f * v[j];
         }
     }
@@ -751,6 +879,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
     sh.keep = reinterpret_cast<int*>(sh.red + NT / 32);
     sh.sel = sh.keep + n;
     sh.misc = sh.sel + n;
+    sh.gt = reinterpret_cast<double*>(dyn) + 7 * n + NT / 32 + (2 * n + 16 + 1) / 2;
     const int tid = threadIdx.x;
     const int n_tot = nv + nvh;
     const size_t nn = (size_t)n * n;
@@ -776,8 +905,10 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
         __syncthreads();
         tridiagonalise(A, n, sh);
         bisect_prepare(n, sh);
+        if (tid < 32) max_eig_warp(n, sh);
+        __syncthreads();
         if (tid == 0) {
-            const double smax = bisect_one(n - 1, n, sh);
+            const double smax = sh.red[0];
             sh.misc[7] = smax > 0.0 ? n - sturm_below(sh.d, sh.p, n, fmax(tau * smax, floor_t)) : 0;
         }
         __syncthreads();
@@ -834,51 +965,20 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             __syncthreads();
             twisted_vectors(n, rk, Zt, Y, T1, n, sh);
             if (sh.misc[6]) {
-                // M_W = Z^T T Z (rk x rk, ld rk) into Y
-                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
-                    const int pp = e / rk, q = e - pp * rk;
-                    if (pp > q) continue;
-                    double acc = 0.0;
-                    for (int i = 0; i < n; ++i) {
-                        double tz = sh.d[i] * Zt[(size_t)i * n + q];
-                        if (i > 0) tz = fma(sh.off[i - 1], Zt[(size_t)(i - 1) * n + q], tz);
-                        if (i + 1 < n) tz = fma(sh.off[i], Zt[(size_t)(i + 1) * n + q], tz);
-                        acc = fma(Zt[(size_t)i * n + pp], tz, acc);
-                    }
-                    Y[(size_t)pp * rk + q] = acc;
-                    Y[(size_t)q * rk + pp] = acc;
-                }
-                __syncthreads();
-                back_transform(A, n, Zt, n, rk, sh);  // columns of Zt: kept eigenvectors of K_W
-                // T1 = K_Z Yc (n x rk, ld rk)
+                // W = T Z (n x rk, ld rk) into T1, then M_W = Z^T W (rk x rk, ld rk) into Y
                 for (int e = tid; e < n * rk; e += (int)blockDim.x) {
                     const int i = e / rk, q = e - i * rk;
-                    const double* zr = Zk + (size_t)i * n;
-                    double s0 = 0.0, s1 = 0.0;
-                    int m = 0;
-                    for (; m + 1 < n; m += 2) {
-                        s0 = fma(zr[m], Zt[(size_t)m * n + q], s0);
-                        s1 = fma(zr[m + 1], Zt[(size_t)(m + 1) * n + q], s1);
-                    }
-                    if (m < n) s0 = fma(zr[m], Zt[(size_t)m * n + q], s0);
-                    T1[(size_t)i * rk + q] = s0 + s1;
+                    double tz = sh.d[i] * Zt[(size_t)i * n + q];
+                    if (i > 0) tz = fma(sh.off[i - 1], Zt[(size_t)(i - 1) * n + q], tz);
+                    if (i + 1 < n) tz = fma(sh.off[i], Zt[(size_t)(i + 1) * n + q], tz);
+                    T1[(size_t)i * rk + q] = tz;
                 }
                 __syncthreads();
-                // M_Z = Yc^T T1 (rk x rk, ld rk) into A (the reflectors are no longer needed)
-                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
-                    const int pp = e / rk, q = e - pp * rk;
-                    if (pp > q) continue;
-                    double s0 = 0.0, s1 = 0.0;
-                    int i = 0;
-                    for (; i + 1 < n; i += 2) {
-                        s0 = fma(Zt[(size_t)i * n + pp], T1[(size_t)i * rk + q], s0);
-                        s1 = fma(Zt[(size_t)(i + 1) * n + pp], T1[(size_t)(i + 1) * rk + q], s1);
-                    }
-                    if (i < n) s0 = fma(Zt[(size_t)i * n + pp], T1[(size_t)i * rk + q], s0);
-                    A[(size_t)pp * rk + q] = s0 + s1;
-                    A[(size_t)q * rk + pp] = s0 + s1;
-                }
-                __syncthreads();
+                gemm_tn(Zt, n, T1, rk, n, rk, rk, Y, rk, true, sh);
+                back_transform(A, n, Zt, n, rk, sh);  // columns of Zt: kept eigenvectors of K_W
+                // T1 = K_Z Yc (n x rk, ld rk; K_Z is symmetric), M_Z = Yc^T T1 into A
+                gemm_tn(Zk, n, Zt, n, n, n, rk, T1, rk, false, sh);
+                gemm_tn(Zt, n, T1, rk, n, rk, rk, A, rk, true, sh);
                 stale = true;
                 if (cholesky_lower(Y, rk, sh)) {
                     trsm_lower(Y, A, rk, sh);          // A = L^-1 M_Z
@@ -1049,7 +1149,9 @@ int workspace_ctas(int n_v) {
     return g < 1 ? 1 : (int)g;
 }
 
-size_t solve_smem(int n) { return (size_t)7 * n * sizeof(double) + (NT / 32) * sizeof(double) + (2 * n + 16) * sizeof(int); }
+size_t solve_smem(int n) {
+    return (size_t)(7 * n + NT / 32 + (2 * n + 16 + 1) / 2 + 2 * 32 * 33) * sizeof(double);
+}
 
 }  // namespace
 
