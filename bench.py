@@ -134,7 +134,24 @@ def _traffic(kernel: str):
 FP64_FMA_PER_SM_CLK = 2   # measured: FMA chains reach 1.20 TFLOP/s on 152 SMs at 2.07 GHz
 
 
-def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks):
+def solve_flops(ranks, n: int) -> float:
+    """Float64 flops of the per-point solver, by the route each point takes (kept rank r):
+    r = 0: Householder reduction of K_W (4/3 n^3); r = n: reduction, Cholesky (n^3/3), two
+    triangular solves (2 n^3), reduction of C (4/3 n^3); 0 < r < n: reduction, back-transform
+    (2 n^2 r), K_Z Y (2 n^2 r), Y^T K_Z Y and Z^T T Z (2 n r^2), Cholesky, solves and
+    reduction of the r x r pencil (r^3/3 + 2 r^3 + 4/3 r^3)."""
+    tot = 0.0
+    for r in ranks:
+        f = 4.0 / 3.0 * n ** 3
+        if r == n:
+            f += n ** 3 / 3.0 + 2.0 * n ** 3 + 4.0 / 3.0 * n ** 3
+        elif r > 0:
+            f += 4.0 * n * n * r + 2.0 * n * r * r + (1.0 / 3.0 + 2.0 + 4.0 / 3.0) * r ** 3
+        tot += f
+    return tot
+
+
+def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=None):
     """Per-kernel algorithmic work / measured launch time against its bound.
 
     Algorithmic work per launch (stated in the design doc):
@@ -142,7 +159,7 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks):
       gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
       gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
       assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step
-      solve_kernel         flops = n_t (14.3 n_v^3)  (eigh with vectors 9 n^3, B 4 n^3, eigvals 1.3 n^3)
+      solve_kernel         flops = sum over points of the route's count (solve_flops)
     """
     N = st.n
     n_tot = c["n_v"] + c["n_vh"]
@@ -186,7 +203,7 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks):
                     ms_per_step=a_ms,
                     peak_source="fp64 peak: 152 SMs x 2 FMA/clk x 2 x %.0f MHz (FMA-chain probe: 1.20 TFLOP/s)"
                                 % sm_mhz))
-    s_flops = n_t * 14.3 * nv ** 3
+    s_flops = solve_flops(ranks, nv) if ranks is not None else n_t * 14.3 * nv ** 3
     s_ms = stats["ms_solve"] / steps
     out.append(dict(kernel="solve_kernel", bound="alu", achieved=s_flops / (s_ms * 1e-3) / 1e12, peak=fp64_peak,
                     unit="TFLOP/s", traffic=None, work_per_launch=s_flops, launch_ms=s_ms, ms_per_step=s_ms,
@@ -335,7 +352,10 @@ def run_gpu(args, c, st, W, csr):
     hbm, bf16, bf16s, peak_kind = _peaks()
     phases = {k: stats[k] / args.steps for k in ("ms_coeffs", "ms_recurrence", "ms_gram", "ms_reduce",
                                                   "ms_assemble", "ms_solve", "ms_kpm")}
-    roofs = kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, ck)
+    # kept ranks of the sweep points (untimed) decide each point's solver route
+    _, _, rk = S.ssm_dos(plan, td, sigma, want_kpm=False)
+    ranks = [int(v) for v in rk[:, 0].cpu().numpy()]
+    roofs = kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, ck, ranks)
     dominant = max(roofs, key=lambda r: r["ms_per_step"])
     roofline = dict(dominant)
 

@@ -333,7 +333,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-// Slab sums in float64, coalesced: ge[e] = sum_s pe[s][lo][hi] (upper element of
+// Compensated (Neumaier) float32 sum: the slab partials are float32, and their
+// sum in this form keeps float64-level accuracy with float32 operations only
+// (float64 runs at 1/58 of the float32 rate on this part and was the bound of
+// a plain float64 sum of ~150 partials per element and step).
+struct Sum32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Slab sums (compensated float32 per warp, float64 across warps), coalesced: ge[e] = sum_s pe[s][lo][hi] (upper element of
 // the pair), go[e] = sum_s po[s][e]; the symmetrisation of go reads it transposed
 // from this small float64 buffer in a second pass.  A block covers 32
 // consecutive elements; its 8 warps take every 8th slab and their partial
@@ -346,26 +360,15 @@ sum_tc_kernel(const float* __restrict__ pe, int n_e, const float* __restrict__ p
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
         const size_t e = e0 + lane;
-        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        Sum32 a, b;
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
-            if (i <= j) {
-                int s = w;
-                for (; s + 8 < n_e; s += 16) {
-                    a0 += (double)pe[(size_t)s * nn + e];
-                    a1 += (double)pe[(size_t)(s + 8) * nn + e];
-                }
-                for (; s < n_e; s += 8) a0 += (double)pe[(size_t)s * nn + e];
-            }
-            int s = w;
-            for (; s + 8 < n_o; s += 16) {
-                b0 += (double)po[(size_t)s * nn + e];
-                b1 += (double)po[(size_t)(s + 8) * nn + e];
-            }
-            for (; s < n_o; s += 8) b0 += (double)po[(size_t)s * nn + e];
+            if (i <= j)
+                for (int s = w; s < n_e; s += 8) a.add(pe[(size_t)s * nn + e]);
+            for (int s = w; s < n_o; s += 8) b.add(po[(size_t)s * nn + e]);
         }
-        se[w][lane] = a0 + a1;
-        so[w][lane] = b0 + b1;
+        se[w][lane] = a.value();
+        so[w][lane] = b.value();
         __syncthreads();
         if (w == 0 && e < nn) {
             double a = 0.0, b = 0.0;
@@ -393,26 +396,15 @@ sum_tc_batch_kernel(const float* __restrict__ ring, size_t slot, int n_e, int n_
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
         const size_t e = e0 + lane;
-        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        Sum32 a, b;
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
-            if (i <= j) {
-                int s = w;
-                for (; s + 8 < n_e; s += 16) {
-                    a0 += (double)pe[(size_t)s * nn + e];
-                    a1 += (double)pe[(size_t)(s + 8) * nn + e];
-                }
-                for (; s < n_e; s += 8) a0 += (double)pe[(size_t)s * nn + e];
-            }
-            int s = w;
-            for (; s + 8 < n_o; s += 16) {
-                b0 += (double)po[(size_t)s * nn + e];
-                b1 += (double)po[(size_t)(s + 8) * nn + e];
-            }
-            for (; s < n_o; s += 8) b0 += (double)po[(size_t)s * nn + e];
+            if (i <= j)
+                for (int s = w; s < n_e; s += 8) a.add(pe[(size_t)s * nn + e]);
+            for (int s = w; s < n_o; s += 8) b.add(po[(size_t)s * nn + e]);
         }
-        se[w][lane] = a0 + a1;
-        so[w][lane] = b0 + b1;
+        se[w][lane] = a.value();
+        so[w][lane] = b.value();
         __syncthreads();
         if (w == 0 && e < nn) {
             double a = 0.0, b = 0.0;
@@ -475,16 +467,16 @@ sum_tc_seg_kernel(const float* __restrict__ pe, const float* __restrict__ po, co
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
         const size_t e = e0 + lane;
-        double a0 = 0.0, b0 = 0.0;
+        Sum32 a, b;
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
             if (i <= j)
-                for (int sl = e0s + w; sl < e1s; sl += 8) a0 += (double)pe[(size_t)sl * nn + e];
+                for (int sl = e0s + w; sl < e1s; sl += 8) a.add(pe[(size_t)sl * nn + e]);
             if (odd)
-                for (int sl = o0s + w; sl < o1s; sl += 8) b0 += (double)po[(size_t)sl * nn + e];
+                for (int sl = o0s + w; sl < o1s; sl += 8) b.add(po[(size_t)sl * nn + e]);
         }
-        se_[w][lane] = a0;
-        so_[w][lane] = b0;
+        se_[w][lane] = a.value();
+        so_[w][lane] = b.value();
         __syncthreads();
         if (w == 0 && e < nn) {
             double a = 0.0, c = 0.0;

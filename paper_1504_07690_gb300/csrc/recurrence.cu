@@ -14,6 +14,7 @@
 // by the warps working next to them.
 #include <cuda_bf16.h>
 
+
 #include "internal.h"
 
 namespace ssm {
@@ -96,13 +97,41 @@ struct RowInfo {
     uint32_t has;  // bit a: neighbour a present; bit 31: row exists
 };
 
+// Operands of one (row, 16-byte chunk) item of a stencil step: the centre
+// value, the neighbour sums per axis, V_{k-1} and the folded diagonal.
+template <typename T>
+struct ItemLoads {
+    typename Vec16<T>::type x, s[3], vp;
+    T dg;
+    bool ok;
+};
+
+template <typename T, typename VT = typename Vec16<T>::type>
+__device__ __forceinline__ void load_item(ItemLoads<T>& L, const RowInfo& ri, uint32_t i, uint32_t cc,
+                                          uint32_t nchunk, const VT* vc, const VT* vp, const T* diag2, bool need_vp) {
+    L.ok = (ri.has >> 31) != 0;
+    if (!L.ok) return;
+    const size_t base = (size_t)i * nchunk;
+    L.x = ldg_stream(vc + base + cc);
+    L.dg = __ldg(diag2 + i);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool lo = (ri.has >> (2 * a)) & 1u, hi = (ri.has >> (2 * a + 1)) & 1u;
+        VT sacc = vzero(T(0));
+        if (lo) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a] * nchunk + cc));
+        if (hi) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a + 1] * nchunk + cc));
+        L.s[a] = sacc;
+    }
+    L.vp = need_vp ? ldg_stream(vp + base + cc) : vzero(T(0));
+}
+
 // A CTA owns one 32-row panel at a time (grid-stride over panels): the first
 // 32 threads tabulate the rows' neighbour rows, then all 256 threads walk the
 // panel's (row, 16-byte chunk) items, so loads and stores are coalesced and
 // every lane is busy; with PANEL the split-bf16 copy of the panel is staged
 // in shared memory and written as whole 512-byte runs.
 template <typename T, bool PANEL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                     const T* __restrict__ diag2, StencilGeom g, T o0, T o1, T o2, T c, T d,
                     uint32_t nchunk, uint32_t n_rows, PanelOut po) {
@@ -143,30 +172,37 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
             info[threadIdx.x] = ri;
         }
         __syncthreads();
-        for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
-            const uint32_t r = (it * mdiv) >> 20, cc = it - r * nchunk;
-            const RowInfo& ri = info[r];
-            VT out = vzero(T(0));
-            if (ri.has >> 31) {
-                const uint32_t i = pnl * 32 + r;
-                const size_t base = (size_t)i * nchunk;
-                const VT x = ldg_stream(vc + base + cc);
-                VT acc = vscale(__ldg(diag2 + i), x);
+        // two items per thread per pass, all their loads issued before either is used
+        for (uint32_t it0 = threadIdx.x; it0 < items; it0 += 2 * blockDim.x) {
+            ItemLoads<T> L[2];
+            uint32_t rr[2], cq[2];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const bool lo = (ri.has >> (2 * a)) & 1u, hi = (ri.has >> (2 * a + 1)) & 1u;
-                    if (lo || hi) {
-                        VT sacc = vzero(T(0));
-                        if (lo) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a] * nchunk + cc));
-                        if (hi) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a + 1] * nchunk + cc));
-                        acc = vfma(w[a], sacc, acc);
-                    }
+            for (int u = 0; u < 2; ++u) {
+                const uint32_t it = it0 + u * blockDim.x;
+                L[u].ok = false;
+                rr[u] = 0;
+                cq[u] = 0;
+                if (it < items) {
+                    rr[u] = (it * mdiv) >> 20;
+                    cq[u] = it - rr[u] * nchunk;
+                    load_item(L[u], info[rr[u]], pnl * 32 + rr[u], cq[u], nchunk, vc, vp, diag2, d != T(0));
                 }
-                out = vscale(c, acc);
-                if (d != T(0)) out = vfma(-d, ldg_stream(vp + base + cc), out);
-                vn[base + cc] = out;
             }
-            if constexpr (PANEL) stage_split4p(stage, po.G, r, 4 * cc, out);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const uint32_t it = it0 + u * blockDim.x;
+                if (it >= items) continue;
+                VT out = vzero(T(0));
+                if (L[u].ok) {
+                    VT acc = vscale(L[u].dg, L[u].x);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) acc = vfma(w[a], L[u].s[a], acc);
+                    out = vscale(c, acc);
+                    if (d != T(0)) out = vfma(-d, L[u].vp, out);
+                    vn[(size_t)(pnl * 32 + rr[u]) * nchunk + cq[u]] = out;
+                }
+                if constexpr (PANEL) stage_split4p(stage, po.G, rr[u], 4 * cq[u], out);
+            }
         }
         if constexpr (PANEL) {
             __syncthreads();
