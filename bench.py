@@ -159,6 +159,7 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
       gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
       gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
       assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step
+      assemble_df_kernel   12 float32 instructions per term of the same sums (mixed plans)
       solve_kernel         flops = sum over points of the route's count (solve_flops)
     """
     N = st.n
@@ -196,13 +197,23 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
                         ms_per_step=stats["ms_gram"] / steps,
                         peak_source="%s CUDA-core peak: 152 SMs x %d FMA/clk x 2 x %.0f MHz" % (
                             "fp32" if mixed else "fp64", 128 if mixed else FP64_FMA_PER_SM_CLK, sm_mhz)))
-    a_flops = 2.0 * n_t * ((M // 2 + 1) * n_tot * (n_tot + 1) / 2.0 + (M + 1) * nv * (nv + 1) / 2.0)
+    a_terms = n_t * ((M // 2 + 1) * n_tot * (n_tot + 1) / 2.0 + (M + 1) * nv * (nv + 1) / 2.0)
     a_ms = stats["ms_assemble"] / steps
-    out.append(dict(kernel="assemble_kernel", bound="alu", achieved=a_flops / (a_ms * 1e-3) / 1e12, peak=fp64_peak,
-                    unit="TFLOP/s", traffic=None, work_per_launch=a_flops / 2, launch_ms=a_ms / 2,
-                    ms_per_step=a_ms,
-                    peak_source="fp64 peak: 152 SMs x 2 FMA/clk x 2 x %.0f MHz (FMA-chain probe: 1.20 TFLOP/s)"
-                                % sm_mhz))
+    if mixed:
+        # compensated float-pair arithmetic: 12 float32 instructions per term (two-product,
+        # cross terms, two-sum, low-part update) against the float32 issue rate
+        a_ins = 12.0 * a_terms
+        out.append(dict(kernel="assemble_df_kernel", bound="alu", achieved=a_ins / (a_ms * 1e-3) / 1e12,
+                        peak=152 * 128 * sm_mhz * 1e6 / 1e12, unit="T float32 instructions/s", traffic=None,
+                        work_per_launch=a_ins / 2, launch_ms=a_ms / 2, ms_per_step=a_ms,
+                        peak_source="float32 issue: 152 SMs x 128 lanes x %.0f MHz" % sm_mhz))
+    else:
+        a_flops = 2.0 * a_terms
+        out.append(dict(kernel="assemble_kernel", bound="alu", achieved=a_flops / (a_ms * 1e-3) / 1e12,
+                        peak=fp64_peak, unit="TFLOP/s", traffic=None, work_per_launch=a_flops / 2,
+                        launch_ms=a_ms / 2, ms_per_step=a_ms,
+                        peak_source="fp64 peak: 152 SMs x 2 FMA/clk x 2 x %.0f MHz (FMA-chain probe: 1.20 TFLOP/s)"
+                                    % sm_mhz))
     s_flops = solve_flops(ranks, nv) if ranks is not None else n_t * 14.3 * nv ** 3
     s_ms = stats["ms_solve"] / steps
     out.append(dict(kernel="solve_kernel", bound="alu", achieved=s_flops / (s_ms * 1e-3) / 1e12, peak=fp64_peak,

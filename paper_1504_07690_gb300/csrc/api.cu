@@ -333,8 +333,10 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
         if (st != SSM_OK) return st;
         if (want_ss) {
             Scope sc(h, PH_ASSEMBLE);
-            CUDA_OR_FAIL(h, launch_assemble(h->d_mu, M + 1, nb, K + 1, P.d_X, n_tot, n_tot, n_tot, h->d_K, P.stream));
-            CUDA_OR_FAIL(h, launch_assemble(h->d_nu, M + 1, nb, M + 1, P.d_X, n_tot, nv, nv, h->d_KZ, P.stream));
+            CUDA_OR_FAIL(h, launch_assemble(h->d_mu, M + 1, nb, K + 1, P.d_X, n_tot, n_tot, n_tot, h->d_K, P.stream,
+                                            P.mixed));
+            CUDA_OR_FAIL(h, launch_assemble(h->d_nu, M + 1, nb, M + 1, P.d_X, n_tot, nv, nv, h->d_KZ, P.stream,
+                                            P.mixed));
             P.stats.launches += 2;
         }
         if (want_ss) {
@@ -399,9 +401,9 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
             if (want_ss) {
                 Scope sc(h, PH_ASSEMBLE);
                 CUDA_OR_FAIL(h, launch_assemble(h->d_mu + off * (M + 1), M + 1, n_tp, K + 1, P.d_X + b * xs, n_tot,
-                                                n_tot, n_tot, h->d_K + off * n_tot * n_tot, P.stream));
+                                                n_tot, n_tot, h->d_K + off * n_tot * n_tot, P.stream, P.mixed));
                 CUDA_OR_FAIL(h, launch_assemble(h->d_nu + off * (M + 1), M + 1, n_tp, M + 1, P.d_X + b * xs, n_tot,
-                                                nv, nv, h->d_KZ + off * nv * nv, P.stream));
+                                                nv, nv, h->d_KZ + off * nv * nv, P.stream, P.mixed));
                 P.stats.launches += 2;
             }
             {

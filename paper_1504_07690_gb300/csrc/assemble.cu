@@ -107,14 +107,136 @@ assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, co
     }
 }
 
+// Compensated variant for the mixed path: every float64 operand is split into
+// a float pair (hi = rn(v), lo = rn(v - hi), 48 significant bits), each product
+// is formed error-free in float32 (fma two-product plus the cross terms) and
+// accumulated in a float pair with an error-free two-sum (Knuth), so a term costs
+// ~10 float32 operations instead of one float64 fma at 1/58 of the rate.  The
+// result carries ~2^-44 relative error per term: far below the error of the
+// mixed moments it combines.  Same tiling and summation order as assemble_kernel.
+__device__ __forceinline__ void split_f2(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__global__ void __launch_bounds__(256)
+assemble_df_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, const double* __restrict__ X,
+                   int n_tot, int rows, int cols, double* __restrict__ out) {
+    __shared__ float Ch[TL][TT + 1], Cl[TL][TT + 1];
+    __shared__ float Xh[TL][TE], Xl[TL][TE];
+    __shared__ int xoff[TE];
+    __shared__ int ooff[2 * TE];
+    const int64_t ne = (int64_t)rows * (rows + 1) / 2;
+    const int64_t nsq = (int64_t)rows * cols;
+    const int64_t t0 = (int64_t)blockIdx.y * TT;
+    const int64_t e0 = (int64_t)blockIdx.x * TE;
+    const size_t nn = (size_t)n_tot * n_tot;
+    if (threadIdx.x < TE) {
+        const int64_t e = e0 + threadIdx.x;
+        int off = -1, oij = -1, oji = -1;
+        if (e < ne) {
+            const double nn1 = 2.0 * rows + 1.0;
+            int i = (int)((nn1 - sqrt(nn1 * nn1 - 8.0 * (double)e)) * 0.5);
+            if (i < 0) i = 0;
+            if (i > rows - 1) i = rows - 1;
+            while (i > 0 && (int64_t)i * rows - (int64_t)i * (i - 1) / 2 > e) --i;
+            while (i + 1 < rows && (int64_t)(i + 1) * rows - (int64_t)(i + 1) * i / 2 <= e) ++i;
+            const int j = (int)(e - ((int64_t)i * rows - (int64_t)i * (i - 1) / 2)) + i;
+            off = i * n_tot + j;
+            oij = i * cols + j;
+            oji = j * cols + i;
+        }
+        xoff[threadIdx.x] = off;
+        ooff[threadIdx.x] = oij;
+        ooff[TE + threadIdx.x] = oji;
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float sh_[4][4], sl_[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sh_[p][q] = sl_[p][q] = 0.f;
+    __syncthreads();
+    for (int l0 = 0; l0 < L; l0 += TL) {
+        for (int e = threadIdx.x; e < TL * TT; e += 256) {
+            const int ll = e / TT, tt = e - ll * TT;
+            const int64_t ti = t0 + tt;
+            const int l = l0 + ll;
+            float h = 0.f, lo = 0.f;
+            if (ti < n_t && l < L) split_f2(coef[ti * ldc + l], h, lo);
+            Ch[ll][tt] = h;
+            Cl[ll][tt] = lo;
+        }
+        for (int e = threadIdx.x; e < TL * TE; e += 256) {
+            const int ll = e / TE, ee = e - ll * TE;
+            const int l = l0 + ll;
+            const int off = xoff[ee];
+            float h = 0.f, lo = 0.f;
+            if (off >= 0 && l < L) split_f2(X[(size_t)l * nn + off], h, lo);
+            Xh[ll][ee] = h;
+            Xl[ll][ee] = lo;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int ll = 0; ll < TL; ++ll) {
+            float ch[4], cl[4], xh[4], xl[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                ch[p] = Ch[ll][ty * 4 + p];
+                cl[p] = Cl[ll][ty * 4 + p];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xh[q] = Xh[ll][tx + 16 * q];
+                xl[q] = Xl[ll][tx + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    // product: p0 + e exactly-ish (two-product plus cross terms)
+                    const float p0 = ch[p] * xh[q];
+                    float err = fmaf(ch[p], xh[q], -p0);
+                    err = fmaf(ch[p], xl[q], err);
+                    err = fmaf(cl[p], xh[q], err);
+                    // two-sum of the running hi part and p0
+                    const float s = sh_[p][q] + p0;
+                    const float bb = s - sh_[p][q];
+                    const float tw = (sh_[p][q] - (s - bb)) + (p0 - bb);
+                    sh_[p][q] = s;
+                    sl_[p][q] += tw + err;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int64_t ti = t0 + ty * 4 + p;
+        if (ti >= n_t) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ee = tx + 16 * q;
+            const int oij = ooff[ee];
+            if (oij >= 0) {
+                const double v = (double)sh_[p][q] + (double)sl_[p][q];
+                out[ti * nsq + oij] = v;
+                out[ti * nsq + ooff[TE + ee]] = v;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X, int n_tot,
-                            int rows, int cols, double* out, cudaStream_t s) {
+                            int rows, int cols, double* out, cudaStream_t s, bool compensated) {
     if (rows != cols) return cudaErrorInvalidValue;
     const int64_t ne = (int64_t)rows * (rows + 1) / 2;
     dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
-    assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
+    if (compensated)
+        assemble_df_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
+    else
+        assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
     return cudaGetLastError();
 }
 
