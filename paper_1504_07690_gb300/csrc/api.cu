@@ -125,18 +125,19 @@ size_t take_event(ssm_plan_s* h) {
 struct Scope {
     ssm_plan_s* h;
     int phase;
+    cudaStream_t st;
     size_t e0 = (size_t)-1;
-    Scope(ssm_plan_s* hh, int ph) : h(hh), phase(ph) {
+    Scope(ssm_plan_s* hh, int ph, cudaStream_t s = nullptr) : h(hh), phase(ph), st(s ? s : hh->P.stream) {
         if (h->P.timing) {
             e0 = take_event(h);
-            if (e0 != (size_t)-1) cudaEventRecord(h->events[e0], h->P.stream);
+            if (e0 != (size_t)-1) cudaEventRecord(h->events[e0], st);
         }
     }
     ~Scope() {
         if (h->P.timing && e0 != (size_t)-1) {
             size_t e1 = take_event(h);
             if (e1 != (size_t)-1) {
-                cudaEventRecord(h->events[e1], h->P.stream);
+                cudaEventRecord(h->events[e1], st);
                 h->marks.push_back({phase, e0, e1});
             }
         }
@@ -205,8 +206,10 @@ void free_plan(ssm_plan_s* h) {
     dev_free(P.d_part_tc);
     dev_free(P.d_ring);
     dev_free(P.d_ring_sum);
-    dev_free(P.d_panel[0]);
-    dev_free(P.d_panel[1]);
+    for (auto& pb : P.d_panel) dev_free(pb);
+    for (auto& e : P.ev_st) if (e) cudaEventDestroy(e);
+    for (auto& e : P.ev_gr) if (e) cudaEventDestroy(e);
+    if (P.gstream) cudaStreamDestroy(P.gstream);
     dev_free(P.d_X);
     dev_free(P.d_flag);
     dev_free(P.d_stage);
@@ -812,6 +815,10 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
             CREATE_CUDA(cudaMalloc((void**)&pb, pbytes));
             CREATE_CUDA(cudaMemsetAsync(pb, 0, pbytes, P.stream));  // rows past N stay zero
         }
+        // the Gram products of step k run on a second stream, next to step k+1 of the recurrence
+        CREATE_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
+        for (auto& e : P.ev_st) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto& e : P.ev_gr) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     } else {
         P.n_split = gram_split_count(P.n, P.n_tot);
         CREATE_CUDA(dev_alloc(&P.d_part, (size_t)P.n_split * 2 * P.n_tot * P.n_tot));
@@ -1071,15 +1078,20 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     }
     CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, P.stream));
     P.stats.launches++;
-    // split-bf16 panels of V_j live in d_panel[j % 2] (tensor-core path)
+    // Tensor-core path: split-bf16 panels of V_j live in d_panel[j % 3]; the Gram
+    // products and reductions run on gstream, so the Gram of step k overlaps the
+    // recurrence of step k+1.  Step k writes panel (k+1) % 3, last read by the Gram
+    // of step k-1: it waits for that Gram only.
+    const bool ovl = P.use_tc && P.gstream;
+    cudaStream_t gs = ovl ? P.gstream : P.stream;
     auto gram = [&](const void* A, const void* B, int j) -> cudaError_t {
         if (P.use_tc) {
             // steps k = j-1 >= 1 write into the ring; V_0 and step 0 into d_part_tc
             float* dst = (j >= 2) ? P.d_ring + (size_t)((j - 2) % P.tc_ring) *
                                                    gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot)
                                   : P.d_part_tc;
-            return launch_gram_tc(P.d_panel[j & 1], B ? P.d_panel[(j + 1) & 1] : nullptr, P.n_tot, P.n, P.tc_ne,
-                                  P.tc_no, dst, P.d_flag, P.stream);
+            return launch_gram_tc(P.d_panel[j % 3], B ? P.d_panel[(j + 2) % 3] : nullptr, P.n_tot, P.n, P.tc_ne,
+                                  P.tc_no, dst, P.d_flag, gs);
         }
         if (P.mixed)
             return launch_gram_f32((const float*)A, (const float*)B, P.ld, P.n_tot, P.n, P.n_split, P.d_part,
@@ -1091,15 +1103,19 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         CUDA_OR_FAIL(h, launch_panelize(P, (const float*)P.d_V[0], P.d_panel[0], P.stream));
         P.stats.launches++;
     }
+    if (ovl) {
+        CUDA_OR_FAIL(h, cudaEventRecord(P.ev_st[2], P.stream));
+        CUDA_OR_FAIL(h, cudaStreamWaitEvent(gs, P.ev_st[2], 0));
+    }
     {
-        Scope sc(h, PH_GRAM);
+        Scope sc(h, PH_GRAM, gs);
         CUDA_OR_FAIL(h, gram(P.d_V[0], nullptr, 0));
         P.stats.launches++;
         P.stats.gram_launches++;
     }
     {
-        Scope sc(h, PH_REDUCE);
-        CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, -1, P.stream)
+        Scope sc(h, PH_REDUCE, gs);
+        CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, -1, gs)
                                  : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, -1, P.stream));
         P.stats.launches++;
     }
@@ -1108,11 +1124,12 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         void* Vp = P.d_V[(k + 2) % 3];
         void* Vn = P.d_V[(k + 1) % 3];
         const double c = (k == 0) ? 0.5 : 1.0, d = (k == 0) ? 0.0 : 1.0;
+        if (ovl && k >= 2) CUDA_OR_FAIL(h, cudaStreamWaitEvent(P.stream, P.ev_gr[(k - 1) % 3], 0));
         {
             Scope sc(h, PH_REC);
             cudaError_t e;
             if (P.mixed) {
-                uint8_t* pn = P.use_tc ? P.d_panel[(k + 1) & 1] : nullptr;
+                uint8_t* pn = P.use_tc ? P.d_panel[(k + 1) % 3] : nullptr;
                 e = P.is_stencil ? launch_stencil_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn,
                                                            (float)c, (float)d, pn, P.stream)
                                  : launch_csr_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn, (float)c,
@@ -1133,27 +1150,36 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
             CUDA_OR_FAIL(h, cudaMemcpyAsync(ck, Vc, bb, cudaMemcpyDeviceToDevice, P.stream));
             CUDA_OR_FAIL(h, cudaMemcpyAsync(ck + bb, Vn, bb, cudaMemcpyDeviceToDevice, P.stream));
         }
+        if (ovl) {
+            CUDA_OR_FAIL(h, cudaEventRecord(P.ev_st[k % 3], P.stream));
+            CUDA_OR_FAIL(h, cudaStreamWaitEvent(gs, P.ev_st[k % 3], 0));
+        }
         {
-            Scope sc(h, PH_GRAM);
+            Scope sc(h, PH_GRAM, gs);
             CUDA_OR_FAIL(h, gram(Vn, Vc, k + 1));
             P.stats.launches++;
             P.stats.gram_launches++;
         }
+        if (ovl) CUDA_OR_FAIL(h, cudaEventRecord(P.ev_gr[(k + 1) % 3], gs));
         if (!P.use_tc || k == 0) {
-            Scope sc(h, PH_REDUCE);
-            CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k, P.stream)
+            Scope sc(h, PH_REDUCE, gs);
+            CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k, gs)
                                      : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, k, P.stream));
             P.stats.launches += P.use_tc ? 2 : 1;
         } else if ((k % P.tc_ring) == 0 || k == S - 1) {
             // ring slots hold steps k0..k; reduce them in one batch
             const int k0 = ((k - 1) / P.tc_ring) * P.tc_ring + 1;
             const int nk = k - k0 + 1;
-            Scope sc(h, PH_REDUCE);
+            Scope sc(h, PH_REDUCE, gs);
             const size_t nn2 = (size_t)P.n_tot * P.n_tot;
             CUDA_OR_FAIL(h, launch_reduce_tc_batch(P.d_ring, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k0, nk, P.d_ring_sum,
-                                                   P.d_ring_sum + (size_t)P.tc_ring * nn2, P.stream));
+                                                   P.d_ring_sum + (size_t)P.tc_ring * nn2, gs));
             P.stats.launches += 2;
         }
+    }
+    if (ovl) {  // join
+        CUDA_OR_FAIL(h, cudaEventRecord(P.ev_gr[0], gs));
+        CUDA_OR_FAIL(h, cudaStreamWaitEvent(P.stream, P.ev_gr[0], 0));
     }
     CUDA_OR_FAIL(h, launch_check_finite(P.d_X, (int64_t)(M + 1) * nn, P.d_flag, P.stream));
     P.stats.launches++;

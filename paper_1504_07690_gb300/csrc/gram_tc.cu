@@ -15,7 +15,7 @@
 // no-swizzle shared-memory operand layout of tcgen05 (K stride 128 B, MN
 // stride 528 B).  This kernel
 // therefore does no conversion: one thread streams panels into a shared-
-// memory ring (6 stages of 32 KB for Ge, 3 of 64 KB for Go) with 1-D bulk TMA copies (cp.async.bulk, completion
+// memory ring (4 stages of 33 KB for Ge, 2 of 66 KB for Go) with 1-D bulk TMA copies (cp.async.bulk, completion
 // counted in bytes on an mbarrier), one thread issues M=128
 // tcgen05.mma.kind::f16 into TMEM and releases each stage through
 // tcgen05.commit, and at the end all four warps read the accumulators back
@@ -40,8 +40,8 @@ namespace {
 
 constexpr int KC = 32;                 // rows per panel (K of one pipeline stage)
 constexpr int KG = KC / 8;             // 8-row core groups per panel
-constexpr int STAGES_E = 6;            // one-source stages (32 KB each)
-constexpr int STAGES_O = 3;            // two-source stages (64 KB each)
+constexpr int STAGES_E = 4;            // one-source stages (33 KB each)
+constexpr int STAGES_O = 2;            // two-source stages (66 KB each)
 constexpr int STAGES = 6;              // barrier slots
 constexpr int NTHREADS = 128;
 // A column group of a panel is 4 core matrices (512 B) plus a 16-byte pad:
@@ -51,7 +51,9 @@ constexpr int GROUP_BYTES = KG * 128 + 16;
 constexpr int PART_BYTES = 32 * GROUP_BYTES;  // one part of one stage: 32 column groups
 constexpr int TMEM_COLS = 512;
 constexpr long WAIT_LIMIT = 1L << 26;  // bounded mbarrier polls
-constexpr int SMEM_BYTES = STAGES_E * 2 * PART_BYTES + 1024;  // > half of an SM: one CTA per SM
+// > half of an SM (one Gram CTA per SM, it owns all 512 TMEM columns) and small enough
+// that two recurrence CTAs (34 KB each) share the SM with it
+constexpr int SMEM_BYTES = STAGES_E * 2 * PART_BYTES + 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

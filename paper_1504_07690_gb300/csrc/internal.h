@@ -59,7 +59,10 @@ struct Plan {
     int tc_ring = 0;
     int panel_groups = 0;              // split-bf16 panels: column groups of 8
     int64_t n_panels = 0;              // panels of 32 rows
-    uint8_t* d_panel[2] = {nullptr, nullptr};  // panels of V_j for j even / odd
+    uint8_t* d_panel[3] = {nullptr, nullptr, nullptr};  // panels of V_j in d_panel[j % 3] (batched: j % 2)
+    cudaStream_t gstream = nullptr;    // Gram products of step k, next to the recurrence of step k+1
+    cudaEvent_t ev_st[3] = {nullptr, nullptr, nullptr};  // recurrence step done
+    cudaEvent_t ev_gr[3] = {nullptr, nullptr, nullptr};  // Gram of step j done
     double* d_X = nullptr;             // (M+1) x n_tot x n_tot
     bool have_moments = false;
     double x0max = 0;                  // max_i X_0[i][i] over the first n_v probes
