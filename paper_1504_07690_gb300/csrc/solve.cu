@@ -946,7 +946,30 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     }
                 }
                 __syncthreads();
-                phi = range_sum(A, n, xl, xh, sh, &rs);
+                // Inertia first: if C - xl I and xh I - C are both positive definite (two
+                // Cholesky attempts, n^3/3 flops together), every eigenvalue lies in
+                // (xl, xh) and their sum is the trace of C; only otherwise is C reduced to
+                // tridiagonal form and its eigenvalues bracketed.
+                for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                    const int i = e / n, j = e - i * n;
+                    const double v = A[e];
+                    T1[e] = (i == j) ? v - xl : v;
+                    Y[e] = (i == j) ? xh - v : -v;
+                }
+                __syncthreads();
+                if (cholesky_lower(T1, n, sh) && cholesky_lower(Y, n, sh)) {
+                    if (tid == 0) {
+                        double tr = 0.0;
+                        for (int i = 0; i < n; ++i) tr += A[(size_t)i * n + i];
+                        sh.p[0] = tr;
+                    }
+                    __syncthreads();
+                    phi = sh.p[0];
+                    rs = n;
+                    __syncthreads();
+                } else {
+                    phi = range_sum(A, n, xl, xh, sh, &rs);
+                }
                 r = n;
                 done = true;
             }
