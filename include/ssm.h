@@ -102,8 +102,12 @@ typedef struct {
                            (float32) instead of the tensor cores (split bf16); used for
                            cross-checks.  bit 1 (SSM_OPT_ADJOINT): ssm_moments keeps
                            checkpoints of the recurrence (2 ceil(S / ceil(sqrt(S))) blocks
-                           of N x n_tot, S = M/2) for ssm_moments_adjoint.  Other bits
-                           must be 0 (SSM_EINVAL otherwise). */
+                           of N x n_tot, S = M/2) for ssm_moments_adjoint.  bit 2: a
+                           mixed stencil plan with n_tot <= 256 runs each recurrence step
+                           and its tensor-core Gram products as one fused launch instead
+                           of separate kernels (same float32 blocks; moments equal up to
+                           the grouping of float32 sums).  Other bits must be 0
+                           (SSM_EINVAL otherwise). */
     double eps_floor;   /* rounding unit of the floor of Alg. 4's truncation: an eigenvalue
                            of K_W(t) is also dropped below
                            8 n_v eps_floor max_i X_0[i][i] sum_{l<=M/2} (l+1)|mu_l(t)|,

@@ -15,6 +15,7 @@ SSM_FP64 = 0
 SSM_MIXED = 1
 SSM_OPT_CUDA_CORE_GRAM = 1
 SSM_OPT_ADJOINT = 2
+SSM_OPT_FUSED_STEP = 4  # mixed stencil plans: recurrence step and Gram products in one launch
 
 
 class ssm_stencil(C.Structure):

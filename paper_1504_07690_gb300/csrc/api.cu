@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -207,6 +208,7 @@ void free_plan(ssm_plan_s* h) {
     dev_free(P.d_ring);
     dev_free(P.d_ring_sum);
     for (auto& pb : P.d_panel) dev_free(pb);
+    dev_free(P.d_fmeta);
     for (auto& e : P.ev_st) if (e) cudaEventDestroy(e);
     for (auto& e : P.ev_gr) if (e) cudaEventDestroy(e);
     if (P.gstream) cudaStreamDestroy(P.gstream);
@@ -624,7 +626,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if (p.precision != SSM_FP64 && p.precision != SSM_MIXED) return fail(nullptr, SSM_EINVAL, "unknown precision");
     if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
     if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
-    if (p.options & ~3) return fail(nullptr, SSM_EINVAL, "unknown option bits");
+    if (p.options & ~7) return fail(nullptr, SSM_EINVAL, "unknown option bits");
 
     ssm_plan_s* h = new ssm_plan_s();
     Plan& P = h->P;
@@ -799,21 +801,32 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     P.use_tc = P.mixed && !(p.options & 1) && gram_tc_supported(P.n_tot, P.ld);
     if (P.use_tc) {
         gram_tc_slabs(P.n, &P.tc_ne, &P.tc_no);
-        CREATE_CUDA(dev_alloc(&P.d_part_tc, gram_tc_partial_floats_total(P.tc_ne, P.tc_no, P.n_tot) + 2));
-        // partials of up to 64 steps are reduced in one batch (at most 1 GiB of ring)
-        const size_t slot = gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot);
+        // options bit 2: stencil steps fused with their Gram products in one launch
+        // (the separate recurrence and Gram kernels are faster on the workloads measured)
+        P.use_fused = P.is_stencil && (p.options & 4) && fused_tc_config(P, &P.fcfg);
+        size_t slot = gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot);
+        if (P.use_fused) slot = std::max(slot, fused_tc_partial_floats(P.fcfg, P.n_tot));
+        P.tc_slot = slot;
+        CREATE_CUDA(dev_alloc(&P.d_part_tc,
+                              std::max(gram_tc_partial_floats_total(P.tc_ne, P.tc_no, P.n_tot), slot) + 2));
+        // partials of up to 64 steps are reduced in one batch (at most 1 GiB of ring; the
+        // fused path uses the ring as two halves and needs two slots)
         int ring = (int)(((size_t)1 << 30) / (slot * sizeof(float)));
         if (ring > 64) ring = 64;
-        if (ring < 1) ring = 1;
+        if (ring < (P.use_fused ? 2 : 1)) ring = P.use_fused ? 2 : 1;
         P.tc_ring = ring;
         CREATE_CUDA(dev_alloc(&P.d_ring, slot * ring));
         CREATE_CUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * ring * P.n_tot * P.n_tot));
+        if (P.use_fused) {
+            CREATE_CUDA(cudaMalloc((void**)&P.d_fmeta, fused_tc_meta_bytes(P)));
+            CREATE_CUDA(launch_fused_meta(P, P.fcfg, P.d_fmeta, P.stream));
+        }
         P.panel_groups = gram_tc_groups(P.n_tot);
         P.n_panels = (P.n + 31) / 32;
         const size_t pbytes = (size_t)P.n_panels * 2 * P.panel_groups * 528;
-        for (auto& pb : P.d_panel) {
-            CREATE_CUDA(cudaMalloc((void**)&pb, pbytes));
-            CREATE_CUDA(cudaMemsetAsync(pb, 0, pbytes, P.stream));  // rows past N stay zero
+        for (int j = 0; j < (P.use_fused ? 1 : 3); ++j) {  // the fused path needs panels of V_0 only
+            CREATE_CUDA(cudaMalloc((void**)&P.d_panel[j], pbytes));
+            CREATE_CUDA(cudaMemsetAsync(P.d_panel[j], 0, pbytes, P.stream));  // rows past N stay zero
         }
         // the Gram products of step k run on a second stream, next to step k+1 of the recurrence
         CREATE_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
@@ -1082,7 +1095,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     // products and reductions run on gstream, so the Gram of step k overlaps the
     // recurrence of step k+1.  Step k writes panel (k+1) % 3, last read by the Gram
     // of step k-1: it waits for that Gram only.
-    const bool ovl = P.use_tc && P.gstream;
+    const bool ovl = P.use_tc && P.gstream && !P.use_fused;
     cudaStream_t gs = ovl ? P.gstream : P.stream;
     auto gram = [&](const void* A, const void* B, int j) -> cudaError_t {
         if (P.use_tc) {
@@ -1119,7 +1132,51 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
                                  : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, -1, P.stream));
         P.stats.launches++;
     }
-    for (int k = 0; k < S; ++k) {
+    // Fused path: launch k evaluates step k of the stencil with tile 0 of its Gram
+    // products and forms tile 1 of step k-1 (launch S: tile 1 of the last step), so step
+    // j is complete after launch j+1 (after launch j when there is no tile 1).  Step 0's
+    // partials live in d_part_tc, step j >= 1's in ring slot (j-1) % 2R; steps are
+    // reduced in batches of R, one half of the ring while the other fills.
+    const int nF = P.fcfg.nA + P.fcfg.nB;
+    const int R = P.tc_ring / 2 > 0 ? P.tc_ring / 2 : 1;
+    auto fslot = [&](int j) -> float* {
+        return j == 0 ? P.d_part_tc : P.d_ring + (size_t)((j - 1) % (2 * R)) * P.tc_slot;
+    };
+    const bool tile1 = P.fcfg.nB > 0;
+    for (int k = 0; k <= S && P.use_fused; ++k) {
+        const bool a_on = k < S, b_on = tile1 && k >= 1;
+        const void* Vc = P.d_V[k % 3];
+        const void* Vp = P.d_V[(k + 2) % 3];
+        void* Vn = P.d_V[(k + 1) % 3];
+        if (a_on || b_on) {
+            Scope sc(h, PH_REC);
+            CUDA_OR_FAIL(h, launch_fused_step_tc(P, P.fcfg, P.d_fmeta, (const float*)Vc,
+                                                 k == 0 ? nullptr : (const float*)Vp, (float*)Vn,
+                                                 k == 0 ? 0.5f : 1.f, k == 0 ? 0.f : 1.f, a_on ? fslot(k) : nullptr,
+                                                 b_on ? (const float*)Vc : nullptr, b_on ? (const float*)Vp : nullptr,
+                                                 b_on ? fslot(k - 1) : nullptr, P.d_flag, P.stream));
+            P.stats.launches++;
+            P.stats.recurrence_launches += a_on ? 1 : 0;
+            P.stats.gram_launches++;
+        }
+        if (a_on && P.adjoint && (k % P.ck_c) == 0) {
+            const size_t bb = (size_t)P.n * P.ld * sizeof(float);
+            uint8_t* ck = (uint8_t*)P.d_ck + (size_t)(2 * (k / P.ck_c)) * bb;
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(ck, Vc, bb, cudaMemcpyDeviceToDevice, P.stream));
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(ck + bb, Vn, bb, cudaMemcpyDeviceToDevice, P.stream));
+        }
+        const int j = tile1 ? k - 1 : k;  // the step completed by this launch
+        if (j < 0 || j >= S) continue;
+        if (j == 0 || (j % R) == 0 || j == S - 1) {
+            const int k0 = j == 0 ? 0 : ((j - 1) / R) * R + 1;
+            const size_t nn2 = (size_t)P.n_tot * P.n_tot;
+            Scope sc(h, PH_REDUCE);
+            CUDA_OR_FAIL(h, launch_reduce_fused(fslot(k0), P.tc_slot, P.fcfg.nA, nF, P.n_tot, P.d_X, k0, j - k0 + 1,
+                                                P.d_ring_sum, P.d_ring_sum + (size_t)P.tc_ring * nn2, P.stream));
+            P.stats.launches += 2;
+        }
+    }
+    for (int k = 0; k < S && !P.use_fused; ++k) {
         void* Vc = P.d_V[k % 3];
         void* Vp = P.d_V[(k + 2) % 3];
         void* Vn = P.d_V[(k + 1) % 3];
@@ -1428,6 +1485,7 @@ ssm_status ssm_plan_set_diag(ssm_plan_t h, const double* diag) {
     if (lo < P.a || hi > P.b)
         return fail(h, SSM_EDOMAIN, "the new Gershgorin interval leaves the plan's interval (a, b)");
     CUDA_OR_FAIL(h, launch_fold_stencil(P, P.d_stage, P.extra, P.stream));
+    if (P.use_fused) CUDA_OR_FAIL(h, launch_fused_meta(P, P.fcfg, P.d_fmeta, P.stream));  // holds the diagonal
     P.stats.launches += 2;
     return sync_and_settle(h);
 }

@@ -33,10 +33,13 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace ssm {
 
 namespace {
+
+using namespace tc;
 
 constexpr int KC = 32;                 // rows per panel (K of one pipeline stage)
 constexpr int KG = KC / 8;             // 8-row core groups per panel
@@ -50,78 +53,9 @@ constexpr int NTHREADS = 128;
 constexpr int GROUP_BYTES = KG * 128 + 16;
 constexpr int PART_BYTES = 32 * GROUP_BYTES;  // one part of one stage: 32 column groups
 constexpr int TMEM_COLS = 512;
-constexpr long WAIT_LIMIT = 1L << 26;  // bounded mbarrier polls
 // > half of an SM (one Gram CTA per SM, it owns all 512 TMEM columns) and small enough
 // that two recurrence CTAs (34 KB each) share the SM with it
 constexpr int SMEM_BYTES = STAGES_E * 2 * PART_BYTES + 1024;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// tcgen05 shared-memory matrix descriptor, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version
-    return d;
-}
-
-// kind::f16 instruction descriptor: D f32, A/B bf16, both MN-major, M = 128.
-__device__ __forceinline__ uint32_t instr_desc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
-           ((128u >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    for (long i = 0; i < WAIT_LIMIT; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Two 16-column loads in flight, one wait.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr + 16u));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 struct TcArgs {
     const uint8_t* PX;  // panels of V_{k+1}
@@ -136,37 +70,6 @@ struct TcArgs {
     int* flag;
     const int2* slabs;  // NULL: uniform slabs; else panel range [x, y) of every CTA
 };
-
-__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(m)), "r"(bytes)
-                 : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(m)) : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* m) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(smem_u32(m))
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* m) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(m))
-                 : "memory");
-}
 
 __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -198,9 +101,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
         reinterpret_cast<uint4*>(smem)[t] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tmem_alloc(&tmem_slot, TMEM_COLS);
     }
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -332,7 +233,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // Compensated (Neumaier) float32 sum: the slab partials are float32, and their
@@ -516,7 +417,63 @@ __global__ void moments_tc_seg_kernel(const double* __restrict__ ge, const doubl
     }
 }
 
+// Fused-step partials (fused_tc.cu): slab s holds accumulator rows 0..127 for
+// s < nA and rows 128.. for s >= nA, so element (i, j) sums the slabs of its
+// row range, in the fixed order of sum_tc_kernel.  blockIdx.y selects the step.
+__global__ void __launch_bounds__(256)
+sum_fused_kernel(const float* __restrict__ ring, size_t slot, int nA, int nF, int n_tot, double* __restrict__ ge,
+                 double* __restrict__ go) {
+    __shared__ double se[8][32], so[8][32];
+    const size_t nn = (size_t)n_tot * n_tot;
+    const float* pe = ring + (size_t)blockIdx.y * slot;
+    const float* po = pe + (size_t)nF * nn;
+    double* gq = ge + (size_t)blockIdx.y * nn;
+    double* oq = go + (size_t)blockIdx.y * nn;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (size_t e0 = (size_t)blockIdx.x * 32; e0 < nn; e0 += (size_t)gridDim.x * 32) {
+        const size_t e = e0 + lane;
+        Sum32 a, b;
+        if (e < nn) {
+            const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
+            const int s0 = i < 128 ? 0 : nA, s1 = i < 128 ? nA : nF;
+            if (i <= j)
+                for (int s = s0 + w; s < s1; s += 8) a.add(pe[(size_t)s * nn + e]);
+            for (int s = s0 + w; s < s1; s += 8) b.add(po[(size_t)s * nn + e]);
+        }
+        se[w][lane] = a.value();
+        so[w][lane] = b.value();
+        __syncthreads();
+        if (w == 0 && e < nn) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                a += se[k][lane];
+                b += so[k][lane];
+            }
+            gq[e] = a;
+            oq[e] = b;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_reduce_fused(const float* ring, size_t slot, int nA, int nF, int n_tot, double* X, int k0,
+                                int nk, double* ge, double* go, cudaStream_t s) {
+    if (k0 == 0 && nk != 1) return cudaErrorInvalidValue;
+    const int64_t nn = (int64_t)n_tot * n_tot;
+    int64_t sb = (nn + 31) / 32;
+    if (sb > 1024) sb = 1024;
+    sum_fused_kernel<<<dim3((unsigned)sb, (unsigned)nk), 256, 0, s>>>(ring, slot, nA, nF, n_tot, ge, go);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned mb = (unsigned)((nn + 255) / 256 > 512 ? 512 : (nn + 255) / 256);
+    if (k0 == 0)
+        moments_tc_kernel<<<mb, 256, 0, s>>>(ge, go, n_tot, X, 0);
+    else
+        moments_tc_batch_kernel<<<dim3(mb, (unsigned)nk), 256, 0, s>>>(ge, go, n_tot, X, k0);
+    return cudaGetLastError();
+}
 
 bool gram_tc_supported(int n_tot, int ld) { return n_tot >= 1 && n_tot <= 256 && (ld % 4) == 0; }
 

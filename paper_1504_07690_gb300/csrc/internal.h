@@ -21,6 +21,17 @@ struct StencilGeom {
     uint32_t active[3];      // axis contributes (offdiag != 0 and has a neighbour)
 };
 
+// Fused recurrence + tensor-core Gram step (fused_tc.cu): CTAs of tile 0 / tile 1,
+// pipeline depths and shared-memory carve-up.
+struct FusedCfg {
+    int nA = 0, nB = 0;             // CTAs owning accumulator rows 0..127 / 128..
+    int NX = 0, NS = 0;             // float32 slots, operand stages
+    int nblk = 0;                   // stride blocks copied per panel
+    int blk_axis[4] = {0, 0, 0, 0};
+    int blk_dir[4] = {0, 0, 0, 0};
+    uint32_t slot_bytes = 0, stage_bytes = 0;
+};
+
 // ---------------------------------------------------------------- plan
 
 struct Plan {
@@ -57,6 +68,10 @@ struct Plan {
     float* d_ring = nullptr;           // ring of tc_ring partial slots (steps >= 1)
     double* d_ring_sum = nullptr;      // 2 x tc_ring x n_tot^2 float64 slab sums
     int tc_ring = 0;
+    size_t tc_slot = 0;                // floats per ring slot
+    bool use_fused = false;            // stencil steps fused with the Gram products
+    FusedCfg fcfg{};
+    uint8_t* d_fmeta = nullptr;        // neighbour tables of the fused step
     int panel_groups = 0;              // split-bf16 panels: column groups of 8
     int64_t n_panels = 0;              // panels of 32 rows
     uint8_t* d_panel[3] = {nullptr, nullptr, nullptr};  // panels of V_j in d_panel[j % 3] (batched: j % 2)
@@ -185,6 +200,24 @@ cudaError_t launch_reduce_tc(const float* part, int n_e, int n_o, int n_tot, dou
 // Moments of steps k0..k0+nk-1 from a ring of nk partial slots (float64 scratch ge, go: nk x n_tot^2 each).
 cudaError_t launch_reduce_tc_batch(const float* ring, int n_e, int n_o, int n_tot, double* X, int k0, int nk,
                                    double* ge, double* go, cudaStream_t s);
+
+// Fused recurrence + Gram step (fused_tc.cu): false if the plan does not qualify (mixed
+// stencil plan, n_tot <= 256, shared-memory budget).  Partials [2][nA + nB][n_tot][n_tot].
+bool fused_tc_config(const Plan& P, FusedCfg* cfg);
+size_t fused_tc_partial_floats(const FusedCfg& cfg, int n_tot);
+// Neighbour tables of the panels (once per plan, and again when the diagonal changes).
+size_t fused_tc_meta_bytes(const Plan& P);
+cudaError_t launch_fused_meta(const Plan& P, const FusedCfg& cfg, uint8_t* meta, cudaStream_t s);
+// One launch: stencil CTAs do step k (Vn = c 2A~ Vc - d Vp, tile-0 partials into part_a;
+// part_a NULL: none), tile-1 CTAs the products of step k-1 from Xb = V_k, Yb = V_{k-1}
+// (tile-1 partials into part_b; NULL: none).
+cudaError_t launch_fused_step_tc(const Plan& P, const FusedCfg& cfg, const uint8_t* meta, const float* Vc,
+                                 const float* Vp, float* Vn, float c, float d, float* part_a, const float* Xb,
+                                 const float* Yb, float* part_b, int* flag, cudaStream_t s);
+// Moments of steps k0..k0+nk-1 (k0 = 0 only with nk = 1) from fused-step partials in
+// consecutive slots of `slot` floats: rows < 128 sum slabs [0, nA), the rest [nA, nF).
+cudaError_t launch_reduce_fused(const float* ring, size_t slot, int nA, int nF, int n_tot, double* X, int k0,
+                                int nk, double* ge, double* go, cudaStream_t s);
 
 // Reduce partials into the moments of step k (see moments.cu).
 cudaError_t launch_reduce_moments(const double* part, int n_split, int n_tot, double* X, int step,

@@ -6,7 +6,8 @@ stored), element by element:
 * float64: dL/d diag, dL/d offdiag (stencil, per axis) and dL/dA_ij (CSR,
   per stored entry) within 1e-10 of the largest entry, for general G_l and
   for G_l = g_l I;
-* float32 recurrence (mixed plans): within 1e-4 of the largest entry;
+* float32 recurrence (mixed plans, separate or fused recurrence + Gram steps):
+  within 1e-4 of the largest entry;
 * the dense-eigh closed form (W = sqrt(N) I, G_l = g_l I);
 * the autograd Function against central finite differences of its own
   float64 forward pass (KPM loss plus Tr exp(-A) by Alg. 8's weights).
@@ -125,13 +126,14 @@ def test_csr_adjoint_fp64_per_entry(S):
     assert np.max(np.abs(dval - gp.data)) <= 1e-10 * scale
 
 
-def test_stencil_adjoint_mixed(S):
+@pytest.mark.parametrize("options", [2, 6], ids=["separate", "fused-step"])
+def test_stencil_adjoint_mixed(S, options):
     st = STENCILS[1][1]()
     n_tot, M = 8, 26
     rng = np.random.default_rng(13)
     W = rng.standard_normal((st.n, n_tot))
     G = rng.standard_normal((M + 1, n_tot, n_tot))
-    plan = S.ssm_plan_create(stencil=st, n_v=n_tot, degree=M, precision="mixed", options=2)
+    plan = S.ssm_plan_create(stencil=st, n_v=n_tot, degree=M, precision="mixed", options=options)
     info = S.ssm_plan_info(plan)
     dd, do = _gpu(S, plan, W, G)
     gd, go = _oracle_stencil(st, W, M, G, info["a"], info["b"])

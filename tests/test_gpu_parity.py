@@ -294,3 +294,49 @@ def test_mixed_tensor_core_moments(S, nv, nvh, nx):
     # split-bf16 tensor products vs float32 CUDA-core products on the same blocks
     assert np.max(np.abs(Xtc - Xcc)) <= 1e-5 * scale
     assert np.array_equal(Xtc, np.transpose(Xtc, (0, 2, 1)))
+
+
+# ------------------------------------------------------------------ fused recurrence + Gram step
+
+FUSED_SHAPES = [
+    # (dims, periodic, offdiag, n_v, n_vh): 2D periodic with two accumulator tiles and
+    # ~10 panels per CTA (every pipeline barrier wraps), ragged N, 3D with four stride
+    # blocks, a periodic extent-1 axis (self coupling), N < 16, an inactive middle axis,
+    # the largest n_tot
+    ((1, 128, 128), (False, True, True), (0.0, -1.0, -1.0), 150, 50),
+    ((1, 47, 47), (False, True, True), (0.0, -1.0, -1.0), 200, 0),
+    ((5, 6, 7), (True, False, True), (-0.8, -1.0, -1.2), 100, 36),
+    ((1, 7, 8), (True, True, False), (-0.5, -1.0, -1.0), 8, 0),
+    ((1, 1, 11), (False, False, True), (0.0, 0.0, -1.0), 20, 0),
+    ((3, 1, 33), (True, False, False), (-1.0, 0.0, -1.0), 129, 0),
+    ((1, 64, 64), (False, True, True), (0.0, -1.0, -1.0), 256, 0),
+]
+
+
+@pytest.mark.parametrize("dims,per,off,nv,nvh", FUSED_SHAPES,
+                         ids=[f"{d[0]}x{d[1]}x{d[2]}-{n + h}" for d, _, _, n, h in FUSED_SHAPES])
+def test_fused_step_matches_separate_kernels_and_oracle(S, dims, per, off, nv, nvh):
+    n = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(sum(dims) + nv)
+    st = wl.Stencil(dims=dims, periodic=per, diag=rng.uniform(-2, 2, n), offdiag=off)
+    n_tot = nv + nvh
+    W = wl.random_block(n, n_tot, 77 + n_tot, "rademacher")
+    M = 40
+    fused = S.ssm_plan_create(stencil=st, n_v=nv, n_vh=nvh, degree=M, precision="mixed", options=4)
+    sep = S.ssm_plan_create(stencil=st, n_v=nv, n_vh=nvh, degree=M, precision="mixed")
+    Wd = torch.from_numpy(W).cuda()
+    Xf = S.ssm_moments(fused, Wd, return_moments=True).cpu().numpy()
+    Xs = S.ssm_moments(sep, Wd, return_moments=True).cpu().numpy()
+    info = S.ssm_plan_info(fused)
+    X64 = O.moments_direct(O.transform(_csr_A(st), info["a"], info["b"]), W, M)
+    scale = np.max(np.abs(X64))
+    ef, es, efs = (np.max(np.abs(a - b)) / scale for a, b in ((Xf, X64), (Xs, X64), (Xf, Xs)))
+    # identical float32 blocks; only the grouping of the float32 Gram sums differs
+    assert efs <= 2e-6, (ef, es, efs)
+    # split-bf16 products (~2^-17 relative per term, doubled by the doubling identities)
+    # on float32 blocks: within 5e-5 of the float64 oracle, as the separate kernels are
+    assert ef <= 5e-5 and es <= 5e-5, (ef, es, efs)
+    assert np.array_equal(Xf, np.transpose(Xf, (0, 2, 1)))
+    # a second call on the same plan repeats bit for bit
+    Xf2 = S.ssm_moments(fused, Wd, return_moments=True).cpu().numpy()
+    assert np.array_equal(Xf, Xf2)
