@@ -47,7 +47,7 @@ struct Shared {
     double* red;   // NT / 32
     int* misc;     // [0] nkeep, [1] nsel, [5] QL limit hit, [6] Cholesky pivot ok, [7] rank, [8..13] QL buffers
     double* beta;  // n: Householder scalars
-    double* gt;    // 2 x 32 x 33: staged tiles of gemm_tn
+    double* gt;    // 3 x 32 x 33: staged tiles of gemm_tn and cholesky_lower
 };
 
 __device__ double block_sum(double v, double* red) {
@@ -94,14 +94,17 @@ __device__ __forceinline__ double dot8(const double* __restrict__ a, size_t sa, 
 
 // Householder reduction of the symmetric n x n matrix A (row-major, ld n) to
 // tridiagonal T = H^T A H: sh.d, sh.off receive T; row k of A (columns k+1..)
-// receives the k-th Householder vector and sh.beta[k] its scalar.
+// receives the k-th Householder vector and sh.beta[k] its scalar.  Only the
+// lower triangle of A is read and kept up to date: the product p = A22 v takes
+// row i left of the diagonal and column i below it, and the rank-2 update
+// touches the lower triangle only (no mirrored, uncoalesced stores).
 __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
     const int tid = threadIdx.x;
     for (int k = 0; k + 2 < n; ++k) {
         const int L = n - k - 1;
-        const double* x = A + (size_t)k * n + k + 1;  // row k == column k (symmetric)
+        const double* x = A + (size_t)(k + 1) * n + k;  // column k below the diagonal (stride n)
         double f = 0.0;
-        for (int i = tid; i < L; i += (int)blockDim.x) f = fma(x[i], x[i], f);
+        for (int i = tid; i < L; i += (int)blockDim.x) f = fma(x[(size_t)i * n], x[(size_t)i * n], f);
         const double nrm2 = block_sum(f, sh.red);
         const double x0 = x[0];
         double beta = 0.0, alpha = x0;
@@ -110,7 +113,7 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             const double v0 = x0 - alpha;
             const double vtv = nrm2 - x0 * x0 + v0 * v0;
             beta = 2.0 / vtv;
-            for (int i = tid; i < L; i += (int)blockDim.x) sh.v[i] = (i == 0) ? v0 : x[i];
+            for (int i = tid; i < L; i += (int)blockDim.x) sh.v[i] = (i == 0) ? v0 : x[(size_t)i * n];
         }
         __syncthreads();
         if (tid == 0) {
@@ -119,32 +122,28 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             sh.beta[k] = beta;
         }
         if (beta != 0.0) {
-            // p = beta A22 v: thread i walks column i of the symmetric A22 (row i
-            // transposed), so a warp reads 32 consecutive doubles per step and
-            // every thread has its own independent loads in flight
+            // p = beta A22 v: row i of the lower triangle (j < i) and column i from the
+            // diagonal down (j >= i, consecutive threads read consecutive doubles)
+            const double* A22 = A + (size_t)(k + 1) * n + k + 1;
             for (int i = tid; i < L; i += (int)blockDim.x)
-                sh.p[i] = beta * dot8(A + (size_t)(k + 1) * n + k + 1 + i, n, sh.v, 1, L);
+                sh.p[i] = beta * (dot8(A22 + (size_t)i * n, 1, sh.v, 1, i) +
+                                  dot8(A22 + (size_t)i * n + i, n, sh.v + i, 1, L - i));
             __syncthreads();
             double g = 0.0;
             for (int i = tid; i < L; i += (int)blockDim.x) g = fma(sh.p[i], sh.v[i], g);
             const double K = 0.5 * beta * block_sum(g, sh.red);
             for (int i = tid; i < L; i += (int)blockDim.x) sh.p[i] -= K * sh.v[i];  // p becomes w
             __syncthreads();
-            // A22 -= v w^T + w v^T on the lower triangle (warp per row, lanes along the
-            // row), mirrored to the upper one: half the float64 work, exact symmetry
+            // A22 -= v w^T + w v^T on the lower triangle (warp per row, lanes along the row)
             {
                 const int nw = (int)(blockDim.x >> 5), wp = tid >> 5, ln = tid & 31;
                 for (int i = wp; i < L; i += nw) {
                     const double vi = sh.v[i], pi = sh.p[i];
                     double* rowi = A + (size_t)(k + 1 + i) * n + k + 1;
-                    for (int j = ln; j <= i; j += 32) {
-                        const double a = fma(-vi, sh.p[j], fma(-pi, sh.v[j], rowi[j]));
-                        rowi[j] = a;
-                        A[(size_t)(k + 1 + j) * n + k + 1 + i] = a;
-                    }
+                    for (int j = ln; j <= i; j += 32) rowi[j] = fma(-vi, sh.p[j], fma(-pi, sh.v[j], rowi[j]));
                 }
             }
-            // keep v in row k for the accumulation
+            // keep v in row k (right of the diagonal, unused by the reduction) for the accumulation
             for (int i = tid; i < L; i += (int)blockDim.x) A[(size_t)k * n + k + 1 + i] = sh.v[i];
         }
         __syncthreads();
@@ -152,7 +151,7 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
     if (tid == 0) {
         if (n >= 2) {
             sh.d[n - 2] = A[(size_t)(n - 2) * n + n - 2];
-            sh.off[n - 2] = A[(size_t)(n - 2) * n + n - 1];
+            sh.off[n - 2] = A[(size_t)(n - 1) * n + n - 2];
             sh.beta[n - 2] = 0.0;
         }
         sh.d[n - 1] = A[(size_t)(n - 1) * n + n - 1];
@@ -493,38 +492,117 @@ __device__ void bisect_all(int n, Shared& sh) {
 }
 
 // Cholesky factor of the symmetric positive definite n x n matrix A
-// (row-major), right-looking: the lower triangle of A receives L (A = L L^T)
-// and sh.v[k] = 1 / L[k][k].  Returns false (on every thread) at the first
-// pivot that is not positive.
+// (row-major): the lower triangle of A receives L (A = L L^T) and sh.v[k] =
+// 1 / L[k][k].  Returns false (on every thread) at the first pivot that is not
+// positive.  Blocked, left-looking, panels of 32 columns: each 32-row tile of
+// the panel is formed as A - L[:, :jb] L[panel, :jb]^T from 32 x 32 tiles
+// staged in shared memory (2 x 2 outputs per thread, as gemm_tn); the diagonal
+// block is then factored in shared memory by one warp (one row per lane), and
+// the tiles below it are solved against it (L = C L_D^-T) by one warp, also in
+// shared memory.  Only L's finished columns are read from global memory, once
+// per panel, instead of a read-modify-write of the whole trailing matrix for
+// every column.
 __device__ bool cholesky_lower(double* __restrict__ A, int n, Shared& sh) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int k = 0; k < n; ++k) {
-        if (tid == 0) {
-            const double piv = A[(size_t)k * n + k];
-            const bool pos = piv > 0.0;
-            const double r = pos ? rsqrt(piv) : 0.0;
-            // one Newton step on 1/sqrt(piv)
-            const double rr = pos ? r * fma(-0.5 * piv * r, r, 1.5) : 0.0;
-            sh.v[k] = rr;
-            A[(size_t)k * n + k] = piv * rr;
-            sh.misc[6] = pos;
+    double* ta = sh.gt;            // [32][33]: staged L rows of the tile, then the tile itself
+    double* tb = sh.gt + 32 * 33;  // [32][33]: staged L rows of the panel
+    double* td = tb + 32 * 33;     // [32][33]: factored diagonal block L_D
+    const int tid = threadIdx.x, nt = (int)blockDim.x, warp = tid >> 5, lane = tid & 31;
+    for (int jb = 0; jb < n; jb += 32) {
+        const int w = n - jb < 32 ? n - jb : 32;
+        for (int i0 = jb; i0 < n; i0 += 32) {
+            const int h = n - i0 < 32 ? n - i0 : 32;
+            double acc[4][2][2] = {};
+            for (int k0 = 0; k0 < jb; k0 += 32) {
+                __syncthreads();
+                for (int e = tid; e < 32 * 32; e += nt) {
+                    const int ii = e >> 5, kk = e & 31;
+                    const int k = k0 + kk;
+                    ta[kk * 33 + ii] = (ii < h && k < jb) ? A[(size_t)(i0 + ii) * n + k] : 0.0;
+                    tb[kk * 33 + ii] = (ii < w && k < jb) ? A[(size_t)(jb + ii) * n + k] : 0.0;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) {
+                    const int t = tid + pass * nt;
+                    if (t < 256) {
+                        const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+#pragma unroll 8
+                        for (int kk = 0; kk < 32; ++kk) {
+                            const double a0 = ta[kk * 33 + pi], a1 = ta[kk * 33 + pi + 1];
+                            const double b0 = tb[kk * 33 + qj], b1 = tb[kk * 33 + qj + 1];
+                            acc[pass][0][0] = fma(a0, b0, acc[pass][0][0]);
+                            acc[pass][0][1] = fma(a0, b1, acc[pass][0][1]);
+                            acc[pass][1][0] = fma(a1, b0, acc[pass][1][0]);
+                            acc[pass][1][1] = fma(a1, b1, acc[pass][1][1]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // the updated tile C = A[i0.., jb..] - acc into ta[row][col]
+#pragma unroll
+            for (int pass = 0; pass < 4; ++pass) {
+                const int t = tid + pass * nt;
+                if (t < 256) {
+                    const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+                    for (int i = 0; i < 2; ++i)
+                        for (int j = 0; j < 2; ++j) {
+                            const int ii = pi + i, c = qj + j;
+                            if (ii < h && c < w) ta[ii * 33 + c] = A[(size_t)(i0 + ii) * n + jb + c] - acc[pass][i][j];
+                        }
+                }
+            }
+            __syncthreads();
+            if (i0 == jb) {
+                // diagonal block: right-looking in shared memory, lane = row
+                if (warp == 0) {
+                    bool pos = true;
+                    for (int c = 0; c < w && pos; ++c) {
+                        const double piv = ta[c * 33 + c];
+                        pos = piv > 0.0;
+                        if (!pos) break;
+                        const double r0 = rsqrt(piv);
+                        const double rr = r0 * fma(-0.5 * piv * r0, r0, 1.5);  // one Newton step
+                        if (lane == 0) sh.v[jb + c] = rr;
+                        __syncwarp();
+                        if (lane == c) ta[c * 33 + c] = piv * rr;
+                        if (lane > c && lane < w) ta[lane * 33 + c] *= rr;
+                        __syncwarp();
+                        if (lane > c && lane < w) {
+                            const double lic = ta[lane * 33 + c];
+                            for (int j = c + 1; j <= lane; ++j) ta[lane * 33 + j] = fma(-lic, ta[j * 33 + c], ta[lane * 33 + j]);
+                        }
+                        __syncwarp();
+                    }
+                    if (lane == 0) sh.misc[6] = pos;
+                }
+                __syncthreads();
+                if (!sh.misc[6]) return false;
+                for (int e = tid; e < 32 * 32; e += nt) {
+                    const int ii = e >> 5, c = e & 31;
+                    if (ii < w && c <= ii) {
+                        const double v = ta[ii * 33 + c];
+                        td[ii * 33 + c] = v;
+                        A[(size_t)(jb + ii) * n + jb + c] = v;
+                    }
+                }
+            } else {
+                // rows below the diagonal block: forward substitution, lane = row
+                if (warp == 0 && lane < h) {
+                    for (int c = 0; c < w; ++c) {
+                        double s = ta[lane * 33 + c];
+                        for (int m = 0; m < c; ++m) s = fma(-ta[lane * 33 + m], td[c * 33 + m], s);
+                        ta[lane * 33 + c] = s * sh.v[jb + c];
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < 32 * 32; e += nt) {
+                    const int ii = e >> 5, c = e & 31;
+                    if (ii < h && c < w) A[(size_t)(i0 + ii) * n + jb + c] = ta[ii * 33 + c];
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (!sh.misc[6]) return false;
-        const double rk = sh.v[k];
-        for (int i = k + 1 + tid; i < n; i += (int)blockDim.x) {
-            const double v = A[(size_t)i * n + k] * rk;
-            A[(size_t)i * n + k] = v;
-            sh.p[i] = v;
-        }
-        __syncthreads();
-        // A[i][j] -= l_i l_j for k < j <= i (warp per row, lanes along the row)
-        for (int i = k + 1 + warp; i < n; i += (int)(blockDim.x >> 5)) {
-            const double li = sh.p[i];
-            double* row = A + (size_t)i * n;
-            for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fma(-li, sh.p[j], row[j]);
-        }
-        __syncthreads();
     }
     return true;
 }
@@ -823,6 +901,28 @@ __device__ void twisted_vectors(int n, int r, double* __restrict__ Z, double* __
 // was reduced from.  One thread per column.
 __device__ void back_transform(const double* __restrict__ A, int n, double* __restrict__ Z, int ldz, int r,
                                const Shared& sh) {
+    const int nw = (int)(blockDim.x >> 5);
+    if (r <= nw) {
+        // few columns: a warp per column, lanes along the reflector
+        const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+        if (wp < r) {
+            double* z = Z + wp;
+            for (int k = n - 3; k >= 0; --k) {
+                const double beta = sh.beta[k];
+                if (beta == 0.0) continue;
+                const int L = n - k - 1;
+                const double* v = A + (size_t)k * n + k + 1;
+                double f = 0.0;
+                for (int j = ln; j < L; j += 32) f = fma(v[j], z[(size_t)(k + 1 + j) * ldz], f);
+                for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+                f *= beta;
+                for (int j = ln; j < L; j += 32) z[(size_t)(k + 1 + j) * ldz] -= f * v[j];
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        return;
+    }
     for (int q = threadIdx.x; q < r; q += (int)blockDim.x) {
         for (int k = n - 3; k >= 0; --k) {
             const double beta = sh.beta[k];
@@ -832,6 +932,71 @@ __device__ void back_transform(const double* __restrict__ A, int n, double* __re
             const double f = beta * dot8(v, 1, Z + (size_t)(k + 1) * ldz + q, ldz, L);
             for (int j = 0; j < L; ++j) Z[(size_t)(k + 1 + j) * ldz + q] -= f * v[j];
         }
+    }
+    __syncthreads();
+}
+
+// Householder QR of the n x d matrix Q (columns 0..d-1, ld ldq): column j
+// receives the reflector u_j in rows j.. (u_j[j] = x_j - alpha) and sh.beta[j]
+// its scalar, so that H_{d-1} ... H_0 Q is upper triangular; the span of Q is
+// that of the first d columns of H_0 ... H_{d-1}, its orthogonal complement that
+// of the others.
+__device__ void householder_qr_cols(double* __restrict__ Q, int ldq, int n, int d, Shared& sh) {
+    const int tid = threadIdx.x;
+    for (int j = 0; j < d; ++j) {
+        double f = 0.0;
+        for (int i = j + tid; i < n; i += (int)blockDim.x) f = fma(Q[(size_t)i * ldq + j], Q[(size_t)i * ldq + j], f);
+        const double nrm2 = block_sum(f, sh.red);
+        const double x0 = Q[(size_t)j * ldq + j];
+        double beta = 0.0, v0 = x0;
+        if (nrm2 - x0 * x0 > 0.0) {
+            const double alpha = -copysign(sqrt(nrm2), x0);
+            v0 = x0 - alpha;
+            beta = 2.0 / (nrm2 - x0 * x0 + v0 * v0);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            Q[(size_t)j * ldq + j] = v0;
+            sh.beta[j] = beta;
+        }
+        __syncthreads();
+        if (beta != 0.0)
+            for (int c = j + 1 + tid; c < d; c += (int)blockDim.x) {
+                double g = 0.0;
+                for (int i = j; i < n; ++i) g = fma(Q[(size_t)i * ldq + j], Q[(size_t)i * ldq + c], g);
+                g *= beta;
+                for (int i = j; i < n; ++i) Q[(size_t)i * ldq + c] = fma(-g, Q[(size_t)i * ldq + j], Q[(size_t)i * ldq + c]);
+            }
+        __syncthreads();
+    }
+}
+
+// K <- H_j K H_j on the trailing block K[j.., j..] of the symmetric n x n K (ld n),
+// H_j = I - beta u u^T with u = column j of Q (rows j.., ld ldq), beta = sh.beta[j]:
+// p = beta K u, w = p - (beta/2)(u^T p) u, K -= u w^T + w u^T.  Rows and columns
+// below j are left as they are: the trailing blocks of later reflections never
+// read them.
+__device__ void reflect_two_sided(double* __restrict__ K, int n, const double* __restrict__ Q, int ldq, int j,
+                                  Shared& sh) {
+    const int tid = threadIdx.x;
+    const double beta = sh.beta[j];
+    if (beta == 0.0) return;
+    const int L = n - j;
+    for (int i = tid; i < L; i += (int)blockDim.x) sh.v[i] = Q[(size_t)(j + i) * ldq + j];
+    __syncthreads();
+    for (int i = tid; i < L; i += (int)blockDim.x)
+        sh.p[i] = beta * dot8(K + (size_t)j * n + j + i, n, sh.v, 1, L);
+    __syncthreads();
+    double g = 0.0;
+    for (int i = tid; i < L; i += (int)blockDim.x) g = fma(sh.p[i], sh.v[i], g);
+    const double c = 0.5 * beta * block_sum(g, sh.red);
+    for (int i = tid; i < L; i += (int)blockDim.x) sh.p[i] = fma(-c, sh.v[i], sh.p[i]);
+    __syncthreads();
+    const int nw = (int)(blockDim.x >> 5), wp = tid >> 5, ln = tid & 31;
+    for (int i = wp; i < L; i += nw) {
+        const double vi = sh.v[i], wi = sh.p[i];
+        double* row = K + (size_t)(j + i) * n + j;
+        for (int l = ln; l < L; l += 32) row[l] = fma(-vi, sh.p[l], fma(-wi, sh.v[l], row[l]));
     }
     __syncthreads();
 }
@@ -903,16 +1068,41 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             A[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
         }
         __syncthreads();
-        tridiagonalise(A, n, sh);
-        bisect_prepare(n, sh);
-        if (tid < 32) max_eig_warp(n, sh);
-        __syncthreads();
-        if (tid == 0) {
-            const double smax = sh.red[0];
-            sh.misc[7] = smax > 0.0 ? n - sturm_below(sh.d, sh.p, n, fmax(tau * smax, floor_t)) : 0;
+        // 1'. Without hybrid columns, "every direction is kept" needs no eigenvalues:
+        //     g = the largest absolute column sum of K_W bounds smax, and if
+        //     K_W - max(tau g, floor) I is positive definite (one Cholesky attempt on T1)
+        //     every eigenvalue exceeds max(tau smax, floor), so r = n exactly.
+        bool full = false;
+        if (nvh == 0) {
+            double g = 0.0;
+            for (int j = tid; j < n; j += (int)blockDim.x) {
+                double cs = 0.0;
+                for (int i = 0; i < n; ++i) cs += fabs(A[(size_t)i * n + j]);
+                g = fmax(g, cs);
+            }
+            g = block_max(g, sh.red);
+            if (g > 0.0) {
+                const double thr_ub = fmax(tau * g, floor_t);
+                for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                    const int i = e / n, j = e - i * n;
+                    T1[e] = (i == j) ? A[e] - thr_ub : A[e];
+                }
+                __syncthreads();
+                full = cholesky_lower(T1, n, sh);
+            }
         }
-        __syncthreads();
-        const int r_est = sh.misc[7];
+        if (!full) {
+            tridiagonalise(A, n, sh);
+            bisect_prepare(n, sh);
+            if (tid < 32) max_eig_warp(n, sh);
+            __syncthreads();
+            if (tid == 0) {
+                const double smax = sh.red[0];
+                sh.misc[7] = smax > 0.0 ? n - sturm_below(sh.d, sh.p, n, fmax(tau * smax, floor_t)) : 0;
+            }
+            __syncthreads();
+        }
+        const int r_est = full ? n : sh.misc[7];
         double phi = 0.0;
         int r = 0, rs = 0;
         bool ok = true, done = false;
@@ -974,51 +1164,118 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 done = true;
             }
         }
-        bool stale = false;  // the tridiagonal form of K_W was overwritten
+        bool stale = full;  // A does not hold the tridiagonal form of K_W
         if (!done && r_est > 0 && r_est < n && nvh == 0) {
-            // 2''. Some directions are truncated (the subspace route).  Alg. 4's B is the
-            //     pencil (U~^T K_Z U~, U~^T K_W U~ = S~) on the kept invariant subspace of
-            //     K_W, and its eigenvalues are the same in any basis of that subspace:
-            //     with Y = H Z, Z the twisted-factorization eigenvectors of the kept
-            //     eigenvalues of the tridiagonal T = H^T K_W H, they are those of
-            //     L^-1 (Y^T K_Z Y) L^-T, L L^T = Z^T T Z.  No QL sweeps, no full eigenvector
-            //     matrix; the kept count comes from the same Sturm counts.
-            const int rk = r_est, j0 = n - r_est;
-            for (int q = tid; q < rk; q += (int)blockDim.x) sh.v[q] = bisect_one(j0 + q, n, sh);
-            __syncthreads();
-            twisted_vectors(n, rk, Zt, Y, T1, n, sh);
-            if (sh.misc[6]) {
-                // W = T Z (n x rk, ld rk) into T1, then M_W = Z^T W (rk x rk, ld rk) into Y
-                for (int e = tid; e < n * rk; e += (int)blockDim.x) {
-                    const int i = e / rk, q = e - i * rk;
-                    double tz = sh.d[i] * Zt[(size_t)i * n + q];
-                    if (i > 0) tz = fma(sh.off[i - 1], Zt[(size_t)(i - 1) * n + q], tz);
-                    if (i + 1 < n) tz = fma(sh.off[i], Zt[(size_t)(i + 1) * n + q], tz);
-                    T1[(size_t)i * rk + q] = tz;
-                }
+            // 2''. Some directions are truncated.  Alg. 4's B is the pencil
+            //     (U~^T K_Z U~, U~^T K_W U~ = S~) on the kept invariant subspace of K_W,
+            //     and its eigenvalues are the same in any basis Y of that subspace: those
+            //     of L^-1 (Y^T K_Z Y) L^-T, L L^T = Y^T K_W Y.  No QL sweeps and no full
+            //     eigenvector matrix; the kept count comes from the same Sturm counts.
+            const int rk = r_est, dn = n - r_est;
+            double* Lw = nullptr;  // Y^T K_W Y (rk x rk, ld rk), factored in place below
+            double* Mz = nullptr;  // Y^T K_Z Y
+            double* S1 = nullptr;  // free rk x rk buffers for the inertia test
+            double* S2 = nullptr;
+            if (3 * dn < rk) {
+                // Few dropped directions: Y spans the complement of the dn dropped
+                //     eigenvectors (twisted factorization of the smallest eigenvalues of the
+                //     tridiagonal, back-transformed), as the trailing columns of the
+                //     Householder reflectors of their QR; K_W and K_Z are reflected
+                //     two-sided by those dn reflectors and their trailing rk x rk blocks
+                //     are Y^T K_W Y and Y^T K_Z Y (O(dn n^2) instead of O(rk n^2)).
+                for (int q = tid; q < dn; q += (int)blockDim.x) sh.v[q] = bisect_one(q, n, sh);
                 __syncthreads();
-                gemm_tn(Zt, n, T1, rk, n, rk, rk, Y, rk, true, sh);
-                back_transform(A, n, Zt, n, rk, sh);  // columns of Zt: kept eigenvectors of K_W
-                // T1 = K_Z Yc (n x rk, ld rk; K_Z is symmetric), M_Z = Yc^T T1 into A
-                gemm_tn(Zk, n, Zt, n, n, n, rk, T1, rk, false, sh);
-                gemm_tn(Zt, n, T1, rk, n, rk, rk, A, rk, true, sh);
-                stale = true;
-                if (cholesky_lower(Y, rk, sh)) {
-                    trsm_lower(Y, A, rk, sh);          // A = L^-1 M_Z
-                    trsm_lower_t(Y, A, T1, rk, sh);    // T1 = L^-1 M_Z L^-T
-                    for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
-                        const int i = e / rk, j = e - i * rk;
-                        if (i < j) {
-                            const double v = 0.5 * (T1[e] + T1[(size_t)j * rk + i]);
-                            T1[e] = v;
-                            T1[(size_t)j * rk + i] = v;
-                        }
+                twisted_vectors(n, dn, Zt, Y, T1, n, sh);
+                if (sh.misc[6]) {
+                    back_transform(A, n, Zt, n, dn, sh);  // columns 0..dn-1: dropped eigenvectors of K_W
+                    householder_qr_cols(Zt, n, n, dn, sh);
+                    for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                        const int i = e / n, j = e - i * n;
+                        Y[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
+                        T1[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
                     }
                     __syncthreads();
-                    phi = range_sum(T1, rk, xl, xh, sh, &rs);
-                    r = rk;
-                    done = true;
+                    for (int j = 0; j < dn; ++j) {
+                        reflect_two_sided(Y, n, Zt, n, j, sh);
+                        reflect_two_sided(T1, n, Zt, n, j, sh);
+                    }
+                    for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                        const int i = e / rk, j = e - i * rk;
+                        A[e] = Y[(size_t)(dn + i) * n + dn + j];
+                        Zt[e] = T1[(size_t)(dn + i) * n + dn + j];
+                    }
+                    __syncthreads();
+                    Lw = A;
+                    Mz = Zt;
+                    S1 = Zt;
+                    S2 = Y;
+                    stale = true;
                 }
+            } else {
+                // Y = H Z, Z the twisted-factorization eigenvectors of the kept eigenvalues
+                //     of the tridiagonal T = H^T K_W H; Y^T K_W Y = Z^T T Z.
+                const int j0 = n - r_est;
+                for (int q = tid; q < rk; q += (int)blockDim.x) sh.v[q] = bisect_one(j0 + q, n, sh);
+                __syncthreads();
+                twisted_vectors(n, rk, Zt, Y, T1, n, sh);
+                if (sh.misc[6]) {
+                    // W = T Z (n x rk, ld rk) into T1, then M_W = Z^T W (rk x rk, ld rk) into Y
+                    for (int e = tid; e < n * rk; e += (int)blockDim.x) {
+                        const int i = e / rk, q = e - i * rk;
+                        double tz = sh.d[i] * Zt[(size_t)i * n + q];
+                        if (i > 0) tz = fma(sh.off[i - 1], Zt[(size_t)(i - 1) * n + q], tz);
+                        if (i + 1 < n) tz = fma(sh.off[i], Zt[(size_t)(i + 1) * n + q], tz);
+                        T1[(size_t)i * rk + q] = tz;
+                    }
+                    __syncthreads();
+                    gemm_tn(Zt, n, T1, rk, n, rk, rk, Y, rk, true, sh);
+                    back_transform(A, n, Zt, n, rk, sh);  // columns of Zt: kept eigenvectors of K_W
+                    // T1 = K_Z Yc (n x rk, ld rk; K_Z is symmetric), M_Z = Yc^T T1 into A
+                    gemm_tn(Zk, n, Zt, n, n, n, rk, T1, rk, false, sh);
+                    gemm_tn(Zt, n, T1, rk, n, rk, rk, A, rk, true, sh);
+                    Lw = Y;
+                    Mz = A;
+                    S1 = A;
+                    S2 = Zt;
+                    stale = true;
+                }
+            }
+            if (Lw && cholesky_lower(Lw, rk, sh)) {
+                trsm_lower(Lw, Mz, rk, sh);         // Mz = L^-1 M_Z
+                trsm_lower_t(Lw, Mz, T1, rk, sh);   // T1 = L^-1 M_Z L^-T
+                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                    const int i = e / rk, j = e - i * rk;
+                    if (i < j) {
+                        const double v = 0.5 * (T1[e] + T1[(size_t)j * rk + i]);
+                        T1[e] = v;
+                        T1[(size_t)j * rk + i] = v;
+                    }
+                }
+                __syncthreads();
+                // inertia first, as on the route above: every eigenvalue in (xl, xh)
+                // makes the sum the trace
+                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                    const int i = e / rk, j = e - i * rk;
+                    const double v = T1[e];
+                    S1[e] = (i == j) ? v - xl : v;
+                    S2[e] = (i == j) ? xh - v : -v;
+                }
+                __syncthreads();
+                if (cholesky_lower(S1, rk, sh) && cholesky_lower(S2, rk, sh)) {
+                    if (tid == 0) {
+                        double tr = 0.0;
+                        for (int i = 0; i < rk; ++i) tr += T1[(size_t)i * rk + i];
+                        sh.p[0] = tr;
+                    }
+                    __syncthreads();
+                    phi = sh.p[0];
+                    rs = rk;
+                    __syncthreads();
+                } else {
+                    phi = range_sum(T1, rk, xl, xh, sh, &rs);
+                }
+                r = rk;
+                done = true;
             }
         }
         if (!done) {
@@ -1173,7 +1430,7 @@ int workspace_ctas(int n_v) {
 }
 
 size_t solve_smem(int n) {
-    return (size_t)(7 * n + NT / 32 + (2 * n + 16 + 1) / 2 + 2 * 32 * 33) * sizeof(double);
+    return (size_t)(7 * n + NT / 32 + (2 * n + 16 + 1) / 2 + 3 * 32 * 33) * sizeof(double);
 }
 
 }  // namespace

@@ -118,6 +118,27 @@ def test_ress_dos_fp64(cfg1):
     assert np.array_equal(g["rank"][ok, 1], r["rank_xi"][ok])
 
 
+def test_duplicated_probe_columns_few_dropped_directions(S):
+    # Two pairs of equal probe columns: K_W(t) has two exactly null directions at every
+    # sweep point, so inside the spectrum all but two directions are kept and the solver
+    # works in the complement of the two dropped eigenvectors (Householder reflections of
+    # K_W and K_Z) instead of a basis of the 38 kept ones.
+    st = wl.make_operator("lap2d_dirichlet_32")
+    c = wl.CONFIGS["lap2d_dirichlet_32"]
+    W = wl.random_block(st.n, c["n_v"], c["probe_seed"], c["probe"])
+    W[:, 1] = W[:, 0]
+    W[:, 3] = W[:, 2]
+    sigma = 0.3  # ~200 eigenvalues under the Gaussian: K_W(t) has full rank but for the pairs
+    g = _run(S, st, W, c["n_v"], 0, c["M"], sigma, n_t=61)
+    r = _oracle(st, W, c["n_v"], g["t"], c["M"], sigma, g["info"])
+    ok = ~r["flagged"]
+    assert np.sum(ok & (r["rank_s"] == c["n_v"] - 2)) >= 0.9 * ok.size  # the route is exercised
+    tol, ok = _ss_tolerance(st, W, c["n_v"], g["t"], c["M"], sigma, g["info"], r, ok)
+    assert O.relative_l1_error(g["ss"][ok], r["dos_ss"][ok]) <= tol
+    assert np.array_equal(g["rank"][ok, 0], r["rank_s"][ok])
+    assert np.array_equal(g["rank"][ok, 1], r["rank_xi"][ok])
+
+
 def test_hybrid_fp64_ragged_columns(S):
     # 20 + 17 columns: n_tot not a multiple of the vector width; Alg. 6 correction on.
     st = wl.make_operator("lap2d_dirichlet_32", nx=23)
