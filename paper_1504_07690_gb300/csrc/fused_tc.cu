@@ -42,7 +42,9 @@
 //
 // Warps: 0 = loader (lane 0 sets the byte count, lanes issue the copies),
 // 1 = MMA issuer (lane 0; the warp allocates TMEM), 2..17 = producers
-// (stencil, splits, then the accumulator read-back).  Every wait is bounded
+// (stencil, splits, then the accumulator read-back).  Waiting threads are
+// suspended on the mbarrier (try_wait with a time hint) rather than polling,
+// so they leave the issue slots to the working warps.  Every wait is bounded
 // and also ends when another thread has recorded a failure; on failure the
 // CTA sets bit 2 of the status word, waits (bounded) for its MMAs, frees
 // TMEM and returns.
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_step_tc_kernel(FArgs P) {
         const char* ysrc = reinterpret_cast<const char*>(t1 ? P.Yb : P.Vp);
         for (int c = 0; c < nch; ++c) {
             const int sx = c % NX;
-            bool okw = c < NX || mbar_wait_or_fail(smem_u32(&xempty[sx]), ((c / NX) - 1) & 1, vfail);
+            bool okw = c < NX || mbar_wait_sleep(smem_u32(&xempty[sx]), ((c / NX) - 1) & 1, vfail);
             okw = __all_sync(0xffffffffu, okw);  // one decision for the whole warp
             if (!okw) {
                 if (lane == 0) atomicOr(&fail, 1);
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_step_tc_kernel(FArgs P) {
             int issued = 0;
             for (int c = 0; c < nch; ++c) {
                 const int ps = c % NS;
-                if (!mbar_wait_or_fail(smem_u32(&full[ps]), (c / NS) & 1, vfail)) {
+                if (!mbar_wait_sleep(smem_u32(&full[ps]), (c / NS) & 1, vfail)) {
                     ok = false;
                     break;
                 }
@@ -368,8 +370,8 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_step_tc_kernel(FArgs P) {
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int c = 0; c < nch; ++c) {
             const int sx = c % NX, ps = c % NS;
-            bool ok = mbar_wait_or_fail(smem_u32(&xfull[sx]), (c / NX) & 1, vfail);
-            if (ok && c >= NS) ok = mbar_wait_or_fail(smem_u32(&empty[ps]), ((c / NS) - 1) & 1, vfail);
+            bool ok = mbar_wait_sleep(smem_u32(&xfull[sx]), (c / NX) & 1, vfail);
+            if (ok && c >= NS) ok = mbar_wait_sleep(smem_u32(&empty[ps]), ((c / NS) - 1) & 1, vfail);
             ok = __all_sync(0xffffffffu, ok);  // one decision for the whole warp
             if (!ok) {
                 if (lane == 0) atomicOr(&fail, 1);
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(FTHREADS, 1) fused_step_tc_kernel(FArgs P) {
     }
 
     // ---------------------------------------------------------------- read-back
-    const bool dn = mbar_wait(smem_u32(&done), 0);
+    const bool dn = mbar_wait_sleep(smem_u32(&done), 0, nullptr);
     __syncthreads();
     const bool ok = dn && fail == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

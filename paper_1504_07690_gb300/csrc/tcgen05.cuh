@@ -64,6 +64,32 @@ __device__ __forceinline__ bool mbar_wait_or_fail(uint32_t addr, uint32_t parity
     return false;
 }
 
+// As mbar_try, but the thread is suspended until the phase completes or about
+// hint_ns nanoseconds pass, instead of returning at once: waiting warps do not
+// take issue slots from the warps that work.
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t addr, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr long SLEEP_WAIT_LIMIT = 1L << 22;  // bounded suspended polls (~4 s at 1 us each)
+
+// Bounded, suspending wait that gives up as soon as another thread of the CTA
+// has recorded a failure in *fail.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t addr, uint32_t parity, const volatile int* fail) {
+    for (long i = 0; i < SLEEP_WAIT_LIMIT; ++i) {
+        if (mbar_try_sleep(addr, parity, 1000u)) return true;
+        if (fail && *fail) return false;
+    }
+    return false;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
 }
