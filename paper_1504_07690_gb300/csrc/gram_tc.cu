@@ -18,7 +18,8 @@
 // memory ring (4 stages of 33 KB for Ge, 2 of 66 KB for Go) with 1-D bulk TMA copies (cp.async.bulk, completion
 // counted in bytes on an mbarrier), one thread issues M=128
 // tcgen05.mma.kind::f16 into TMEM and releases each stage through
-// tcgen05.commit, and at the end all four warps read the accumulators back
+// tcgen05.commit (waiting threads are suspended on the mbarriers, not polling),
+// and at the end all four warps read the accumulators back
 // with tcgen05.ld and write one float32 partial per slab; partials are
 // reduced in slab order in float64.
 //
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
             const uint32_t copy = (uint32_t)G * GROUP_BYTES;
             for (int c = 0; c < nch; ++c) {
                 const int s = c % nstage;
-                if (c >= nstage && !mbar_wait(smem_u32(&empty[s]), ((c / nstage) - 1) & 1)) {
+                if (c >= nstage && !mbar_wait_sleep(smem_u32(&empty[s]), ((c / nstage) - 1) & 1, nullptr)) {
                     atomicOr(&fail, 1);
                     break;
                 }
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
             bool ok = true;
             for (int c = 0; c < nch; ++c) {
                 const int s = c % nstage;
-                if (!mbar_wait(smem_u32(&full[s]), (c / nstage) & 1)) {
+                if (!mbar_wait_sleep(smem_u32(&full[s]), (c / nstage) & 1, nullptr)) {
                     ok = false;
                     break;
                 }
@@ -189,17 +190,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
         }
         __syncwarp();
     }
-    const bool dn = mbar_wait(smem_u32(&done), 0);
+    const bool dn = mbar_wait_sleep(smem_u32(&done), 0, nullptr);
     __syncthreads();
     const bool ok = dn && fail == 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        // each lane owns one row m of a tile: 32 columns per TMEM round trip, written
-        // as whole 128-byte runs (float4) when the row is 16-byte aligned
-        const bool vec = (n_tot & 3) == 0;
+        // each lane holds one accumulator row; 32 columns per TMEM round trip go out
+        // through a per-warp 32 x 33 shared-memory tile (the stage ring is free now) as
+        // coalesced 128-byte row stores
+        float* tbuf = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * 33;
         for (int t = 0; t < nt; ++t) {
-            const int m = t_m0[t] + 32 * warp + lane;
-            float* orow = out + (size_t)m * n_tot + t_n0[t];
+            const int mrow0 = t_m0[t] + 32 * warp;
             for (int cc = 0; cc < t_n[t]; cc += 32) {
                 float v[32];
                 const int w = t_n[t] - cc >= 32 ? 32 : 16;
@@ -213,18 +214,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = 0.f;
                 }
-                if (m < n_tot) {
-                    if (vec && t_n0[t] + cc + w <= n_tot) {
-                        float4* o4 = reinterpret_cast<float4*>(orow + cc);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            if (4 * q < w) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < w && t_n0[t] + cc + j < n_tot) orow[cc + j] = v[j];
-                    }
+                for (int j = 0; j < 32; ++j) tbuf[lane * 33 + j] = v[j];
+                __syncwarp();
+                const int col = t_n0[t] + cc + lane;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int m = mrow0 + rr;
+                    if (m < n_tot && lane < w && col < n_tot) out[(size_t)m * n_tot + col] = tbuf[rr * 33 + lane];
                 }
+                __syncwarp();
             }
         }
     } else if (tid == 0) {
