@@ -135,18 +135,30 @@ FP64_FMA_PER_SM_CLK = 2   # measured: FMA chains reach 1.20 TFLOP/s on 152 SMs a
 
 
 def solve_flops(ranks, n: int) -> float:
-    """Float64 flops of the per-point solver, by the route each point takes (kept rank r):
-    r = 0: Householder reduction of K_W (4/3 n^3); r = n: reduction, Cholesky (n^3/3), two
-    triangular solves (2 n^3), reduction of C (4/3 n^3); 0 < r < n: reduction, back-transform
-    (2 n^2 r), K_Z Y (2 n^2 r), Y^T K_Z Y and Z^T T Z (2 n r^2), Cholesky, solves and
-    reduction of the r x r pencil (r^3/3 + 2 r^3 + 4/3 r^3)."""
+    """Float64 flops of the per-point solver, by the route each point takes (kept rank r;
+    the paths that run when every test passes):
+    r = n: the full-rank test (Cholesky of K_W less the threshold, n^3/3), Cholesky of K_W
+    (n^3/3), two triangular solves (2 n^3) and the inertia test (two Choleskys, 2/3 n^3);
+    r = 0: the Householder reduction of K_W (4/3 n^3), an upper bound (the Gershgorin test
+    can skip it);
+    0 < r < n: reduction (4/3 n^3), then with d = n - r dropped directions and 3 d < r the
+    dropped eigenvectors' back-transform (2 n^2 d) and two-sided reflections of K_W and K_Z
+    (8 n^2 d), else the kept basis: back-transform (2 n^2 r), K_Z Y (2 n^2 r), Y^T K_Z Y and
+    Z^T T Z (2 n r^2); then Cholesky, solves and inertia test of the r x r pencil
+    (r^3/3 + 2 r^3 + 2/3 r^3)."""
     tot = 0.0
     for r in ranks:
-        f = 4.0 / 3.0 * n ** 3
         if r == n:
-            f += n ** 3 / 3.0 + 2.0 * n ** 3 + 4.0 / 3.0 * n ** 3
-        elif r > 0:
-            f += 4.0 * n * n * r + 2.0 * n * r * r + (1.0 / 3.0 + 2.0 + 4.0 / 3.0) * r ** 3
+            f = (1.0 / 3.0 + 1.0 / 3.0 + 2.0 + 2.0 / 3.0) * n ** 3
+        elif r == 0:
+            f = 4.0 / 3.0 * n ** 3
+        else:
+            d = n - r
+            f = 4.0 / 3.0 * n ** 3 + (1.0 / 3.0 + 2.0 + 2.0 / 3.0) * r ** 3
+            if 3 * d < r:
+                f += 10.0 * n * n * d
+            else:
+                f += 4.0 * n * n * r + 2.0 * n * r * r
         tot += f
     return tot
 

@@ -1072,7 +1072,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
         //     g = the largest absolute column sum of K_W bounds smax, and if
         //     K_W - max(tau g, floor) I is positive definite (one Cholesky attempt on T1)
         //     every eigenvalue exceeds max(tau smax, floor), so r = n exactly.
-        bool full = false;
+        bool full = false, empty = false;
         if (nvh == 0) {
             double g = 0.0;
             for (int j = tid; j < n; j += (int)blockDim.x) {
@@ -1081,7 +1081,10 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 g = fmax(g, cs);
             }
             g = block_max(g, sh.red);
-            if (g > 0.0) {
+            // and "nothing is kept" neither: every eigenvalue is at most g, so g below the
+            // rounding floor (and hence below max(tau smax, floor)) gives r = 0 exactly
+            empty = g < floor_t || g <= 0.0;
+            if (!empty) {
                 const double thr_ub = fmax(tau * g, floor_t);
                 for (int e = tid; e < n * n; e += (int)blockDim.x) {
                     const int i = e / n, j = e - i * n;
@@ -1091,7 +1094,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 full = cholesky_lower(T1, n, sh);
             }
         }
-        if (!full) {
+        if (!full && !empty) {
             tridiagonalise(A, n, sh);
             bisect_prepare(n, sh);
             if (tid < 32) max_eig_warp(n, sh);
@@ -1102,7 +1105,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             }
             __syncthreads();
         }
-        const int r_est = full ? n : sh.misc[7];
+        const int r_est = full ? n : (empty ? 0 : sh.misc[7]);
         double phi = 0.0;
         int r = 0, rs = 0;
         bool ok = true, done = false;
