@@ -248,6 +248,22 @@ struct Sum32 {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// s.add(p[k nn + e]) for k = k0, k0 + 8, k0 + 16, ... < n, in that order; the loads of
+// four slabs are issued before their adds (a zero added to a compensated sum leaves it
+// unchanged, so the tail needs no separate loop).
+__device__ __forceinline__ void sum_slabs(Sum32& s, const float* __restrict__ p, size_t nn, size_t e, int k0, int n) {
+    for (int k = k0; k < n; k += 32) {
+        const float v0 = p[(size_t)k * nn + e];
+        const float v1 = k + 8 < n ? p[(size_t)(k + 8) * nn + e] : 0.f;
+        const float v2 = k + 16 < n ? p[(size_t)(k + 16) * nn + e] : 0.f;
+        const float v3 = k + 24 < n ? p[(size_t)(k + 24) * nn + e] : 0.f;
+        s.add(v0);
+        s.add(v1);
+        s.add(v2);
+        s.add(v3);
+    }
+}
+
 // Slab sums (compensated float32 per warp, float64 across warps), coalesced: ge[e] = sum_s pe[s][lo][hi] (upper element of
 // the pair), go[e] = sum_s po[s][e]; the symmetrisation of go reads it transposed
 // from this small float64 buffer in a second pass.  A block covers 32
@@ -264,9 +280,8 @@ sum_tc_kernel(const float* __restrict__ pe, int n_e, const float* __restrict__ p
         Sum32 a, b;
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
-            if (i <= j)
-                for (int s = w; s < n_e; s += 8) a.add(pe[(size_t)s * nn + e]);
-            for (int s = w; s < n_o; s += 8) b.add(po[(size_t)s * nn + e]);
+            if (i <= j) sum_slabs(a, pe, nn, e, w, n_e);
+            sum_slabs(b, po, nn, e, w, n_o);
         }
         se[w][lane] = a.value();
         so[w][lane] = b.value();
@@ -300,9 +315,8 @@ sum_tc_batch_kernel(const float* __restrict__ ring, size_t slot, int n_e, int n_
         Sum32 a, b;
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
-            if (i <= j)
-                for (int s = w; s < n_e; s += 8) a.add(pe[(size_t)s * nn + e]);
-            for (int s = w; s < n_o; s += 8) b.add(po[(size_t)s * nn + e]);
+            if (i <= j) sum_slabs(a, pe, nn, e, w, n_e);
+            sum_slabs(b, po, nn, e, w, n_o);
         }
         se[w][lane] = a.value();
         so[w][lane] = b.value();
@@ -371,10 +385,8 @@ sum_tc_seg_kernel(const float* __restrict__ pe, const float* __restrict__ po, co
         Sum32 a, b;
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
-            if (i <= j)
-                for (int sl = e0s + w; sl < e1s; sl += 8) a.add(pe[(size_t)sl * nn + e]);
-            if (odd)
-                for (int sl = o0s + w; sl < o1s; sl += 8) b.add(po[(size_t)sl * nn + e]);
+            if (i <= j) sum_slabs(a, pe, nn, e, e0s + w, e1s);
+            if (odd) sum_slabs(b, po, nn, e, o0s + w, o1s);
         }
         se_[w][lane] = a.value();
         so_[w][lane] = b.value();
@@ -434,9 +446,8 @@ sum_fused_kernel(const float* __restrict__ ring, size_t slot, int nA, int nF, in
         if (e < nn) {
             const int i = (int)(e / n_tot), j = (int)(e - (size_t)i * n_tot);
             const int s0 = i < 128 ? 0 : nA, s1 = i < 128 ? nA : nF;
-            if (i <= j)
-                for (int s = s0 + w; s < s1; s += 8) a.add(pe[(size_t)s * nn + e]);
-            for (int s = s0 + w; s < s1; s += 8) b.add(po[(size_t)s * nn + e]);
+            if (i <= j) sum_slabs(a, pe, nn, e, s0 + w, s1);
+            sum_slabs(b, po, nn, e, s0 + w, s1);
         }
         se[w][lane] = a.value();
         so[w][lane] = b.value();
