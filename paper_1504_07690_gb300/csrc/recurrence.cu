@@ -89,7 +89,26 @@ __device__ __forceinline__ void stage_split4p(uint8_t* stage, int G, int row, in
     *reinterpret_cast<uint2*>(stage + stage_off(G, 0, row, g) + half * 8) = *reinterpret_cast<const uint2*>(h);
     *reinterpret_cast<uint2*>(stage + stage_off(G, 1, row, g) + half * 8) = *reinterpret_cast<const uint2*>(l);
 }
-__device__ __forceinline__ void stage_split4p(uint8_t*, int, int, int, double2) {}
+
+// Split 4 consecutive columns (col0 = 4 q) of row `row` (0..31) of panel `panel` and
+// store the bf16 hi and lo parts straight into the panel layout (8 bytes each).
+__device__ __forceinline__ void panel_store4(PanelOut po, uint32_t panel, uint32_t row, uint32_t col0, float4 v) {
+    __align__(8) __nv_bfloat16 h[4];
+    __align__(8) __nv_bfloat16 l[4];
+    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        h[q] = __float2bfloat16_rn(x[q]);
+        l[q] = __float2bfloat16_rn(x[q] - __bfloat162float(h[q]));
+    }
+    const uint32_t g = col0 >> 3, half = (col0 >> 2) & 1;
+    const size_t inner = (size_t)row * 16 + half * 8;
+    uint8_t* hi = po.base + (((size_t)panel * 2) * po.G + g) * 528 + inner;
+    uint8_t* lo = po.base + (((size_t)panel * 2 + 1) * po.G + g) * 528 + inner;
+    *reinterpret_cast<uint2*>(hi) = *reinterpret_cast<const uint2*>(h);
+    *reinterpret_cast<uint2*>(lo) = *reinterpret_cast<const uint2*>(l);
+}
+__device__ __forceinline__ void panel_store4(PanelOut, uint32_t, uint32_t, uint32_t, double2) {}
 
 // Per-row neighbour table of a 32-row panel.
 struct RowInfo {
@@ -128,15 +147,15 @@ __device__ __forceinline__ void load_item(ItemLoads<T>& L, const RowInfo& ri, ui
 // A CTA owns one 32-row panel at a time (grid-stride over panels): the first
 // 32 threads tabulate the rows' neighbour rows, then all 256 threads walk the
 // panel's (row, 16-byte chunk) items, so loads and stores are coalesced and
-// every lane is busy; with PANEL the split-bf16 copy of the panel is staged
-// in shared memory and written as whole 512-byte runs.
+// every lane is busy; with PANEL each item's split-bf16 hi and lo parts go
+// straight to their place in the panel (8-byte stores: no shared-memory stage
+// and no barrier per panel, so more of these CTAs fit next to a Gram CTA).
 template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256, 4)
 stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                     const T* __restrict__ diag2, StencilGeom g, T o0, T o1, T o2, T c, T d,
                     uint32_t nchunk, uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
-    __shared__ __align__(16) uint8_t stage[PANEL ? 2 * 32 * 33 * 16 : 16];
     __shared__ RowInfo info[32];
     const uint32_t mdiv = ((1u << 20) + nchunk - 1) / nchunk;  // it / nchunk for it < 32 nchunk
     const VT* vc = reinterpret_cast<const VT*>(Vc);
@@ -144,13 +163,10 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
     VT* vn = reinterpret_cast<VT*>(Vn);
     const uint32_t s1 = g.d2, s0 = g.d1 * g.d2;
     const T w[3] = {g.active[0] ? o0 : T(0), g.active[1] ? o1 : T(0), g.active[2] ? o2 : T(0)};
-    if (PANEL)
-        for (uint32_t t = threadIdx.x; t < 2 * 32 * 33; t += blockDim.x)
-            reinterpret_cast<uint4*>(stage)[t] = make_uint4(0, 0, 0, 0);
     const uint32_t n_pan = (n_rows + 31) / 32;
     const uint32_t items = 32 * nchunk;
     for (uint32_t pnl = blockIdx.x; pnl < n_pan; pnl += gridDim.x) {
-        __syncthreads();  // info / stage free
+        __syncthreads();  // info free
         if (threadIdx.x < 32) {
             const uint32_t i = pnl * 32 + threadIdx.x;
             RowInfo ri;
@@ -201,12 +217,8 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
                     if (d != T(0)) out = vfma(-d, L[u].vp, out);
                     vn[(size_t)(pnl * 32 + rr[u]) * nchunk + cq[u]] = out;
                 }
-                if constexpr (PANEL) stage_split4p(stage, po.G, rr[u], 4 * cq[u], out);
+                if constexpr (PANEL) panel_store4(po, pnl, rr[u], 4 * cq[u], out);
             }
-        }
-        if constexpr (PANEL) {
-            __syncthreads();
-            flush_panel(stage, po, pnl);
         }
     }
 }
@@ -218,17 +230,12 @@ csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restric
                 const T* __restrict__ val2, T beta, const T* __restrict__ beta_row, T c, T d, uint32_t nchunk,
                 uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
-    __shared__ __align__(16) uint8_t stage[PANEL ? 2 * 32 * 33 * 16 : 16];
     const VT* vc = reinterpret_cast<const VT*>(Vc);
     const VT* vp = reinterpret_cast<const VT*>(Vp);
     VT* vn = reinterpret_cast<VT*>(Vn);
-    if (PANEL)
-        for (uint32_t t = threadIdx.x; t < 2 * 32 * 33; t += blockDim.x)
-            reinterpret_cast<uint4*>(stage)[t] = make_uint4(0, 0, 0, 0);
     const uint32_t n_pan = (n_rows + 31) / 32;
     const uint32_t items = 32 * nchunk;
     for (uint32_t pnl = blockIdx.x; pnl < n_pan; pnl += gridDim.x) {
-        if (PANEL) __syncthreads();
         for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
             const uint32_t r = it / nchunk, cc = it - r * nchunk;
             const uint32_t i = pnl * 32 + r;
@@ -245,11 +252,7 @@ csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restric
                 if (d != T(0)) out = vfma(-d, ldg_stream(vp + base + cc), out);
                 vn[base + cc] = out;
             }
-            if constexpr (PANEL) stage_split4p(stage, po.G, r, 4 * cc, out);
-        }
-        if constexpr (PANEL) {
-            __syncthreads();
-            flush_panel(stage, po, pnl);
+            if constexpr (PANEL) panel_store4(po, pnl, r, 4 * cc, out);
         }
     }
 }
