@@ -829,7 +829,14 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
             CREATE_CUDA(cudaMemsetAsync(P.d_panel[j], 0, pbytes, P.stream));  // rows past N stay zero
         }
         // the Gram products of step k run on a second stream, next to step k+1 of the recurrence
-        CREATE_CUDA(cudaStreamCreateWithFlags(&P.gstream, cudaStreamNonBlocking));
+        // highest priority: when the Gram of step k and the recurrence of step k+1 become
+        // ready together, the Gram's CTAs are placed first and the recurrence CTAs fill
+        // the room left on each SM
+        {
+            int prio_lo = 0, prio_hi = 0;
+            CREATE_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+            CREATE_CUDA(cudaStreamCreateWithPriority(&P.gstream, cudaStreamNonBlocking, prio_hi));
+        }
         for (auto& e : P.ev_st) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         for (auto& e : P.ev_gr) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     } else {
