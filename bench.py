@@ -137,8 +137,9 @@ FP64_FMA_PER_SM_CLK = 2   # measured: FMA chains reach 1.20 TFLOP/s on 152 SMs a
 def solve_flops(ranks, n: int) -> float:
     """Float64 flops of the per-point solver, by the route each point takes (kept rank r;
     the paths that run when every test passes):
-    r = n: the full-rank test (Cholesky of K_W less the threshold, n^3/3), Cholesky of K_W
-    (n^3/3), two triangular solves (2 n^3) and the inertia test (two Choleskys, 2/3 n^3);
+    r = n: the full-rank test (Cholesky of K_W less the threshold, n^3/3), the inertia test
+    by congruence (two Choleskys, 2/3 n^3), Cholesky of K_W (n^3/3), one triangular solve
+    (n^3) and a triangular inverse (n^3/3) for the trace;
     r = 0: the Householder reduction of K_W (4/3 n^3), an upper bound (the Gershgorin test
     can skip it);
     0 < r < n: reduction (4/3 n^3), then with d = n - r dropped directions and 3 d < r the
@@ -149,7 +150,7 @@ def solve_flops(ranks, n: int) -> float:
     tot = 0.0
     for r in ranks:
         if r == n:
-            f = (1.0 / 3.0 + 1.0 / 3.0 + 2.0 + 2.0 / 3.0) * n ** 3
+            f = (1.0 / 3.0 + 2.0 / 3.0 + 1.0 / 3.0 + 1.0 + 1.0 / 3.0) * n ** 3
         elif r == 0:
             f = 4.0 / 3.0 * n ** 3
         else:

@@ -629,6 +629,19 @@ __device__ void trsm_lower_t(const double* __restrict__ L, const double* __restr
     __syncthreads();
 }
 
+// X <- L^{-1} (n x n row-major, lower triangular; zero above the diagonal), L from
+// cholesky_lower (rdiag = sh.v): one column per thread, forward substitution on the
+// unit vector e_c from row c down (n^3 / 3 flops).
+__device__ void trinv_lower(const double* __restrict__ L, double* __restrict__ X, int n, const Shared& sh) {
+    for (int c = threadIdx.x; c < n; c += (int)blockDim.x) {
+        for (int i = 0; i < c; ++i) X[(size_t)i * n + c] = 0.0;
+        for (int i = c; i < n; ++i)
+            X[(size_t)i * n + c] =
+                ((i == c ? 1.0 : 0.0) - dot8(L + (size_t)i * n + c, 1, X + (size_t)c * n + c, n, i - c)) * sh.v[i];
+    }
+    __syncthreads();
+}
+
 // Sum (and count) of the eigenvalues of the symmetric m x m matrix C (ld m,
 // destroyed) that lie in [xl, xh].  Tridiagonal form; the Sturm counts at xl
 // and xh give how many eigenvalues lie below and above the interval, and only
@@ -1117,6 +1130,21 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             //     orthogonal) of K_W, G^-1 K_Z G^-T = Q^T B Q has the same eigenvalues,
             //     so B's eigenvalues come from the Cholesky factor L instead:
             //     C = L^-1 K_Z L^-T, without the eigenvectors of K_W.
+            // Inertia first, by congruence (C = L^-1 K_Z L^-T): C - xl I and xh I - C are
+            // positive definite exactly when K_Z - xl K_W and xh K_W - K_Z are (two Cholesky
+            // attempts, n^3/3 flops together, no C).  Then every eigenvalue lies in
+            // (xl, xh) and their sum is tr C = sum_ik (L^-1 K_Z)_ik (L^-1)_ik: one triangular
+            // solve and a triangular inverse.  Only otherwise is C formed, reduced to
+            // tridiagonal form and its eigenvalues bracketed.
+            for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                const int i = e / n, j = e - i * n;
+                const double kw = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
+                const double kz = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
+                T1[e] = kz - xl * kw;
+                Y[e] = xh * kw - kz;
+            }
+            __syncthreads();
+            const bool inside = cholesky_lower(T1, n, sh) && cholesky_lower(Y, n, sh);
             for (int e = tid; e < n * n; e += (int)blockDim.x) {
                 const int i = e / n, j = e - i * n;
                 Zt[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
@@ -1128,39 +1156,27 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     Y[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
                 }
                 __syncthreads();
-                trsm_lower(Zt, Y, n, sh);         // Y = L^-1 K_Z
-                trsm_lower_t(Zt, Y, A, n, sh);    // A = L^-1 Y^T = L^-1 K_Z L^-T
-                for (int e = tid; e < n * n; e += (int)blockDim.x) {  // symmetrise (upper from lower)
-                    const int i = e / n, j = e - i * n;
-                    if (i < j) {
-                        const double v = 0.5 * (A[e] + A[(size_t)j * n + i]);
-                        A[e] = v;
-                        A[(size_t)j * n + i] = v;
+                trsm_lower(Zt, Y, n, sh);  // Y = L^-1 K_Z
+                if (inside) {
+                    trinv_lower(Zt, T1, n, sh);  // T1 = L^-1
+                    double f = 0.0;
+                    for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                        const int i = e / n, k = e - i * n;
+                        if (k <= i) f = fma(Y[e], T1[e], f);
                     }
-                }
-                __syncthreads();
-                // Inertia first: if C - xl I and xh I - C are both positive definite (two
-                // Cholesky attempts, n^3/3 flops together), every eigenvalue lies in
-                // (xl, xh) and their sum is the trace of C; only otherwise is C reduced to
-                // tridiagonal form and its eigenvalues bracketed.
-                for (int e = tid; e < n * n; e += (int)blockDim.x) {
-                    const int i = e / n, j = e - i * n;
-                    const double v = A[e];
-                    T1[e] = (i == j) ? v - xl : v;
-                    Y[e] = (i == j) ? xh - v : -v;
-                }
-                __syncthreads();
-                if (cholesky_lower(T1, n, sh) && cholesky_lower(Y, n, sh)) {
-                    if (tid == 0) {
-                        double tr = 0.0;
-                        for (int i = 0; i < n; ++i) tr += A[(size_t)i * n + i];
-                        sh.p[0] = tr;
-                    }
-                    __syncthreads();
-                    phi = sh.p[0];
+                    phi = block_sum(f, sh.red);
                     rs = n;
-                    __syncthreads();
                 } else {
+                    trsm_lower_t(Zt, Y, A, n, sh);  // A = L^-1 Y^T = L^-1 K_Z L^-T
+                    for (int e = tid; e < n * n; e += (int)blockDim.x) {  // symmetrise (upper from lower)
+                        const int i = e / n, j = e - i * n;
+                        if (i < j) {
+                            const double v = 0.5 * (A[e] + A[(size_t)j * n + i]);
+                            A[e] = v;
+                            A[(size_t)j * n + i] = v;
+                        }
+                    }
+                    __syncthreads();
                     phi = range_sum(A, n, xl, xh, sh, &rs);
                 }
                 r = n;
