@@ -172,7 +172,8 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
       gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
       gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
       assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step
-      assemble_df_kernel   12 float32 instructions per term of the same sums (mixed plans)
+      assemble_df_kernel   12 float32 instructions per term of the same sums (mixed plans); its time is
+                           the assembly phase, which also holds the float-pair split launches
       solve_kernel         flops = sum over points of the route's count (solve_flops)
     """
     N = st.n

@@ -40,6 +40,11 @@ struct ssm_plan_s {
     // batched plans: per-point floor scale
     double* d_fpt = nullptr;
     size_t cap_fpt = 0;
+    // mixed path: float pairs (hi, lo) of the moments and of one batch's mu and nu
+    float* d_xpair = nullptr;
+    size_t cap_xpair = 0;
+    float* d_cpair = nullptr;
+    size_t cap_cpair = 0;
 };
 
 namespace {
@@ -239,6 +244,8 @@ void free_plan(ssm_plan_s* h) {
     if (P.graph) cudaGraphExecDestroy(P.graph);
     if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
     dev_free(h->d_fpt);
+    dev_free(h->d_xpair);
+    dev_free(h->d_cpair);
     dev_free(h->d_t);
     dev_free(h->d_mu);
     dev_free(h->d_nu);
@@ -324,6 +331,58 @@ ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, doub
     return SSM_OK;
 }
 
+// Mixed path: the float pairs of all moments of the plan (B (M+1) n_tot^2 values,
+// split once per DOS call) and room for the pairs of one batch's mu and nu.
+ssm_status split_moments(ssm_plan_s* h) {
+    Plan& P = h->P;
+    const size_t nx = (size_t)(P.B > 1 ? P.B : 1) * (P.p.degree + 1) * P.n_tot * P.n_tot;
+    const size_t nc = 4 * h->cap_batch * (P.p.degree + 1);
+    if (2 * nx > h->cap_xpair) {
+        dev_free(h->d_xpair);
+        h->d_xpair = nullptr;
+        h->cap_xpair = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_xpair, 2 * nx));
+        h->cap_xpair = 2 * nx;
+    }
+    if (nc > h->cap_cpair) {
+        dev_free(h->d_cpair);
+        h->d_cpair = nullptr;
+        h->cap_cpair = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_cpair, nc));
+        h->cap_cpair = nc;
+    }
+    CUDA_OR_FAIL(h, launch_split_pairs(P.d_X, (int64_t)nx, h->d_xpair, h->d_xpair + nx, P.stream));
+    P.stats.launches++;
+    return SSM_OK;
+}
+
+// K (from mu, K+1 terms) and K_Z (from nu, M+1 terms) of n_t points with
+// coefficient rows at mu/nu (leading dimension M+1) from the moments of matrix b.
+ssm_status assemble_pencils(ssm_plan_s* h, const double* mu, const double* nu, int64_t n_t, int b, double* K_out,
+                            double* KZ_out) {
+    Plan& P = h->P;
+    const int M = P.p.degree, K = M / 2, nv = P.p.n_v, n_tot = P.n_tot;
+    const size_t xs = (size_t)(M + 1) * n_tot * n_tot;
+    if (!P.mixed) {
+        CUDA_OR_FAIL(h, launch_assemble(mu, M + 1, n_t, K + 1, P.d_X + b * xs, n_tot, n_tot, n_tot, K_out, P.stream));
+        CUDA_OR_FAIL(h, launch_assemble(nu, M + 1, n_t, M + 1, P.d_X + b * xs, n_tot, nv, nv, KZ_out, P.stream));
+        P.stats.launches += 2;
+        return SSM_OK;
+    }
+    const size_t nx = h->cap_xpair / 2, nc = (size_t)n_t * (M + 1);
+    const float* xh = h->d_xpair + b * xs;
+    const float* xl = h->d_xpair + nx + b * xs;
+    float* c = h->d_cpair;
+    CUDA_OR_FAIL(h, launch_split_pairs(mu, (int64_t)nc, c, c + nc, P.stream));
+    CUDA_OR_FAIL(h, launch_split_pairs(nu, (int64_t)nc, c + 2 * nc, c + 3 * nc, P.stream));
+    CUDA_OR_FAIL(h, launch_assemble_pairs(c, c + nc, M + 1, n_t, K + 1, xh, xl, n_tot, n_tot, n_tot, K_out,
+                                          P.stream));
+    CUDA_OR_FAIL(h, launch_assemble_pairs(c + 2 * nc, c + 3 * nc, M + 1, n_t, M + 1, xh, xl, n_tot, nv, nv, KZ_out,
+                                          P.stream));
+    P.stats.launches += 4;
+    return SSM_OK;
+}
+
 // DOS at n device points d_tpts into h->d_dos_ss / h->d_dos_kpm (device), ranks into h->d_rank.
 ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigma, bool want_ss = true) {
     Plan& P = h->P;
@@ -332,17 +391,19 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
     const double gmax = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
     const double xlo = -P.p.kappa * gmax, xhi = (1.0 + P.p.kappa) * gmax;
     const int64_t bt = batch_points(P);
+    if (want_ss && P.mixed) {
+        Scope sc(h, PH_ASSEMBLE);
+        ssm_status st = split_moments(h);
+        if (st != SSM_OK) return st;
+    }
     for (int64_t t0 = 0; t0 < n_t; t0 += bt) {
         const int64_t nb = (n_t - t0) < bt ? (n_t - t0) : bt;
         ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, want_ss ? h->d_nu : nullptr);
         if (st != SSM_OK) return st;
         if (want_ss) {
             Scope sc(h, PH_ASSEMBLE);
-            CUDA_OR_FAIL(h, launch_assemble(h->d_mu, M + 1, nb, K + 1, P.d_X, n_tot, n_tot, n_tot, h->d_K, P.stream,
-                                            P.mixed));
-            CUDA_OR_FAIL(h, launch_assemble(h->d_nu, M + 1, nb, M + 1, P.d_X, n_tot, nv, nv, h->d_KZ, P.stream,
-                                            P.mixed));
-            P.stats.launches += 2;
+            st = assemble_pencils(h, h->d_mu, h->d_nu, nb, 0, h->d_K, h->d_KZ);
+            if (st != SSM_OK) return st;
         }
         if (want_ss) {
             Scope sc(h, PH_SOLVE);
@@ -396,6 +457,11 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
     }
     CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_fpt, fpt.data(), 3 * n_t * sizeof(double), cudaMemcpyHostToDevice,
                                     P.stream));
+    if (want_ss && P.mixed) {
+        Scope sc(h, PH_ASSEMBLE);
+        ssm_status st = split_moments(h);
+        if (st != SSM_OK) return st;
+    }
     for (int64_t b0 = 0; b0 < P.B; b0 += mb) {
         const int64_t b1 = b0 + mb < P.B ? b0 + mb : P.B;
         for (int64_t b = b0; b < b1; ++b) {
@@ -405,11 +471,9 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
             if (st != SSM_OK) return st;
             if (want_ss) {
                 Scope sc(h, PH_ASSEMBLE);
-                CUDA_OR_FAIL(h, launch_assemble(h->d_mu + off * (M + 1), M + 1, n_tp, K + 1, P.d_X + b * xs, n_tot,
-                                                n_tot, n_tot, h->d_K + off * n_tot * n_tot, P.stream, P.mixed));
-                CUDA_OR_FAIL(h, launch_assemble(h->d_nu + off * (M + 1), M + 1, n_tp, M + 1, P.d_X + b * xs, n_tot,
-                                                nv, nv, h->d_KZ + off * nv * nv, P.stream, P.mixed));
-                P.stats.launches += 2;
+                st = assemble_pencils(h, h->d_mu + off * (M + 1), h->d_nu + off * (M + 1), n_tp, (int)b,
+                                      h->d_K + off * n_tot * n_tot, h->d_KZ + off * nv * nv);
+                if (st != SSM_OK) return st;
             }
             {
                 Scope sc(h, PH_KPM);

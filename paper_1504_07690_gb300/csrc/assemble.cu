@@ -108,7 +108,8 @@ assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, co
 }
 
 // Compensated variant for the mixed path: every float64 operand is split into
-// a float pair (hi = rn(v), lo = rn(v - hi), 48 significant bits), each product
+// a float pair (hi = rn(v), lo = rn(v - hi), 48 significant bits) beforehand
+// (split_pairs_kernel), each product
 // is formed error-free in float32 (fma two-product plus the cross terms) and
 // accumulated in a float pair with an error-free two-sum (Knuth), so a term costs
 // ~10 float32 operations instead of one float64 fma at 1/58 of the rate.  The
@@ -119,9 +120,22 @@ __device__ __forceinline__ void split_f2(double v, float& hi, float& lo) {
     lo = (float)(v - (double)hi);
 }
 
+// The float pairs of n float64 values (the moments once per DOS call, the coefficient
+// tables once per batch), so that the assembly's tile loads do no float64 work.
+__global__ void split_pairs_kernel(const double* __restrict__ v, int64_t n, float* __restrict__ hi,
+                                   float* __restrict__ lo) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float h, l;
+        split_f2(v[i], h, l);
+        hi[i] = h;
+        lo[i] = l;
+    }
+}
+
 __global__ void __launch_bounds__(256)
-assemble_df_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, const double* __restrict__ X,
-                   int n_tot, int rows, int cols, double* __restrict__ out) {
+assemble_df_kernel(const float* __restrict__ coef_hi, const float* __restrict__ coef_lo, int ldc, int64_t n_t, int L,
+                   const float* __restrict__ X_hi, const float* __restrict__ X_lo, int n_tot, int rows, int cols,
+                   double* __restrict__ out) {
     __shared__ float Ch[TL][TT + 1], Cl[TL][TT + 1];
     __shared__ float Xh[TL][TE], Xl[TL][TE];
     __shared__ int xoff[TE];
@@ -163,7 +177,10 @@ assemble_df_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L,
             const int64_t ti = t0 + tt;
             const int l = l0 + ll;
             float h = 0.f, lo = 0.f;
-            if (ti < n_t && l < L) split_f2(coef[ti * ldc + l], h, lo);
+            if (ti < n_t && l < L) {
+                h = coef_hi[ti * ldc + l];
+                lo = coef_lo[ti * ldc + l];
+            }
             Ch[ll][tt] = h;
             Cl[ll][tt] = lo;
         }
@@ -172,7 +189,10 @@ assemble_df_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L,
             const int l = l0 + ll;
             const int off = xoff[ee];
             float h = 0.f, lo = 0.f;
-            if (off >= 0 && l < L) split_f2(X[(size_t)l * nn + off], h, lo);
+            if (off >= 0 && l < L) {
+                h = X_hi[(size_t)l * nn + off];
+                lo = X_lo[(size_t)l * nn + off];
+            }
             Xh[ll][ee] = h;
             Xl[ll][ee] = lo;
         }
@@ -229,14 +249,29 @@ assemble_df_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L,
 }  // namespace
 
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X, int n_tot,
-                            int rows, int cols, double* out, cudaStream_t s, bool compensated) {
+                            int rows, int cols, double* out, cudaStream_t s) {
     if (rows != cols) return cudaErrorInvalidValue;
     const int64_t ne = (int64_t)rows * (rows + 1) / 2;
     dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
-    if (compensated)
-        assemble_df_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
-    else
-        assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
+    assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, int ldc, int64_t n_t, int L,
+                                  const float* X_hi, const float* X_lo, int n_tot, int rows, int cols, double* out,
+                                  cudaStream_t s) {
+    if (rows != cols) return cudaErrorInvalidValue;
+    const int64_t ne = (int64_t)rows * (rows + 1) / 2;
+    dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
+    assemble_df_kernel<<<grid, 256, 0, s>>>(coef_hi, coef_lo, ldc, n_t, L, X_hi, X_lo, n_tot, rows, cols, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_pairs(const double* v, int64_t n, float* hi, float* lo, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    split_pairs_kernel<<<(unsigned)b, 256, 0, s>>>(v, n, hi, lo);
     return cudaGetLastError();
 }
 

@@ -235,10 +235,15 @@ cudaError_t launch_nu(const double* mu, int ldmu, int64_t n_t, int M, double* nu
 cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const double* X, int n_tot,
                        double* zeta, double* out, cudaStream_t s);
 
-// Assembly: out[t][i*cols+j] = sum_{l<L} coef[t][l] X[l][i][j] (assemble.cu); `compensated`
-// selects the float-pair arithmetic of the mixed path instead of float64.
+// Assembly: out[t][i*cols+j] = sum_{l<L} coef[t][l] X[l][i][j] (assemble.cu) in float64;
+// the mixed path's variant takes coef and X as float pairs (launch_split_pairs) and sums
+// in float-pair arithmetic.
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X,
-                            int n_tot, int rows, int cols, double* out, cudaStream_t s, bool compensated = false);
+                            int n_tot, int rows, int cols, double* out, cudaStream_t s);
+cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, int ldc, int64_t n_t, int L,
+                                  const float* X_hi, const float* X_lo, int n_tot, int rows, int cols, double* out,
+                                  cudaStream_t s);
+cudaError_t launch_split_pairs(const double* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 
 // Per-point Alg. 4 + Alg. 6 solve (solve.cu).
 size_t solve_workspace_bytes(int n_v);
