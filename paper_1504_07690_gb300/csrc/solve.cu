@@ -95,16 +95,31 @@ __device__ __forceinline__ double dot8(const double* __restrict__ a, size_t sa, 
 // Householder reduction of the symmetric n x n matrix A (row-major, ld n) to
 // tridiagonal T = H^T A H: sh.d, sh.off receive T; row k of A (columns k+1..)
 // receives the k-th Householder vector and sh.beta[k] its scalar.  Only the
-// lower triangle of A is read and kept up to date: the product p = A22 v takes
-// row i left of the diagonal and column i below it, and the rank-2 update
-// touches the lower triangle only (no mirrored, uncoalesced stores).
+// lower triangle of A is read and kept up to date.
+//
+// One pass over the trailing matrix per column: the rank-2 update
+// A22 -= v w^T + w v^T of step k is applied to column k+1 at once (step k+1
+// reduces it) and to the rest of the trailing matrix during the pass of step
+// k+1, element by element as it is read for that step's product p = A22 v.
+// The pass sweeps the lower triangle in tiles of 4 w x 32 elements (w warps,
+// four rows a thread, lanes along a row), staged through shared memory
+// (sh.gt, two buffers) for the row sums (sum_j a_ij v_j, j <= i) and the
+// column sums (sum_i a_ij v_i, i > j) of the symmetric product; the loads of
+// the next tile are in flight meanwhile.
 __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, nthr = (int)blockDim.x, nw = nthr >> 5, h = 4 * nw;
+    const int wp = tid >> 5, ln = tid & 31;
+    double* vc = sh.v;   // this step's Householder vector
+    double* wc = sh.p;   // this step's row sums, then w
+    double* vq = sh.rc;  // the pending update (previous step): v
+    double* wq = sh.rs;  //                                     w
+    double* pc = sh.gt + 2 * 32 * 33;  // this step's column sums
+    bool pending = false;
     for (int k = 0; k + 2 < n; ++k) {
         const int L = n - k - 1;
         const double* x = A + (size_t)(k + 1) * n + k;  // column k below the diagonal (stride n)
         double f = 0.0;
-        for (int i = tid; i < L; i += (int)blockDim.x) f = fma(x[(size_t)i * n], x[(size_t)i * n], f);
+        for (int i = tid; i < L; i += nthr) f = fma(x[(size_t)i * n], x[(size_t)i * n], f);
         const double nrm2 = block_sum(f, sh.red);
         const double x0 = x[0];
         double beta = 0.0, alpha = x0;
@@ -113,42 +128,111 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             const double v0 = x0 - alpha;
             const double vtv = nrm2 - x0 * x0 + v0 * v0;
             beta = 2.0 / vtv;
-            for (int i = tid; i < L; i += (int)blockDim.x) sh.v[i] = (i == 0) ? v0 : x[(size_t)i * n];
+            for (int i = tid; i < L; i += nthr) vc[i] = (i == 0) ? v0 : x[(size_t)i * n];
         }
-        __syncthreads();
+        for (int i = tid; i < L; i += nthr) {
+            wc[i] = 0.0;
+            pc[i] = 0.0;
+        }
         if (tid == 0) {
             sh.d[k] = A[(size_t)k * n + k];
             sh.off[k] = alpha;
             sh.beta[k] = beta;
         }
-        if (beta != 0.0) {
-            // p = beta A22 v: row i of the lower triangle (j < i) and column i from the
-            // diagonal down (j >= i, consecutive threads read consecutive doubles)
-            const double* A22 = A + (size_t)(k + 1) * n + k + 1;
-            for (int i = tid; i < L; i += (int)blockDim.x)
-                sh.p[i] = beta * (dot8(A22 + (size_t)i * n, 1, sh.v, 1, i) +
-                                  dot8(A22 + (size_t)i * n + i, n, sh.v + i, 1, L - i));
+        __syncthreads();
+        const bool sums = beta != 0.0;
+        if (sums)  // keep v in row k (right of the diagonal, unused by the reduction) for the accumulation
+            for (int i = tid; i < L; i += nthr) A[(size_t)k * n + k + 1 + i] = vc[i];
+        if (sums || pending) {
+            double* B = A + (size_t)(k + 1) * n + k + 1;  // A22, ld n
+            const int nbr = (L + h - 1) / h, nbc = (L + 31) >> 5;
+            double a[4];
+            auto load = [&](int I, int J) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = I * h + wp + nw * u, j = 32 * J + ln;
+                    a[u] = (i < L && j <= i) ? B[(size_t)i * n + j] : 0.0;
+                }
+            };
+            int I = 0, J = 0, buf = 0;
+            load(0, 0);
+            while (I < nbr) {
+                double* T = sh.gt + buf * (32 * 33);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = wp + nw * u, i = I * h + r, j = 32 * J + ln;
+                    if (pending && i < L && j <= i) {
+                        a[u] = fma(-vq[i + 1], wq[j + 1], fma(-wq[i + 1], vq[j + 1], a[u]));
+                        B[(size_t)i * n + j] = a[u];
+                    }
+                    T[r * 33 + ln] = a[u];
+                }
+                __syncthreads();
+                const int cI = I, cJ = J;
+                if (++J > min(nbc - 1, (I * h + h - 1) >> 5)) {
+                    ++I;
+                    J = 0;
+                }
+                if (I < nbr) load(I, J);
+                if (sums) {
+                    {  // row sums: eight threads a row, four columns each
+                        const int r = tid >> 3, q = tid & 7, i = cI * h + r;
+                        double s = 0.0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = 32 * cJ + 4 * q + u;
+                            if (j < L) s = fma(T[r * 33 + 4 * q + u], vc[j], s);
+                        }
+                        s += __shfl_xor_sync(0xffffffffu, s, 1);
+                        s += __shfl_xor_sync(0xffffffffu, s, 2);
+                        s += __shfl_xor_sync(0xffffffffu, s, 4);
+                        if (q == 0 && i < L) wc[i] += s;
+                    }
+                    {  // column sums below the diagonal: w threads a column, four rows each
+                        const int c = tid / nw, g = tid - c * nw, j = 32 * cJ + c;
+                        double s = 0.0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int r = g + nw * u, i = cI * h + r;
+                            if (i < L && i != j) s = fma(T[r * 33 + c], vc[i], s);
+                        }
+                        for (int o = 1; o < nw; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        if (g == 0 && j < L) pc[j] += s;
+                    }
+                }
+                buf ^= 1;
+            }
+            __syncthreads();
+        }
+        if (sums) {
+            for (int i = tid; i < L; i += nthr) wc[i] = beta * (wc[i] + pc[i]);
             __syncthreads();
             double g = 0.0;
-            for (int i = tid; i < L; i += (int)blockDim.x) g = fma(sh.p[i], sh.v[i], g);
+            for (int i = tid; i < L; i += nthr) g = fma(wc[i], vc[i], g);
             const double K = 0.5 * beta * block_sum(g, sh.red);
-            for (int i = tid; i < L; i += (int)blockDim.x) sh.p[i] -= K * sh.v[i];  // p becomes w
+            for (int i = tid; i < L; i += nthr) wc[i] -= K * vc[i];  // p becomes w
             __syncthreads();
-            // A22 -= v w^T + w v^T on the lower triangle (warp per row, lanes along the row)
-            {
-                const int nw = (int)(blockDim.x >> 5), wp = tid >> 5, ln = tid & 31;
-                for (int i = wp; i < L; i += nw) {
-                    const double vi = sh.v[i], pi = sh.p[i];
-                    double* rowi = A + (size_t)(k + 1 + i) * n + k + 1;
-                    for (int j = ln; j <= i; j += 32) rowi[j] = fma(-vi, sh.p[j], fma(-pi, sh.v[j], rowi[j]));
-                }
+            // column k+1 (with its diagonal) takes this step's update now
+            const double v0 = vc[0], w0 = wc[0];
+            for (int i = tid; i < L; i += nthr) {
+                double* e = A + (size_t)(k + 1 + i) * n + k + 1;
+                *e = fma(-vc[i], w0, fma(-wc[i], v0, *e));
             }
-            // keep v in row k (right of the diagonal, unused by the reduction) for the accumulation
-            for (int i = tid; i < L; i += (int)blockDim.x) A[(size_t)k * n + k + 1 + i] = sh.v[i];
         }
+        pending = sums;
+        double* t = vc;
+        vc = vq;
+        vq = t;
+        t = wc;
+        wc = wq;
+        wq = t;
         __syncthreads();
     }
     if (tid == 0) {
+        if (pending) {  // the last update on the last diagonal element (frame of step n-3)
+            double* e = A + (size_t)(n - 1) * n + n - 1;
+            *e = fma(-vq[1], wq[1], fma(-wq[1], vq[1], *e));
+        }
         if (n >= 2) {
             sh.d[n - 2] = A[(size_t)(n - 2) * n + n - 2];
             sh.off[n - 2] = A[(size_t)(n - 1) * n + n - 2];
@@ -629,17 +713,21 @@ __device__ void trsm_lower_t(const double* __restrict__ L, const double* __restr
     __syncthreads();
 }
 
-// X <- L^{-1} (n x n row-major, lower triangular; zero above the diagonal), L from
-// cholesky_lower (rdiag = sh.v): one column per thread, forward substitution on the
-// unit vector e_c from row c down (n^3 / 3 flops).
-__device__ void trinv_lower(const double* __restrict__ L, double* __restrict__ X, int n, const Shared& sh) {
+// sum_ik X_ik^2 for X = L^{-1} M, M lower triangular (its lower triangle is read;
+// X overwrites it), L from cholesky_lower (rdiag = sh.v).  X is lower triangular
+// as well, so column c is a forward substitution from row c down (n^3 / 3 flops),
+// one column per thread.
+__device__ double trtr_sumsq(const double* __restrict__ L, double* __restrict__ M, int n, const Shared& sh) {
+    double f = 0.0;
     for (int c = threadIdx.x; c < n; c += (int)blockDim.x) {
-        for (int i = 0; i < c; ++i) X[(size_t)i * n + c] = 0.0;
-        for (int i = c; i < n; ++i)
-            X[(size_t)i * n + c] =
-                ((i == c ? 1.0 : 0.0) - dot8(L + (size_t)i * n + c, 1, X + (size_t)c * n + c, n, i - c)) * sh.v[i];
+        for (int i = c; i < n; ++i) {
+            const double x =
+                (M[(size_t)i * n + c] - dot8(L + (size_t)i * n + c, 1, M + (size_t)c * n + c, n, i - c)) * sh.v[i];
+            M[(size_t)i * n + c] = x;
+            f = fma(x, x, f);
+        }
     }
-    __syncthreads();
+    return block_sum(f, sh.red);
 }
 
 // Sum (and count) of the eigenvalues of the symmetric m x m matrix C (ld m,
@@ -1106,6 +1194,20 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 __syncthreads();
                 full = cholesky_lower(T1, n, sh);
             }
+            // nothing is kept either when the largest eigenvalue is below the floor:
+            // floor I - K_W positive definite (possible only if every diagonal entry is)
+            if (!empty && !full) {
+                double dm = -DBL_MAX;
+                for (int i = tid; i < n; i += (int)blockDim.x) dm = fmax(dm, A[(size_t)i * n + i]);
+                if (block_max(dm, sh.red) < floor_t) {
+                    for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                        const int i = e / n, j = e - i * n;
+                        T1[e] = (i == j) ? floor_t - A[e] : -A[e];
+                    }
+                    __syncthreads();
+                    empty = cholesky_lower(T1, n, sh);
+                }
+            }
         }
         if (!full && !empty) {
             tridiagonalise(A, n, sh);
@@ -1132,10 +1234,10 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             //     C = L^-1 K_Z L^-T, without the eigenvectors of K_W.
             // Inertia first, by congruence (C = L^-1 K_Z L^-T): C - xl I and xh I - C are
             // positive definite exactly when K_Z - xl K_W and xh K_W - K_Z are (two Cholesky
-            // attempts, n^3/3 flops together, no C).  Then every eigenvalue lies in
-            // (xl, xh) and their sum is tr C = sum_ik (L^-1 K_Z)_ik (L^-1)_ik: one triangular
-            // solve and a triangular inverse.  Only otherwise is C formed, reduced to
-            // tridiagonal form and its eigenvalues bracketed.
+            // attempts, n^3/3 flops each, no C).  Then every eigenvalue lies in (xl, xh) and
+            // their sum is tr C = ||L^-1 L1||_F^2 + xl n, L1 L1^T = K_Z - xl K_W: both
+            // factors are lower triangular, so one more n^3/3 solve.  Only otherwise is C
+            // formed, reduced to tridiagonal form and its eigenvalues bracketed.
             for (int e = tid; e < n * n; e += (int)blockDim.x) {
                 const int i = e / n, j = e - i * n;
                 const double kw = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
@@ -1151,22 +1253,16 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
             }
             __syncthreads();
             if (cholesky_lower(Zt, n, sh)) {
-                for (int e = tid; e < n * n; e += (int)blockDim.x) {
-                    const int i = e / n, j = e - i * n;
-                    Y[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
-                }
-                __syncthreads();
-                trsm_lower(Zt, Y, n, sh);  // Y = L^-1 K_Z
                 if (inside) {
-                    trinv_lower(Zt, T1, n, sh);  // T1 = L^-1
-                    double f = 0.0;
-                    for (int e = tid; e < n * n; e += (int)blockDim.x) {
-                        const int i = e / n, k = e - i * n;
-                        if (k <= i) f = fma(Y[e], T1[e], f);
-                    }
-                    phi = block_sum(f, sh.red);
+                    phi = fma(xl, (double)n, trtr_sumsq(Zt, T1, n, sh));
                     rs = n;
                 } else {
+                    for (int e = tid; e < n * n; e += (int)blockDim.x) {
+                        const int i = e / n, j = e - i * n;
+                        Y[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
+                    }
+                    __syncthreads();
+                    trsm_lower(Zt, Y, n, sh);       // Y = L^-1 K_Z
                     trsm_lower_t(Zt, Y, A, n, sh);  // A = L^-1 Y^T = L^-1 K_Z L^-T
                     for (int e = tid; e < n * n; e += (int)blockDim.x) {  // symmetrise (upper from lower)
                         const int i = e / n, j = e - i * n;
@@ -1226,8 +1322,8 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     __syncthreads();
                     Lw = A;
                     Mz = Zt;
-                    S1 = Zt;
-                    S2 = Y;
+                    S1 = Y;
+                    S2 = T1;
                     stale = true;
                 }
             } else {
@@ -1254,47 +1350,43 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     gemm_tn(Zt, n, T1, rk, n, rk, rk, A, rk, true, sh);
                     Lw = Y;
                     Mz = A;
-                    S1 = A;
-                    S2 = Zt;
+                    S1 = Zt;
+                    S2 = T1;
                     stale = true;
                 }
             }
-            if (Lw && cholesky_lower(Lw, rk, sh)) {
-                trsm_lower(Lw, Mz, rk, sh);         // Mz = L^-1 M_Z
-                trsm_lower_t(Lw, Mz, T1, rk, sh);   // T1 = L^-1 M_Z L^-T
+            if (Lw) {
+                // inertia first, by congruence as on the route above: every eigenvalue of
+                // the pencil (M_Z, M_W) in (xl, xh) makes the sum its trace,
+                // ||L^-1 L1||_F^2 + xl rk with L1 L1^T = M_Z - xl M_W and L L^T = M_W
                 for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
-                    const int i = e / rk, j = e - i * rk;
-                    if (i < j) {
-                        const double v = 0.5 * (T1[e] + T1[(size_t)j * rk + i]);
-                        T1[e] = v;
-                        T1[(size_t)j * rk + i] = v;
-                    }
+                    const double lw = Lw[e], mz = Mz[e];
+                    S1[e] = mz - xl * lw;
+                    S2[e] = xh * lw - mz;
                 }
                 __syncthreads();
-                // inertia first, as on the route above: every eigenvalue in (xl, xh)
-                // makes the sum the trace
-                for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
-                    const int i = e / rk, j = e - i * rk;
-                    const double v = T1[e];
-                    S1[e] = (i == j) ? v - xl : v;
-                    S2[e] = (i == j) ? xh - v : -v;
-                }
-                __syncthreads();
-                if (cholesky_lower(S1, rk, sh) && cholesky_lower(S2, rk, sh)) {
-                    if (tid == 0) {
-                        double tr = 0.0;
-                        for (int i = 0; i < rk; ++i) tr += T1[(size_t)i * rk + i];
-                        sh.p[0] = tr;
+                const bool inside = cholesky_lower(S1, rk, sh) && cholesky_lower(S2, rk, sh);
+                if (cholesky_lower(Lw, rk, sh)) {
+                    if (inside) {
+                        phi = fma(xl, (double)rk, trtr_sumsq(Lw, S1, rk, sh));
+                        rs = rk;
+                    } else {
+                        trsm_lower(Lw, Mz, rk, sh);        // Mz = L^-1 M_Z
+                        trsm_lower_t(Lw, Mz, T1, rk, sh);  // T1 = L^-1 M_Z L^-T
+                        for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                            const int i = e / rk, j = e - i * rk;
+                            if (i < j) {
+                                const double v = 0.5 * (T1[e] + T1[(size_t)j * rk + i]);
+                                T1[e] = v;
+                                T1[(size_t)j * rk + i] = v;
+                            }
+                        }
+                        __syncthreads();
+                        phi = range_sum(T1, rk, xl, xh, sh, &rs);
                     }
-                    __syncthreads();
-                    phi = sh.p[0];
-                    rs = rk;
-                    __syncthreads();
-                } else {
-                    phi = range_sum(T1, rk, xl, xh, sh, &rs);
+                    r = rk;
+                    done = true;
                 }
-                r = rk;
-                done = true;
             }
         }
         if (!done) {
