@@ -504,7 +504,7 @@ __device__ int sturm_below_f32(const float* __restrict__ d, const float* __restr
 // Bisection on Sturm counts for eigenvalues of the tridiagonal (sh.d,
 // sh.off).  bisect_prepare stores e2 = off^2 in sh.p (float64), float32
 // copies of d and e2 in sh.rs, and a Gershgorin bracket of the spectrum in
-// sh.rc[0..1]; bisect_one then returns the j-th smallest eigenvalue.  The
+// sh.rc[0..1]; bisect_many then brackets the eigenvalues it is asked for.  The
 // interval is first narrowed in float32 (with a float32 count the j-th
 // eigenvalue is certain to lie within a few float32 ulps of the float32
 // bracket, so the bracket is widened by 8 ulps of its magnitude before the
@@ -534,44 +534,84 @@ __device__ void bisect_prepare(int n, Shared& sh) {
     __syncthreads();
 }
 
-__device__ double bisect_one(int j, int n, const Shared& sh) {
+// The eigenvalues j = idx(q), q < m, of the tridiagonal (after bisect_prepare) into
+// out[q].  A group of g lanes of one warp (g a power of two, as large as g m <= the
+// CTA allows) brackets each eigenvalue: every round each lane counts the eigenvalues
+// below one of g points that split the bracket into g + 1 parts, and the bracket
+// becomes the part in which the count passes j.  Float32 counts first, then float64
+// counts in the widened bracket down to a width of 4 eps max|Gershgorin bound| (the
+// resolution of a float64 count itself).  Called by every thread of the CTA.
+template <typename Idx>
+__device__ void bisect_many(int m, Idx idx, double* __restrict__ out, int n, const Shared& sh) {
     const float* d32 = reinterpret_cast<const float*>(sh.rs);
     const float* e32 = d32 + n;
     const double glo = sh.rc[0], ghi = sh.rc[1];
     const double scale = fmax(fabs(glo), fabs(ghi));
-    // coarse float32 pass
-    float flo = (float)glo, fhi = (float)ghi;
-    for (int it = 0; it < 28; ++it) {
-        const float mid = 0.5f * (flo + fhi);
-        if (mid <= flo || mid >= fhi) break;
-        if (sturm_below_f32(d32, e32, n, mid) > j)
-            fhi = mid;
-        else
-            flo = mid;
+    const double tol = 4.0 * DBL_EPSILON * scale;
+    const int nthr = (int)blockDim.x, lane = (int)(threadIdx.x & 31);
+    int g = 1;
+    while (g < 32 && 2 * g * m <= nthr) g <<= 1;
+    const int per = nthr / g, t = lane & (g - 1), base = lane & ~(g - 1);
+    const unsigned gmask = g == 32 ? 0xffffffffu : ((1u << g) - 1u) << base;
+    const float rg32 = 1.f / (float)(g + 1);
+    const double rg = 1.0 / (double)(g + 1);
+    int r32 = 0;  // float32 rounds: the bracket shrinks by 2^-28 at least
+    for (float w = 1.f; w > 0x1p-28f; w *= rg32) ++r32;
+    for (int q0 = 0; q0 < m; q0 += per) {
+        const int q = q0 + (int)threadIdx.x / g;
+        const bool act = q < m;
+        const int j = act ? idx(q) : 0;
+        float flo = (float)glo, fhi = (float)ghi;
+        for (int r = 0; r < r32; ++r) {
+            const float w = (fhi - flo) * rg32;
+            const bool above = act && sturm_below_f32(d32, e32, n, fmaf(w, (float)(t + 1), flo)) > j;
+            const unsigned bits = (__ballot_sync(0xffffffffu, above) & gmask) >> base;
+            const int k = bits ? __ffs((int)bits) - 1 : g;  // first point whose count passes j
+            const float nh = k < g ? fmaf(w, (float)(k + 1), flo) : fhi;
+            if (k > 0) flo = fmaf(w, (float)k, flo);
+            fhi = nh;
+        }
+        // float32 rounding of T moves eigenvalues by up to ~n ulp(|T|): widen, and
+        // fall back to the whole spectrum if the j-th eigenvalue is not inside
+        const double pad = scale * (4e-7 * n + 1e-6) + DBL_MIN;
+        double lo = fmax(glo, (double)flo - pad), hi = fmin(ghi, (double)fhi + pad);
+        bool bad = false;
+        if (act) {
+            if (g == 1)
+                bad = !(sturm_below(sh.d, sh.p, n, lo) <= j && sturm_below(sh.d, sh.p, n, hi) > j);
+            else if (t == 0)
+                bad = !(sturm_below(sh.d, sh.p, n, lo) <= j);
+            else if (t == 1)
+                bad = !(sturm_below(sh.d, sh.p, n, hi) > j);
+        }
+        if (__ballot_sync(0xffffffffu, bad) & gmask) {
+            lo = glo;
+            hi = ghi;
+        }
+        bool stuck = false;
+        for (int r = 0; r < 80; ++r) {
+            const bool done = !act || stuck || !(hi - lo > tol);
+            if (__all_sync(0xffffffffu, done)) break;
+            const double w = (hi - lo) * rg;
+            const bool above = !done && sturm_below(sh.d, sh.p, n, fma(w, (double)(t + 1), lo)) > j;
+            const unsigned bits = (__ballot_sync(0xffffffffu, above) & gmask) >> base;
+            if (!done) {
+                const int k = bits ? __ffs((int)bits) - 1 : g;
+                const double nh = k < g ? fma(w, (double)(k + 1), lo) : hi;
+                const double nl = k > 0 ? fma(w, (double)k, lo) : lo;
+                stuck = nl == lo && nh == hi;
+                lo = nl;
+                hi = nh;
+            }
+        }
+        if (act && t == 0) out[q] = 0.5 * (lo + hi);
     }
-    // float32 rounding of T moves eigenvalues by up to ~n ulp(|T|): widen
-    const double pad = scale * (4e-7 * n + 1e-6) + DBL_MIN;
-    double lo = fmax(glo, (double)flo - pad), hi = fmin(ghi, (double)fhi + pad);
-    // the widened bracket must still contain the j-th eigenvalue; fall back if not
-    if (!(sturm_below(sh.d, sh.p, n, lo) <= j && sturm_below(sh.d, sh.p, n, hi) > j)) {
-        lo = glo;
-        hi = ghi;
-    }
-    for (int it = 0; it < 80; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (sturm_below(sh.d, sh.p, n, mid) > j)
-            hi = mid;
-        else
-            lo = mid;
-    }
-    return 0.5 * (lo + hi);
 }
 
-// All eigenvalues, one thread per eigenvalue, into sh.v (ascending).
+// All eigenvalues into sh.v (ascending).
 __device__ void bisect_all(int n, Shared& sh) {
     bisect_prepare(n, sh);
-    for (int j = threadIdx.x; j < n; j += (int)blockDim.x) sh.v[j] = bisect_one(j, n, sh);
+    bisect_many(n, [](int q) { return q; }, sh.v, n, sh);
     __syncthreads();
 }
 
@@ -754,23 +794,20 @@ __device__ double range_sum(double* __restrict__ C, int m, double xl, double xh,
     if (by_trace) {
         // the outside eigenvalues, and the two next to the interval's edges (their side
         // is decided by value, as in the direct sum)
-        for (int q = tid; q < nout + 2 * (jhi > jlo); q += (int)blockDim.x) {
-            int j;
-            if (q < jlo) j = q;
-            else if (q < nout) j = jhi + (q - jlo);
-            else j = (q == nout) ? jlo : jhi - 1;
-            sh.v[j] = bisect_one(j, m, sh);
-        }
+        // (into sh.v[q]: q < nout the outside ones in ascending order, then the edges)
+        bisect_many(
+            nout + 2 * (jhi > jlo),
+            [=](int q) { return q < jlo ? q : (q < nout ? jhi + (q - jlo) : (q == nout ? jlo : jhi - 1)); }, sh.v,
+            m, sh);
         __syncthreads();
         if (tid == 0) {
             double tr = 0.0;
             for (int i = 0; i < m; ++i) tr += sh.d[i];
             int cnt = jhi - jlo;
             double out = 0.0;
-            for (int j = 0; j < jlo; ++j) out += sh.v[j];
-            for (int j = jhi; j < m; ++j) out += sh.v[j];
+            for (int q = 0; q < nout; ++q) out += sh.v[q];
             if (jhi > jlo) {  // edge eigenvalues that rounding puts outside
-                const double a0 = sh.v[jlo], a1 = sh.v[jhi - 1];
+                const double a0 = sh.v[nout], a1 = sh.v[nout + 1];
                 if (!(a0 >= xl && a0 <= xh)) {
                     out += a0;
                     --cnt;
@@ -784,13 +821,13 @@ __device__ double range_sum(double* __restrict__ C, int m, double xl, double xh,
             sh.p[0] = tr - out;
         }
     } else {
-        for (int j = jlo + tid; j < jhi; j += (int)blockDim.x) sh.v[j] = bisect_one(j, m, sh);
+        bisect_many(jhi - jlo, [=](int q) { return jlo + q; }, sh.v, m, sh);
         __syncthreads();
         if (tid == 0) {
             int q = 0;
             double f = 0.0;
             for (int j = jlo; j < jhi; ++j) {
-                const double xi = sh.v[j];
+                const double xi = sh.v[j - jlo];
                 if (xi >= xl && xi <= xh) {
                     ++q;
                     f += xi;
@@ -1298,7 +1335,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 //     Householder reflectors of their QR; K_W and K_Z are reflected
                 //     two-sided by those dn reflectors and their trailing rk x rk blocks
                 //     are Y^T K_W Y and Y^T K_Z Y (O(dn n^2) instead of O(rk n^2)).
-                for (int q = tid; q < dn; q += (int)blockDim.x) sh.v[q] = bisect_one(q, n, sh);
+                bisect_many(dn, [](int q) { return q; }, sh.v, n, sh);
                 __syncthreads();
                 twisted_vectors(n, dn, Zt, Y, T1, n, sh);
                 if (sh.misc[6]) {
@@ -1330,7 +1367,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 // Y = H Z, Z the twisted-factorization eigenvectors of the kept eigenvalues
                 //     of the tridiagonal T = H^T K_W H; Y^T K_W Y = Z^T T Z.
                 const int j0 = n - r_est;
-                for (int q = tid; q < rk; q += (int)blockDim.x) sh.v[q] = bisect_one(j0 + q, n, sh);
+                bisect_many(rk, [=](int q) { return j0 + q; }, sh.v, n, sh);
                 __syncthreads();
                 twisted_vectors(n, rk, Zt, Y, T1, n, sh);
                 if (sh.misc[6]) {
