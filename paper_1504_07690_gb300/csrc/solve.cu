@@ -1061,6 +1061,43 @@ __device__ void back_transform(const double* __restrict__ A, int n, double* __re
         __syncthreads();
         return;
     }
+    if ((nw + 1) * r <= 3 * 32 * 33) {
+        // more columns: lanes along the r columns of a row (contiguous in Z), warps
+        // splitting the rows; per-warp partial dots summed through shared memory
+        const int tid = threadIdx.x, wp = tid >> 5, ln = tid & 31;
+        double* part = sh.gt;        // [nw][r]
+        double* fq = sh.gt + nw * r;  // [r]
+        for (int k = n - 3; k >= 0; --k) {
+            const double beta = sh.beta[k];
+            if (beta == 0.0) continue;
+            const int L = n - k - 1;
+            const double* v = A + (size_t)k * n + k + 1;
+            double* zk = Z + (size_t)(k + 1) * ldz;
+            for (int q = ln; q < r; q += 32) {
+                double s0 = 0.0, s1 = 0.0;
+                int j = wp;
+                for (; j + nw < L; j += 2 * nw) {
+                    s0 = fma(v[j], zk[(size_t)j * ldz + q], s0);
+                    s1 = fma(v[j + nw], zk[(size_t)(j + nw) * ldz + q], s1);
+                }
+                if (j < L) s0 = fma(v[j], zk[(size_t)j * ldz + q], s0);
+                part[wp * r + q] = s0 + s1;
+            }
+            __syncthreads();
+            for (int q = tid; q < r; q += (int)blockDim.x) {
+                double f = 0.0;
+                for (int w = 0; w < nw; ++w) f += part[w * r + q];
+                fq[q] = beta * f;
+            }
+            __syncthreads();
+            for (int q = ln; q < r; q += 32) {
+                const double f = fq[q];
+                for (int j = wp; j < L; j += nw) zk[(size_t)j * ldz + q] = fma(-f, v[j], zk[(size_t)j * ldz + q]);
+            }
+            __syncthreads();
+        }
+        return;
+    }
     for (int q = threadIdx.x; q < r; q += (int)blockDim.x) {
         for (int k = n - 3; k >= 0; --k) {
             const double beta = sh.beta[k];
@@ -1109,32 +1146,78 @@ __device__ void householder_qr_cols(double* __restrict__ Q, int ldq, int n, int 
     }
 }
 
-// K <- H_j K H_j on the trailing block K[j.., j..] of the symmetric n x n K (ld n),
-// H_j = I - beta u u^T with u = column j of Q (rows j.., ld ldq), beta = sh.beta[j]:
-// p = beta K u, w = p - (beta/2)(u^T p) u, K -= u w^T + w u^T.  Rows and columns
-// below j are left as they are: the trailing blocks of later reflections never
-// read them.
-__device__ void reflect_two_sided(double* __restrict__ K, int n, const double* __restrict__ Q, int ldq, int j,
-                                  Shared& sh) {
-    const int tid = threadIdx.x;
+// K <- H_j K H_j on the trailing blocks K[j.., j..] of the two symmetric n x n
+// matrices K = K1, K2 (ld n), H_j = I - beta u u^T with u = column j of Q (rows j..,
+// ld ldq), beta = sh.beta[j]: p = beta K u, w = p - (beta/2)(u^T p) u,
+// K -= u w^T + w u^T.  Rows and columns below j are left as they are: the trailing
+// blocks of later reflections never read them.  sh.v holds u, sh.p and sh.rc the two
+// p/w, sh.rs the two block sums.
+__device__ void reflect_two_sided2(double* __restrict__ K1, double* __restrict__ K2, int n,
+                                   const double* __restrict__ Q, int ldq, int j, Shared& sh) {
+    const int tid = threadIdx.x, nthr = (int)blockDim.x;
     const double beta = sh.beta[j];
     if (beta == 0.0) return;
     const int L = n - j;
-    for (int i = tid; i < L; i += (int)blockDim.x) sh.v[i] = Q[(size_t)(j + i) * ldq + j];
+    double* u = sh.v;
+    double* w1 = sh.p;
+    double* w2 = sh.rc;
+    for (int i = tid; i < L; i += nthr) u[i] = Q[(size_t)(j + i) * ldq + j];
     __syncthreads();
-    for (int i = tid; i < L; i += (int)blockDim.x)
-        sh.p[i] = beta * dot8(K + (size_t)j * n + j + i, n, sh.v, 1, L);
+    double g1 = 0.0, g2 = 0.0;
+    for (int i = tid; i < L; i += nthr) {
+        // column i of the symmetric blocks (consecutive threads read consecutive doubles)
+        const double p1 = beta * dot8(K1 + (size_t)j * n + j + i, n, u, 1, L);
+        const double p2 = beta * dot8(K2 + (size_t)j * n + j + i, n, u, 1, L);
+        w1[i] = p1;
+        w2[i] = p2;
+        g1 = fma(p1, u[i], g1);
+        g2 = fma(p2, u[i], g2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+    }
+    if ((tid & 31) == 0) {
+        sh.red[tid >> 5] = g1;
+        sh.rs[tid >> 5] = g2;
+    }
     __syncthreads();
-    double g = 0.0;
-    for (int i = tid; i < L; i += (int)blockDim.x) g = fma(sh.p[i], sh.v[i], g);
-    const double c = 0.5 * beta * block_sum(g, sh.red);
-    for (int i = tid; i < L; i += (int)blockDim.x) sh.p[i] = fma(-c, sh.v[i], sh.p[i]);
+    double c1 = 0.0, c2 = 0.0;
+    for (int w = 0; w < (nthr >> 5); ++w) {
+        c1 += sh.red[w];
+        c2 += sh.rs[w];
+    }
+    c1 *= 0.5 * beta;
+    c2 *= 0.5 * beta;
     __syncthreads();
-    const int nw = (int)(blockDim.x >> 5), wp = tid >> 5, ln = tid & 31;
-    for (int i = wp; i < L; i += nw) {
-        const double vi = sh.v[i], wi = sh.p[i];
-        double* row = K + (size_t)(j + i) * n + j;
-        for (int l = ln; l < L; l += 32) row[l] = fma(-vi, sh.p[l], fma(-wi, sh.v[l], row[l]));
+    for (int i = tid; i < L; i += nthr) {
+        w1[i] = fma(-c1, u[i], w1[i]);
+        w2[i] = fma(-c2, u[i], w2[i]);
+    }
+    __syncthreads();
+    // rank-2 updates, element-parallel, four elements of each matrix in flight a thread
+    const int LL = L * L;
+    for (int e0 = tid; e0 < LL; e0 += 4 * nthr) {
+        double a1[4], a2[4];
+        int ri[4], ci[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = e0 + q * nthr;
+            ri[q] = e / L;
+            ci[q] = e - ri[q] * L;
+            if (e < LL) {
+                a1[q] = K1[(size_t)(j + ri[q]) * n + j + ci[q]];
+                a2[q] = K2[(size_t)(j + ri[q]) * n + j + ci[q]];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (e0 + q * nthr < LL) {
+                const int r = ri[q], c = ci[q];
+                K1[(size_t)(j + r) * n + j + c] = fma(-u[r], w1[c], fma(-w1[r], u[c], a1[q]));
+                K2[(size_t)(j + r) * n + j + c] = fma(-u[r], w2[c], fma(-w2[r], u[c], a2[q]));
+            }
+        }
     }
     __syncthreads();
 }
@@ -1347,10 +1430,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                         T1[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
                     }
                     __syncthreads();
-                    for (int j = 0; j < dn; ++j) {
-                        reflect_two_sided(Y, n, Zt, n, j, sh);
-                        reflect_two_sided(T1, n, Zt, n, j, sh);
-                    }
+                    for (int j = 0; j < dn; ++j) reflect_two_sided2(Y, T1, n, Zt, n, j, sh);
                     for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
                         const int i = e / rk, j = e - i * rk;
                         A[e] = Y[(size_t)(dn + i) * n + dn + j];
