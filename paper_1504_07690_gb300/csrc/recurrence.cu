@@ -279,6 +279,23 @@ panelize_kernel(const float* __restrict__ V, uint32_t nchunk, uint32_t n_rows, P
 }
 
 // One CTA per 32-row panel (grid-stride beyond 2^20 panels).
+// Threads of a stencil-step CTA: the multiple of 32 up to 256 whose passes of two
+// items a thread leave the fewest idle lanes over the 32 nchunk items of a panel
+// (ties to the larger CTA).
+int stencil_threads(uint32_t nchunk) {
+    const uint32_t items = 32 * nchunk;
+    int best = 256;
+    uint32_t best_idle = ~0u;
+    for (int t = 256; t >= 128; t -= 32) {
+        const uint32_t per = 2u * (uint32_t)t, idle = (items + per - 1) / per * per - items;
+        if (idle < best_idle) {
+            best = t;
+            best_idle = idle;
+        }
+    }
+    return best;
+}
+
 int panel_grid(uint64_t n_rows) {
     uint64_t blocks = (n_rows + 31) / 32;
     if (blocks > (1u << 20)) blocks = 1u << 20;
@@ -293,10 +310,10 @@ static cudaError_t stencil_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, 
     const uint32_t nchunk = (uint32_t)(P.ld / Vec16<T>::W);
     const PanelOut po{panel, (uint32_t)P.panel_groups};
     if (panel)
-        stencil_step_kernel<T, true><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
+        stencil_step_kernel<T, true><<<panel_grid(P.n), stencil_threads(nchunk), 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
                                                                         o1, o2, c, d, nchunk, (uint32_t)P.n, po);
     else
-        stencil_step_kernel<T, false><<<panel_grid(P.n), 256, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
+        stencil_step_kernel<T, false><<<panel_grid(P.n), stencil_threads(nchunk), 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
                                                                          o1, o2, c, d, nchunk, (uint32_t)P.n, po);
     return cudaGetLastError();
 }
