@@ -648,8 +648,8 @@ __device__ bool cholesky_lower(double* __restrict__ A, int n, Shared& sh) {
 #pragma unroll
                 for (int pass = 0; pass < 4; ++pass) {
                     const int t = tid + pass * nt;
-                    if (t < 256) {
-                        const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+                    const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+                    if (t < 256 && pi < h && qj < w) {  // rows past a ragged last block: whole warps idle
 #pragma unroll 8
                         for (int kk = 0; kk < 32; ++kk) {
                             const double a0 = ta[kk * 33 + pi], a1 = ta[kk * 33 + pi + 1];
@@ -914,13 +914,14 @@ __device__ void gemm_tn(const double* __restrict__ Am, int lda, const double* __
                 tb[kk * 33 + c] = (k < K && q0 + c < Q) ? Bm[(size_t)k * ldb + q0 + c] : 0.0;
             }
             __syncthreads();
+            const int kn = K - k0 < 32 ? K - k0 : 32;  // a ragged last k block stops early
 #pragma unroll
             for (int pass = 0; pass < 4; ++pass) {
                 const int t = tid + pass * nt;
-                if (t < 256) {
-                    const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+                const int pi = 2 * (t >> 4), qj = 2 * (t & 15);
+                if (t < 256 && p0 + pi < P && q0 + qj < Q) {  // rows past a ragged tile: whole warps idle
 #pragma unroll 8
-                    for (int kk = 0; kk < 32; ++kk) {
+                    for (int kk = 0; kk < kn; ++kk) {
                         const double a0 = ta[kk * 33 + pi], a1 = ta[kk * 33 + pi + 1];
                         const double b0 = tb[kk * 33 + qj], b1 = tb[kk * 33 + qj + 1];
                         acc[pass][0][0] = fma(a0, b0, acc[pass][0][0]);
