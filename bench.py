@@ -135,27 +135,28 @@ FP64_FMA_PER_SM_CLK = 2   # measured: FMA chains reach 1.20 TFLOP/s on 152 SMs a
 
 
 def solve_flops(ranks, n: int) -> float:
-    """Float64 flops of the per-point solver, by the route each point takes (kept rank r;
-    the paths that run when every test passes):
+    """Float64 flops of the per-point solver, by the route each point takes ((r, r_s) per
+    point: kept rank, eigenvalues inside the filter; the paths that run when every test
+    passes):
     r = n: the full-rank test (Cholesky of K_W less the threshold, n^3/3), the inertia test
-    by congruence (two Choleskys, 2/3 n^3), Cholesky of K_W (n^3/3), one triangular solve
-    (n^3) and a triangular inverse (n^3/3) for the trace;
-    r = 0: the Householder reduction of K_W (4/3 n^3), an upper bound (the Gershgorin test
-    can skip it);
+    by congruence (two Choleskys, 2/3 n^3), Cholesky of K_W (n^3/3) and the trace from a
+    triangular solve with a triangular right-hand side (n^3/3): 5/3 n^3 (when the inertia
+    test fails: two solves (2 n^3) and the reduction of C (4/3 n^3) instead of the last);
+    r = 0: counted as nothing (the Gershgorin bound or one Cholesky of floor I - K_W decides);
     0 < r < n: reduction (4/3 n^3), then with d = n - r dropped directions and 3 d < r the
     dropped eigenvectors' back-transform (2 n^2 d) and two-sided reflections of K_W and K_Z
     (8 n^2 d), else the kept basis: back-transform (2 n^2 r), K_Z Y (2 n^2 r), Y^T K_Z Y and
-    Z^T T Z (2 n r^2); then Cholesky, solves and inertia test of the r x r pencil
-    (r^3/3 + 2 r^3 + 2/3 r^3)."""
+    Z^T T Z (2 n r^2); then the r x r pencil as in the r = n case without the full-rank
+    test (4/3 r^3, or 13/3 r^3 when the inertia test fails)."""
     tot = 0.0
-    for r in ranks:
+    for r, rs in ranks:
         if r == n:
-            f = (1.0 / 3.0 + 2.0 / 3.0 + 1.0 / 3.0 + 1.0 + 1.0 / 3.0) * n ** 3
+            f = 5.0 / 3.0 * n ** 3 if rs == r else (1.0 / 3.0 + 2.0 / 3.0 + 1.0 / 3.0 + 2.0 + 4.0 / 3.0) * n ** 3
         elif r == 0:
-            f = 4.0 / 3.0 * n ** 3
+            f = 0.0
         else:
             d = n - r
-            f = 4.0 / 3.0 * n ** 3 + (1.0 / 3.0 + 2.0 + 2.0 / 3.0) * r ** 3
+            f = 4.0 / 3.0 * n ** 3 + (4.0 / 3.0 if rs == r else 13.0 / 3.0) * r ** 3
             if 3 * d < r:
                 f += 10.0 * n * n * d
             else:
@@ -379,7 +380,7 @@ def run_gpu(args, c, st, W, csr):
                                                   "ms_assemble", "ms_solve", "ms_kpm")}
     # kept ranks of the sweep points (untimed) decide each point's solver route
     _, _, rk = S.ssm_dos(plan, td, sigma, want_kpm=False)
-    ranks = [int(v) for v in rk[:, 0].cpu().numpy()]
+    ranks = [(int(a), int(b)) for a, b in rk.cpu().numpy()]
     roofs = kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, ck, ranks)
     dominant = max(roofs, key=lambda r: r["ms_per_step"])
     roofline = dict(dominant)
