@@ -45,6 +45,10 @@ struct ssm_plan_s {
     size_t cap_xpair = 0;
     float* d_cpair = nullptr;
     size_t cap_cpair = 0;
+    // solver schedule: n_t of the last single-launch solve (its ranks in d_rank), 0 if none
+    int32_t* d_perm = nullptr;
+    size_t cap_perm = 0;
+    int64_t sched_nt = 0;
 };
 
 namespace {
@@ -246,6 +250,7 @@ void free_plan(ssm_plan_s* h) {
     dev_free(h->d_fpt);
     dev_free(h->d_xpair);
     dev_free(h->d_cpair);
+    dev_free(h->d_perm);
     dev_free(h->d_t);
     dev_free(h->d_mu);
     dev_free(h->d_nu);
@@ -408,10 +413,30 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
         if (want_ss) {
             Scope sc(h, PH_SOLVE);
             const double floor_scale = 8.0 * nv * P.eps_floor * P.x0max;
+            // one launch over every point: order the points by the routes they took in the
+            // previous such launch, so that the slowest get an SM of their own
+            const bool single = t0 == 0 && nb == n_t;
+            const int32_t* perm = nullptr;
+            if (single && h->sched_nt == n_t) {
+                const int64_t slots = solve_slots(nv);
+                if (slots >= n_t) {
+                    if ((size_t)slots > h->cap_perm) {
+                        dev_free(h->d_perm);
+                        h->d_perm = nullptr;
+                        h->cap_perm = 0;
+                        CUDA_OR_FAIL(h, dev_alloc(&h->d_perm, (size_t)slots));
+                        h->cap_perm = (size_t)slots;
+                    }
+                    CUDA_OR_FAIL(h, launch_solve_schedule(h->d_rank, n_t, nv, h->d_perm, P.stream));
+                    P.stats.launches++;
+                    perm = h->d_perm;
+                }
+            }
             CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, h->d_mu, M + 1, K,
                                          floor_scale, h->d_solve, h->d_dos_ss + t0, h->d_rank + 2 * t0,
-                                         P.d_flag, P.stream));
+                                         P.d_flag, P.stream, nullptr, perm));
             P.stats.launches++;
+            h->sched_nt = single ? n_t : 0;
         }
         {
             Scope sc(h, PH_KPM);

@@ -252,7 +252,14 @@ size_t solve_workspace_bytes(int n_v);
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh,
                          double tau, double xlo, double xhi, const double* mu, int ldmu, int K,
                          double floor_scale, void* work, double* dos, int32_t* rank, int* flag,
-                         cudaStream_t s, const double* floor_pt = nullptr);
+                         cudaStream_t s, const double* floor_pt = nullptr, const int32_t* perm = nullptr);
+// Resident solver CTAs on the device (SMs x CTAs per SM; 0 if not available): the
+// slots of one wave, the length of a schedule.
+int64_t solve_slots(int n_v);
+// Schedule (perm, solve_slots(n_v) entries) of the next solve launch over n_t points
+// from the kept ranks of the previous launch over the same number of points; a
+// heuristic for speed only: every point is solved whatever perm holds.
+cudaError_t launch_solve_schedule(const int32_t* rank_prev, int64_t n_t, int n_v, int32_t* perm, cudaStream_t s);
 
 // Adjoint of the recurrence (adjoint.cu).  One backward step: Uo (nullable) =
 // Gbar_k + 2 A~ Un1 - Un2 with Gbar_k = Gb if Gb != NULL, else ga Vm + gb V0 + gc Vp;

@@ -1251,7 +1251,8 @@ __global__ void __launch_bounds__(NT, 3)
 solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, int64_t n_t, int nv, int nvh,
              double tau, double xlo, double xhi, const double* __restrict__ mu, int ldmu, int K,
              double floor_scale, double* __restrict__ work, double* __restrict__ dos,
-             int32_t* __restrict__ rank, int* __restrict__ flag, const double* __restrict__ floor_pt) {
+             int32_t* __restrict__ rank, int* __restrict__ flag, const double* __restrict__ floor_pt,
+             const int32_t* __restrict__ perm, int64_t n_slot) {
     extern __shared__ __align__(16) double dyn[];
     const int n = nv;
     Shared sh;
@@ -1274,7 +1275,11 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
     double* Zt = A + nn;
     double* Y = Zt + nn;
     double* T1 = Y + nn;
-    for (int64_t it = blockIdx.x; it < n_t; it += gridDim.x) {
+    // slot -> point: the identity, or a schedule that gives the slowest points an SM of
+    // their own (perm[slot] < 0: no point)
+    for (int64_t sl = blockIdx.x; sl < n_slot; sl += gridDim.x) {
+        const int64_t it = perm ? (int64_t)perm[sl] : sl;
+        if (it < 0 || it >= n_t) continue;
         const double* Kt = Kfull + (size_t)it * n_tot * n_tot;
         const double* Zk = KZ + (size_t)it * nn;
         // rounding floor of K_W(t)
@@ -1668,18 +1673,94 @@ size_t solve_workspace_bytes(int n_v) {
     return (size_t)workspace_ctas(n_v) * 4 * (size_t)n_v * n_v * sizeof(double);
 }
 
+// Schedule of the next solve launch from the routes of the previous one (its kept
+// ranks): CTA b runs on SM b mod S of the first wave (b < S k, k CTAs per SM), so the
+// points that kept part of the directions (the longest, bound by float64 issue) take
+// blocks 0.. and their SMs' other slots go to points that kept nothing (the shortest)
+// or stay empty, as far as free slots allow; every other point fills the rest in order.
+// One thread; perm has S k entries.
+__global__ void solve_schedule_kernel(const int32_t* __restrict__ rank_prev, int64_t n_t, int n, int S, int k,
+                                      int32_t* __restrict__ perm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t slots = (int64_t)S * k;
+    auto cls = [&](int64_t i) {  // 0 nothing kept, 1 part, 2 everything
+        const int r = rank_prev[2 * i];
+        return r <= 0 ? 0 : (r >= n ? 2 : 1);
+    };
+    for (int64_t b = 0; b < slots; ++b) perm[b] = -2;  // unassigned
+    int64_t free_slots = slots - n_t;
+    int np = 0;
+    int64_t ce = 0;  // cursor over the points that kept nothing
+    for (int64_t i = 0; i < n_t && np < S; ++i)
+        if (cls(i) == 1) perm[np++] = (int32_t)i;
+    for (int s = 0; s < np; ++s)
+        for (int j = 1; j < k; ++j) {
+            while (ce < n_t && cls(ce) != 0) ++ce;
+            if (ce < n_t) {
+                perm[s + (int64_t)j * S] = (int32_t)ce++;
+            } else if (free_slots > 0) {
+                perm[s + (int64_t)j * S] = -1;
+                --free_slots;
+            }
+        }
+    // the rest in order: points not placed yet into the unassigned slots
+    int64_t b = 0;
+    int placed_part = 0;
+    for (int64_t i = 0; i < n_t; ++i) {
+        const int c = cls(i);
+        if (c == 1 && placed_part < np) {
+            ++placed_part;
+            continue;
+        }
+        if (c == 0 && i < ce) continue;  // placed next to a part point (cursor passed it)
+        while (b < slots && perm[b] != -2) ++b;
+        if (b >= slots) break;  // cannot happen: holes never exceed the free slots
+        perm[b++] = (int32_t)i;
+    }
+    for (; b < slots; ++b)
+        if (perm[b] == -2) perm[b] = -1;
+}
+
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh, double tau,
                          double xlo, double xhi, const double* mu, int ldmu, int K, double floor_scale, void* work,
-                         double* dos, int32_t* rank, int* flag, cudaStream_t s, const double* floor_pt) {
+                         double* dos, int32_t* rank, int* flag, cudaStream_t s, const double* floor_pt,
+                         const int32_t* perm) {
     if (n_t <= 0) return cudaSuccess;
     if (n_v > MAXN) return cudaErrorInvalidValue;
     const size_t smem = solve_smem(n_v);
     cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = workspace_ctas(n_v);
-    if (grid > n_t) grid = n_t;
+    int64_t grid = workspace_ctas(n_v), n_slot = n_t;
+    if (perm) {
+        n_slot = solve_slots(n_v);
+        if (n_slot < n_t || n_slot > grid) return cudaErrorInvalidValue;
+    }
+    if (grid > n_slot) grid = n_slot;
     solve_kernel<<<(int)grid, solve_threads(n_v), smem, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K,
-                                                   floor_scale, (double*)work, dos, rank, flag, floor_pt);
+                                                   floor_scale, (double*)work, dos, rank, flag, floor_pt, perm,
+                                                   n_slot);
+    return cudaGetLastError();
+}
+
+int64_t solve_slots(int n_v) {
+    int dev = 0, sms = 0, k = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = solve_smem(n_v);
+    if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, solve_kernel, solve_threads(n_v), smem) != cudaSuccess)
+        return 0;
+    const int64_t slots = (int64_t)sms * k;
+    return slots <= workspace_ctas(n_v) ? slots : 0;
+}
+
+cudaError_t launch_solve_schedule(const int32_t* rank_prev, int64_t n_t, int n_v, int32_t* perm, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t slots = solve_slots(n_v);
+    if (slots < n_t || slots <= 0) return cudaErrorInvalidValue;
+    solve_schedule_kernel<<<1, 32, 0, s>>>(rank_prev, n_t, n_v, sms, (int)(slots / sms), perm);
     return cudaGetLastError();
 }
 
