@@ -361,3 +361,27 @@ def test_fused_step_matches_separate_kernels_and_oracle(S, dims, per, off, nv, n
     # a second call on the same plan repeats bit for bit
     Xf2 = S.ssm_moments(fused, Wd, return_moments=True).cpu().numpy()
     assert np.array_equal(Xf, Xf2)
+
+
+def test_solver_schedule_repeats_bit_for_bit(S):
+    # The second and later DOS calls over the same number of points run the points in an
+    # order taken from the routes of the call before (points that keep part of the
+    # directions on SMs of their own).  Each point's arithmetic does not depend on the CTA
+    # that runs it: every call gives the same bits, and at least two routes occur.
+    st = wl.make_operator("lap2d_dirichlet_32")
+    c = wl.CONFIGS["lap2d_dirichlet_32"]
+    W = wl.random_block(st.n, c["n_v"], c["probe_seed"], c["probe"])
+    for precision in ("fp64", "mixed"):
+        plan = S.ssm_plan_create(stencil=st, n_v=c["n_v"], n_vh=0, degree=c["M"], precision=precision)
+        info = S.ssm_plan_info(plan)
+        # sigma = 0.3: full rank inside the spectrum, part of the directions towards and
+        # past its ends (checked on the oracle)
+        t = torch.from_numpy(np.linspace(info["lo"] - 3.0, info["hi"] + 3.0, 157)).cuda()
+        S.ssm_moments(plan, torch.from_numpy(W).cuda())
+        runs = [S.ssm_dos(plan, t, 0.3) for _ in range(3)]
+        r0 = runs[0][2].cpu().numpy()[:, 0]
+        classes = {int(np.sum(r0 == 0) > 0), 2 * int(np.sum((r0 > 0) & (r0 < c["n_v"])) > 0),
+                   4 * int(np.sum(r0 == c["n_v"]) > 0)} - {0}
+        assert len(classes) >= 2, np.unique(r0)
+        for ss, kp, rk in runs[1:]:
+            assert torch.equal(ss, runs[0][0]) and torch.equal(rk, runs[0][2]) and torch.equal(kp, runs[0][1])
