@@ -102,10 +102,11 @@ __device__ __forceinline__ double dot8(const double* __restrict__ a, size_t sa, 
 // reduces it) and to the rest of the trailing matrix during the pass of step
 // k+1, element by element as it is read for that step's product p = A22 v.
 // The pass sweeps the lower triangle in tiles of 4 w x 32 elements (w warps,
-// four rows a thread, lanes along a row), staged through shared memory
-// (sh.gt, two buffers) for the row sums (sum_j a_ij v_j, j <= i) and the
-// column sums (sum_i a_ij v_i, i > j) of the symmetric product; the loads of
-// the next tile are in flight meanwhile.
+// a warp four consecutive rows, lanes along a row), staged through shared
+// memory (sh.gt, two buffers); then half of the CTA forms the row sums
+// (sum_j a_ij v_j, j <= i) and the other half the column sums
+// (sum_i a_ij v_i, i > j) of the symmetric product, with the loads of the
+// next tile in flight.
 __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
     const int tid = threadIdx.x, nthr = (int)blockDim.x, nw = nthr >> 5, h = 4 * nw;
     const int wp = tid >> 5, ln = tid & 31;
@@ -147,25 +148,30 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
             double* B = A + (size_t)(k + 1) * n + k + 1;  // A22, ld n
             const int nbr = (L + h - 1) / h, nbc = (L + 31) >> 5;
             double a[4];
+            // warp wp owns rows 4 wp .. 4 wp + 3 of a tile (rows past L: the whole warp idles)
             auto load = [&](int I, int J) {
+                const int i0 = I * h + 4 * wp, j = 32 * J + ln;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = I * h + wp + nw * u, j = 32 * J + ln;
-                    a[u] = (i < L && j <= i) ? B[(size_t)i * n + j] : 0.0;
-                }
+                for (int u = 0; u < 4; ++u) a[u] = (i0 + u < L && j <= i0 + u) ? B[(size_t)(i0 + u) * n + j] : 0.0;
             };
             int I = 0, J = 0, buf = 0;
             load(0, 0);
+            const int half = nthr >> 1, cg = nw >> 1;  // column-sum threads per column
             while (I < nbr) {
                 double* T = sh.gt + buf * (32 * 33);
+                {
+                    const int i0 = I * h + 4 * wp, j = 32 * J + ln;
+                    if (i0 < L) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int r = wp + nw * u, i = I * h + r, j = 32 * J + ln;
-                    if (pending && i < L && j <= i) {
-                        a[u] = fma(-vq[i + 1], wq[j + 1], fma(-wq[i + 1], vq[j + 1], a[u]));
-                        B[(size_t)i * n + j] = a[u];
+                        for (int u = 0; u < 4; ++u) {
+                            const int i = i0 + u;
+                            if (pending && i < L && j <= i) {
+                                a[u] = fma(-vq[i + 1], wq[j + 1], fma(-wq[i + 1], vq[j + 1], a[u]));
+                                B[(size_t)i * n + j] = a[u];
+                            }
+                            T[(4 * wp + u) * 33 + ln] = a[u];
+                        }
                     }
-                    T[r * 33 + ln] = a[u];
                 }
                 __syncthreads();
                 const int cI = I, cJ = J;
@@ -175,28 +181,28 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
                 }
                 if (I < nbr) load(I, J);
                 if (sums) {
-                    {  // row sums: eight threads a row, four columns each
-                        const int r = tid >> 3, q = tid & 7, i = cI * h + r;
+                    if (tid < half) {  // row sums (j <= i): four threads a row, eight columns each
+                        const int r = tid >> 2, q = tid & 3, i = cI * h + r;
                         double s = 0.0;
+                        if (i < L) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int j = 32 * cJ + 4 * q + u;
-                            if (j < L) s = fma(T[r * 33 + 4 * q + u], vc[j], s);
+                            for (int u = 0; u < 8; ++u) {
+                                const int j = 32 * cJ + 8 * q + u;
+                                if (j < L) s = fma(T[r * 33 + 8 * q + u], vc[j], s);
+                            }
                         }
                         s += __shfl_xor_sync(0xffffffffu, s, 1);
                         s += __shfl_xor_sync(0xffffffffu, s, 2);
-                        s += __shfl_xor_sync(0xffffffffu, s, 4);
                         if (q == 0 && i < L) wc[i] += s;
-                    }
-                    {  // column sums below the diagonal: w threads a column, four rows each
-                        const int c = tid / nw, g = tid - c * nw, j = 32 * cJ + c;
+                    } else {  // column sums below the diagonal: w/2 threads a column, eight rows each
+                        const int t = tid - half, c = t / cg, g = t - c * cg, j = 32 * cJ + c;
                         double s = 0.0;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int r = g + nw * u, i = cI * h + r;
+                        for (int u = 0; u < 8; ++u) {
+                            const int r = 8 * g + u, i = cI * h + r;
                             if (i < L && i != j) s = fma(T[r * 33 + c], vc[i], s);
                         }
-                        for (int o = 1; o < nw; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        for (int o = 1; o < cg; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                         if (g == 0 && j < L) pc[j] += s;
                     }
                 }
