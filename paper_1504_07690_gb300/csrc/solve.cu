@@ -34,6 +34,7 @@ namespace {
 constexpr int NT = 256;          // largest CTA (solve_threads picks the size per n_v)
 constexpr int MAXN = 1024;       // largest n_v
 constexpr int MAX_QL_ITER = 60;
+constexpr int BT_CHUNKS = 8;     // columns a lane keeps in registers in back_transform: 32 x 8
 
 struct Shared {
     double* d;     // n: diagonal, then eigenvalues
@@ -92,24 +93,95 @@ __device__ __forceinline__ double dot8(const double* __restrict__ a, size_t sa, 
     return ((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7));
 }
 
+// One pass over the lower triangle of the symmetric L x L block B (ld n): when
+// `pending`, the rank-2 update B -= v' w'^T + w' v'^T with v' = vq + 1, w' = wq + 1
+// (the update's vectors start one row above B) is applied to each element as it is
+// read and stored back; when `sums`, wc[i] += sum_{j <= i} b_ij vc_j and
+// pc[j] += sum_{i > j} b_ij vc_i (wc, pc zeroed by the caller), so that wc + pc = B vc.
+// The lower triangle is swept in tiles of 4 w x 32 elements (w warps, a warp four
+// consecutive rows, lanes along a row), staged through shared memory (sh.gt, two
+// buffers); then half of the CTA forms the row sums and the other half the column
+// sums, with the loads of the next tile in flight.  Ends with a barrier.
+__device__ void sym_pass(double* __restrict__ B, int n, int L, const double* vq, const double* wq, bool pending,
+                         const double* vc, bool sums, double* wc, double* pc, Shared& sh) {
+    const int tid = threadIdx.x, nthr = (int)blockDim.x, nw = nthr >> 5, h = 4 * nw;
+    const int wp = tid >> 5, ln = tid & 31;
+    const int nbr = (L + h - 1) / h, nbc = (L + 31) >> 5;
+    double a[4];
+    // warp wp owns rows 4 wp .. 4 wp + 3 of a tile (rows past L: the whole warp idles)
+    auto load = [&](int I, int J) {
+        const int i0 = I * h + 4 * wp, j = 32 * J + ln;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = (i0 + u < L && j <= i0 + u) ? B[(size_t)(i0 + u) * n + j] : 0.0;
+    };
+    int I = 0, J = 0, buf = 0;
+    load(0, 0);
+    const int half = nthr >> 1, cg = nw >> 1;  // column-sum threads per column
+    while (I < nbr) {
+        double* T = sh.gt + buf * (32 * 33);
+        {
+            const int i0 = I * h + 4 * wp, j = 32 * J + ln;
+            if (i0 < L) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u;
+                    if (pending && i < L && j <= i) {
+                        a[u] = fma(-vq[i + 1], wq[j + 1], fma(-wq[i + 1], vq[j + 1], a[u]));
+                        B[(size_t)i * n + j] = a[u];
+                    }
+                    T[(4 * wp + u) * 33 + ln] = a[u];
+                }
+            }
+        }
+        __syncthreads();
+        const int cI = I, cJ = J;
+        if (++J > min(nbc - 1, (I * h + h - 1) >> 5)) {
+            ++I;
+            J = 0;
+        }
+        if (I < nbr) load(I, J);
+        if (sums) {
+            if (tid < half) {  // row sums (j <= i): four threads a row, eight columns each
+                const int r = tid >> 2, q = tid & 3, i = cI * h + r;
+                double s = 0.0;
+                if (i < L) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = 32 * cJ + 8 * q + u;
+                        if (j < L) s = fma(T[r * 33 + 8 * q + u], vc[j], s);
+                    }
+                }
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                if (q == 0 && i < L) wc[i] += s;
+            } else {  // column sums below the diagonal: w/2 threads a column, eight rows each
+                const int t = tid - half, c = t / cg, g = t - c * cg, j = 32 * cJ + c;
+                double s = 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int r = 8 * g + u, i = cI * h + r;
+                    if (i < L && i != j) s = fma(T[r * 33 + c], vc[i], s);
+                }
+                for (int o = 1; o < cg; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (g == 0 && j < L) pc[j] += s;
+            }
+        }
+        buf ^= 1;
+    }
+    __syncthreads();
+}
+
 // Householder reduction of the symmetric n x n matrix A (row-major, ld n) to
 // tridiagonal T = H^T A H: sh.d, sh.off receive T; row k of A (columns k+1..)
 // receives the k-th Householder vector and sh.beta[k] its scalar.  Only the
 // lower triangle of A is read and kept up to date.
 //
-// One pass over the trailing matrix per column: the rank-2 update
+// One pass over the trailing matrix per column (sym_pass): the rank-2 update
 // A22 -= v w^T + w v^T of step k is applied to column k+1 at once (step k+1
 // reduces it) and to the rest of the trailing matrix during the pass of step
 // k+1, element by element as it is read for that step's product p = A22 v.
-// The pass sweeps the lower triangle in tiles of 4 w x 32 elements (w warps,
-// a warp four consecutive rows, lanes along a row), staged through shared
-// memory (sh.gt, two buffers); then half of the CTA forms the row sums
-// (sum_j a_ij v_j, j <= i) and the other half the column sums
-// (sum_i a_ij v_i, i > j) of the symmetric product, with the loads of the
-// next tile in flight.
 __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
-    const int tid = threadIdx.x, nthr = (int)blockDim.x, nw = nthr >> 5, h = 4 * nw;
-    const int wp = tid >> 5, ln = tid & 31;
+    const int tid = threadIdx.x, nthr = (int)blockDim.x;
     double* vc = sh.v;   // this step's Householder vector
     double* wc = sh.p;   // this step's row sums, then w
     double* vq = sh.rc;  // the pending update (previous step): v
@@ -144,72 +216,8 @@ __device__ void tridiagonalise(double* __restrict__ A, int n, Shared& sh) {
         const bool sums = beta != 0.0;
         if (sums)  // keep v in row k (right of the diagonal, unused by the reduction) for the accumulation
             for (int i = tid; i < L; i += nthr) A[(size_t)k * n + k + 1 + i] = vc[i];
-        if (sums || pending) {
-            double* B = A + (size_t)(k + 1) * n + k + 1;  // A22, ld n
-            const int nbr = (L + h - 1) / h, nbc = (L + 31) >> 5;
-            double a[4];
-            // warp wp owns rows 4 wp .. 4 wp + 3 of a tile (rows past L: the whole warp idles)
-            auto load = [&](int I, int J) {
-                const int i0 = I * h + 4 * wp, j = 32 * J + ln;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = (i0 + u < L && j <= i0 + u) ? B[(size_t)(i0 + u) * n + j] : 0.0;
-            };
-            int I = 0, J = 0, buf = 0;
-            load(0, 0);
-            const int half = nthr >> 1, cg = nw >> 1;  // column-sum threads per column
-            while (I < nbr) {
-                double* T = sh.gt + buf * (32 * 33);
-                {
-                    const int i0 = I * h + 4 * wp, j = 32 * J + ln;
-                    if (i0 < L) {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int i = i0 + u;
-                            if (pending && i < L && j <= i) {
-                                a[u] = fma(-vq[i + 1], wq[j + 1], fma(-wq[i + 1], vq[j + 1], a[u]));
-                                B[(size_t)i * n + j] = a[u];
-                            }
-                            T[(4 * wp + u) * 33 + ln] = a[u];
-                        }
-                    }
-                }
-                __syncthreads();
-                const int cI = I, cJ = J;
-                if (++J > min(nbc - 1, (I * h + h - 1) >> 5)) {
-                    ++I;
-                    J = 0;
-                }
-                if (I < nbr) load(I, J);
-                if (sums) {
-                    if (tid < half) {  // row sums (j <= i): four threads a row, eight columns each
-                        const int r = tid >> 2, q = tid & 3, i = cI * h + r;
-                        double s = 0.0;
-                        if (i < L) {
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const int j = 32 * cJ + 8 * q + u;
-                                if (j < L) s = fma(T[r * 33 + 8 * q + u], vc[j], s);
-                            }
-                        }
-                        s += __shfl_xor_sync(0xffffffffu, s, 1);
-                        s += __shfl_xor_sync(0xffffffffu, s, 2);
-                        if (q == 0 && i < L) wc[i] += s;
-                    } else {  // column sums below the diagonal: w/2 threads a column, eight rows each
-                        const int t = tid - half, c = t / cg, g = t - c * cg, j = 32 * cJ + c;
-                        double s = 0.0;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int r = 8 * g + u, i = cI * h + r;
-                            if (i < L && i != j) s = fma(T[r * 33 + c], vc[i], s);
-                        }
-                        for (int o = 1; o < cg; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if (g == 0 && j < L) pc[j] += s;
-                    }
-                }
-                buf ^= 1;
-            }
-            __syncthreads();
-        }
+        if (sums || pending)
+            sym_pass(A + (size_t)(k + 1) * n + k + 1, n, L, vq, wq, pending, vc, sums, wc, pc, sh);
         if (sums) {
             for (int i = tid; i < L; i += nthr) wc[i] = beta * (wc[i] + pc[i]);
             __syncthreads();
@@ -1040,6 +1048,68 @@ __device__ void twisted_vectors(int n, int r, double* __restrict__ Z, double* __
     __syncthreads();
 }
 
+// back_transform for NC x 32 columns or fewer (r > 32 (NC - 1)): lanes along the r
+// columns of a row (contiguous in Z), warps splitting the rows, a lane's NC columns in
+// independent accumulators; per-warp partial dots summed through shared memory.
+template <int NC>
+__device__ void back_transform_cols(const double* __restrict__ A, int n, double* __restrict__ Z, int ldz, int r,
+                                    const Shared& sh) {
+    const int nw = (int)(blockDim.x >> 5);
+    const int tid = threadIdx.x, wp = tid >> 5, ln = tid & 31;
+    double* part = sh.gt;        // [nw][r]
+    double* fq = sh.gt + nw * r;  // [r]
+    for (int k = n - 3; k >= 0; --k) {
+        const double beta = sh.beta[k];
+        if (beta == 0.0) continue;
+        const int L = n - k - 1;
+        const double* v = A + (size_t)k * n + k + 1;
+        double* zk = Z + (size_t)(k + 1) * ldz;
+        // a lane's columns ln + 32 c (c < NC), two rows at a time, in independent accumulators
+        double acc[NC], acc2[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = acc2[c] = 0.0;
+        int j = wp;
+        for (; j + nw < L; j += 2 * nw) {
+            const double v0 = v[j], v1 = v[j + nw];
+            const double* z0 = zk + (size_t)j * ldz + ln;
+            const double* z1 = z0 + (size_t)nw * ldz;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (ln + 32 * c < r) {
+                    acc[c] = fma(v0, z0[32 * c], acc[c]);
+                    acc2[c] = fma(v1, z1[32 * c], acc2[c]);
+                }
+        }
+        if (j < L) {
+            const double v0 = v[j];
+            const double* z0 = zk + (size_t)j * ldz + ln;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (ln + 32 * c < r) acc[c] = fma(v0, z0[32 * c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            if (ln + 32 * c < r) part[wp * r + ln + 32 * c] = acc[c] + acc2[c];
+        __syncthreads();
+        for (int q = tid; q < r; q += (int)blockDim.x) {
+            double f = 0.0;
+            for (int w = 0; w < nw; ++w) f += part[w * r + q];
+            fq[q] = beta * f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = ln + 32 * c < r ? fq[ln + 32 * c] : 0.0;
+        for (int j = wp; j < L; j += nw) {
+            const double vj = v[j];
+            double* zr = zk + (size_t)j * ldz + ln;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (ln + 32 * c < r) zr[32 * c] = fma(-acc[c], vj, zr[32 * c]);
+        }
+        __syncthreads();
+    }
+}
+
 // z <- H z for the r columns of Z (ld ldz), H = H_0 H_1 ... H_{n-3} the
 // Householder factor left by tridiagonalise (vector k in row k of A from column
 // k+1, scalar sh.beta[k]): the eigenvectors of T become those of the matrix it
@@ -1068,40 +1138,16 @@ __device__ void back_transform(const double* __restrict__ A, int n, double* __re
         __syncthreads();
         return;
     }
-    if ((nw + 1) * r <= 3 * 32 * 33) {
-        // more columns: lanes along the r columns of a row (contiguous in Z), warps
-        // splitting the rows; per-warp partial dots summed through shared memory
-        const int tid = threadIdx.x, wp = tid >> 5, ln = tid & 31;
-        double* part = sh.gt;        // [nw][r]
-        double* fq = sh.gt + nw * r;  // [r]
-        for (int k = n - 3; k >= 0; --k) {
-            const double beta = sh.beta[k];
-            if (beta == 0.0) continue;
-            const int L = n - k - 1;
-            const double* v = A + (size_t)k * n + k + 1;
-            double* zk = Z + (size_t)(k + 1) * ldz;
-            for (int q = ln; q < r; q += 32) {
-                double s0 = 0.0, s1 = 0.0;
-                int j = wp;
-                for (; j + nw < L; j += 2 * nw) {
-                    s0 = fma(v[j], zk[(size_t)j * ldz + q], s0);
-                    s1 = fma(v[j + nw], zk[(size_t)(j + nw) * ldz + q], s1);
-                }
-                if (j < L) s0 = fma(v[j], zk[(size_t)j * ldz + q], s0);
-                part[wp * r + q] = s0 + s1;
-            }
-            __syncthreads();
-            for (int q = tid; q < r; q += (int)blockDim.x) {
-                double f = 0.0;
-                for (int w = 0; w < nw; ++w) f += part[w * r + q];
-                fq[q] = beta * f;
-            }
-            __syncthreads();
-            for (int q = ln; q < r; q += 32) {
-                const double f = fq[q];
-                for (int j = wp; j < L; j += nw) zk[(size_t)j * ldz + q] = fma(-f, v[j], zk[(size_t)j * ldz + q]);
-            }
-            __syncthreads();
+    if ((nw + 1) * r <= 3 * 32 * 33 && r <= 32 * BT_CHUNKS) {
+        switch ((r + 31) >> 5) {
+            case 1: back_transform_cols<1>(A, n, Z, ldz, r, sh); break;
+            case 2: back_transform_cols<2>(A, n, Z, ldz, r, sh); break;
+            case 3: back_transform_cols<3>(A, n, Z, ldz, r, sh); break;
+            case 4: back_transform_cols<4>(A, n, Z, ldz, r, sh); break;
+            case 5: back_transform_cols<5>(A, n, Z, ldz, r, sh); break;
+            case 6: back_transform_cols<6>(A, n, Z, ldz, r, sh); break;
+            case 7: back_transform_cols<7>(A, n, Z, ldz, r, sh); break;
+            default: back_transform_cols<8>(A, n, Z, ldz, r, sh); break;
         }
         return;
     }
@@ -1153,80 +1199,76 @@ __device__ void householder_qr_cols(double* __restrict__ Q, int ldq, int n, int 
     }
 }
 
-// K <- H_j K H_j on the trailing blocks K[j.., j..] of the two symmetric n x n
-// matrices K = K1, K2 (ld n), H_j = I - beta u u^T with u = column j of Q (rows j..,
-// ld ldq), beta = sh.beta[j]: p = beta K u, w = p - (beta/2)(u^T p) u,
-// K -= u w^T + w u^T.  Rows and columns below j are left as they are: the trailing
-// blocks of later reflections never read them.  sh.v holds u, sh.p and sh.rc the two
-// p/w, sh.rs the two block sums.
-__device__ void reflect_two_sided2(double* __restrict__ K1, double* __restrict__ K2, int n,
-                                   const double* __restrict__ Q, int ldq, int j, Shared& sh) {
+// The d reflections H_0 .. H_{d-1} (H_j = I - beta_j u_j u_j^T, u_j = column j of Q
+// from row j, ld ldq, beta_j = sh.beta[j]) applied two-sided to the symmetric n x n
+// K1 and K2 (ld n): on return the lower triangle of the trailing blocks K[d.., d..]
+// holds that of H_{d-1} .. H_0 K H_0 .. H_{d-1} (rows and columns above d and the
+// upper triangle are left stale).  As in tridiagonalise, the rank-2 update of
+// reflection j reaches the trailing block during the pass (sym_pass) that forms the
+// product K u_{j+1} of the next one: one read and one write of the lower triangle per
+// reflection and matrix.  Uses sh.v, sh.p, sh.rc, sh.rs, sh.d, sh.off as vectors.
+__device__ void reflect_all(double* __restrict__ K1, double* __restrict__ K2, int n, const double* __restrict__ Q,
+                            int ldq, int d, Shared& sh) {
     const int tid = threadIdx.x, nthr = (int)blockDim.x;
-    const double beta = sh.beta[j];
-    if (beta == 0.0) return;
-    const int L = n - j;
-    double* u = sh.v;
-    double* w1 = sh.p;
-    double* w2 = sh.rc;
-    for (int i = tid; i < L; i += nthr) u[i] = Q[(size_t)(j + i) * ldq + j];
-    __syncthreads();
-    double g1 = 0.0, g2 = 0.0;
-    for (int i = tid; i < L; i += nthr) {
-        // column i of the symmetric blocks (consecutive threads read consecutive doubles)
-        const double p1 = beta * dot8(K1 + (size_t)j * n + j + i, n, u, 1, L);
-        const double p2 = beta * dot8(K2 + (size_t)j * n + j + i, n, u, 1, L);
-        w1[i] = p1;
-        w2[i] = p2;
-        g1 = fma(p1, u[i], g1);
-        g2 = fma(p2, u[i], g2);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-    }
-    if ((tid & 31) == 0) {
-        sh.red[tid >> 5] = g1;
-        sh.rs[tid >> 5] = g2;
-    }
-    __syncthreads();
-    double c1 = 0.0, c2 = 0.0;
-    for (int w = 0; w < (nthr >> 5); ++w) {
-        c1 += sh.red[w];
-        c2 += sh.rs[w];
-    }
-    c1 *= 0.5 * beta;
-    c2 *= 0.5 * beta;
-    __syncthreads();
-    for (int i = tid; i < L; i += nthr) {
-        w1[i] = fma(-c1, u[i], w1[i]);
-        w2[i] = fma(-c2, u[i], w2[i]);
-    }
-    __syncthreads();
-    // rank-2 updates, element-parallel, four elements of each matrix in flight a thread
-    const int LL = L * L;
-    for (int e0 = tid; e0 < LL; e0 += 4 * nthr) {
-        double a1[4], a2[4];
-        int ri[4], ci[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = e0 + q * nthr;
-            ri[q] = e / L;
-            ci[q] = e - ri[q] * L;
-            if (e < LL) {
-                a1[q] = K1[(size_t)(j + ri[q]) * n + j + ci[q]];
-                a2[q] = K2[(size_t)(j + ri[q]) * n + j + ci[q]];
-            }
+    double* uc = sh.v;   // this reflection's u
+    double* uq = sh.p;   // the pending one's
+    double* w1c = sh.rc;
+    double* w1q = sh.rs;
+    double* w2c = sh.d;
+    double* w2q = sh.off;
+    double* pc = sh.gt + 2 * 32 * 33;
+    bool pending = false;
+    for (int j = 0; j < d; ++j) {
+        const int L = n - j;
+        const double beta = sh.beta[j];
+        const bool act = beta != 0.0;
+        for (int i = tid; i < L; i += nthr) {
+            uc[i] = Q[(size_t)(j + i) * ldq + j];
+            w1c[i] = 0.0;
+            w2c[i] = 0.0;
+            pc[i] = 0.0;
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (e0 + q * nthr < LL) {
-                const int r = ri[q], c = ci[q];
-                K1[(size_t)(j + r) * n + j + c] = fma(-u[r], w1[c], fma(-w1[r], u[c], a1[q]));
-                K2[(size_t)(j + r) * n + j + c] = fma(-u[r], w2[c], fma(-w2[r], u[c], a2[q]));
+        __syncthreads();
+        if (act || pending) sym_pass(K1 + (size_t)j * n + j, n, L, uq, w1q, pending, uc, act, w1c, pc, sh);
+        if (act) {
+            for (int i = tid; i < L; i += nthr) {
+                w1c[i] = beta * (w1c[i] + pc[i]);
+                pc[i] = 0.0;
             }
+            __syncthreads();
         }
+        if (act || pending) sym_pass(K2 + (size_t)j * n + j, n, L, uq, w2q, pending, uc, act, w2c, pc, sh);
+        if (act) {
+            for (int i = tid; i < L; i += nthr) w2c[i] = beta * (w2c[i] + pc[i]);
+            __syncthreads();
+            double g1 = 0.0, g2 = 0.0;
+            for (int i = tid; i < L; i += nthr) {
+                g1 = fma(w1c[i], uc[i], g1);
+                g2 = fma(w2c[i], uc[i], g2);
+            }
+            const double c1 = 0.5 * beta * block_sum(g1, sh.red);
+            const double c2 = 0.5 * beta * block_sum(g2, sh.red);
+            for (int i = tid; i < L; i += nthr) {  // p becomes w
+                w1c[i] = fma(-c1, uc[i], w1c[i]);
+                w2c[i] = fma(-c2, uc[i], w2c[i]);
+            }
+            __syncthreads();
+        }
+        pending = act;
+        double* t = uc;
+        uc = uq;
+        uq = t;
+        t = w1c;
+        w1c = w1q;
+        w1q = t;
+        t = w2c;
+        w2c = w2q;
+        w2q = t;
     }
-    __syncthreads();
+    if (pending) {  // the last reflection's update on the trailing blocks
+        sym_pass(K1 + (size_t)d * n + d, n, n - d, uq, w1q, true, nullptr, false, nullptr, nullptr, sh);
+        sym_pass(K2 + (size_t)d * n + d, n, n - d, uq, w2q, true, nullptr, false, nullptr, nullptr, sh);
+    }
 }
 
 // Eigen-decomposition of the symmetric n x n matrix A (destroyed): sh.d gets
@@ -1442,11 +1484,12 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                         T1[e] = 0.5 * (Zk[(size_t)i * n + j] + Zk[(size_t)j * n + i]);
                     }
                     __syncthreads();
-                    for (int j = 0; j < dn; ++j) reflect_two_sided2(Y, T1, n, Zt, n, j, sh);
-                    for (int e = tid; e < rk * rk; e += (int)blockDim.x) {
+                    reflect_all(Y, T1, n, Zt, n, dn, sh);
+                    for (int e = tid; e < rk * rk; e += (int)blockDim.x) {  // lower triangles, mirrored
                         const int i = e / rk, j = e - i * rk;
-                        A[e] = Y[(size_t)(dn + i) * n + dn + j];
-                        Zt[e] = T1[(size_t)(dn + i) * n + dn + j];
+                        const size_t src = (size_t)(dn + max(i, j)) * n + dn + min(i, j);
+                        A[e] = Y[src];
+                        Zt[e] = T1[src];
                     }
                     __syncthreads();
                     Lw = A;
