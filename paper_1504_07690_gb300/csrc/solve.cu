@@ -107,15 +107,28 @@ __device__ void sym_pass(double* __restrict__ B, int n, int L, const double* vq,
     const int tid = threadIdx.x, nthr = (int)blockDim.x, nw = nthr >> 5, h = 4 * nw;
     const int wp = tid >> 5, ln = tid & 31;
     const int nbr = (L + h - 1) / h, nbc = (L + 31) >> 5;
-    double a[4];
+    double a[4], an[4];  // this tile's elements, the next tile's (loads two tiles ahead)
     // warp wp owns rows 4 wp .. 4 wp + 3 of a tile (rows past L: the whole warp idles)
-    auto load = [&](int I, int J) {
+    auto load_next = [&](int I, int J) {
         const int i0 = I * h + 4 * wp, j = 32 * J + ln;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = (i0 + u < L && j <= i0 + u) ? B[(size_t)(i0 + u) * n + j] : 0.0;
+        for (int u = 0; u < 4; ++u) an[u] = (i0 + u < L && j <= i0 + u) ? B[(size_t)(i0 + u) * n + j] : 0.0;
+    };
+    auto advance = [&](int& I, int& J) {  // the next tile of the lower triangle, row block by row block
+        if (++J > min(nbc - 1, (I * h + h - 1) >> 5)) {
+            ++I;
+            J = 0;
+        }
     };
     int I = 0, J = 0, buf = 0;
-    load(0, 0);
+    int I1 = 0, J1 = 0;
+    advance(I1, J1);  // tile after (I, J)
+    int I2 = I1, J2 = J1;
+    advance(I2, J2);  // two tiles after
+    load_next(0, 0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = an[u];
+    if (I1 < nbr) load_next(I1, J1);
     const int half = nthr >> 1, cg = nw >> 1;  // column-sum threads per column
     while (I < nbr) {
         double* T = sh.gt + buf * (32 * 33);
@@ -135,11 +148,14 @@ __device__ void sym_pass(double* __restrict__ B, int n, int L, const double* vq,
         }
         __syncthreads();
         const int cI = I, cJ = J;
-        if (++J > min(nbc - 1, (I * h + h - 1) >> 5)) {
-            ++I;
-            J = 0;
-        }
-        if (I < nbr) load(I, J);
+        I = I1;
+        J = J1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = an[u];
+        I1 = I2;
+        J1 = J2;
+        if (I1 < nbr) load_next(I1, J1);
+        advance(I2, J2);
         if (sums) {
             if (tid < half) {  // row sums (j <= i): four threads a row, eight columns each
                 const int r = tid >> 2, q = tid & 3, i = cI * h + r;
@@ -1727,47 +1743,52 @@ size_t solve_workspace_bytes(int n_v) {
 // points that kept part of the directions (the longest, bound by float64 issue) take
 // blocks 0.. and their SMs' other slots go to points that kept nothing (the shortest)
 // or stay empty, as far as free slots allow; every other point fills the rest in order.
-// One thread; perm has S k entries.
+// One CTA (the placement by one thread, in shared memory); perm has S k entries.
 __global__ void solve_schedule_kernel(const int32_t* __restrict__ rank_prev, int64_t n_t, int n, int S, int k,
-                                      int32_t* __restrict__ perm) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                                      int32_t* __restrict__ perm_out) {
+    extern __shared__ int32_t sched[];  // perm (S k), then the route class of each point
     const int64_t slots = (int64_t)S * k;
-    auto cls = [&](int64_t i) {  // 0 nothing kept, 1 part, 2 everything
+    int32_t* perm = sched;
+    int32_t* cl = sched + slots;  // 0 nothing kept, 1 part, 2 everything
+    for (int64_t i = threadIdx.x; i < n_t; i += blockDim.x) {
         const int r = rank_prev[2 * i];
-        return r <= 0 ? 0 : (r >= n ? 2 : 1);
-    };
-    for (int64_t b = 0; b < slots; ++b) perm[b] = -2;  // unassigned
-    int64_t free_slots = slots - n_t;
-    int np = 0;
-    int64_t ce = 0;  // cursor over the points that kept nothing
-    for (int64_t i = 0; i < n_t && np < S; ++i)
-        if (cls(i) == 1) perm[np++] = (int32_t)i;
-    for (int s = 0; s < np; ++s)
-        for (int j = 1; j < k; ++j) {
-            while (ce < n_t && cls(ce) != 0) ++ce;
-            if (ce < n_t) {
-                perm[s + (int64_t)j * S] = (int32_t)ce++;
-            } else if (free_slots > 0) {
-                perm[s + (int64_t)j * S] = -1;
-                --free_slots;
-            }
-        }
-    // the rest in order: points not placed yet into the unassigned slots
-    int64_t b = 0;
-    int placed_part = 0;
-    for (int64_t i = 0; i < n_t; ++i) {
-        const int c = cls(i);
-        if (c == 1 && placed_part < np) {
-            ++placed_part;
-            continue;
-        }
-        if (c == 0 && i < ce) continue;  // placed next to a part point (cursor passed it)
-        while (b < slots && perm[b] != -2) ++b;
-        if (b >= slots) break;  // cannot happen: holes never exceed the free slots
-        perm[b++] = (int32_t)i;
+        cl[i] = r <= 0 ? 0 : (r >= n ? 2 : 1);
     }
-    for (; b < slots; ++b)
-        if (perm[b] == -2) perm[b] = -1;
+    for (int64_t b = threadIdx.x; b < slots; b += blockDim.x) perm[b] = -2;  // unassigned
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t free_slots = slots - n_t;
+        int np = 0;
+        int64_t ce = 0;  // cursor over the points that kept nothing
+        for (int64_t i = 0; i < n_t && np < S; ++i)
+            if (cl[i] == 1) perm[np++] = (int32_t)i;
+        for (int s = 0; s < np; ++s)
+            for (int j = 1; j < k; ++j) {
+                while (ce < n_t && cl[ce] != 0) ++ce;
+                if (ce < n_t) {
+                    perm[s + (int64_t)j * S] = (int32_t)ce++;
+                } else if (free_slots > 0) {
+                    perm[s + (int64_t)j * S] = -1;
+                    --free_slots;
+                }
+            }
+        // the rest in order: points not placed yet into the unassigned slots
+        int64_t b = 0;
+        int placed_part = 0;
+        for (int64_t i = 0; i < n_t; ++i) {
+            const int c = cl[i];
+            if (c == 1 && placed_part < np) {
+                ++placed_part;
+                continue;
+            }
+            if (c == 0 && i < ce) continue;  // placed next to a part point (cursor passed it)
+            while (b < slots && perm[b] != -2) ++b;
+            if (b >= slots) break;  // cannot happen: holes never exceed the free slots
+            perm[b++] = (int32_t)i;
+        }
+    }
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < slots; b += blockDim.x) perm_out[b] = perm[b] == -2 ? -1 : perm[b];
 }
 
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh, double tau,
@@ -1809,7 +1830,9 @@ cudaError_t launch_solve_schedule(const int32_t* rank_prev, int64_t n_t, int n_v
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t slots = solve_slots(n_v);
     if (slots < n_t || slots <= 0) return cudaErrorInvalidValue;
-    solve_schedule_kernel<<<1, 32, 0, s>>>(rank_prev, n_t, n_v, sms, (int)(slots / sms), perm);
+    const size_t smem = (size_t)(slots + n_t) * sizeof(int32_t);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    solve_schedule_kernel<<<1, 256, smem, s>>>(rank_prev, n_t, n_v, sms, (int)(slots / sms), perm);
     return cudaGetLastError();
 }
 
