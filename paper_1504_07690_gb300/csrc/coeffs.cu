@@ -29,11 +29,14 @@ __global__ void cos_table_kernel(double* ctab, int n_theta) {
 }
 
 // One CTA per sweep point; threads over l.  g is staged chunk by chunk in
-// shared memory.
+// shared memory.  A narrow Gaussian is exactly 0 (exp underflows) at most nodes:
+// the sums of a chunk run over its nonzero span only (the zero terms it skips add
+// nothing, so the result is the same to the bit).
 __global__ void __launch_bounds__(256)
 mu_kernel(const double* __restrict__ t, int64_t n_t, double sigma, double inv_norm, double xc, double xh,
           int M, int n_theta, const double* __restrict__ ctab, double* __restrict__ mu, int ldmu) {
     __shared__ double gs[GCHUNK];
+    __shared__ int span[2];  // first and last nonzero g of the chunk
     const int n2 = 2 * n_theta;
     const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
     for (int64_t it = blockIdx.x; it < n_t; it += gridDim.x) {
@@ -45,20 +48,37 @@ mu_kernel(const double* __restrict__ t, int64_t n_t, double sigma, double inv_no
         for (int j0 = 0; j0 <= n_theta; j0 += GCHUNK) {
             const int jn = min(GCHUNK, n_theta + 1 - j0);
             __syncthreads();
+            if (threadIdx.x == 0) {
+                span[0] = jn;
+                span[1] = -1;
+            }
+            __syncthreads();
+            int lo = jn, hi = -1;
             for (int jj = threadIdx.x; jj < jn; jj += blockDim.x) {
                 const int j = j0 + jj;
                 const double x = xc + xh * ctab[j];
                 const double u = ti - x;
                 const double w = (j == 0 || j == n_theta) ? 1.0 : 2.0;
-                gs[jj] = w * (exp(-u * u * inv2s2) * inv_norm);
+                const double g = w * (exp(-u * u * inv2s2) * inv_norm);
+                gs[jj] = g;
+                if (g != 0.0) {
+                    lo = min(lo, jj);
+                    hi = max(hi, jj);
+                }
+            }
+            if (hi >= 0) {
+                atomicMin(&span[0], lo);
+                atomicMax(&span[1], hi);
             }
             __syncthreads();
+            const int jlo = span[0], jhi = span[1];
+            if (jhi < jlo) continue;  // the whole chunk is zero
             for (int r = 0; r < nl && r < 8; ++r) {
                 const int l = threadIdx.x + 256 * r;
                 if (l > M) break;
                 double acc = 0.0;
-                int m = (int)(((int64_t)j0 * l) % n2);
-                for (int jj = 0; jj < jn; ++jj) {
+                int m = (int)(((int64_t)(j0 + jlo) * l) % n2);
+                for (int jj = jlo; jj <= jhi; ++jj) {
                     acc = fma(gs[jj], ctab[m], acc);
                     m += l;
                     if (m >= n2) m -= n2;
