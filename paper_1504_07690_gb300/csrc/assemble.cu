@@ -132,12 +132,13 @@ __global__ void split_pairs_kernel(const double* __restrict__ v, int64_t n, floa
     }
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 assemble_df_kernel(const float* __restrict__ coef_hi, const float* __restrict__ coef_lo, int ldc, int64_t n_t, int L,
                    const float* __restrict__ X_hi, const float* __restrict__ X_lo, int n_tot, int rows, int cols,
                    double* __restrict__ out) {
-    __shared__ float Ch[TL][TT + 1], Cl[TL][TT + 1];
-    __shared__ float Xh[TL][TE], Xl[TL][TE];
+    // two slab buffers: the next slab's values wait in registers while this one is summed
+    __shared__ float Ch[2][TL][TT + 1], Cl[2][TL][TT + 1];
+    __shared__ float Xh[2][TL][TE], Xl[2][TL][TE];
     __shared__ int xoff[TE];
     __shared__ int ooff[2 * TE];
     const int64_t ne = (int64_t)rows * (rows + 1) / 2;
@@ -171,44 +172,54 @@ assemble_df_kernel(const float* __restrict__ coef_hi, const float* __restrict__ 
 #pragma unroll
         for (int q = 0; q < 4; ++q) sh_[p][q] = sl_[p][q] = 0.f;
     __syncthreads();
-    for (int l0 = 0; l0 < L; l0 += TL) {
-        for (int e = threadIdx.x; e < TL * TT; e += 256) {
-            const int ll = e / TT, tt = e - ll * TT;
+    // thread -> slab elements: (ll, tt) = (e / TT, e % TT) and (ll, ee) = (e / TE, e % TE),
+    // e = threadIdx.x + 256 u, u < 4 (TL TT = TL TE = 1024 = 4 x 256)
+    float pch[4], pcl[4], pxh[4], pxl[4];
+    auto fetch = [&](int l0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            const int ll = e / TT, tt = e - ll * TT, ee = e - ll * TE;
+            const int l = l0 + ll;
             const int64_t ti = t0 + tt;
-            const int l = l0 + ll;
-            float h = 0.f, lo = 0.f;
+            pch[u] = pcl[u] = pxh[u] = pxl[u] = 0.f;
             if (ti < n_t && l < L) {
-                h = coef_hi[ti * ldc + l];
-                lo = coef_lo[ti * ldc + l];
+                pch[u] = coef_hi[ti * ldc + l];
+                pcl[u] = coef_lo[ti * ldc + l];
             }
-            Ch[ll][tt] = h;
-            Cl[ll][tt] = lo;
-        }
-        for (int e = threadIdx.x; e < TL * TE; e += 256) {
-            const int ll = e / TE, ee = e - ll * TE;
-            const int l = l0 + ll;
             const int off = xoff[ee];
-            float h = 0.f, lo = 0.f;
             if (off >= 0 && l < L) {
-                h = X_hi[(size_t)l * nn + off];
-                lo = X_lo[(size_t)l * nn + off];
+                pxh[u] = X_hi[(size_t)l * nn + off];
+                pxl[u] = X_lo[(size_t)l * nn + off];
             }
-            Xh[ll][ee] = h;
-            Xl[ll][ee] = lo;
         }
-        __syncthreads();
+    };
+    fetch(0);
+    int buf = 0;
+    for (int l0 = 0; l0 < L; l0 += TL) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            const int ll = e / TT, tt = e - ll * TT, ee = e - ll * TE;
+            Ch[buf][ll][tt] = pch[u];
+            Cl[buf][ll][tt] = pcl[u];
+            Xh[buf][ll][ee] = pxh[u];
+            Xl[buf][ll][ee] = pxl[u];
+        }
+        __syncthreads();  // this slab staged; the slab before it (other buffer) no longer read
+        if (l0 + TL < L) fetch(l0 + TL);
 #pragma unroll 4
         for (int ll = 0; ll < TL; ++ll) {
             float ch[4], cl[4], xh[4], xl[4];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                ch[p] = Ch[ll][ty * 4 + p];
-                cl[p] = Cl[ll][ty * 4 + p];
+                ch[p] = Ch[buf][ll][ty * 4 + p];
+                cl[p] = Cl[buf][ll][ty * 4 + p];
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                xh[q] = Xh[ll][tx + 16 * q];
-                xl[q] = Xl[ll][tx + 16 * q];
+                xh[q] = Xh[buf][ll][tx + 16 * q];
+                xl[q] = Xl[buf][ll][tx + 16 * q];
             }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
@@ -227,7 +238,7 @@ assemble_df_kernel(const float* __restrict__ coef_hi, const float* __restrict__ 
                     sl_[p][q] += tw + err;
                 }
         }
-        __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
