@@ -11,18 +11,24 @@
 //   5. C~ = U~ S~^-1/2 X~
 //   phi = sum xi~ + (Tr K_W~ - ||K_C C~||_F^2) / N~_v   (second term only if N~_v > 0)
 //
-// Symmetric eigensolver (float64 is 1/58 of the float32 rate on this part,
-// so the flop count matters): Householder reduction to tridiagonal form,
-// explicit accumulation of the orthogonal factor, then the implicit-shift QL
-// iteration on the tridiagonal matrix (the Householder/QL method of Martin,
-// Reinsch and Wilkinson, Numer. Math. 11, 1968), ~7.7 n^3 flops with vectors.
-// In each QL sweep one thread computes the chain of plane rotations and the
-// whole CTA then applies it to the eigenvector rows, one column per thread,
-// coalesced.  Eigenvalues of B alone (no hybrid correction) skip the
-// accumulation and the QL sweeps: they come from bisection on Sturm counts,
-// one thread per eigenvalue (~0.7 n^3 flops for the reduction).
-// Matrices live in a per-CTA global workspace (L2 resident); eigenvectors
-// are kept as rows.  QL sweeps are bounded (60 per eigenvalue).
+// Float64 runs at 1/58 of the float32 rate on this part (2 FMA/clk per SM), so the
+// routes below are chosen to do the fewest float64 operations that settle each point
+// exactly (in floating point) as Alg. 4 and Alg. 6 define it:
+//   - r = 0 by the Gershgorin bound of K_W or one Cholesky of floor I - K_W;
+//   - r = n by one Cholesky of K_W - max(tau g, floor) I; then the inertia of the
+//     pencil (K_Z, K_W) against [xlo, xhi] by two Choleskys (congruence), and the sum
+//     as a trace from those factors (no eigenvalues), or else C = L^-1 K_Z L^-T reduced
+//     and bracketed;
+//   - 0 < r < n in a basis of the kept invariant subspace of K_W (Householder
+//     reduction, Sturm counts, twisted-factorization eigenvectors), then as above;
+//   - otherwise (hybrid columns, a failed check) Alg. 4 step by step: Householder
+//     reduction, accumulated factor, implicit-shift QL (Martin, Reinsch and Wilkinson,
+//     Numer. Math. 11, 1968), bounded at 60 sweeps per eigenvalue.
+// The Householder reduction makes one pass over the lower triangle per column
+// (sym_pass), bisection splits each bracket over a group of lanes, Cholesky factors and
+// AB^T products are blocked through shared-memory tiles.  Matrices live in a per-CTA
+// global workspace; a schedule from the previous launch's routes gives the slowest
+// points an SM without full-rank points beside them.
 #include <float.h>
 
 #include "internal.h"
