@@ -57,24 +57,39 @@ struct Shared {
     double* gt;    // 3 x 32 x 33: staged tiles of gemm_tn and cholesky_lower
 };
 
+// CTA-wide sum and maximum: per-warp shuffles, then warp 0 combines the (at most 8)
+// warp results and publishes the total in red[0] (float64 is slow on this part: one
+// warp does those few operations, not every thread).
 __device__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if (lane == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    if (threadIdx.x < 32) {
+        double s = lane < nw ? red[lane] : 0.0;
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    const double s = red[0];
     __syncthreads();
     return s;
 }
 
 __device__ double block_max(double v, double* red) {
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if (lane == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double s = red[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
+    if (threadIdx.x < 32) {
+        double s = lane < nw ? red[lane] : -DBL_MAX;
+        for (int o = 4; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    const double s = red[0];
     __syncthreads();
     return s;
 }
@@ -136,6 +151,7 @@ __device__ void sym_pass(double* __restrict__ B, int n, int L, const double* vq,
     for (int u = 0; u < 4; ++u) a[u] = an[u];
     if (I1 < nbr) load_next(I1, J1);
     const int half = nthr >> 1, cg = nw >> 1;  // column-sum threads per column
+    double racc = 0.0;  // row sums: this thread's part of its row over the row block's tiles
     while (I < nbr) {
         double* T = sh.gt + buf * (32 * 33);
         {
@@ -165,17 +181,20 @@ __device__ void sym_pass(double* __restrict__ B, int n, int L, const double* vq,
         if (sums) {
             if (tid < half) {  // row sums (j <= i): four threads a row, eight columns each
                 const int r = tid >> 2, q = tid & 3, i = cI * h + r;
-                double s = 0.0;
                 if (i < L) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int j = 32 * cJ + 8 * q + u;
-                        if (j < L) s = fma(T[r * 33 + 8 * q + u], vc[j], s);
+                        if (j < L) racc = fma(T[r * 33 + 8 * q + u], vc[j], racc);
                     }
                 }
-                s += __shfl_xor_sync(0xffffffffu, s, 1);
-                s += __shfl_xor_sync(0xffffffffu, s, 2);
-                if (q == 0 && i < L) wc[i] += s;
+                if (I != cI) {  // the row block ends with this tile (I: the next tile's)
+                    double s = racc;
+                    s += __shfl_xor_sync(0xffffffffu, s, 1);
+                    s += __shfl_xor_sync(0xffffffffu, s, 2);
+                    if (q == 0 && i < L) wc[i] += s;
+                    racc = 0.0;
+                }
             } else {  // column sums below the diagonal: w/2 threads a column, eight rows each
                 const int t = tid - half, c = t / cg, g = t - c * cg, j = 32 * cJ + c;
                 double s = 0.0;
