@@ -119,7 +119,20 @@ typedef struct {
                            bound; 2^-36 was the best of 2^-30..2^-40 against the float64
                            path on a 65536-row Anderson model), a negative value disables
                            the floor */
+    int32_t damping;    /* damping of the truncated Chebyshev series (the paper uses none; the
+                           factors are those of the KPM literature its KPM remark cites, Weisse
+                           et al., Rev. Mod. Phys. 78, 275 (2006)):  SSM_DAMP_NONE (0),
+                           SSM_DAMP_JACKSON (1): g_n = [(L-n+1) cos(pi n/(L+1))
+                           + sin(pi n/(L+1)) cot(pi/(L+1))] / (L+1),  SSM_DAMP_LORENTZ (2):
+                           g_n = sinh(lambda (1 - n/L)) / sinh(lambda), for a series of L terms.
+                           The KPM line's mu_l (L = M+1 terms) and Alg. 7's degree-M/2 mu_l
+                           (L = M/2+1 terms) are multiplied by their factors before anything is
+                           formed from them, so nu (Proposition 1) is the exact square of the
+                           damped series K_W uses.  Other values: SSM_EINVAL. */
+    double damping_lambda;  /* lambda of the Lorentz factors; <= 0 selects 4 */
 } ssm_params;
+
+enum { SSM_DAMP_NONE = 0, SSM_DAMP_JACKSON = 1, SSM_DAMP_LORENTZ = 2 };
 
 typedef struct ssm_plan_s* ssm_plan_t;
 
@@ -297,8 +310,10 @@ ssm_status ssm_gram_pair_noalloc(const double* A, const double* B, int64_t n_row
                                  int64_t ld, double* G_aa, double* G_ab, void* stream);
 
 /* Chebyshev coefficient tables of Alg. 1 and Proposition 1 at n_t points
- * (host or device t): mu: n_t x (M+1), mu_l(t_i) of g_sigma(t_i - .) in T_l(A~);
- * nu: n_t x (M+1), the coefficients of the square of the degree-M/2 series.
+ * (host or device t): mu: n_t x (M+1), mu_l(t_i) of g_sigma(t_i - .) in T_l(A~)
+ * (times the damping factors of M+1 terms when the plan damps);
+ * nu: n_t x (M+1), the coefficients of the square of the degree-M/2 series
+ * (of the damped series, factors of M/2+1 terms, when the plan damps).
  * Either output may be NULL.  Needs no moments. */
 ssm_status ssm_coefficients(ssm_plan_t plan, const double* t, int64_t n_t, double sigma,
                             double* mu, double* nu);

@@ -42,7 +42,8 @@ from scipy.special import erf
 __all__ = [
     "csr_matrix", "gershgorin", "spectral_interval", "transform",
     "g_sigma", "g_max", "dgc_coefficients", "squared_coefficients",
-    "coefficient_tables", "moments_direct", "moments_doubling",
+    "jackson_factors", "lorentz_factors", "damping_factors", "coefficient_tables",
+    "moments_direct", "moments_doubling",
     "kpm_dos", "assemble", "rounding_floor", "geneig", "ress_dos_point", "ress_dgc",
     "exact_dos", "relative_l1_error", "trace_grid", "deconvolve_h",
     "trace_f",
@@ -143,14 +144,55 @@ def squared_coefficients(mu_half: np.ndarray, M: int,
     return nu
 
 
+# --------------------------------------------------------------------------
+# Optional damping of the truncated series (the KPM literature the paper's
+# KPM remark cites: Weisse, Wellein, Alvermann and Fehske, Rev. Mod. Phys. 78,
+# 275 (2006), Section II.C).  The paper itself uses no damping; these factors
+# multiply mu_l before anything else is formed from them.
+# --------------------------------------------------------------------------
+
+def jackson_factors(n_mom: int) -> np.ndarray:
+    """Jackson factors g_n, n = 0..n_mom-1, for a series of n_mom terms.
+
+    g_n = [(n_mom - n + 1) cos(pi n / (n_mom + 1))
+           + sin(pi n / (n_mom + 1)) cot(pi / (n_mom + 1))] / (n_mom + 1),
+    the closed form of the kernel that is the squared modulus of a
+    sine-weighted trigonometric polynomial (so it is nonnegative and g_0 = 1).
+    """
+    n = np.arange(n_mom, dtype=np.float64)
+    q = math.pi / (n_mom + 1)
+    return ((n_mom - n + 1) * np.cos(q * n) + np.sin(q * n) / math.tan(q)) / (n_mom + 1)
+
+
+def lorentz_factors(n_mom: int, lam: float = 4.0) -> np.ndarray:
+    """Lorentz factors g_n = sinh(lam (1 - n / n_mom)) / sinh(lam), n < n_mom."""
+    n = np.arange(n_mom, dtype=np.float64)
+    return np.sinh(lam * (1.0 - n / n_mom)) / math.sinh(lam)
+
+
+def damping_factors(kind: int, n_mom: int, lam: float = 4.0) -> np.ndarray:
+    """0: none (the paper), 1: Jackson, 2: Lorentz with parameter lam."""
+    if kind == 0:
+        return np.ones(n_mom)
+    if kind == 1:
+        return jackson_factors(n_mom)
+    if kind == 2:
+        return lorentz_factors(n_mom, lam)
+    raise ValueError(f"unknown damping kind {kind}")
+
+
 def coefficient_tables(t: np.ndarray, M: int, sigma: float, N: int, a: float, b: float,
-                       n_theta: Optional[int] = None) -> Dict[str, np.ndarray]:
+                       n_theta: Optional[int] = None, damping: int = 0,
+                       lam: float = 4.0) -> Dict[str, np.ndarray]:
     """Per-sweep-point tables used by Algorithms 2 and 7.
 
     mu_full[i, l], l <= M (the DGC/KPM line, Alg. 2);
     mu_half[i, l], l <= M/2 and zero above (Alg. 7, step 1);
     nu[i, l], l <= M (Alg. 7, step 2, via Prop. 1).
     All three use the same 2 N_theta-point grid, N_theta = 2M by default.
+    With damping (see damping_factors) the degree-M series is multiplied by the
+    factors of M+1 terms and the degree-M/2 series by those of M/2+1 terms
+    before nu is formed, so nu stays the exact square of the series K_W uses.
     """
     if M % 2:
         raise ValueError("RESS-DGC needs an even degree M")
@@ -161,9 +203,11 @@ def coefficient_tables(t: np.ndarray, M: int, sigma: float, N: int, a: float, b:
     mu_full = np.zeros((nt, M + 1))
     mu_half = np.zeros((nt, M + 1))
     nu = np.zeros((nt, M + 1))
+    gf = damping_factors(damping, M + 1, lam)
+    gh = damping_factors(damping, M // 2 + 1, lam)
     for i in range(nt):
-        mu_full[i] = dgc_coefficients(t[i], M, sigma, N, a, b, n_theta)
-        mh = dgc_coefficients(t[i], M // 2, sigma, N, a, b, n_theta)
+        mu_full[i] = gf * dgc_coefficients(t[i], M, sigma, N, a, b, n_theta)
+        mh = gh * dgc_coefficients(t[i], M // 2, sigma, N, a, b, n_theta)
         mu_half[i, : M // 2 + 1] = mh
         nu[i] = squared_coefficients(mh, M, n_theta)
     return dict(mu_full=mu_full, mu_half=mu_half, nu=nu)
@@ -202,17 +246,15 @@ def moments_doubling(At: sp.spmatrix, W: np.ndarray, M: int) -> np.ndarray:
     W = np.asarray(W, dtype=np.float64)
     n, k = W.shape
     X = np.empty((M + 1, k, k))
-    V = [W, At @ W]
-    for j in range(1, M // 2):
-        V.append(2.0 * (At @ V[j]) - V[j - 1])
-    X0 = W.T @ W
-    X1 = W.T @ V[1]
-    for l in range(M + 1):
-        j = l // 2
-        if l % 2 == 0:
-            X[l] = 2.0 * V[j].T @ V[j] - X0 if l else X0
-        else:
-            X[l] = 2.0 * V[j + 1].T @ V[j] - X1 if l > 1 else X1
+    Vm, Vc = W, At @ W          # V_{j-1}, V_j with j = 1; only three blocks live
+    X[0] = W.T @ W
+    X[1] = W.T @ Vc
+    for j in range(1, M // 2 + 1):
+        X[2 * j] = 2.0 * Vc.T @ Vc - X[0]
+        if 2 * j + 1 <= M:
+            Vn = 2.0 * (At @ Vc) - Vm
+            X[2 * j + 1] = 2.0 * Vn.T @ Vc - X[1]
+            Vm, Vc = Vc, Vn
     return 0.5 * (X + np.transpose(X, (0, 2, 1)))
 
 
@@ -317,18 +359,20 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
              sigma: float, tau: float = 1e-7, kappa: float = 1e-6,
              interval: Optional[Tuple[float, float]] = None,
              n_theta: Optional[int] = None, flag_eps: float = 0.0,
-             moments: str = "direct", eps_floor: float = EPS_FP64) -> Dict[str, np.ndarray]:
+             moments: str = "direct", eps_floor: float = EPS_FP64, damping: int = 0,
+             lam: float = 4.0) -> Dict[str, np.ndarray]:
     """RESS-DGC (Alg. 7) and the DGC/KPM line (Alg. 2) on the same probes.
 
     W_all = [W, W~] (N x (n_v + n_vh)).  eps_floor sets the rounding floor
-    of Alg. 4's truncation (0 disables it).  Returns dos_ss, dos_kpm, the
-    kept ranks, the flags, the interval and the moments.
+    of Alg. 4's truncation (0 disables it).  damping / lam select optional
+    damping factors of the series (coefficient_tables).  Returns dos_ss,
+    dos_kpm, the kept ranks, the flags, the interval and the moments.
     """
     A = sp.csr_matrix(A)
     N = A.shape[0]
     a, b = interval if interval is not None else spectral_interval(A)
     At = transform(A, a, b)
-    tab = coefficient_tables(t, M, sigma, N, a, b, n_theta)
+    tab = coefficient_tables(t, M, sigma, N, a, b, n_theta, damping, lam)
     X = (moments_direct if moments == "direct" else moments_doubling)(At, W_all, M)
     gm = g_max(sigma, N)
     nt = len(t)

@@ -13,6 +13,8 @@ STATUS_NAMES = {0: "SSM_OK", 1: "SSM_EINVAL", 2: "SSM_ENOMEM", 3: "SSM_ECUDA", 4
                 9: "SSM_ENOCONV"}
 SSM_FP64 = 0
 SSM_MIXED = 1
+PRECISIONS = {"fp64": SSM_FP64, "mixed": SSM_MIXED}
+SSM_DAMP_NONE, SSM_DAMP_JACKSON, SSM_DAMP_LORENTZ = 0, 1, 2
 SSM_OPT_CUDA_CORE_GRAM = 1
 SSM_OPT_ADJOINT = 2
 SSM_OPT_FUSED_STEP = 4  # mixed stencil plans: recurrence step and Gram products in one launch
@@ -31,7 +33,8 @@ class ssm_csr(C.Structure):
 class ssm_params(C.Structure):
     _fields_ = [("n_v", C.c_int32), ("n_vh", C.c_int32), ("degree", C.c_int32), ("precision", C.c_int32),
                 ("lo", C.c_double), ("hi", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
-                ("n_theta", C.c_int32), ("options", C.c_int32), ("eps_floor", C.c_double)]
+                ("n_theta", C.c_int32), ("options", C.c_int32), ("eps_floor", C.c_double),
+                ("damping", C.c_int32), ("damping_lambda", C.c_double)]
 
 
 class ssm_stats(C.Structure):

@@ -99,15 +99,26 @@ class Plan:
             pass
 
 
+_DAMPING = {None: 0, "none": 0, "jackson": 1, "lorentz": 2, 0: 0, 1: 1, 2: 2}
+
+
+def _params(n_v, n_vh, degree, precision, lo, hi, tau, kappa, n_theta, options, eps_floor, damping,
+            damping_lambda):
+    # names are translated; other integers go to the library unchanged (it rejects them)
+    code = _DAMPING[damping] if damping in _DAMPING else int(damping)
+    return N.ssm_params(n_v=n_v, n_vh=n_vh, degree=degree, precision=N.PRECISIONS[precision], lo=lo, hi=hi,
+                        tau=tau, kappa=kappa, n_theta=n_theta, options=options, eps_floor=eps_floor,
+                        damping=code, damping_lambda=damping_lambda)
+
+
 def ssm_plan_create(stencil=None, csr=None, *, n_v: int, degree: int, n_vh: int = 0,
                     precision: str = "fp64", lo: float = 0.0, hi: float = 0.0, tau: float = 0.0,
                     kappa: float = -1.0, n_theta: int = 0, eps_floor: float = 0.0, options: int = 0,
-                    stream=None) -> Plan:
+                    damping=None, damping_lambda: float = 0.0, stream=None) -> Plan:
     """ssm_plan_create: operator (stencil descriptor or CSR) + parameters -> Plan."""
     lib = N.load()
-    p = N.ssm_params(n_v=n_v, n_vh=n_vh, degree=degree,
-                     precision={"fp64": N.SSM_FP64, "mixed": N.SSM_MIXED}[precision],
-                     lo=lo, hi=hi, tau=tau, kappa=kappa, n_theta=n_theta, options=options, eps_floor=eps_floor)
+    p = _params(n_v, n_vh, degree, precision, lo, hi, tau, kappa, n_theta, options, eps_floor, damping,
+                damping_lambda)
     keep = []
     st_p = None
     csr_p = None
@@ -135,12 +146,12 @@ def ssm_plan_create(stencil=None, csr=None, *, n_v: int, degree: int, n_vh: int 
 
 def ssm_plan_create_batched(csrs, *, n_v: int, degree: int, n_vh: int = 0, precision: str = "mixed",
                             lo: float = 0.0, hi: float = 0.0, tau: float = 0.0, kappa: float = -1.0,
-                            n_theta: int = 0, eps_floor: float = 0.0, options: int = 0, stream=None) -> Plan:
+                            n_theta: int = 0, eps_floor: float = 0.0, options: int = 0, damping=None,
+                            damping_lambda: float = 0.0, stream=None) -> Plan:
     """ssm_plan_create_batched: B CSR operators of uneven size in one plan."""
     lib = N.load()
-    p = N.ssm_params(n_v=n_v, n_vh=n_vh, degree=degree,
-                     precision={"fp64": N.SSM_FP64, "mixed": N.SSM_MIXED}[precision],
-                     lo=lo, hi=hi, tau=tau, kappa=kappa, n_theta=n_theta, options=options, eps_floor=eps_floor)
+    p = _params(n_v, n_vh, degree, precision, lo, hi, tau, kappa, n_theta, options, eps_floor, damping,
+                damping_lambda)
     keep = []
     arr = (N.ssm_csr * len(csrs))()
     for k, c in enumerate(csrs):

@@ -24,6 +24,7 @@ struct ssm_plan_s {
     // per-point buffers
     double* d_t = nullptr;
     double* d_mu = nullptr;
+    double* d_muh = nullptr;   // damped degree-M/2 table (plans with damping)
     double* d_nu = nullptr;
     double* d_K = nullptr;
     double* d_KZ = nullptr;
@@ -253,6 +254,7 @@ void free_plan(ssm_plan_s* h) {
     dev_free(h->d_perm);
     dev_free(h->d_t);
     dev_free(h->d_mu);
+    dev_free(h->d_muh);
     dev_free(h->d_nu);
     dev_free(h->d_K);
     dev_free(h->d_KZ);
@@ -299,12 +301,14 @@ ssm_status ensure_points(ssm_plan_s* h, int64_t n_t) {
     const int64_t nb = n_t < bt ? n_t : bt;
     if ((size_t)nb > h->cap_batch) {
         dev_free(h->d_mu);
+        dev_free(h->d_muh);
         dev_free(h->d_nu);
         dev_free(h->d_K);
         dev_free(h->d_KZ);
-        h->d_mu = h->d_nu = h->d_K = h->d_KZ = nullptr;
+        h->d_mu = h->d_muh = h->d_nu = h->d_K = h->d_KZ = nullptr;
         h->cap_batch = 0;
         CUDA_OR_FAIL(h, dev_alloc(&h->d_mu, (size_t)nb * (M + 1)));
+        if (P.p.damping) CUDA_OR_FAIL(h, dev_alloc(&h->d_muh, (size_t)nb * (M + 1)));
         CUDA_OR_FAIL(h, dev_alloc(&h->d_nu, (size_t)nb * (M + 1)));
         CUDA_OR_FAIL(h, dev_alloc(&h->d_K, (size_t)nb * P.n_tot * P.n_tot));
         CUDA_OR_FAIL(h, dev_alloc(&h->d_KZ, (size_t)nb * P.p.n_v * P.p.n_v));
@@ -318,8 +322,10 @@ ssm_status ensure_points(ssm_plan_s* h, int64_t n_t) {
 }
 
 // Coefficient tables for n points at d_tpts (device): mu -> dmu, nu -> dnu (ld M+1).
+// With damping, dmu gets the factors of M+1 terms (KPM line) and dmuh (required then)
+// the degree-M/2 table with the factors of M/2+1 terms, from which nu is formed.
 ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, double sigma, double* dmu,
-                            double* dnu, int mat = -1) {
+                            double* dnu, int mat = -1, double* dmuh = nullptr) {
     Plan& P = h->P;
     const int M = P.p.degree;
     // batched plans: the interval and size of matrix `mat`
@@ -329,8 +335,15 @@ ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, doub
     Scope sc(h, PH_COEFFS);
     CUDA_OR_FAIL(h, launch_mu(d_tpts, n, sigma, inv_norm, a, b, M, P.n_theta, P.d_ctab, dmu, M + 1, P.stream));
     P.stats.launches++;
+    const double* half = dmu;
+    if (P.p.damping) {
+        if (!dmuh && dnu) return fail(h, SSM_EINVAL, "internal: damping needs a degree-M/2 table");
+        CUDA_OR_FAIL(h, launch_damp(dmu, M + 1, n, M, P.p.damping, P.p.damping_lambda, dmuh, P.stream));
+        P.stats.launches++;
+        half = dmuh;
+    }
     if (dnu) {
-        CUDA_OR_FAIL(h, launch_nu(dmu, M + 1, n, M, dnu, M + 1, P.stream));
+        CUDA_OR_FAIL(h, launch_nu(half, M + 1, n, M, dnu, M + 1, P.stream));
         P.stats.launches++;
     }
     return SSM_OK;
@@ -403,11 +416,13 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
     }
     for (int64_t t0 = 0; t0 < n_t; t0 += bt) {
         const int64_t nb = (n_t - t0) < bt ? (n_t - t0) : bt;
-        ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, want_ss ? h->d_nu : nullptr);
+        ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, want_ss ? h->d_nu : nullptr, -1,
+                                         h->d_muh);
         if (st != SSM_OK) return st;
+        const double* muh = P.p.damping ? h->d_muh : h->d_mu;  // Alg. 7's degree-M/2 table
         if (want_ss) {
             Scope sc(h, PH_ASSEMBLE);
-            st = assemble_pencils(h, h->d_mu, h->d_nu, nb, 0, h->d_K, h->d_KZ);
+            st = assemble_pencils(h, muh, h->d_nu, nb, 0, h->d_K, h->d_KZ);
             if (st != SSM_OK) return st;
         }
         if (want_ss) {
@@ -432,7 +447,7 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
                     perm = h->d_perm;
                 }
             }
-            CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, h->d_mu, M + 1, K,
+            CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, muh, M + 1, K,
                                          floor_scale, h->d_solve, h->d_dos_ss + t0, h->d_rank + 2 * t0,
                                          P.d_flag, P.stream, nullptr, perm));
             P.stats.launches++;
@@ -492,11 +507,13 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
         for (int64_t b = b0; b < b1; ++b) {
             const int64_t off = (b - b0) * n_tp;
             ssm_status st = coefficients_dev(h, d_tpts + b * n_tp, n_tp, sigma, h->d_mu + off * (M + 1),
-                                             want_ss ? h->d_nu + off * (M + 1) : nullptr, (int)b);
+                                             want_ss ? h->d_nu + off * (M + 1) : nullptr, (int)b,
+                                             h->d_muh ? h->d_muh + off * (M + 1) : nullptr);
             if (st != SSM_OK) return st;
             if (want_ss) {
                 Scope sc(h, PH_ASSEMBLE);
-                st = assemble_pencils(h, h->d_mu + off * (M + 1), h->d_nu + off * (M + 1), n_tp, (int)b,
+                st = assemble_pencils(h, (P.p.damping ? h->d_muh : h->d_mu) + off * (M + 1), h->d_nu + off * (M + 1),
+                                      n_tp, (int)b,
                                       h->d_K + off * n_tot * n_tot, h->d_KZ + off * nv * nv);
                 if (st != SSM_OK) return st;
             }
@@ -510,7 +527,8 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
         if (want_ss) {
             Scope sc(h, PH_SOLVE);
             const int64_t nb = (b1 - b0) * n_tp;
-            CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, 0.0, 0.0, h->d_mu, M + 1, K, 0.0,
+            CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, 0.0, 0.0,
+                                         P.p.damping ? h->d_muh : h->d_mu, M + 1, K, 0.0,
                                          h->d_solve, h->d_dos_ss + b0 * n_tp, h->d_rank + 2 * b0 * n_tp, P.d_flag,
                                          P.stream, h->d_fpt + 3 * b0 * n_tp));
             P.stats.launches++;
@@ -716,12 +734,16 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
     if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
     if (p.options & ~7) return fail(nullptr, SSM_EINVAL, "unknown option bits");
+    if (p.damping < SSM_DAMP_NONE || p.damping > SSM_DAMP_LORENTZ)
+        return fail(nullptr, SSM_EINVAL, "damping must be SSM_DAMP_NONE, SSM_DAMP_JACKSON or SSM_DAMP_LORENTZ");
+    if (!isfinite(p.damping_lambda)) return fail(nullptr, SSM_EINVAL, "damping_lambda must be finite");
 
     ssm_plan_s* h = new ssm_plan_s();
     Plan& P = h->P;
     P.p = p;
     if (P.p.tau <= 0.0) P.p.tau = 1e-7;
     if (P.p.kappa < 0.0) P.p.kappa = 1e-6;
+    if (P.p.damping_lambda <= 0.0) P.p.damping_lambda = 4.0;
     if (P.p.eps_floor == 0.0)  // 2^-36 (mixed, measured) and 2^-52 (float64)
         P.eps_floor = (p.precision == SSM_MIXED) ? 1.0 / 68719476736.0 : 1.0 / 4503599627370496.0;
     else
@@ -1366,16 +1388,17 @@ ssm_status ssm_coefficients(ssm_plan_t h, const double* t, int64_t n_t, double s
     if (!t) return fail(h, SSM_EINVAL, "t is NULL");
     CUDA_OR_FAIL(h, cudaSetDevice(P.device));
     const int M = P.p.degree;
-    double *dmu = nullptr, *dnu = nullptr, *dt = nullptr;
+    double *dmu = nullptr, *dnu = nullptr, *dt = nullptr, *dmuh = nullptr;
     CUDA_OR_FAIL(h, dev_alloc(&dt, n_t));
     cudaError_t e = dev_alloc(&dmu, (size_t)n_t * (M + 1));
     if (e == cudaSuccess) e = dev_alloc(&dnu, (size_t)n_t * (M + 1));
+    if (e == cudaSuccess && P.p.damping) e = dev_alloc(&dmuh, (size_t)n_t * (M + 1));
     if (e == cudaSuccess) e = to_device(dt, t, n_t * sizeof(double), P.stream);
     ssm_status s = SSM_OK;
     if (e != cudaSuccess) {
         s = fail(h, e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA, cudaGetErrorString(e));
     } else {
-        s = coefficients_dev(h, dt, n_t, sigma, dmu, dnu);
+        s = coefficients_dev(h, dt, n_t, sigma, dmu, dnu, -1, dmuh);
     }
     if (s == SSM_OK && mu) {
         e = from_device(mu, dmu, (size_t)n_t * (M + 1) * sizeof(double), P.stream);
@@ -1390,6 +1413,7 @@ ssm_status ssm_coefficients(ssm_plan_t h, const double* t, int64_t n_t, double s
     dev_free(dt);
     dev_free(dmu);
     dev_free(dnu);
+    dev_free(dmuh);
     return s;
 }
 

@@ -14,6 +14,10 @@
 // (The CPU oracle integrates the squared series instead; both are exact.)
 //
 // KPM line (Alg. 2): phi(t_i) = sum_l mu_l(t_i) zeta_l, zeta_l = Tr X_l / n_tot.
+//
+// Optional damping (not in the paper; Jackson and Lorentz factors of the KPM
+// literature): the degree-M table for the KPM line and the degree-M/2 table
+// for Alg. 7 get the factors of their own lengths, before nu is formed.
 #include "internal.h"
 
 namespace ssm {
@@ -154,6 +158,32 @@ __global__ void nu_kernel(const double* __restrict__ mu, int ldmu, int64_t n_t, 
     }
 }
 
+// Damping factor n of a series of L terms (ssm_params.damping): Jackson's
+// closed form or the Lorentz factor sinh(lam (1 - n/L)) / sinh(lam).
+__device__ double damping_factor(int kind, int n, int L, double lam) {
+    if (kind == 1) {
+        const double q = 1.0 / (double)(L + 1);
+        return ((double)(L - n + 1) * cospi(q * n) + sinpi(q * n) * (cospi(q) / sinpi(q))) * q;
+    }
+    if (kind == 2) return sinh(lam * (1.0 - (double)n / (double)L)) / sinh(lam);
+    return 1.0;
+}
+
+// muh[t][l] = g^{(K+1)}_l mu[t][l] (l <= K, the degree-K series of Alg. 7) and
+// mu[t][l] <- g^{(M+1)}_l mu[t][l] (l <= M, the KPM line), from the undamped table.
+__global__ void damp_kernel(double* __restrict__ mu, int ldmu, int64_t n_t, int M, int kind, double lam,
+                            double* __restrict__ muh) {
+    const int K = M / 2;
+    const int64_t total = n_t * (int64_t)(M + 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t it = e / (M + 1);
+        const int l = (int)(e - it * (M + 1));
+        const double v = mu[it * ldmu + l];
+        if (muh) muh[it * ldmu + l] = l <= K ? damping_factor(kind, l, K + 1, lam) * v : 0.0;
+        mu[it * ldmu + l] = damping_factor(kind, l, M + 1, lam) * v;
+    }
+}
+
 __global__ void zeta_kernel(const double* __restrict__ X, int n_tot, int M, double* __restrict__ zeta) {
     const size_t nn = (size_t)n_tot * n_tot;
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= M; l += gridDim.x * blockDim.x) {
@@ -206,6 +236,12 @@ cudaError_t launch_mu(const double* t, int64_t n_t, double sigma, double inv_nor
 
 cudaError_t launch_nu(const double* mu, int ldmu, int64_t n_t, int M, double* nu, int ldnu, cudaStream_t s) {
     nu_kernel<<<nblocks(n_t * (M + 1), 256), 256, 0, s>>>(mu, ldmu, n_t, M, nu, ldnu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damp(double* mu, int ldmu, int64_t n_t, int M, int kind, double lam, double* muh,
+                        cudaStream_t s) {
+    damp_kernel<<<nblocks(n_t * (M + 1), 256), 256, 0, s>>>(mu, ldmu, n_t, M, kind, lam, muh);
     return cudaGetLastError();
 }
 

@@ -232,6 +232,10 @@ cudaError_t launch_mu(const double* t, int64_t n_t, double sigma, double inv_nor
                       int M, int n_theta, const double* ctab, double* mu, int ldmu, cudaStream_t s);
 cudaError_t launch_nu(const double* mu, int ldmu, int64_t n_t, int M, double* nu, int ldnu,
                       cudaStream_t s);
+// Damping: muh = factors of M/2+1 terms times mu (l <= M/2, zero above), then mu *= factors
+// of M+1 terms (kind 1 Jackson, 2 Lorentz with parameter lam).
+cudaError_t launch_damp(double* mu, int ldmu, int64_t n_t, int M, int kind, double lam, double* muh,
+                        cudaStream_t s);
 cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const double* X, int n_tot,
                        double* zeta, double* out, cudaStream_t s);
 

@@ -325,3 +325,85 @@ def test_rounding_floor_drops_noise_only():
         K = O.assemble(tab["mu_half"][i], tab["nu"][i], r1["X"], 12)
         s = np.linalg.eigvalsh(K[0])
         assert O.rounding_floor(tab["mu_half"][i], r1["X"], 12, O.EPS_FP64) < 1e-3 * 1e-7 * s.max()
+
+
+# ---------------------------------------------------------------- damping (KPM literature)
+
+@pytest.mark.parametrize("L", [1, 2, 7, 64, 501])
+def test_jackson_closed_form_is_autocorrelation_of_sine_sequence(L):
+    # The Jackson kernel is |sum_nu a_nu e^{i nu phi}|^2 / sum a_nu^2 with
+    # a_nu = sin(pi (nu + 1) / (L + 1)); its Fourier coefficients are the
+    # normalised autocorrelations of a, an independent route to the factors.
+    a = np.sin(math.pi * (np.arange(L) + 1) / (L + 1))
+    ac = np.array([np.dot(a[: L - k], a[k:]) for k in range(L)]) / np.dot(a, a)
+    g = O.jackson_factors(L)
+    assert g[0] == pytest.approx(1.0, abs=1e-15)
+    assert np.max(np.abs(g - ac)) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_damping_kernels_are_nonnegative(kind):
+    # Both kernels K(phi) = g_0 + 2 sum_n g_n cos(n phi) are nonnegative (the
+    # Jackson one touches zero), which is what makes damped expansions of
+    # nonnegative functions nonnegative.
+    L = 50
+    g = O.damping_factors(kind, L, 4.0)
+    phi = np.linspace(0.0, math.pi, 4001)
+    K = g[0] + 2.0 * np.cos(np.outer(phi, np.arange(1, L))) @ g[1:]
+    assert g[0] == pytest.approx(1.0, abs=1e-15)
+    assert np.min(K) > -1e-12 * np.max(K)
+    if kind == 2:
+        lam = 4.0
+        assert g[10] == pytest.approx(math.sinh(lam * (1 - 10 / L)) / math.sinh(lam), rel=1e-14)
+
+
+def test_jackson_damped_gaussian_expansion_is_nonnegative():
+    # An under-resolved truncated series of g_sigma(t - x) has negative Gibbs
+    # lobes; the Jackson-damped one is a convolution of g_sigma with a
+    # nonnegative kernel and stays nonnegative on the whole interval.
+    M, sigma, a, b, N = 40, 0.02, -1.0, 1.0, 100
+    t = np.array([0.1])
+    s = np.linspace(-1.0, 1.0, 4001)
+    T = np.cos(np.outer(np.arccos(s), np.arange(M + 1)))
+    plain = T @ O.coefficient_tables(t, M, sigma, N, a, b)["mu_full"][0]
+    damped = T @ O.coefficient_tables(t, M, sigma, N, a, b, damping=1)["mu_full"][0]
+    assert np.min(plain) < -1e-3 * np.max(plain)
+    assert np.min(damped) > -1e-12 * np.max(damped)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_damped_kpm_with_identity_probes_matches_eigenvalue_sum(kind):
+    # W = sqrt(N) I: the KPM line is sum_i sum_l g_l mu_l(t) T_l(lambda~_i) with the
+    # factors of M+1 terms, evaluated here from the eigenvalues; the SS line's
+    # nu is the square of the half-degree series damped with M/2+1 factors.
+    A, lam, Q = _dense_sym(30, 11, -1.0, 2.0)
+    A = sp.csr_matrix(A)
+    N, M, sigma = 30, 60, 0.2
+    a, b = O.spectral_interval(A)
+    t = np.linspace(-1.0, 2.0, 13)
+    r = O.ress_dgc(A, math.sqrt(N) * np.eye(N), N, t, M, sigma, damping=kind)
+    lt = (2 * lam - (a + b)) / (b - a)
+    T = np.cos(np.outer(np.arange(M + 1), np.arccos(lt)))   # (M+1) x N
+    g = O.damping_factors(kind, M + 1)
+    ref = np.array([np.sum((g * O.dgc_coefficients(ti, M, sigma, N, a, b)) @ T) for ti in t])
+    assert np.max(np.abs(r["dos_kpm"] - ref)) < 1e-11 * np.max(np.abs(ref))
+    gh = O.damping_factors(kind, M // 2 + 1)
+    tab = O.coefficient_tables(t, M, sigma, N, a, b, damping=kind)
+    s = np.linspace(-1.0, 1.0, 257)
+    Th = np.cos(np.outer(np.arccos(s), np.arange(M // 2 + 1)))
+    Tf = np.cos(np.outer(np.arccos(s), np.arange(M + 1)))
+    for i in (0, 6, 12):
+        ph = Th @ (gh * O.dgc_coefficients(t[i], M // 2, sigma, N, a, b, 2 * M))
+        assert np.max(np.abs(Tf @ tab["nu"][i] - ph * ph)) < 1e-12 * np.max(ph * ph)
+
+
+def test_damped_kpm_integrates_to_one():
+    st = wl.make_operator("lap2d_dirichlet_32", nx=10)
+    c = wl.stencil_to_csr(st)
+    A = O.csr_matrix(c.n, c.rowptr, c.colind, c.val)
+    W = wl.random_block(c.n, 8, 9, "rademacher")
+    a, b = O.spectral_interval(A)
+    sigma = 0.3
+    t = np.linspace(a - 12 * sigma, b + 12 * sigma, 3001)
+    r = O.ress_dgc(A, W, 8, t, 60, sigma, damping=1)
+    assert abs(np.trapezoid(r["dos_kpm"], t) - 1.0) < 1e-10
