@@ -60,8 +60,15 @@ typedef enum {
 
 typedef enum {
     SSM_FP64 = 0,   /* recurrence, Gram products and everything after in float64 */
-    SSM_MIXED = 1   /* float32 recurrence, split-bf16 tensor-core Gram products with
+    SSM_MIXED = 1,  /* float32 recurrence, split-bf16 tensor-core Gram products with
                        float32 accumulation, float64 moments and per-point solves */
+    SSM_FP64_TC = 2 /* float64 recurrence; Gram products on the tensor cores from an
+                       error-free split of each float64 block into six bf16 slices
+                       (8-bit digits of a per-column fixed point; products of slices
+                       summed exactly in float32 groups, groups added in float pairs
+                       every 320 rows), to float64 accuracy (about 2^-48 of the
+                       largest entry of each column); float64 moments and everything
+                       after as SSM_FP64.  Needs n_v + n_vh <= 256. */
 } ssm_precision;
 
 /* Constant-coefficient stencil operator on a grid of up to three axes:

@@ -13,7 +13,8 @@ STATUS_NAMES = {0: "SSM_OK", 1: "SSM_EINVAL", 2: "SSM_ENOMEM", 3: "SSM_ECUDA", 4
                 9: "SSM_ENOCONV"}
 SSM_FP64 = 0
 SSM_MIXED = 1
-PRECISIONS = {"fp64": SSM_FP64, "mixed": SSM_MIXED}
+SSM_FP64_TC = 2  # float64 recurrence, tensor-core Gram products from exact bf16 slices
+PRECISIONS = {"fp64": SSM_FP64, "mixed": SSM_MIXED, "fp64_tc": SSM_FP64_TC}
 SSM_DAMP_NONE, SSM_DAMP_JACKSON, SSM_DAMP_LORENTZ = 0, 1, 2
 SSM_OPT_CUDA_CORE_GRAM = 1
 SSM_OPT_ADJOINT = 2

@@ -218,6 +218,10 @@ void free_plan(ssm_plan_s* h) {
     dev_free(P.d_ring);
     dev_free(P.d_ring_sum);
     for (auto& pb : P.d_panel) dev_free(pb);
+    for (auto& u : P.d_ozU) dev_free(u);
+    dev_free(P.d_ozcm);
+    dev_free(P.d_ozpart);
+    dev_free(P.d_ozG);
     dev_free(P.d_fmeta);
     for (auto& e : P.ev_st) if (e) cudaEventDestroy(e);
     for (auto& e : P.ev_gr) if (e) cudaEventDestroy(e);
@@ -730,7 +734,10 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         return fail(nullptr, SSM_EINVAL, "need 1 <= n_v <= 1024 and 0 <= n_vh <= 1024");
     if (p.degree < 2 || (p.degree & 1) || p.degree > (1 << 20))
         return fail(nullptr, SSM_EINVAL, "degree M must be even and in [2, 2^20]");
-    if (p.precision != SSM_FP64 && p.precision != SSM_MIXED) return fail(nullptr, SSM_EINVAL, "unknown precision");
+    if (p.precision != SSM_FP64 && p.precision != SSM_MIXED && p.precision != SSM_FP64_TC)
+        return fail(nullptr, SSM_EINVAL, "unknown precision");
+    if (p.precision == SSM_FP64_TC && !gram_oz_supported(p.n_v + p.n_vh))
+        return fail(nullptr, SSM_EINVAL, "SSM_FP64_TC needs n_v + n_vh <= 256");
     if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
     if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
     if (p.options & ~7) return fail(nullptr, SSM_EINVAL, "unknown option bits");
@@ -744,7 +751,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if (P.p.tau <= 0.0) P.p.tau = 1e-7;
     if (P.p.kappa < 0.0) P.p.kappa = 1e-6;
     if (P.p.damping_lambda <= 0.0) P.p.damping_lambda = 4.0;
-    if (P.p.eps_floor == 0.0)  // 2^-36 (mixed, measured) and 2^-52 (float64)
+    if (P.p.eps_floor == 0.0)  // 2^-36 (mixed, measured) and 2^-52 (float64 and float64 tensor-core)
         P.eps_floor = (p.precision == SSM_MIXED) ? 1.0 / 68719476736.0 : 1.0 / 4503599627370496.0;
     else
         P.eps_floor = P.p.eps_floor > 0.0 ? P.p.eps_floor : 0.0;
@@ -950,6 +957,18 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         }
         for (auto& e : P.ev_st) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         for (auto& e : P.ev_gr) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    } else if (p.precision == SSM_FP64_TC) {
+        // float64 blocks; Gram products on the tensor cores from exact bf16 slices
+        P.use_oz = true;
+        for (auto& u : P.d_ozU) CREATE_CUDA(cudaMalloc((void**)&u, (size_t)P.n * P.ld * sizeof(double)));
+        CREATE_CUDA(cudaMalloc((void**)&P.d_ozcm, (size_t)5 * oz_buckets() * P.ld * sizeof(unsigned long long)));
+        CREATE_CUDA(dev_alloc(&P.d_ozpart, oz_partial_floats(P.n_tot, P.n)));
+        CREATE_CUDA(dev_alloc(&P.d_ozG, (size_t)P.n_tot * P.n_tot));
+        int prio_lo = 0, prio_hi = 0;
+        CREATE_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CREATE_CUDA(cudaStreamCreateWithPriority(&P.gstream, cudaStreamNonBlocking, prio_hi));
+        for (auto& e : P.ev_st) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto& e : P.ev_gr) CREATE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     } else {
         P.n_split = gram_split_count(P.n, P.n_tot);
         CREATE_CUDA(dev_alloc(&P.d_part, (size_t)P.n_split * 2 * P.n_tot * P.n_tot));
@@ -971,6 +990,7 @@ ssm_status ssm_plan_create_batched(ssm_plan_t* out, int32_t B, const ssm_csr* cs
     if (!params) return fail(nullptr, SSM_EINVAL, "params is NULL");
     const ssm_params& p = *params;
     if (p.options & 2) return fail(nullptr, SSM_EINVAL, "the adjoint option is not available for batched plans");
+    if (p.precision == SSM_FP64_TC) return fail(nullptr, SSM_EINVAL, "SSM_FP64_TC is not available for batched plans");
     // host copies of every operator (the inputs may live on the device)
     std::vector<int64_t> row_off(B + 1, 0), nb(B), nnz_off(B + 1, 0);
     for (int b = 0; b < B; ++b) {
@@ -1213,9 +1233,24 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     // products and reductions run on gstream, so the Gram of step k overlaps the
     // recurrence of step k+1.  Step k writes panel (k+1) % 3, last read by the Gram
     // of step k-1: it waits for that Gram only.
-    const bool ovl = P.use_tc && P.gstream && !P.use_fused;
+    // SSM_FP64_TC: the same two-stream schedule; step k also writes U_k = V_{k+1} + V_k
+    // (d_ozU[k % 2]) and the column maxima of V_{k+1} (slot (k+1) % 3) and U_k (slot
+    // 3 + k % 2), and the Gram of step k forms V_{k+1}^T V_{k+1} and U_k^T U_k.
+    const bool ovl = (P.use_tc || P.use_oz) && P.gstream && !P.use_fused;
     cudaStream_t gs = ovl ? P.gstream : P.stream;
+    const int nbk = P.use_oz ? oz_buckets() : 0;
+    auto ozcm = [&](int slot) { return P.d_ozcm + (size_t)slot * nbk * P.ld; };
+    const size_t ozcm_bytes = (size_t)nbk * P.ld * sizeof(unsigned long long);
     auto gram = [&](const void* A, const void* B, int j) -> cudaError_t {
+        if (P.use_oz) {
+            // j = 0: V_0 alone; j = k + 1: V_{k+1} and U_k
+            cudaError_t e = launch_gram_oz((const double*)A, ozcm(j % 3), j ? P.d_ozU[(j - 1) % 2] : nullptr,
+                                           j ? ozcm(3 + (j - 1) % 2) : nullptr, P.n_tot, P.ld, P.n, P.d_ozpart,
+                                           P.d_flag, gs);
+            if (e != cudaSuccess) return e;
+            return launch_oz_moments(P.d_ozpart, ozcm(j % 3), j ? ozcm(3 + (j - 1) % 2) : nullptr, P.n_tot, P.ld, P.n,
+                                     P.d_ozG, P.d_X, j - 1, gs);
+        }
         if (P.use_tc) {
             // steps k = j-1 >= 1 write into the ring; V_0 and step 0 into d_part_tc
             float* dst = (j >= 2) ? P.d_ring + (size_t)((j - 2) % P.tc_ring) *
@@ -1234,6 +1269,11 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         CUDA_OR_FAIL(h, launch_panelize(P, (const float*)P.d_V[0], P.d_panel[0], P.stream));
         P.stats.launches++;
     }
+    if (P.use_oz) {
+        CUDA_OR_FAIL(h, cudaMemsetAsync(ozcm(0), 0, ozcm_bytes, P.stream));
+        CUDA_OR_FAIL(h, launch_colmax((const double*)P.d_V[0], P.ld, P.n_tot, P.n, ozcm(0), P.stream));
+        P.stats.launches++;
+    }
     if (ovl) {
         CUDA_OR_FAIL(h, cudaEventRecord(P.ev_st[2], P.stream));
         CUDA_OR_FAIL(h, cudaStreamWaitEvent(gs, P.ev_st[2], 0));
@@ -1244,7 +1284,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         P.stats.launches++;
         P.stats.gram_launches++;
     }
-    {
+    if (!P.use_oz) {  // (the float64 tensor-core Gram forms its moments in the same call)
         Scope sc(h, PH_REDUCE, gs);
         CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, -1, gs)
                                  : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, -1, P.stream));
@@ -1309,6 +1349,17 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
                                                            (float)c, (float)d, pn, P.stream)
                                  : launch_csr_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn, (float)c,
                                                        (float)d, pn, P.stream);
+            } else if (P.use_oz) {
+                e = cudaMemsetAsync(ozcm((k + 1) % 3), 0, ozcm_bytes, P.stream);
+                if (e == cudaSuccess) e = cudaMemsetAsync(ozcm(3 + k % 2), 0, ozcm_bytes, P.stream);
+                if (e == cudaSuccess)
+                    e = P.is_stencil
+                            ? launch_stencil_step_f64_oz(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d,
+                                                         P.d_ozU[k % 2], ozcm((k + 1) % 3), ozcm(3 + k % 2), nbk,
+                                                         P.stream)
+                            : launch_csr_step_f64_oz(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d,
+                                                     P.d_ozU[k % 2], ozcm((k + 1) % 3), ozcm(3 + k % 2), nbk,
+                                                     P.stream);
             } else {
                 e = P.is_stencil ? launch_stencil_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c,
                                                            d, P.stream)
@@ -1336,7 +1387,9 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
             P.stats.gram_launches++;
         }
         if (ovl) CUDA_OR_FAIL(h, cudaEventRecord(P.ev_gr[(k + 1) % 3], gs));
-        if (!P.use_tc || k == 0) {
+        if (P.use_oz) {
+            // moments formed by the Gram call
+        } else if (!P.use_tc || k == 0) {
             Scope sc(h, PH_REDUCE, gs);
             CUDA_OR_FAIL(h, P.use_tc ? launch_reduce_tc(P.d_part_tc, P.tc_ne, P.tc_no, P.n_tot, P.d_X, k, gs)
                                      : launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X, k, P.stream));
