@@ -208,6 +208,8 @@ void free_plan(ssm_plan_s* h) {
     Plan& P = h->P;
     dev_free(P.d_diag64);
     dev_free(P.d_diag32);
+    dev_free(P.d_diag32lo);
+    dev_free(P.d_val32lo);
     dev_free(P.d_rowptr);
     dev_free(P.d_colind);
     dev_free(P.d_val64);
@@ -738,6 +740,8 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         return fail(nullptr, SSM_EINVAL, "unknown precision");
     if (p.precision == SSM_FP64_TC && !gram_oz_supported(p.n_v + p.n_vh))
         return fail(nullptr, SSM_EINVAL, "SSM_FP64_TC needs n_v + n_vh <= 256");
+    if (p.precision == SSM_FP64_TC && (p.options & 6))
+        return fail(nullptr, SSM_EINVAL, "SSM_FP64_TC plans take no adjoint or fused-step option");
     if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
     if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
     if (p.options & ~7) return fail(nullptr, SSM_EINVAL, "unknown option bits");
@@ -901,7 +905,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     dev_free(d_raw);
     d_raw = nullptr;
     // recurrence and moment buffers
-    const int vec = P.mixed ? 4 : 2;
+    const int vec = (P.mixed || p.precision == SSM_FP64_TC) ? 4 : 2;  // 16-byte vectors of the blocks
     P.ld = (P.n_tot + vec - 1) / vec * vec;
     if ((uint64_t)P.n * (uint64_t)(P.ld / vec) >= (1ULL << 32)) return bail(SSM_EINVAL, "N x n_tot too large");
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
@@ -961,6 +965,14 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         // float64 blocks; Gram products on the tensor cores from exact bf16 slices
         P.use_oz = true;
         for (auto& u : P.d_ozU) CREATE_CUDA(cudaMalloc((void**)&u, (size_t)P.n * P.ld * sizeof(double)));
+        // float pairs of the folded operator for the float-pair recurrence
+        if (P.is_stencil) {
+            CREATE_CUDA(dev_alloc(&P.d_diag32lo, P.n));
+            CREATE_CUDA(launch_split_df(P.d_diag64, P.n, P.d_diag32, P.d_diag32lo, P.stream));
+        } else {
+            CREATE_CUDA(dev_alloc(&P.d_val32lo, P.nnz > 0 ? P.nnz : 1));
+            if (P.nnz > 0) CREATE_CUDA(launch_split_df(P.d_val64, P.nnz, P.d_val32, P.d_val32lo, P.stream));
+        }
         CREATE_CUDA(cudaMalloc((void**)&P.d_ozcm, (size_t)5 * oz_buckets() * P.ld * sizeof(unsigned long long)));
         CREATE_CUDA(dev_alloc(&P.d_ozpart, oz_partial_floats(P.n_tot, P.n)));
         CREATE_CUDA(dev_alloc(&P.d_ozG, (size_t)P.n_tot * P.n_tot));
@@ -1227,7 +1239,14 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
         CUDA_OR_FAIL(h, launch_check_finite(src, P.n * (int64_t)P.n_tot, P.d_flag, P.stream));
         P.stats.launches++;
     }
-    CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, P.stream));
+    if (P.use_oz) {  // float pairs and the column maxima of V_0 (slot 0)
+        CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_ozcm, 0, (size_t)oz_buckets() * P.ld * sizeof(unsigned long long),
+                                        P.stream));
+        CUDA_OR_FAIL(h, launch_convert_in_df(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.d_ozcm, oz_buckets(),
+                                             P.stream));
+    } else {
+        CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, P.d_V[0], P.ld, P.n, P.n_tot, P.mixed, P.stream));
+    }
     P.stats.launches++;
     // Tensor-core path: split-bf16 panels of V_j live in d_panel[j % 3]; the Gram
     // products and reductions run on gstream, so the Gram of step k overlaps the
@@ -1244,7 +1263,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     auto gram = [&](const void* A, const void* B, int j) -> cudaError_t {
         if (P.use_oz) {
             // j = 0: V_0 alone; j = k + 1: V_{k+1} and U_k
-            cudaError_t e = launch_gram_oz((const double*)A, ozcm(j % 3), j ? P.d_ozU[(j - 1) % 2] : nullptr,
+            cudaError_t e = launch_gram_oz((const float*)A, ozcm(j % 3), j ? (const float*)P.d_ozU[(j - 1) % 2] : nullptr,
                                            j ? ozcm(3 + (j - 1) % 2) : nullptr, P.n_tot, P.ld, P.n, P.d_ozpart,
                                            P.d_flag, gs);
             if (e != cudaSuccess) return e;
@@ -1267,11 +1286,6 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     };
     if (P.use_tc) {
         CUDA_OR_FAIL(h, launch_panelize(P, (const float*)P.d_V[0], P.d_panel[0], P.stream));
-        P.stats.launches++;
-    }
-    if (P.use_oz) {
-        CUDA_OR_FAIL(h, cudaMemsetAsync(ozcm(0), 0, ozcm_bytes, P.stream));
-        CUDA_OR_FAIL(h, launch_colmax((const double*)P.d_V[0], P.ld, P.n_tot, P.n, ozcm(0), P.stream));
         P.stats.launches++;
     }
     if (ovl) {
@@ -1353,13 +1367,8 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
                 e = cudaMemsetAsync(ozcm((k + 1) % 3), 0, ozcm_bytes, P.stream);
                 if (e == cudaSuccess) e = cudaMemsetAsync(ozcm(3 + k % 2), 0, ozcm_bytes, P.stream);
                 if (e == cudaSuccess)
-                    e = P.is_stencil
-                            ? launch_stencil_step_f64_oz(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d,
-                                                         P.d_ozU[k % 2], ozcm((k + 1) % 3), ozcm(3 + k % 2), nbk,
-                                                         P.stream)
-                            : launch_csr_step_f64_oz(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d,
-                                                     P.d_ozU[k % 2], ozcm((k + 1) % 3), ozcm(3 + k % 2), nbk,
-                                                     P.stream);
+                    e = launch_step_df(P, Vc, k == 0 ? nullptr : Vp, Vn, P.d_ozU[k % 2], (float)c, (float)d,
+                                       ozcm((k + 1) % 3), ozcm(3 + k % 2), nbk, P.stream);
             } else {
                 e = P.is_stencil ? launch_stencil_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c,
                                                            d, P.stream)
@@ -1659,6 +1668,7 @@ ssm_status ssm_plan_set_diag(ssm_plan_t h, const double* diag) {
         return fail(h, SSM_EDOMAIN, "the new Gershgorin interval leaves the plan's interval (a, b)");
     CUDA_OR_FAIL(h, launch_fold_stencil(P, P.d_stage, P.extra, P.stream));
     if (P.use_fused) CUDA_OR_FAIL(h, launch_fused_meta(P, P.fcfg, P.d_fmeta, P.stream));  // holds the diagonal
+    if (P.use_oz) CUDA_OR_FAIL(h, launch_split_df(P.d_diag64, P.n, P.d_diag32, P.d_diag32lo, P.stream));
     P.stats.launches += 2;
     return sync_and_settle(h);
 }

@@ -11,13 +11,12 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59 (2012)).
 //
-// Splitting.  Column j of a block Y gets a scale 2^E_j > max_r |Y_rj| (the
-// recurrence kernel records the column maxima).  x = Y_rj 2^-E_j is rounded
-// to the fixed-point integer X = round(x 2^47) (|X| <= 2^47, integer
-// operations on the float64 bit pattern) and written in balanced base 256,
-//   X = sum_{k=1..6} d_k 256^(6-k),   d_1 in [-128, 128], d_k in [-128, 127],
-// so x = sum_k d_k 2^-(7+8(k-1)) up to 2^-48.  Slice k holds the bf16 value
-// s_k = d_k 2^-(7+8(k-1)) (exact: |d_k| <= 2^7 needs 8 significand bits).
+// Splitting.  The blocks are float pairs hi + lo (recurrence_df.cu).  Column j
+// of a block Y gets a scale 2^E_j > max_r |Y_rj| (the recurrence kernel
+// records the column maxima).  x = Y_rj 2^-E_j is split into six slices
+// s_k = d_k 2^-(7+8(k-1)) with integers |d_1..d_3| <= 128 and |d_4..d_6| <= 256
+// (split_df, float operations only), x = sum_k s_k up to 2^-48; every s_k
+// is exact in bf16 (at most 8 significant bits).
 //
 // Products.  G = Y^T Y = sum_{i+j<=7} S_i^T S_j (the terms with i+j > 7 are
 // below 2^-48 of |x|^2 and dropped).  A product s_i s_j is d_i d_j
@@ -27,9 +26,10 @@
 // sums at most 3 weighted terms per row: over 320 rows the sums stay below
 // 2^24 units, so every partial sum is exact in float32.  Group >= 5 rounds,
 // at 2^-24 of terms that are themselves below 2^-24 of the leading ones.
-// Every 320 rows the four groups are read back (tcgen05.ld), added in
-// float-pair arithmetic (about 2^-48 relative) to a running sum the CTA keeps
-// in global memory (L2), and restarted.
+// Every 320 rows the four groups are read back (tcgen05.ld): the three exact
+// ones, as integers in units of 2^-30, are added to an int64 running sum (no
+// rounding at all), the fourth to a float32 one, both kept per CTA in global
+// memory (L2); the slab sums are added as integers again.
 //
 // Tiles.  The output (n_tot <= 256) is cut into 128-row tiles: D0 = rows and
 // columns 0..127, O = rows 0..127 x columns 128.., D1 = rows and columns
@@ -37,11 +37,14 @@
 // i <= j are issued, those with i < j against a second copy of slice j
 // doubled (P = sum_i S_i^T S_i + 2 sum_{i<j} S_i^T S_j, G = (P + P^T) / 2);
 // O needs every pair.  A CTA owns one tile of one block over a slab of rows:
-// one thread streams the rows' float64 values into shared memory with 1-D
-// bulk copies, six warps split them into the slice operands (MN-major,
+// one thread streams the rows' float pairs into shared memory with 1-D
+// bulk copies (one per plane and 16-row stage: every tile takes whole rows,
+// which are contiguous), six warps split them into the slice operands (MN-major,
 // no-swizzle core matrices), one thread issues tcgen05.mma kind::f16 into
-// TMEM, and eight warps drain the accumulators.  Every wait is bounded; on
-// expiry the CTA sets bit 2 of the status word and stops.
+// TMEM, and eight warps drain the accumulators.  The short hand-offs between
+// stages spin on the mbarriers (mbarrier.test_wait); the drain warps, which
+// wait a whole interval, suspend.  Every wait is bounded; on expiry the CTA
+// sets bit 2 of the status word and stops.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -70,9 +73,11 @@ constexpr int NBUCKET = 32;        // column-maximum buckets written by the recu
 __host__ __device__ constexpr int slice_regions(int tile) { return tile == 1 ? 2 * NSL : 2 * NSL - 1; }
 
 struct OzArgs {
-    const double* Y[2];                       // block of each Gram (0: V_{k+1}, 1: U_k)
+    const float* Y[2];                        // float-pair block of each Gram (0: V_{k+1}, 1: U_k):
+                                              // hi plane (n_rows x ld) then lo plane
     const unsigned long long* cmax[2];        // NBUCKET x ld column maxima (bit patterns of |y|)
-    float2* part;                             // running sums, one region per CTA
+    int4* part;                               // running sums, one 128 x 128 region per CTA:
+                                              // (int64 exact groups in units of 2^-30, float group >= 5)
     int* flag;
     int n_tot, ld, ntp;                       // columns, leading dimension, n_tot rounded to 16
     int64_t n_rows;
@@ -84,61 +89,55 @@ struct OzArgs {
 };
 
 // 2^E > m (E = 0 for m = 0): the column scale of the splitting.
+// (clamped to [-126, 126]: 2^-E is then a normal float; columns below 2^-127 keep
+// 2^E = 2^-126 > m, and columns of magnitude 2^126 and beyond are not supported)
 __device__ __forceinline__ int col_exponent(double m) {
     if (!(m > 0.0)) return 0;
     int e;
     frexp(m, &e);  // m = f 2^e, f in [0.5, 1): m < 2^e
-    return e;
+    return e < -126 ? -126 : (e > 126 ? 126 : e);
 }
 
-// round(y 2^(47 - E)) from the bit pattern of y (|y| < 2^E): |X| <= 2^47.
-__device__ __forceinline__ long long fixed47(double y, int E) {
-    const long long b = __double_as_longlong(y);
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0) return 0;  // zero (and subnormals, far below any column scale)
-    const long long mant = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
-    const int sh = 1028 + E - e;  // >= 6 because |y| < 2^E
-    if (sh >= 60) return 0;
-    const long long X = (mant + (1LL << (sh - 1))) >> sh;
-    return b < 0 ? -X : X;
+// An integer-valued float (|f| < 2^31) as an integer, from its bit pattern.
+__device__ __forceinline__ long long float_int(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e < 127) return 0;
+    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = e - 150;
+    const long long x = sh >= 0 ? (long long)m << sh : (long long)(m >> (-sh));
+    return (b >> 31) ? -x : x;
 }
 
-// The six bf16 slice values of eight consecutive columns (one 16-byte row of a core
-// matrix per slice): out[k] holds s_k of columns 0..7 packed.
-__device__ __forceinline__ void split8(const double* v, const int* E, uint4* out) {
-    // balanced digits from the unsigned digits of X + B, B = 128 (1 + 256 + ... + 256^5)
-    constexpr long long BIAS = 0x808080808080LL;
-    uint32_t lo[8], hi[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const long long Y = fixed47(v[c], E[c]) + BIAS;  // in [0, 2^48 + 2^47]
-        lo[c] = (uint32_t)Y;
-        hi[c] = (uint32_t)(Y >> 32);
-    }
-    // digit k (1-based): k = 1 -> hi >> 8 (bits 40..48), k = 2 -> hi & 255, k = 3..6 -> bytes 3..0 of lo;
-    // value (u - 128) 2^-(7 + 8(k-1)) formed exactly as (2^23 + u) s - (2^23 + 128) s
+// Six slices of x = (hi + lo) 2^-E (|x| < 1) with float operations only.  Slice k
+// is x rounded to a multiple of u_k = 2^-(7+8(k-1)) after the slices before it
+// are taken away: q = (r + 1.5 2^23 u_k) - 1.5 2^23 u_k rounds r (|r| <= 128 u_k)
+// to the nearest multiple of u_k, and r - q is exact (q is a multiple of the
+// ulp of r).  hi has 24 bits and is split over slices 1..6; lo (|lo 2^-E| <
+// 2^-24 = u_3 / 2) only reaches slices 4..6, where its digits are added (up
+// to 256 u_k, still exact in bf16; those slices enter the rounded group
+// i+j >= 5 only).  s[k-1] = slice k; the residual below 2^-48 is dropped.
+__device__ __forceinline__ void split_df(float hi, float lo, float se, float* s) {
+    float r = hi * se;  // exact: se = 2^-E
+    float t = lo * se;
 #pragma unroll
     for (int k = 1; k <= NSL; ++k) {
-        const float s = __int_as_float((127 - 7 - 8 * (k - 1)) << 23);  // 2^-(7+8(k-1))
-        const float c0 = 8388736.0f * s;                               // (2^23 + 128) s
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float f[2];
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int c = 2 * q + t;
-                uint32_t u;
-                if (k == 1) u = hi[c] >> 8;
-                else if (k == 2) u = hi[c] & 255u;
-                else u = (lo[c] >> (8 * (6 - k))) & 255u;
-                f[t] = fmaf(__uint_as_float(0x4B000000u | u), s, -c0);
-            }
-            const __nv_bfloat162 p = __floats2bfloat162_rn(f[0], f[1]);
-            w[q] = *reinterpret_cast<const uint32_t*>(&p);
+        const float M = __int_as_float((127 + 23 - 7 - 8 * (k - 1)) << 23) * 1.5f;  // 1.5 2^23 u_k
+        const float q = (r + M) - M;
+        r -= q;
+        if (k >= 4) {
+            const float qt = (t + M) - M;
+            t -= qt;
+            s[k - 1] = q + qt;
+        } else {
+            s[k - 1] = q;
         }
-        out[k - 1] = make_uint4(w[0], w[1], w[2], w[3]);
     }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&p);
 }
 
 // Twice each bf16 of a packed 16-byte run (exponent + 1; zeros stay zero).
@@ -163,13 +162,15 @@ struct Tile {
     bool sym;
 };
 
+// Every tile stages all ld columns of its rows: a stage's 16 rows of a plane are
+// then one contiguous run, one bulk copy per plane and stage.
 __device__ __forceinline__ Tile tile_of(int t, int n_tot, int ld, int ntp) {
     Tile T;
     const int G = ntp / 8;
     if (t == 0) {
         T.a0 = 0; T.ga = G < 16 ? G : 16; T.b0 = 0; T.gb = 0; T.sym = true;
         T.N = ntp < 128 ? ntp : 128; T.row0 = 0; T.col0 = 0;
-        T.c0 = 0; T.ncopy = ld < 128 ? ld : 128;
+        T.c0 = 0; T.ncopy = ld;
     } else if (t == 1) {
         T.a0 = 0; T.ga = 16; T.b0 = 128; T.gb = G - 16; T.sym = false;
         T.N = ntp - 128; T.row0 = 0; T.col0 = 128;
@@ -177,26 +178,23 @@ __device__ __forceinline__ Tile tile_of(int t, int n_tot, int ld, int ntp) {
     } else {
         T.a0 = 128; T.ga = G - 16; T.b0 = 128; T.gb = 0; T.sym = true;
         T.N = ntp - 128; T.row0 = 128; T.col0 = 128;
-        T.c0 = 128; T.ncopy = ld - 128;
+        T.c0 = 0; T.ncopy = ld;
     }
     return T;
 }
 
-__host__ __device__ inline size_t oz_fstage_bytes(int ncopy) { return (size_t)KS * ((ncopy * 8 + 15) / 16 * 16); }
+// staging of a stage: KS rows of the hi plane, then KS rows of the lo plane, ncopy floats each
+__host__ __device__ inline size_t oz_fstage_bytes(int ncopy) { return (size_t)KS * 2 * ncopy * 4; }
 
 __host__ __device__ inline size_t oz_smem_bytes(int ld) {
     // worst tile: O (every column copied, two slice sets)
     return (size_t)FST * oz_fstage_bytes(ld) + (size_t)SST * slice_regions(1) * SLICE_BYTES + 1024;
 }
 
-// float-pair accumulation: (h, l) += x, about 2^-48 relative
-__device__ __forceinline__ void fp_add(float& h, float& l, float x) {
-    const float s = h + x;
-    const float bb = s - h;
-    const float err = (h - (s - bb)) + (x - bb);
-    const float t = l + err;
-    h = s + t;
-    l = t - (h - s);
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
@@ -212,49 +210,65 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
     __shared__ uint64_t f_full[FST], f_empty[FST], s_full[SST], s_empty[SST], a_full, a_empty;
     __shared__ uint32_t tmem_slot;
     __shared__ int fail;
-    __shared__ int expo[MAXN];
+    __shared__ float escale[MAXN];  // 2^-E of each column
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // CTA -> (gram, tile, slab)
     const int gram = (int)blockIdx.x / P.cta_per_gram;
     int rem = (int)blockIdx.x - gram * P.cta_per_gram;
     int t = 0;
-    while (t + 1 < P.ntiles && rem >= P.slabs[t]) {
-        rem -= P.slabs[t];
-        ++t;
+    int64_t srows = P.slab_rows[0];
+    if (P.ntiles > 1 && rem >= P.slabs[0]) {
+        rem -= P.slabs[0];
+        t = 1;
+        srows = P.slab_rows[1];
+        if (rem >= P.slabs[1]) {
+            rem -= P.slabs[1];
+            t = 2;
+            srows = P.slab_rows[2];
+        }
     }
     const int slab = rem;
     const Tile T = tile_of(t, P.n_tot, P.ld, P.ntp);
-    const int64_t r0 = (int64_t)slab * P.slab_rows[t];
-    int64_t r1 = r0 + P.slab_rows[t];
+    const int64_t r0 = (int64_t)slab * srows;
+    int64_t r1 = r0 + srows;
     if (r1 > P.n_rows) r1 = P.n_rows;
     const int nst = r1 > r0 ? (int)((r1 - r0 + KS - 1) / KS) : 0;
     const int niv = (nst + DRAIN - 1) / DRAIN;
-    const double* Y = P.Y[gram];
-    // region of this CTA's running sums: 128 x N float pairs
-    size_t off = (size_t)gram * P.cta_per_gram;
-    float2* run = P.part + ((size_t)blockIdx.x) * 128 * 128;
-    (void)off;
+    const float* Yh = gram ? P.Y[1] : P.Y[0];
+    const unsigned long long* cmx = gram ? P.cmax[1] : P.cmax[0];
+    const float* Yl = Yh + (size_t)P.n_rows * P.ld;
+    // region of this CTA's running sums: 128 x N
+    int4* run = P.part + ((size_t)blockIdx.x) * 128 * 128;
 
-    const size_t fpitch = (size_t)((T.ncopy * 8 + 15) / 16 * 16);
-    const size_t fbytes = (size_t)KS * fpitch;
+    const size_t fpitch = (size_t)T.ncopy * 4;   // one plane's row (ld floats, a multiple of 16 bytes)
+    const size_t fbytes = (size_t)KS * 2 * fpitch;  // hi plane's 16 rows, then the lo plane's
     uint8_t* fbase = smem;
     uint8_t* sbase = smem + FST * fbytes;
     const int nreg = slice_regions(T.sym ? 0 : 1);
     const size_t sstage = (size_t)nreg * SLICE_BYTES;
 
     // column exponents (max over the buckets of the block's column maxima)
-    for (int c = tid; c < MAXN; c += NTHREADS) {
-        int E = 0;
+    {
+        // thread (c, half): column c < 256, buckets half*16 .. +15, loads issued together
+        __shared__ unsigned long long cm_half[MAXN];
+        const int c = tid & (MAXN - 1), hb = tid >> 8;
+        unsigned long long m = 0;
         if (c < P.n_tot) {
-            unsigned long long m = 0;
-            for (int b = 0; b < NBUCKET; ++b) {
-                const unsigned long long v = P.cmax[gram][(size_t)b * P.ld + c];
-                m = v > m ? v : m;
-            }
-            E = col_exponent(__longlong_as_double((long long)m));
+            unsigned long long v[NBUCKET / 2];
+#pragma unroll
+            for (int b = 0; b < NBUCKET / 2; ++b) v[b] = cmx[(size_t)(hb * (NBUCKET / 2) + b) * P.ld + c];
+#pragma unroll
+            for (int b = 0; b < NBUCKET / 2; ++b) m = v[b] > m ? v[b] : m;
         }
-        expo[c] = E;
+        if (hb == 1) cm_half[c] = m;
+        __syncthreads();
+        if (hb == 0) {
+            const unsigned long long o = cm_half[c];
+            m = o > m ? o : m;
+            const int E = c < P.n_tot ? col_exponent(__longlong_as_double((long long)m)) : 0;
+            escale[c] = __int_as_float((127 - E) << 23);
+        }
     }
     // slice stages start at zero: groups that are never written (padding) read as 0
     for (size_t q = tid; q < SST * sstage / 16; q += NTHREADS) reinterpret_cast<uint4*>(sbase)[q] = make_uint4(0, 0, 0, 0);
@@ -280,20 +294,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {  // producer: float64 rows into the staging ring
-            const uint32_t rb = (uint32_t)(T.ncopy * 8);
+        if (lane == 0) {  // producer: float-pair rows into the staging ring
+            const uint32_t rb = (uint32_t)(T.ncopy * 4);
             for (int q = 0; q < nst; ++q) {
                 const int fs = q % FST;
-                if (q >= FST && !mbar_wait_sleep(smem_u32(&f_empty[fs]), ((q / FST) - 1) & 1, &fail)) {
+                if (q >= FST && !mbar_spin(smem_u32(&f_empty[fs]), ((q / FST) - 1) & 1, &fail)) {
                     atomicOr(&fail, 1);
                     break;
                 }
                 const int64_t rr = r0 + (int64_t)q * KS;
                 const int nr = (int)((r1 - rr) < KS ? (r1 - rr) : KS);
-                mbar_expect_tx(&f_full[fs], (uint32_t)nr * rb);
+                mbar_expect_tx(&f_full[fs], (uint32_t)nr * 2 * rb);
                 const uint32_t dst = smem_u32(fbase + fs * fbytes);
-                for (int r = 0; r < nr; ++r)
-                    bulk_copy(dst + (uint32_t)(r * fpitch), Y + (size_t)(rr + r) * P.ld + T.c0, rb, &f_full[fs]);
+                const size_t src = (size_t)rr * P.ld;
+                bulk_copy(dst, Yh + src, (uint32_t)nr * rb, &f_full[fs]);
+                bulk_copy(dst + (uint32_t)(KS * fpitch), Yl + src, (uint32_t)nr * rb, &f_full[fs]);
             }
         }
         __syncwarp();
@@ -303,11 +318,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
             bool ok = true;
             for (int q = 0; q < nst && ok; ++q) {
                 const int ss = q % SST, pos = q % DRAIN;
-                if (!mbar_wait_sleep(smem_u32(&s_full[ss]), (q / SST) & 1, &fail)) {
+                if (!mbar_spin(smem_u32(&s_full[ss]), (q / SST) & 1, &fail)) {
                     ok = false;
                     break;
                 }
-                if (pos == 0 && q > 0 && !mbar_wait_sleep(smem_u32(&a_empty), ((q / DRAIN) - 1) & 1, &fail)) {
+                if (pos == 0 && q > 0 && !mbar_spin(smem_u32(&a_empty), ((q / DRAIN) - 1) & 1, &fail)) {
                     ok = false;
                     break;
                 }
@@ -342,48 +357,58 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
         const int m = 32 * quad + lane;  // tile row of this thread
         const int nch = T.N / 16;
         for (int iv = 0; iv < niv; ++iv) {
+            // long waits (a whole drain interval): suspended, so the converters keep the issue slots
             const bool got = mbar_wait_sleep(smem_u32(&a_full), iv & 1, &fail);
             if (!got || fail) {
                 atomicOr(&fail, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int c = half; c < nch; c += 2) {
-                uint32_t v[NGRP][16];
+            for (int c = half; c < 2 * nch; c += 2) {  // 8-column pieces
+                int4* dst = run + (size_t)m * T.N + 8 * c;
+                int4 o[8];
+                if (iv > 0) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) o[e] = dst[e];
+                }
+                uint32_t v[NGRP][8];
 #pragma unroll
                 for (int g = 0; g < NGRP; ++g)
-                    tmem_ld16_nowait(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(g * T.N + 16 * c), v[g]);
+                    tmem_ld8_nowait(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(g * T.N + 8 * c), v[g]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float2* dst = run + (size_t)m * T.N + 16 * c;
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float h = 0.f, l = 0.f;
+                for (int e = 0; e < 8; ++e) {
+                    // groups i+j = 2, 3, 4 hold integers in units of 2^-14, 2^-22, 2^-30 (< 2^24 of them)
+                    const long long n2 = float_int(__uint_as_float(v[0][e]) * 16384.0f);
+                    const long long n3 = float_int(__uint_as_float(v[1][e]) * 4194304.0f);
+                    const long long n4 = float_int(__uint_as_float(v[2][e]) * 1073741824.0f);
+                    long long acc = (n2 << 16) + (n3 << 8) + n4;
+                    float r5 = __uint_as_float(v[3][e]);
                     if (iv > 0) {
-                        const float2 o = dst[e];
-                        h = o.x;
-                        l = o.y;
+                        acc += ((long long)(unsigned)o[e].y << 32) | (unsigned)o[e].x;
+                        r5 += __int_as_float(o[e].z);
                     }
-#pragma unroll
-                    for (int g = 0; g < NGRP; ++g) fp_add(h, l, __uint_as_float(v[g][e]));
-                    dst[e] = make_float2(h, l);
+                    dst[e] = make_int4((int)(unsigned)acc, (int)(acc >> 32), __float_as_int(r5), 0);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&a_empty);
         }
-    } else {  // converters: float64 rows -> slice operands
+    } else {  // converters: float-pair rows -> slice operands
         const int ci = warp < 4 ? warp - 2 : warp - 12 + 2;
         const int ctid = ci * 32 + lane;
-        const int gt = T.ga + T.gb;
+        const int ga = T.ga, gt = T.ga + T.gb;
         const int units = KS * gt;
+        const int a0 = T.a0, b0 = T.b0, c0 = T.c0, n_tot = P.n_tot;
+        const bool sym = T.sym;
         for (int q = 0; q < nst; ++q) {
             const int fs = q % FST, ss = q % SST;
-            if (!mbar_wait_sleep(smem_u32(&f_full[fs]), (q / FST) & 1, &fail)) {
+            if (!mbar_spin(smem_u32(&f_full[fs]), (q / FST) & 1, &fail)) {
                 atomicOr(&fail, 1);
                 break;
             }
-            if (q >= SST && !mbar_wait_sleep(smem_u32(&s_empty[ss]), ((q / SST) - 1) & 1, &fail)) {
+            if (q >= SST && !mbar_spin(smem_u32(&s_empty[ss]), ((q / SST) - 1) & 1, &fail)) {
                 atomicOr(&fail, 1);
                 break;
             }
@@ -391,32 +416,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
             const int nr = (int)((r1 - rr) < KS ? (r1 - rr) : KS);
             const uint8_t* fst = fbase + fs * fbytes;
             uint8_t* st = sbase + ss * sstage;
+            // unit = (row r, 8-column group g): consecutive threads take consecutive groups of
+            // a row (contiguous staging reads, slice stores 272 bytes apart: no bank conflicts)
             for (int u = ctid; u < units; u += NCONV * 32) {
-                const int r = u % KS, g = u / KS;
-                const bool isb = g >= T.ga;
-                const int gl = isb ? g - T.ga : g;
-                const int cb = (isb ? T.b0 : T.a0) + 8 * gl;  // first global column of the unit
-                double v[8];
-                int E[8];
+                const int r = u / gt, g = u - r * gt;
+                const bool isb = g >= ga;
+                const int gl = isb ? g - ga : g;
+                const int cb = (isb ? b0 : a0) + 8 * gl;  // first global column of the unit
+                const bool row_in = r < nr;
+                const float4* ph = reinterpret_cast<const float4*>(fst + (size_t)r * fpitch + (size_t)(cb - c0) * 4);
+                const float4* pl =
+                    reinterpret_cast<const float4*>(fst + (size_t)(KS + r) * fpitch + (size_t)(cb - c0) * 4);
+                const bool full = row_in && cb + 8 <= n_tot;
+                uint32_t w[4][NSL];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int col = cb + c;
-                    const bool in = r < nr && col < P.n_tot;
-                    v[c] = in ? *reinterpret_cast<const double*>(fst + (size_t)r * fpitch + (size_t)(col - T.c0) * 8)
-                              : 0.0;
-                    E[c] = expo[col < MAXN ? col : 0];
+                for (int h4 = 0; h4 < 2; ++h4) {
+                    float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
+                    if (full) {
+                        xh = ph[h4];
+                        xl = pl[h4];
+                    } else if (row_in) {
+                        const float* fh = reinterpret_cast<const float*>(ph) + 4 * h4;
+                        const float* fl = reinterpret_cast<const float*>(pl) + 4 * h4;
+                        const int cc = cb + 4 * h4;
+                        if (cc + 0 < n_tot) { xh.x = fh[0]; xl.x = fl[0]; }
+                        if (cc + 1 < n_tot) { xh.y = fh[1]; xl.y = fl[1]; }
+                        if (cc + 2 < n_tot) { xh.z = fh[2]; xl.z = fl[2]; }
+                        if (cc + 3 < n_tot) { xh.w = fh[3]; xl.w = fl[3]; }
+                    }
+                    const int cc = cb + 4 * h4;
+                    float s0[NSL], s1[NSL], s2[NSL], s3[NSL];
+                    split_df(xh.x, xl.x, escale[cc + 0], s0);
+                    split_df(xh.y, xl.y, escale[cc + 1], s1);
+                    split_df(xh.z, xl.z, escale[cc + 2], s2);
+                    split_df(xh.w, xl.w, escale[cc + 3], s3);
+#pragma unroll
+                    for (int k = 0; k < NSL; ++k) {
+                        w[2 * h4][k] = pack_bf16(s0[k], s1[k]);
+                        w[2 * h4 + 1][k] = pack_bf16(s2[k], s3[k]);
+                    }
                 }
-                uint4 sl[NSL];
-                split8(v, E, sl);
                 const size_t inner = (size_t)gl * GB + (r >> 3) * 128 + (r & 7) * 16;
                 const int base_region = isb ? NSL : 0;
 #pragma unroll
-                for (int k = 0; k < NSL; ++k)
-                    *reinterpret_cast<uint4*>(st + (size_t)(base_region + k) * SLICE_BYTES + inner) = sl[k];
-                if (T.sym) {
-#pragma unroll
-                    for (int k = 1; k < NSL; ++k)
-                        *reinterpret_cast<uint4*>(st + (size_t)(NSL + k - 1) * SLICE_BYTES + inner) = twice8(sl[k]);
+                for (int k = 0; k < NSL; ++k) {
+                    const uint4 val = make_uint4(w[0][k], w[1][k], w[2][k], w[3][k]);
+                    *reinterpret_cast<uint4*>(st + (size_t)(base_region + k) * SLICE_BYTES + inner) = val;
+                    if (sym && k >= 1)
+                        *reinterpret_cast<uint4*>(st + (size_t)(NSL + k - 1) * SLICE_BYTES + inner) = twice8(val);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -438,39 +485,61 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
 // ---------------------------------------------------------------- reduction
 
 // Sum of the slab partials of output element (i, j) (i <= j) of one Gram,
-// symmetrised on the diagonal tiles, scaled back by 2^(E_i + E_j).
+// symmetrised on the diagonal tiles, scaled back by 2^(E_i + E_j): the exact
+// groups as one integer in units of 2^-30 (int64, exact), group >= 5 in
+// float32 (it is below 2^-24 of the total).  Eight lanes share an element
+// (lane q sums the slabs k = q mod 8) and combine their sums in a fixed order.
 struct RedArgs {
-    const float2* part;
+    const int4* part;
     int ntiles, slabs[3], n_tot, ntp, cta_per_gram;
     int tile_cta0[3];  // first CTA of each tile within a Gram
 };
 
-__device__ __forceinline__ double slab_sum(const float2* base, int nsl, int N, int a, int b) {
-    double s = 0.0;
-    for (int k = 0; k < nsl; ++k) {
-        const float2 v = base[(size_t)k * 128 * 128 + (size_t)a * N + b];
-        s += (double)v.x + (double)v.y;
+__device__ __forceinline__ void slab_sum8(const int4* base, int nsl, int N, int a, int b, int q, long long& acc,
+                                          float& r5) {
+    for (int k = q; k < nsl; k += 8) {
+        const int4 v = base[(size_t)k * 128 * 128 + (size_t)a * N + b];
+        acc += (long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x);
+        r5 += __int_as_float(v.z);
     }
-    return s;
 }
 
-__device__ double gram_entry(const RedArgs& R, int gram, int i, int j, const int* E) {
-    const float2* g = R.part + (size_t)gram * R.cta_per_gram * 128 * 128;
-    double s;
+// Lane q's part of the sum of element (i, j) of one Gram; `sym` tells whether
+// the element lies in a diagonal tile (halve (P_ij + P_ji)).
+__device__ __forceinline__ void gram_part(const RedArgs& R, int gram, int i, int j, int q, long long& acc, float& r5,
+                                          bool& sym) {
+    const int4* g = R.part + (size_t)gram * R.cta_per_gram * 128 * 128;
+    acc = 0;
+    r5 = 0.f;
     if (j < 128) {  // D0
         const int N = R.ntp < 128 ? R.ntp : 128;
-        const float2* b = g + (size_t)R.tile_cta0[0] * 128 * 128;
-        s = 0.5 * (slab_sum(b, R.slabs[0], N, i, j) + slab_sum(b, R.slabs[0], N, j, i));
+        const int4* b = g + (size_t)R.tile_cta0[0] * 128 * 128;
+        slab_sum8(b, R.slabs[0], N, i, j, q, acc, r5);
+        slab_sum8(b, R.slabs[0], N, j, i, q, acc, r5);
+        sym = true;
     } else if (i < 128) {  // O
-        const int N = R.ntp - 128;
-        const float2* b = g + (size_t)R.tile_cta0[1] * 128 * 128;
-        s = slab_sum(b, R.slabs[1], N, i, j - 128);
+        const int4* b = g + (size_t)R.tile_cta0[1] * 128 * 128;
+        slab_sum8(b, R.slabs[1], R.ntp - 128, i, j - 128, q, acc, r5);
+        sym = false;
     } else {  // D1
         const int N = R.ntp - 128;
-        const float2* b = g + (size_t)R.tile_cta0[2] * 128 * 128;
-        s = 0.5 * (slab_sum(b, R.slabs[2], N, i - 128, j - 128) + slab_sum(b, R.slabs[2], N, j - 128, i - 128));
+        const int4* b = g + (size_t)R.tile_cta0[2] * 128 * 128;
+        slab_sum8(b, R.slabs[2], N, i - 128, j - 128, q, acc, r5);
+        slab_sum8(b, R.slabs[2], N, j - 128, i - 128, q, acc, r5);
+        sym = true;
     }
-    return ldexp(s, E[i] + E[j]);
+}
+
+// Combine the eight lanes (fixed tree) and scale: the Gram entry in float64.
+__device__ __forceinline__ double gram_combine(long long acc, float r5, bool sym, int Ei, int Ej) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        r5 += __shfl_xor_sync(0xffffffffu, r5, o);
+    }
+    double s = ldexp((double)acc, -30) + (double)r5;
+    if (sym) s *= 0.5;
+    return ldexp(s, Ei + Ej);
 }
 
 // Moments from the Gram products of a step (see launch_oz_moments).
@@ -494,54 +563,58 @@ oz_moments_kernel(RedArgs R, const unsigned long long* cmE, const unsigned long 
     }
     __syncthreads();
     const size_t nn = (size_t)n * n;
-    const size_t npairs = (size_t)n * (n + 1) / 2;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < npairs; e += (size_t)gridDim.x * blockDim.x) {
-        // e -> (i, j), i <= j, row-major over the upper triangle
-        int i = (int)((2.0 * n + 1.0 - sqrt((2.0 * n + 1.0) * (2.0 * n + 1.0) - 8.0 * (double)e)) / 2.0);
-        if (i < 0) i = 0;
-        while (i > 0 && (size_t)i * (2 * n - i + 1) / 2 > e) --i;
-        while ((size_t)(i + 1) * (2 * n - i) / 2 <= e) ++i;
-        const int j = i + (int)(e - (size_t)i * (2 * n - i + 1) / 2);
+    const int q = threadIdx.x & 7;
+    // groups of 8 lanes walk the upper triangle row by row
+    const int64_t ng = (int64_t)gridDim.x * (blockDim.x / 8);
+    const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 3);
+    const int64_t npairs = (int64_t)n * (n + 1) / 2;
+    // every lane of a warp runs the same number of iterations (shuffles)
+    const int64_t iters = (npairs + ng - 1) / ng;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t e = g0 + it * ng;
+        const bool live = e < npairs;
+        int i = 0, j = 0;
+        if (live) {
+            // row i: first index i (2n - i + 1) / 2
+            i = (int)((2.0f * n + 1.0f - sqrtf((2.0f * n + 1.0f) * (2.0f * n + 1.0f) - 8.0f * (float)e)) * 0.5f);
+            if (i < 0) i = 0;
+            if (i > n - 1) i = n - 1;
+            while (i > 0 && (int64_t)i * (2 * n - i + 1) / 2 > e) --i;
+            while ((int64_t)(i + 1) * (2 * n - i) / 2 <= e) ++i;
+            j = i + (int)(e - (int64_t)i * (2 * n - i + 1) / 2);
+        }
+        long long acc;
+        float r5;
+        bool sym;
+        if (live) gram_part(R, 0, i, j, q, acc, r5, sym);
+        else { acc = 0; r5 = 0.f; sym = false; }
+        const double ge = gram_combine(acc, r5, sym, live ? E0[i] : 0, live ? E0[j] : 0);
+        double h = 0.0;
+        if (step >= 0) {
+            if (live) gram_part(R, 1, i, j, q, acc, r5, sym);
+            else { acc = 0; r5 = 0.f; }
+            h = gram_combine(acc, r5, sym, live ? E1[i] : 0, live ? E1[j] : 0);
+        }
+        if (!live || q != 0) continue;
         const size_t ij = (size_t)i * n + j, ji = (size_t)j * n + i;
-        const double ge = gram_entry(R, 0, i, j, E0);
         if (step < 0) {  // X_0 = V_0^T V_0
             X[ij] = X[ji] = ge;
             Gprev[ij] = Gprev[ji] = ge;
             continue;
         }
-        const double h = gram_entry(R, 1, i, j, E1);
         const double gp = Gprev[ij];
         const double x0 = X[ij];
-        double x1, xo;
         if (step == 0) {
-            x1 = 0.5 * (h - ge - gp);  // V_1^T V_0, symmetric part
+            const double x1 = 0.5 * (h - ge - gp);  // V_1^T V_0, symmetric part
             X[nn + ij] = X[nn + ji] = x1;
-            xo = x1;
         } else {
-            x1 = X[nn + ij];
-            xo = h - ge - gp - x1;  // 2 sym(V_{k+1}^T V_k) - X_1
+            const double xo = h - ge - gp - X[nn + ij];  // 2 sym(V_{k+1}^T V_k) - X_1
             X[(size_t)(2 * step + 1) * nn + ij] = X[(size_t)(2 * step + 1) * nn + ji] = xo;
         }
         const double xe = 2.0 * ge - x0;
         X[(size_t)(2 * step + 2) * nn + ij] = X[(size_t)(2 * step + 2) * nn + ji] = xe;
         Gprev[ij] = Gprev[ji] = ge;
     }
-}
-
-// Column maxima of a block into NBUCKET buckets (bucket = block index mod NBUCKET).
-__global__ void __launch_bounds__(256)
-colmax_kernel(const double* __restrict__ V, int ld, int n_cols, int64_t n_rows, unsigned long long* cm) {
-    __shared__ unsigned long long sm[MAXN];
-    for (int c = threadIdx.x; c < MAXN; c += blockDim.x) sm[c] = 0;
-    __syncthreads();
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_rows * ld;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e % ld);
-        if (c < n_cols) atomicMax(&sm[c], (unsigned long long)__double_as_longlong(fabs(V[e])));
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n_cols; c += blockDim.x)
-        if (sm[c]) atomicMax(cm + (size_t)(blockIdx.x % NBUCKET) * ld + c, sm[c]);
 }
 
 struct Layout {
@@ -583,29 +656,20 @@ int oz_buckets() { return NBUCKET; }
 
 size_t oz_partial_floats(int n_tot, int64_t n_rows) {
     const Layout L = oz_layout(n_tot, n_rows);
-    return (size_t)2 * L.cta_per_gram * 128 * 128 * 2;  // float2 per element, two Grams
+    return (size_t)2 * L.cta_per_gram * 128 * 128 * 4;  // int4 per element, two Grams
 }
 
-cudaError_t launch_colmax(const double* V, int ld, int n_cols, int64_t n_rows, unsigned long long* cm,
-                          cudaStream_t s) {
-    int64_t blocks = (n_rows * ld + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
-    colmax_kernel<<<(int)blocks, 256, 0, s>>>(V, ld, n_cols, n_rows, cm);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gram_oz(const double* Y0, const unsigned long long* cm0, const double* Y1,
+cudaError_t launch_gram_oz(const float* Y0, const unsigned long long* cm0, const float* Y1,
                            const unsigned long long* cm1, int n_tot, int ld, int64_t n_rows, float* part, int* flag,
                            cudaStream_t s) {
-    if (!gram_oz_supported(n_tot) || (ld & 1)) return cudaErrorInvalidValue;
+    if (!gram_oz_supported(n_tot) || (ld & 3)) return cudaErrorInvalidValue;
     const Layout L = oz_layout(n_tot, n_rows);
     OzArgs a{};
     a.Y[0] = Y0;
     a.Y[1] = Y1;
     a.cmax[0] = cm0;
     a.cmax[1] = cm1;
-    a.part = reinterpret_cast<float2*>(part);
+    a.part = reinterpret_cast<int4*>(part);
     a.flag = flag;
     a.n_tot = n_tot;
     a.ld = ld;
@@ -630,7 +694,7 @@ cudaError_t launch_oz_moments(const float* part, const unsigned long long* cmE, 
                               cudaStream_t s) {
     const Layout L = oz_layout(n_tot, n_rows);
     RedArgs R{};
-    R.part = reinterpret_cast<const float2*>(part);
+    R.part = reinterpret_cast<const int4*>(part);
     R.ntiles = L.ntiles;
     R.n_tot = n_tot;
     R.ntp = (n_tot + 15) / 16 * 16;
@@ -642,7 +706,7 @@ cudaError_t launch_oz_moments(const float* part, const unsigned long long* cmE, 
         if (t < L.ntiles) c0 += L.slabs[t];
     }
     const int64_t npairs = (int64_t)n_tot * (n_tot + 1) / 2;
-    int64_t blocks = (npairs + 255) / 256;
+    int64_t blocks = (npairs * 8 + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     oz_moments_kernel<<<(int)blocks, 256, 0, s>>>(R, cmE, step >= 0 ? cmH : nullptr, ld, Gprev, X, step);
     return cudaGetLastError();

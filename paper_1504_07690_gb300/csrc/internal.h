@@ -50,10 +50,12 @@ struct Plan {
     float off32[3] = {0, 0, 0};
     double* d_diag64 = nullptr;        // alpha * diag + beta
     float* d_diag32 = nullptr;
+    float* d_diag32lo = nullptr;       // SSM_FP64_TC: alpha diag + beta - d_diag32 (float pair)
     int64_t* d_rowptr = nullptr;
     int32_t* d_colind = nullptr;
     double* d_val64 = nullptr;         // alpha * val (beta applied separately)
     float* d_val32 = nullptr;
+    float* d_val32lo = nullptr;        // SSM_FP64_TC: alpha val - d_val32
     double a = 0, b = 0;               // Chebyshev interval
     double glo = 0, ghi = 0;           // spectral bounds (Gershgorin or user)
     double alpha = 0, beta = 0;
@@ -64,7 +66,7 @@ struct Plan {
     int n_split = 0;
     bool use_tc = false;               // mixed path on tensor cores
     bool use_oz = false;               // float64 plan with tensor-core Gram products (SSM_FP64_TC)
-    double* d_ozU[2] = {nullptr, nullptr};      // U_k = V_{k+1} + V_k, in d_ozU[k % 2]
+    void* d_ozU[2] = {nullptr, nullptr};        // U_k = V_{k+1} + V_k (float pairs), in d_ozU[k % 2]
     unsigned long long* d_ozcm = nullptr;       // column maxima: V_j in slot j % 3, U_k in slot 3 + k % 2
     float* d_ozpart = nullptr;                  // running sums of the Gram CTAs
     double* d_ozG = nullptr;                    // V_k^T V_k of the last step (n_tot^2)
@@ -159,28 +161,29 @@ cudaError_t launch_csr_step_f64(const Plan& P, const double* Vc, const double* V
 cudaError_t launch_csr_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
                                 float c, float d, uint8_t* panel, cudaStream_t s);
 cudaError_t launch_panelize(const Plan& P, const float* V, uint8_t* panel, cudaStream_t s);
-// Float64 steps for the tensor-core float64 Gram: also Un = V_{k+1} + V_k and the column
-// maxima of |V_{k+1}| (cmv) and |Un| (cmu), nbucket x ld arrays (atomicMax of bit patterns;
-// zero them before the step).
-cudaError_t launch_stencil_step_f64_oz(const Plan& P, const double* Vc, const double* Vp, double* Vn, double c,
-                                       double d, double* Un, unsigned long long* cmv, unsigned long long* cmu,
-                                       int nbucket, cudaStream_t s);
-cudaError_t launch_csr_step_f64_oz(const Plan& P, const double* Vc, const double* Vp, double* Vn, double c, double d,
-                                   double* Un, unsigned long long* cmv, unsigned long long* cmu, int nbucket,
-                                   cudaStream_t s);
+// Float-pair recurrence of SSM_FP64_TC plans (recurrence_df.cu): blocks are a hi plane
+// (n x ld floats) followed by a lo plane.  One step writes Vn and Un = Vn + Vc and the
+// column maxima of |Vn| (cmv) and |Un| (cmu), nbucket x ld arrays (atomicMax of bit
+// patterns of an upper bound; zero them before the step).  Vp NULL for the first step.
+cudaError_t launch_step_df(const Plan& P, const void* Vc, const void* Vp, void* Vn, void* Un, float c, float d,
+                           unsigned long long* cmv, unsigned long long* cmu, int nbucket, cudaStream_t s);
+// W (float64, leading dimension ldsrc) -> float-pair block (leading dimension ld) and its
+// column maxima (cm, zeroed before).
+cudaError_t launch_convert_in_df(const double* src, int64_t ldsrc, void* dst, int ld, int64_t n_rows, int n_cols,
+                                 unsigned long long* cm, int nbucket, cudaStream_t s);
+// h = (float)v, l = (float)(v - h).
+cudaError_t launch_split_df(const double* v, int64_t n, float* h, float* l, cudaStream_t s);
 
-// Tensor-core float64 Gram (gram_oz.cu): exact products of bf16 slices of the float64
-// blocks.  One launch forms G_0 = Y0^T Y0 and, if Y1 != NULL, G_1 = Y1^T Y1 (running sums
-// per CTA in `part`, oz_partial_floats floats); launch_oz_moments turns them into the
+// Tensor-core float64-accuracy Gram (gram_oz.cu): exact products of bf16 slices of the
+// float-pair blocks.  One launch forms G_0 = Y0^T Y0 and, if Y1 != NULL, G_1 = Y1^T Y1
+// (running sums per CTA in `part`, oz_partial_floats floats); launch_oz_moments turns them into the
 // moments of a step (step -1: X_0 from V_0; step k: X_{2k+1}, X_{2k+2} from V_{k+1} and
 // U_k = V_{k+1} + V_k, with Gprev = V_k^T V_k, updated to V_{k+1}^T V_{k+1}).  Column
 // scales come from the nbucket x ld column maxima (cm0, cm1).
 bool gram_oz_supported(int n_tot);
 int oz_buckets();
 size_t oz_partial_floats(int n_tot, int64_t n_rows);
-cudaError_t launch_colmax(const double* V, int ld, int n_cols, int64_t n_rows, unsigned long long* cm,
-                          cudaStream_t s);
-cudaError_t launch_gram_oz(const double* Y0, const unsigned long long* cm0, const double* Y1,
+cudaError_t launch_gram_oz(const float* Y0, const unsigned long long* cm0, const float* Y1,
                            const unsigned long long* cm1, int n_tot, int ld, int64_t n_rows, float* part, int* flag,
                            cudaStream_t s);
 cudaError_t launch_oz_moments(const float* part, const unsigned long long* cmE, const unsigned long long* cmH,

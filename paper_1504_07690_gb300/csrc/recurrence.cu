@@ -144,47 +144,19 @@ __device__ __forceinline__ void load_item(ItemLoads<T>& L, const RowInfo& ri, ui
     L.vp = need_vp ? ldg_stream(vp + base + cc) : vzero(T(0));
 }
 
-// Outputs of the float64 step for the tensor-core float64 Gram (gram_oz.cu):
-// U_k = V_{k+1} + V_k (the odd moments come from (V_{k+1} + V_k)^T (V_{k+1} + V_k))
-// and the column maxima of |V_{k+1}| and |U_k| (bit patterns, atomicMax) in
-// bucket blockIdx.x mod nbucket of two nbucket x ld arrays.
-struct OzOut {
-    double* U;                 // NULL: no float64 Gram outputs
-    unsigned long long* cmv;
-    unsigned long long* cmu;
-    uint32_t nbucket;
-};
-
-__device__ __forceinline__ void oz_track(unsigned long long* sm, uint32_t col, double2 v) {
-    atomicMax(sm + col, (unsigned long long)__double_as_longlong(fabs(v.x)));
-    atomicMax(sm + col + 1, (unsigned long long)__double_as_longlong(fabs(v.y)));
-}
-
-__device__ __forceinline__ void oz_flush(const unsigned long long* sm, uint32_t ld, const OzOut& oz) {
-    const size_t b = (size_t)(blockIdx.x % oz.nbucket) * ld;
-    for (uint32_t c = threadIdx.x; c < ld; c += blockDim.x) {
-        if (sm[c]) atomicMax(oz.cmv + b + c, sm[c]);
-        if (sm[ld + c]) atomicMax(oz.cmu + b + c, sm[ld + c]);
-    }
-}
-
 // A CTA owns one 32-row panel at a time (grid-stride over panels): the first
 // 32 threads tabulate the rows' neighbour rows, then all 256 threads walk the
 // panel's (row, 16-byte chunk) items, so loads and stores are coalesced and
 // every lane is busy; with PANEL each item's split-bf16 hi and lo parts go
 // straight to their place in the panel (8-byte stores: no shared-memory stage
 // and no barrier per panel, so more of these CTAs fit next to a Gram CTA).
-template <typename T, bool PANEL, bool OZ = false>
+template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256, 4)
 stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                     const T* __restrict__ diag2, StencilGeom g, T o0, T o1, T o2, T c, T d,
-                    uint32_t nchunk, uint32_t n_rows, PanelOut po, OzOut oz = OzOut{}) {
+                    uint32_t nchunk, uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
     __shared__ RowInfo info[32];
-    extern __shared__ unsigned long long oz_cm[];  // OZ: 2 x ld column maxima of this CTA
-    if constexpr (OZ) {
-        for (uint32_t q = threadIdx.x; q < 4 * nchunk; q += blockDim.x) oz_cm[q] = 0ull;
-    }
     const uint32_t mdiv = ((1u << 20) + nchunk - 1) / nchunk;  // it / nchunk for it < 32 nchunk
     const VT* vc = reinterpret_cast<const VT*>(Vc);
     const VT* vp = reinterpret_cast<const VT*>(Vp);
@@ -244,38 +216,23 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
                     out = vscale(c, acc);
                     if (d != T(0)) out = vfma(-d, L[u].vp, out);
                     vn[(size_t)(pnl * 32 + rr[u]) * nchunk + cq[u]] = out;
-                    if constexpr (OZ) {
-                        const VT uu = vadd(out, L[u].x);
-                        reinterpret_cast<VT*>(oz.U)[(size_t)(pnl * 32 + rr[u]) * nchunk + cq[u]] = uu;
-                        oz_track(oz_cm, 2 * cq[u], out);
-                        oz_track(oz_cm + 2 * nchunk, 2 * cq[u], uu);
-                    }
                 }
                 if constexpr (PANEL) panel_store4(po, pnl, rr[u], 4 * cq[u], out);
             }
         }
     }
-    if constexpr (OZ) {
-        __syncthreads();
-        oz_flush(oz_cm, 2 * nchunk, oz);
-    }
 }
 
-template <typename T, bool PANEL, bool OZ = false>
+template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                 const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                 const T* __restrict__ val2, T beta, const T* __restrict__ beta_row, T c, T d, uint32_t nchunk,
-                uint32_t n_rows, PanelOut po, OzOut oz = OzOut{}) {
+                uint32_t n_rows, PanelOut po) {
     using VT = typename Vec16<T>::type;
     const VT* vc = reinterpret_cast<const VT*>(Vc);
     const VT* vp = reinterpret_cast<const VT*>(Vp);
     VT* vn = reinterpret_cast<VT*>(Vn);
-    extern __shared__ unsigned long long oz_cm_csr[];
-    if constexpr (OZ) {
-        for (uint32_t q = threadIdx.x; q < 4 * nchunk; q += blockDim.x) oz_cm_csr[q] = 0ull;
-        __syncthreads();
-    }
     const uint32_t n_pan = (n_rows + 31) / 32;
     const uint32_t items = 32 * nchunk;
     for (uint32_t pnl = blockIdx.x; pnl < n_pan; pnl += gridDim.x) {
@@ -294,19 +251,9 @@ csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restric
                 out = vscale(c, acc);
                 if (d != T(0)) out = vfma(-d, ldg_stream(vp + base + cc), out);
                 vn[base + cc] = out;
-                if constexpr (OZ) {
-                    const VT uu = vadd(out, ldg_stream(vc + base + cc));
-                    reinterpret_cast<VT*>(oz.U)[base + cc] = uu;
-                    oz_track(oz_cm_csr, 2 * cc, out);
-                    oz_track(oz_cm_csr + 2 * nchunk, 2 * cc, uu);
-                }
             }
             if constexpr (PANEL) panel_store4(po, pnl, r, 4 * cc, out);
         }
-    }
-    if constexpr (OZ) {
-        __syncthreads();
-        oz_flush(oz_cm_csr, 2 * nchunk, oz);
     }
 }
 
@@ -403,33 +350,6 @@ cudaError_t launch_csr_step_f64(const Plan& P, const double* Vc, const double* V
 cudaError_t launch_csr_step_f32(const Plan& P, const float* Vc, const float* Vp, float* Vn,
                                 float c, float d, uint8_t* panel, cudaStream_t s) {
     return csr_step<float>(P, Vc, Vp, Vn, P.d_val32, (float)P.beta, P.d_beta_row32, c, d, panel, s);
-}
-
-cudaError_t launch_stencil_step_f64_oz(const Plan& P, const double* Vc, const double* Vp, double* Vn, double c,
-                                       double d, double* Un, unsigned long long* cmv, unsigned long long* cmu,
-                                       int nbucket, cudaStream_t s) {
-    const uint32_t nchunk = (uint32_t)(P.ld / 2);
-    const PanelOut po{nullptr, 0};
-    const OzOut oz{Un, cmv, cmu, (uint32_t)nbucket};
-    const size_t smem = (size_t)4 * nchunk * sizeof(unsigned long long);
-    stencil_step_kernel<double, false, true><<<panel_grid(P.n), stencil_threads(nchunk), smem, s>>>(
-        Vc, Vp ? Vp : Vc, Vn, P.d_diag64, P.geom, P.off64[0], P.off64[1], P.off64[2], c, d, nchunk, (uint32_t)P.n,
-        po, oz);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_csr_step_f64_oz(const Plan& P, const double* Vc, const double* Vp, double* Vn, double c, double d,
-                                   double* Un, unsigned long long* cmv, unsigned long long* cmu, int nbucket,
-                                   cudaStream_t s) {
-    const uint32_t nchunk = (uint32_t)(P.ld / 2);
-    const PanelOut po{nullptr, 0};
-    const OzOut oz{Un, cmv, cmu, (uint32_t)nbucket};
-    const int nt = P.csr_threads > 0 ? P.csr_threads : 256;
-    const size_t smem = (size_t)4 * nchunk * sizeof(unsigned long long);
-    csr_step_kernel<double, false, true><<<panel_grid(P.n), nt, smem, s>>>(
-        Vc, Vp ? Vp : Vc, Vn, P.d_rowptr, P.d_colind, P.d_val64, P.beta, P.d_beta_row64, c, d, nchunk,
-        (uint32_t)P.n, po, oz);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_panelize(const Plan& P, const float* V, uint8_t* panel, cudaStream_t s) {

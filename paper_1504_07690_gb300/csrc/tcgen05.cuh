@@ -90,6 +90,31 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t addr, uint32_t parity, 
     return false;
 }
 
+// Non-suspending test of a phase (mbarrier.test_wait) and a bounded spin on it
+// that gives up when another thread of the CTA has recorded a failure in *fail
+// (checked every 1024 polls): for short hand-offs between the warps of a
+// pipeline, where a suspended waiter would add its wake-up latency to every stage.
+__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr long SPIN_WAIT_LIMIT = 1L << 30;  // bounded polls (seconds at the poll rate)
+
+__device__ __forceinline__ bool mbar_spin(uint32_t addr, uint32_t parity, const volatile int* fail) {
+    for (long i = 0; i < SPIN_WAIT_LIMIT; ++i) {
+        if (mbar_test(addr, parity)) return true;
+        if ((i & 1023) == 1023 && fail && *fail) return false;
+    }
+    return false;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count));
 }
