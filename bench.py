@@ -8,6 +8,9 @@ N_v = 200 Rademacher probes, degree M = 1000, 400 sweep points, sigma = 0.02:
   ssm_dos      - Alg. 1 / Prop. 1 coefficient tables, per-point assembly,
                  Alg. 4 + Alg. 6 solves (RESS-DGC) and the KPM line.
 Metric: effective matrix-applies/s = nnz * n_tot * M / t_step.
+The line also carries, per precision (mixed, fp64_tc, fp64), its ms/step and
+the relative L1 error of both DOS lines against the CPU oracle run on the
+same workload (Eq. error; the oracle takes about a minute on the host).
 
 --impl reference times the CPU oracle (plain float64 numpy/scipy from the
 paper's formulas) on a bounded sample of the same workload.
@@ -168,7 +171,7 @@ def solve_flops(ranks, n: int) -> float:
 def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=None):
     """Per-kernel algorithmic work / measured launch time against its bound.
 
-    Algorithmic work per launch (stated in the design doc):
+    Algorithmic work per launch:
       stencil_step_kernel  bytes = (3 N n_tot + N) e   (read V_k, V_{k-1}, diag; write V_{k+1})
       gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
       gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
@@ -183,13 +186,15 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
     M, n_t = c["M"], c["n_t"]
     steps = args.steps
     mixed = args.precision == "mixed"
-    e = 4 if mixed else 8
+    e = 4 if mixed else 8  # float64 and float pairs: 8 bytes a value
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     fp64_peak = 152 * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     out = []
     rl = max(1, stats["recurrence_launches"])
     rec_ms = stats["ms_recurrence"] / rl
+    if args.precision == "fp64_tc":
+        return _rooflines_fp64tc(N, n_tot, stats, steps, rec_ms, hbm, bf16, peak_kind)
     rec_bytes = (3.0 * N * n_tot + N) * e
     out.append(dict(kernel="stencil_step_kernel", bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9,
                     peak=hbm, unit="GB/s", traffic=_traffic("stencil_step_kernel"), work_per_launch=rec_bytes,
@@ -234,6 +239,37 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
     out.append(dict(kernel="solve_kernel", bound="alu", achieved=s_flops / (s_ms * 1e-3) / 1e12, peak=fp64_peak,
                     unit="TFLOP/s", traffic=None, work_per_launch=s_flops, launch_ms=s_ms, ms_per_step=s_ms,
                     peak_source="fp64 peak: 152 SMs x 2 FMA/clk x 2 x %.0f MHz" % sm_mhz))
+    for r in out:
+        r["frac"] = r["achieved"] / r["peak"]
+    return out
+
+
+def oz_issued_flops(N: int, n_tot: int) -> float:
+    """bf16 flops the tensor cores issue for the two Gram products of one SSM_FP64_TC step:
+    tile D0 (128 x min(n, 128)) and D1 (128 x (n - 128)) with the 12 slice pairs i <= j,
+    i + j <= 7, tile O (128 x (n - 128)) with all 21 pairs; n = n_tot rounded to 16."""
+    ntp = (n_tot + 15) // 16 * 16
+    per_row = 12 * 128 * min(ntp, 128) * 2.0
+    if ntp > 128:
+        per_row += (21 + 12) * 128 * (ntp - 128) * 2.0
+    return 2.0 * N * per_row
+
+
+def _rooflines_fp64tc(N, n_tot, stats, steps, rec_ms, hbm, bf16, peak_kind):
+    """SSM_FP64_TC: the float-pair recurrence step (read V_k, V_{k-1}, write V_{k+1}, U_k: 8 bytes
+    a value, plus the diagonal pair) and the slice Gram products on the tensor cores."""
+    ld = (n_tot + 3) // 4 * 4
+    rec_bytes = 4.0 * N * ld * 8 + 8.0 * N
+    gl = max(1, stats["gram_launches"])
+    g_ms = stats["ms_gram"] / gl
+    g_flops = oz_issued_flops(N, n_tot)
+    out = [dict(kernel="stencil_step_df_kernel", bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9, peak=hbm,
+                unit="GB/s", traffic=None, work_per_launch=rec_bytes, launch_ms=rec_ms,
+                ms_per_step=stats["ms_recurrence"] / steps, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"),
+           dict(kernel="gram_oz_kernel", bound="tensor", achieved=g_flops / (g_ms * 1e-3) / 1e12, peak=bf16,
+                unit="TFLOP/s", traffic=None, work_per_launch=g_flops, launch_ms=g_ms,
+                ms_per_step=stats["ms_gram"] / steps,
+                peak_source=f"MEASURED_PEAKS.json bf16_tflops ({peak_kind}); issued bf16 slice products")]
     for r in out:
         r["frac"] = r["achieved"] / r["peak"]
     return out
@@ -313,6 +349,55 @@ def run_reference(args, c, st, W, csr):
         "e2e": {"value": value, "unit": "matrix-applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- accuracy
+
+def oracle_reference(c, st, W, csr, t, info):
+    """The oracle's DOS lines on the whole workload (doubling moments, flags at 1e-8)."""
+    from oracle import ssm_oracle as O
+
+    A = O.csr_matrix(csr.n, csr.rowptr, csr.colind, csr.val)
+    t0 = time.perf_counter()
+    r = O.ress_dgc(A, W, c["n_v"], t, c["M"], c["sigma"], interval=(info["a"], info["b"]), flag_eps=1e-8,
+                   moments="doubling")
+    return r, time.perf_counter() - t0
+
+
+def l1_errors(ss, kpm, ref):
+    """Relative L1 errors (Eq. error) of both DOS lines against the oracle; RESS-DGC on the
+    points the oracle does not flag as within 1e-8 of an Alg. 4 threshold."""
+    from oracle import ssm_oracle as O
+
+    ok = ~ref["flagged"]
+    return {"ss_l1": O.relative_l1_error(ss[ok], ref["dos_ss"][ok]),
+            "kpm_l1": O.relative_l1_error(kpm, ref["dos_kpm"]), "points": int(ok.size),
+            "flagged": int((~ok).sum())}
+
+
+def time_precision(S, st, c, Wd, td, precision, units, warmup, steps):
+    """ms/step of one precision's plan (same step as the timed region), and its DOS lines."""
+    import torch
+
+    plan = S.ssm_plan_create(stencil=st, n_v=c["n_v"], n_vh=c["n_vh"], degree=c["M"], precision=precision)
+
+    def step():
+        S.ssm_moments(plan, Wd)
+        return S.ssm_dos(plan, td, c["sigma"], want_rank=False)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ss, kpm, _ = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"ms_per_step": ms, "value": units / (ms * 1e-3), "steps": steps, "warmup": warmup}
+    plan.close()
+    return out, ss.cpu().numpy(), kpm.cpu().numpy()
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -419,6 +504,22 @@ def run_gpu(args, c, st, W, csr):
         cpu = {"value": units / t_cpu, "unit": "matrix-applies/s", "cores": _blas_threads(), "kind": "oracle",
                "sample": sample}
 
+    # accuracy of every precision against the oracle on this workload, next to its speed:
+    # the metric's "vs the float64 GPU path at L1 error"
+    precisions = None
+    if rank == 0 and ws == 1 and not args.no_accuracy:
+        ref, t_oracle = oracle_reference(c, st, W, csr, t, info)
+        ss_m, kp_m, _ = S.ssm_dos(plan, td, sigma, want_rank=False)
+        precisions = {"oracle_s": t_oracle, "mixed": dict({"ms_per_step": ms, "value": value},
+                                                       **l1_errors(ss_m.cpu().numpy(), kp_m.cpu().numpy(), ref))}
+        tc, ss_t, kp_t = time_precision(S, st, c, Wd, td, "fp64_tc", units, args.warmup, args.steps)
+        precisions["fp64_tc"] = dict(tc, **l1_errors(ss_t, kp_t, ref))
+        if not args.no_fp64:
+            f64, ss_f, kp_f = time_precision(S, st, c, Wd, td, "fp64", units, 1, 1)
+            precisions["fp64"] = dict(f64, **l1_errors(ss_f, kp_f, ref))
+        ok = [k for k in ("mixed", "fp64_tc", "fp64") if k in precisions and precisions[k]["ss_l1"] <= 1e-4]
+        precisions["fastest_within_1e-4_ss"] = min(ok, key=lambda k: precisions[k]["ms_per_step"]) if ok else None
+
     batched = adjoint = None
     if rank == 0 and not args.no_batched:
         batched = bench_batched(S, hbm)
@@ -430,7 +531,7 @@ def run_gpu(args, c, st, W, csr):
             "metric": "ssm_dos_effective_matrix_applies_per_s", "value": value,
             "unit": "matrix-applies/s (nnz*n_tot*M/s)", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "dtype": {"mixed": "f32", "fp64": "f64", "fp64_tc": "f32x2"}[args.precision], "data": "synthetic",
             "config": {"workload": "anderson2d_256: 2D Anderson 256x256 periodic, N=65536, nnz=%d, N_v=200 "
                                    "rademacher, M=1000, 400 sweep points, sigma=0.02" % nnz,
                        "precision": args.precision,
@@ -439,6 +540,7 @@ def run_gpu(args, c, st, W, csr):
             "roofline": roofline, "rooflines": roofs, "phases_ms_per_step": phases,
             "gpu_launches": int(stats["launches"]),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+            "precisions": precisions,
             "batched": batched, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
@@ -560,7 +662,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_tc"])
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the oracle run and the per-precision accuracy and speed table")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the CUDA-core float64 plan in that table")
     ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
