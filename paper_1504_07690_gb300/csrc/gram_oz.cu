@@ -39,11 +39,11 @@
 // O needs every pair.  A CTA owns one tile of one block over a slab of rows:
 // one thread streams the rows' float pairs into shared memory with 1-D
 // bulk copies (one per plane and 16-row stage: every tile takes whole rows,
-// which are contiguous), six warps split them into the slice operands (MN-major,
-// no-swizzle core matrices), one thread issues tcgen05.mma kind::f16 into
-// TMEM, and eight warps drain the accumulators.  The short hand-offs between
-// stages spin on the mbarriers (mbarrier.test_wait); the drain warps, which
-// wait a whole interval, suspend.  Every wait is bounded; on expiry the CTA
+// which are contiguous), fourteen warps split them into the slice operands
+// (MN-major, no-swizzle core matrices), one thread issues tcgen05.mma
+// kind::f16 into TMEM, and eight of the converting warps drain the
+// accumulators at the start of each interval.  The hand-offs spin on the
+// mbarriers (mbarrier.test_wait).  Every wait is bounded; on expiry the CTA
 // sets bit 2 of the status word and stops.
 #include <cuda_bf16.h>
 
@@ -65,8 +65,8 @@ constexpr int NGRP = 4;            // accumulator groups: i+j = 2, 3, 4, >= 5
 constexpr int GB = 2 * 128 + 16;   // one 8-column group of a stage: two 8x16-byte core matrices + pad
 constexpr int SLICE_BYTES = 16 * GB;  // one slice of 128 columns (16 groups)
 constexpr int NTHREADS = 512;
-constexpr int NCONV = 6;           // converter warps: 2, 3, 12..15
-constexpr int NEPI = 8;            // epilogue warps: 4..11
+constexpr int NCONV = 14;          // converter warps: 2..15
+constexpr int NEPI = 8;            // of which 4..11 also drain the accumulators
 constexpr int MAXN = 256;
 constexpr int NBUCKET = 32;        // column-maximum buckets written by the recurrence
 
@@ -352,24 +352,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
             }
         }
         __syncwarp();
-    } else if (warp >= 4 && warp < 4 + NEPI) {  // epilogue: drain the four groups into the running sums
+    } else {
+        // warps 2..15 convert stages; warps 4..11 also drain the accumulators at the start
+        // of every interval after the first and once more at the end
+        const bool epi = warp >= 4 && warp < 4 + NEPI;
         const int quad = warp & 3, half = (warp - 4) >> 2;
-        const int m = 32 * quad + lane;  // tile row of this thread
+        const int m = 32 * quad + lane;  // tile row of a draining thread
         const int nch = T.N / 16;
-        for (int iv = 0; iv < niv; ++iv) {
-            // long waits (a whole drain interval): suspended, so the converters keep the issue slots
-            const bool got = mbar_wait_sleep(smem_u32(&a_full), iv & 1, &fail);
-            if (!got || fail) {
+        // drain of interval iv: the exact groups into the int64 running sum, group >= 5 into
+        // the float32 one
+        auto drain = [&](int iv) -> bool {
+            if (!mbar_spin(smem_u32(&a_full), iv & 1, &fail) || fail) {
                 atomicOr(&fail, 1);
-                break;
+                return false;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int c = half; c < 2 * nch; c += 2) {  // 8-column pieces
-                int4* dst = run + (size_t)m * T.N + 8 * c;
-                int4 o[8];
-                if (iv > 0) {
+            // running sums are stored column by column (element (m, col) at col * 128 + m), so
+            // the 32 rows of a warp are one contiguous 512-byte run; the next piece's sums are
+            // loaded while the current one is combined
+            int4 o[8], on[8];
+            if (iv > 0 && half < 2 * nch) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) o[e] = dst[e];
+                for (int e = 0; e < 8; ++e) on[e] = run[(size_t)(8 * half + e) * 128 + m];
+            }
+            for (int c = half; c < 2 * nch; c += 2) {  // 8-column pieces
+#pragma unroll
+                for (int e = 0; e < 8; ++e) o[e] = on[e];
+                if (iv > 0 && c + 2 < 2 * nch) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) on[e] = run[(size_t)(8 * (c + 2) + e) * 128 + m];
                 }
                 uint32_t v[NGRP][8];
 #pragma unroll
@@ -388,28 +399,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
                         acc += ((long long)(unsigned)o[e].y << 32) | (unsigned)o[e].x;
                         r5 += __int_as_float(o[e].z);
                     }
-                    dst[e] = make_int4((int)(unsigned)acc, (int)(acc >> 32), __float_as_int(r5), 0);
+                    run[(size_t)(8 * c + e) * 128 + m] = make_int4((int)(unsigned)acc, (int)(acc >> 32),
+                                                                   __float_as_int(r5), 0);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&a_empty);
-        }
-    } else {  // converters: float-pair rows -> slice operands
-        const int ci = warp < 4 ? warp - 2 : warp - 12 + 2;
-        const int ctid = ci * 32 + lane;
+            return true;
+        };
+        const int ctid = (warp - 2) * 32 + lane;
         const int ga = T.ga, gt = T.ga + T.gb;
         const int units = KS * gt;
         const int a0 = T.a0, b0 = T.b0, c0 = T.c0, n_tot = P.n_tot;
         const bool sym = T.sym;
+        bool alive = true;
         for (int q = 0; q < nst; ++q) {
             const int fs = q % FST, ss = q % SST;
+            if (epi && q > 0 && (q % DRAIN) == 0 && !drain(q / DRAIN - 1)) {
+                alive = false;
+                break;
+            }
             if (!mbar_spin(smem_u32(&f_full[fs]), (q / FST) & 1, &fail)) {
                 atomicOr(&fail, 1);
+                alive = false;
                 break;
             }
             if (q >= SST && !mbar_spin(smem_u32(&s_empty[ss]), ((q / SST) - 1) & 1, &fail)) {
                 atomicOr(&fail, 1);
+                alive = false;
                 break;
             }
             const int64_t rr = r0 + (int64_t)q * KS;
@@ -418,8 +436,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
             uint8_t* st = sbase + ss * sstage;
             // unit = (row r, 8-column group g): consecutive threads take consecutive groups of
             // a row (contiguous staging reads, slice stores 272 bytes apart: no bank conflicts)
-            for (int u = ctid; u < units; u += NCONV * 32) {
-                const int r = u / gt, g = u - r * gt;
+            for (int u = ctid; u < units; u += NCONV * 32) {                const int r = u / gt, g = u - r * gt;
                 const bool isb = g >= ga;
                 const int gl = isb ? g - ga : g;
                 const int cb = (isb ? b0 : a0) + 8 * gl;  // first global column of the unit
@@ -473,6 +490,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_oz_kernel(OzArgs P) {
                 mbar_arrive(&s_full[ss]);
             }
         }
+        if (epi && alive && niv > 0) drain(niv - 1);
     }
     // teardown: every issued MMA has completed before TMEM is released (the last
     // commit on a_full covers all of them, and the epilogue waited for it)
@@ -498,7 +516,7 @@ struct RedArgs {
 __device__ __forceinline__ void slab_sum8(const int4* base, int nsl, int N, int a, int b, int q, long long& acc,
                                           float& r5) {
     for (int k = q; k < nsl; k += 8) {
-        const int4 v = base[(size_t)k * 128 * 128 + (size_t)a * N + b];
+        const int4 v = base[(size_t)k * 128 * 128 + (size_t)b * 128 + a];  // column by column
         acc += (long long)(((unsigned long long)(unsigned)v.y << 32) | (unsigned)v.x);
         r5 += __int_as_float(v.z);
     }
