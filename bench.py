@@ -520,7 +520,9 @@ def run_gpu(args, c, st, W, csr):
         ok = [k for k in ("mixed", "fp64_tc", "fp64") if k in precisions and precisions[k]["ss_l1"] <= 1e-4]
         precisions["fastest_within_1e-4_ss"] = min(ok, key=lambda k: precisions[k]["ms_per_step"]) if ok else None
 
-    batched = adjoint = None
+    batched = adjoint = lap3d = None
+    if rank == 0 and not args.no_lap3d:
+        lap3d = bench_lap3d(S, hbm)
     if rank == 0 and not args.no_batched:
         batched = bench_batched(S, hbm)
     if rank == 0 and not args.no_adjoint:
@@ -541,7 +543,7 @@ def run_gpu(args, c, st, W, csr):
             "gpu_launches": int(stats["launches"]),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
             "precisions": precisions,
-            "batched": batched, "adjoint": adjoint,
+            "lap3d": lap3d, "batched": batched, "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -592,6 +594,60 @@ def bench_batched(S, hbm, warmup: int = 1, steps: int = 2):
                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "traffic": None, "bytes_per_step": step_bytes}}
     plan.close()
+    return out
+
+
+def bench_lap3d(S, hbm, runs=(("mixed", 256, 0), ("fp64_tc", 256, 0), ("mixed", 128, 128), ("fp64_tc", 128, 128)),
+                n_trace: int = 1024):
+    """The 3D log-normal workload (64^3 periodic 7-point -Laplacian + LogNormal(0, 0.5) potential,
+    N = 262144, N_v = 256 Gaussian probes, M = 2000, 800 sweep points, sigma = 0.06) and its
+    Tr log(A + I) by Alg. 8 on an n_trace-point grid, per precision: one warm-up and one timed
+    step (moments + DOS), the trace timed on its own, both trace estimates against the exact
+    log det(A + I) of tests/golden/lap3d_lognormal_64_logdet.json when that file exists.
+    Each precision runs with the 256 probe columns all in W (N~_v = 0) and split evenly
+    between W and the hybrid block W~ (Alg. 6 / Alg. 7's N_v = N~_v split): under each
+    Gaussian of this workload lie thousands of eigenvalues, far more than 256, where the
+    low-rank estimate alone cannot hold them and the hybrid term carries the rest."""
+    import torch
+    name = "lap3d_lognormal_64"
+    c = dict(wl.CONFIGS[name])
+    st = wl.make_operator(name)
+    W = torch.from_numpy(wl.random_block(st.n, c["n_v"], c["probe_seed"], c["probe"])).cuda()
+    exact = None
+    gpath = os.path.join(ROOT, "tests", "golden", "lap3d_lognormal_64_logdet.json")
+    if os.path.exists(gpath):
+        exact = json.load(open(gpath))["logdet"]
+    out = {"workload": "lap3d_lognormal_64: 3D 7-point periodic 64^3 (N=262144) + LogNormal(0,0.5), N_v=256 "
+                       "gaussian, M=2000, 800 points, sigma=0.06; Tr log(A+I) on a %d-point grid" % n_trace,
+           "exact_logdet": exact}
+    for prec, nv, nvh in runs:
+        plan = S.ssm_plan_create(stencil=st, n_v=nv, n_vh=nvh, degree=c["M"], precision=prec)
+        info = S.ssm_plan_info(plan)
+        td = torch.from_numpy(np.linspace(info["lo"], info["hi"], c["n_t"])).cuda()
+        units = float(info["nnz"]) * (nv + nvh) * c["M"]
+
+        def step():
+            S.ssm_moments(plan, W)
+            return S.ssm_dos(plan, td, c["sigma"], want_rank=False)
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t0 = time.perf_counter()
+        tr_ss, tr_kpm = S.ssm_trace_f(plan, lambda v: math.log(v + 1.0), n_trace, c["sigma"], 0.016, 0.93)
+        t_tr = time.perf_counter() - t0
+        r = {"ms_per_step": ms, "value": units / (ms * 1e-3), "trace_ms": t_tr * 1e3, "tr_log_ss": tr_ss,
+             "tr_log_kpm": tr_kpm}
+        if exact is not None:
+            r["tr_log_ss_rel_err"] = (tr_ss - exact) / exact
+            r["tr_log_kpm_rel_err"] = (tr_kpm - exact) / exact
+        out[f"{prec}_nv{nv}_nvh{nvh}"] = r
+        plan.close()
     return out
 
 
@@ -671,6 +727,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-plan row (128 graphs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint row (100^3 potential)")
+    ap.add_argument("--no-lap3d", action="store_true", help="skip the 64^3 log-normal row (Tr log(A+I))")
     ap.add_argument("--ref-rec-steps", type=int, default=100)
     ap.add_argument("--ref-points", type=int, default=20)
     args = ap.parse_args()

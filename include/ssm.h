@@ -303,7 +303,11 @@ ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32
  *   The array exists on every GPU that loads the library, until the
  *   process exits.  The first call on a device looks up the array's device
  *   address (cudaGetSymbolAddress) with that device current; make that first
- *   call before any stream capture.
+ *   call before any stream capture.  Outside stream capture every call looks
+ *   the address up again (after cudaDeviceReset the module is loaded anew at
+ *   another address); a call made while `stream` is being captured uses the
+ *   address of the last call on that device, so after a reset make one call
+ *   outside capture before capturing.
  *   Every call on a device shares the array and it keeps the last call's
  *   contents; no part of it needs to start at zero (a call overwrites every
  *   partial sum it reads).  Calls whose work overlaps on the GPU (different
@@ -324,6 +328,24 @@ ssm_status ssm_gram_pair_noalloc(const double* A, const double* B, int64_t n_row
  * Either output may be NULL.  Needs no moments. */
 ssm_status ssm_coefficients(ssm_plan_t plan, const double* t, int64_t n_t, double sigma,
                             double* mu, double* nu);
+
+/* Failure-detection hooks (the paper has none; they let tests drive the error
+ * paths without faulting a GPU).
+ *
+ * ssm_debug_fail_alloc: from now on, the device allocation of the library that
+ * finds `after` earlier ones counted down fails as if the device were out of
+ * memory (nothing is allocated and the failing call returns SSM_ENOMEM after
+ * releasing what it had allocated); later allocations succeed again.
+ * after = -1 disables the hook, after < -1 is SSM_EINVAL.  Process-wide.
+ *
+ * ssm_selftest_wait: runs the bounded mbarrier wait that every tensor-core
+ * kernel of the library uses, alone (no bulk copy or MMA in flight): an
+ * mbarrier expecting one arrival is tested at most `polls` times; with
+ * arrive != 0 the arrival happens first.  Returns SSM_OK when the phase
+ * completed and SSM_ETIMEOUT when the wait gave up; in both cases the kernel
+ * returns normally and the device stays usable.  SSM_EINVAL for polls < 1. */
+ssm_status ssm_debug_fail_alloc(int32_t after);
+ssm_status ssm_selftest_wait(int32_t polls, int32_t arrive, void* stream);
 
 /* Per-phase device times and launch counts, accumulated over calls since the
  * last reset while timing is enabled.  Timing records CUDA events on the

@@ -313,6 +313,20 @@ def ssm_gram_pair(A, B=None, stream=None):
     return gaa, gab
 
 
+def ssm_debug_fail_alloc(after: int):
+    """ssm_debug_fail_alloc: the device allocation that finds `after` earlier ones counted
+    down fails with SSM_ENOMEM (-1 disables)."""
+    lib = N.load()
+    _check(lib, lib.ssm_debug_fail_alloc(int(after)), None)
+
+
+def ssm_selftest_wait(polls: int, arrive: bool, stream=None):
+    """ssm_selftest_wait: the library's bounded mbarrier wait on its own (raises SSMError
+    with SSM_ETIMEOUT when the wait gives up)."""
+    lib = N.load()
+    _check(lib, lib.ssm_selftest_wait(int(polls), 1 if arrive else 0, _stream(stream)), None)
+
+
 def ssm_timing_enable(plan: Plan, on: bool = True):
     lib = N.load()
     _check(lib, lib.ssm_timing_enable(plan.handle, 1 if on else 0), plan.handle)

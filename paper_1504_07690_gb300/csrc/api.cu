@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "internal.h"
 
 using namespace ssm;
@@ -98,11 +100,29 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Every device allocation of the library goes through here.  ssm_debug_fail_alloc
+// arms a countdown: the allocation that finds it at zero fails as if the device
+// were out of memory (cudaErrorMemoryAllocation, nothing allocated), so tests
+// can drive every SSM_ENOMEM path on the host.
+std::atomic<int> g_fail_alloc_after{-1};
+
+cudaError_t dmalloc(void** p, size_t bytes) {
+    *p = nullptr;
+    int left = g_fail_alloc_after.load();
+    while (left >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) return cudaErrorMemoryAllocation;
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 cudaError_t dev_alloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc((void**)p, count * sizeof(T));
+    return dmalloc((void**)p, count * sizeof(T));
 }
 
 void dev_free(void* p) {
@@ -280,7 +300,7 @@ ssm_status ensure_stage(ssm_plan_s* h, size_t bytes) {
     dev_free(P.d_stage);
     P.d_stage = nullptr;
     P.stage_bytes = 0;
-    CUDA_OR_FAIL(h, cudaMalloc((void**)&P.d_stage, bytes));
+    CUDA_OR_FAIL(h, dmalloc((void**)&P.d_stage, bytes));
     P.stage_bytes = bytes;
     return SSM_OK;
 }
@@ -322,7 +342,7 @@ ssm_status ensure_points(ssm_plan_s* h, int64_t n_t) {
     }
     if (!h->d_zeta) CUDA_OR_FAIL(h, dev_alloc(&h->d_zeta, M + 1));
     if (!h->d_solve) {
-        CUDA_OR_FAIL(h, cudaMalloc((void**)&h->d_solve, solve_workspace_bytes(P.p.n_v)));
+        CUDA_OR_FAIL(h, dmalloc((void**)&h->d_solve, solve_workspace_bytes(P.p.n_v)));
     }
     return SSM_OK;
 }
@@ -782,7 +802,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
                         std::string(#call) + ": " + cudaGetErrorString(e_));                                  \
     } while (0)
 
-    CREATE_CUDA(cudaMalloc((void**)&P.d_flag, sizeof(int)));
+    CREATE_CUDA(dmalloc((void**)&P.d_flag, sizeof(int)));
     CREATE_CUDA(cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
     double extra = 0.0;
     double raw_off[3] = {0, 0, 0};
@@ -909,7 +929,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     P.ld = (P.n_tot + vec - 1) / vec * vec;
     if ((uint64_t)P.n * (uint64_t)(P.ld / vec) >= (1ULL << 32)) return bail(SSM_EINVAL, "N x n_tot too large");
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
-    for (auto& v : P.d_V) CREATE_CUDA(cudaMalloc(&v, (size_t)P.n * P.ld * esz));
+    for (auto& v : P.d_V) CREATE_CUDA(dmalloc(&v, (size_t)P.n * P.ld * esz));
     if (p.options & 2) {
         // checkpoints (V_{jc}, V_{jc+1}) every c = ceil(sqrt(S)) steps for the adjoint
         const int S = p.degree / 2;
@@ -918,7 +938,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         P.adjoint = true;
         P.ck_c = c;
         P.n_ck = (S + c - 1) / c;
-        CREATE_CUDA(cudaMalloc(&P.d_ck, (size_t)2 * P.n_ck * P.n * P.ld * esz));
+        CREATE_CUDA(dmalloc(&P.d_ck, (size_t)2 * P.n_ck * P.n * P.ld * esz));
     }
     P.use_tc = P.mixed && !(p.options & 1) && gram_tc_supported(P.n_tot, P.ld);
     if (P.use_tc) {
@@ -940,14 +960,14 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         CREATE_CUDA(dev_alloc(&P.d_ring, slot * ring));
         CREATE_CUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * ring * P.n_tot * P.n_tot));
         if (P.use_fused) {
-            CREATE_CUDA(cudaMalloc((void**)&P.d_fmeta, fused_tc_meta_bytes(P)));
+            CREATE_CUDA(dmalloc((void**)&P.d_fmeta, fused_tc_meta_bytes(P)));
             CREATE_CUDA(launch_fused_meta(P, P.fcfg, P.d_fmeta, P.stream));
         }
         P.panel_groups = gram_tc_groups(P.n_tot);
         P.n_panels = (P.n + 31) / 32;
         const size_t pbytes = (size_t)P.n_panels * 2 * P.panel_groups * 528;
         for (int j = 0; j < (P.use_fused ? 1 : 3); ++j) {  // the fused path needs panels of V_0 only
-            CREATE_CUDA(cudaMalloc((void**)&P.d_panel[j], pbytes));
+            CREATE_CUDA(dmalloc((void**)&P.d_panel[j], pbytes));
             CREATE_CUDA(cudaMemsetAsync(P.d_panel[j], 0, pbytes, P.stream));  // rows past N stay zero
         }
         // the Gram products of step k run on a second stream, next to step k+1 of the recurrence
@@ -964,7 +984,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     } else if (p.precision == SSM_FP64_TC) {
         // float64 blocks; Gram products on the tensor cores from exact bf16 slices
         P.use_oz = true;
-        for (auto& u : P.d_ozU) CREATE_CUDA(cudaMalloc((void**)&u, (size_t)P.n * P.ld * sizeof(double)));
+        for (auto& u : P.d_ozU) CREATE_CUDA(dmalloc((void**)&u, (size_t)P.n * P.ld * sizeof(double)));
         // float pairs of the folded operator for the float-pair recurrence
         if (P.is_stencil) {
             CREATE_CUDA(dev_alloc(&P.d_diag32lo, P.n));
@@ -973,7 +993,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
             CREATE_CUDA(dev_alloc(&P.d_val32lo, P.nnz > 0 ? P.nnz : 1));
             if (P.nnz > 0) CREATE_CUDA(launch_split_df(P.d_val64, P.nnz, P.d_val32, P.d_val32lo, P.stream));
         }
-        CREATE_CUDA(cudaMalloc((void**)&P.d_ozcm, (size_t)5 * oz_buckets() * P.ld * sizeof(unsigned long long)));
+        CREATE_CUDA(dmalloc((void**)&P.d_ozcm, (size_t)5 * oz_buckets() * P.ld * sizeof(unsigned long long)));
         CREATE_CUDA(dev_alloc(&P.d_ozpart, oz_partial_floats(P.n_tot, P.n)));
         CREATE_CUDA(dev_alloc(&P.d_ozG, (size_t)P.n_tot * P.n_tot));
         int prio_lo = 0, prio_hi = 0;
@@ -1721,9 +1741,9 @@ ssm_status ssm_moments_adjoint(ssm_plan_t h, const double* dL_dX, int32_t kind, 
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
     const size_t bb = (size_t)P.n * P.ld * esz;
     const int64_t nEF = P.is_stencil ? 3 * P.n : P.nnz;
-    if (!P.d_seg) CUDA_OR_FAIL(h, cudaMalloc(&P.d_seg, bb * c));
+    if (!P.d_seg) CUDA_OR_FAIL(h, dmalloc(&P.d_seg, bb * c));
     for (auto& u : P.d_U)
-        if (!u) CUDA_OR_FAIL(h, cudaMalloc(&u, bb));
+        if (!u) CUDA_OR_FAIL(h, dmalloc(&u, bb));
     if (!P.d_D) CUDA_OR_FAIL(h, dev_alloc(&P.d_D, P.n));
     if (!P.d_EF) CUDA_OR_FAIL(h, dev_alloc(&P.d_EF, nEF));
     if (!P.d_adjsum) CUDA_OR_FAIL(h, dev_alloc(&P.d_adjsum, 4));
@@ -1740,8 +1760,8 @@ ssm_status ssm_moments_adjoint(ssm_plan_t h, const double* dL_dX, int32_t kind, 
     } else {
         if (!P.d_G) CUDA_OR_FAIL(h, dev_alloc(&P.d_G, (M + 1) * nn));
         if (!P.d_G1p) CUDA_OR_FAIL(h, dev_alloc(&P.d_G1p, nn));
-        if (!P.d_Gb) CUDA_OR_FAIL(h, cudaMalloc(&P.d_Gb, bb));
-        if (!P.d_Bm) CUDA_OR_FAIL(h, cudaMalloc(&P.d_Bm, 3 * nn * esz));
+        if (!P.d_Gb) CUDA_OR_FAIL(h, dmalloc(&P.d_Gb, bb));
+        if (!P.d_Bm) CUDA_OR_FAIL(h, dmalloc(&P.d_Bm, 3 * nn * esz));
         CUDA_OR_FAIL(h, to_device(P.d_G, dL_dX, (M + 1) * nn * sizeof(double), P.stream));
         CUDA_OR_FAIL(h, launch_check_finite(P.d_G, (int64_t)(M + 1) * nn, P.d_flag, P.stream));
         CUDA_OR_FAIL(h, launch_adj_g1(P.d_G, n, S, P.d_G1p, P.stream));
@@ -1858,7 +1878,7 @@ ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32
     cudaStream_t s = (cudaStream_t)stream;
     const int n_split = gram_split_count(n_rows, n_cols);
     double* part = nullptr;
-    cudaError_t e = cudaMalloc((void**)&part, (size_t)n_split * 2 * n_cols * n_cols * sizeof(double));
+    cudaError_t e = dmalloc((void**)&part, (size_t)n_split * 2 * n_cols * n_cols * sizeof(double));
     if (e != cudaSuccess)
         return fail(nullptr, e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA, cudaGetErrorString(e));
     e = launch_gram_f64(A, B, (int)ld, n_cols, n_rows, n_split, part, s);
@@ -1866,6 +1886,29 @@ ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(part);
     if (e != cudaSuccess) return fail(nullptr, SSM_ECUDA, cudaGetErrorString(e));
+    return SSM_OK;
+}
+
+ssm_status ssm_debug_fail_alloc(int32_t after) {
+    if (after < -1) return fail(nullptr, SSM_EINVAL, "after must be >= -1");
+    g_fail_alloc_after.store(after);
+    return SSM_OK;
+}
+
+ssm_status ssm_selftest_wait(int32_t polls, int32_t arrive, void* stream) {
+    if (polls < 1) return fail(nullptr, SSM_EINVAL, "polls must be >= 1");
+    int* d_status = nullptr;
+    cudaError_t e = dmalloc((void**)&d_status, sizeof(int));
+    if (e != cudaSuccess)
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? SSM_ENOMEM : SSM_ECUDA, cudaGetErrorString(e));
+    int status = -1;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = launch_selftest_wait(polls, arrive != 0, d_status, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(d_status);
+    if (e != cudaSuccess) return fail(nullptr, SSM_ECUDA, cudaGetErrorString(e));
+    if (status != 0) return fail(nullptr, SSM_ETIMEOUT, "the self-test mbarrier wait gave up after its poll limit");
     return SSM_OK;
 }
 

@@ -144,6 +144,11 @@ struct Plan {
     std::string err;
 };
 
+// Bounded-wait self-test (selftest.cu): one CTA initialises an mbarrier and waits for
+// its phase with at most `polls` tests; with `arrive` a thread arrives first.
+// *status = 0 when the phase completed, 1 when the wait gave up.
+cudaError_t launch_selftest_wait(int polls, bool arrive, int* status, cudaStream_t s);
+
 // Message returned by ssm_last_error(NULL) (api.cu).
 void set_global_error(const char* msg);
 

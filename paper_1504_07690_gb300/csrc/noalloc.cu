@@ -26,14 +26,23 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 // Shared by every call on a device; holds the last call's partial sums.
 static __device__ __align__(256) double g_noalloc_part[NOALLOC_PART_VALUES];
 
-// Device address of g_noalloc_part per device (the host-side name of the
-// array is only a stand-in and must never be passed to a kernel).
+// Device address of g_noalloc_part per device (the host-side name of the array
+// is only a stand-in and must never be passed to a kernel).  A device's primary
+// context can be destroyed and made again (cudaDeviceReset), which loads the
+// module anew at another address, so outside stream capture the address is
+// looked up on every call (cudaGetSymbolAddress allocates nothing); while the
+// stream is being captured the last looked-up address is used.
 void* g_part_addr[NOALLOC_MAX_DEVICES] = {nullptr};
 std::mutex g_part_mutex;
 
-cudaError_t part_address(int device, double** out) {
+cudaError_t part_address(int device, cudaStream_t stream, double** out) {
     std::lock_guard<std::mutex> lock(g_part_mutex);
-    if (!g_part_addr[device]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs == cudaStreamCaptureStatusNone || !g_part_addr[device]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_part);
         if (e != cudaSuccess) return e;
@@ -74,7 +83,7 @@ extern "C" ssm_status ssm_gram_pair_noalloc(const double* A, const double* B, in
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= NOALLOC_MAX_DEVICES)
         return reject(SSM_ECUDA, "no usable current device");
     double* part = nullptr;
-    if (part_address(device, &part) != cudaSuccess)
+    if (part_address(device, (cudaStream_t)stream, &part) != cudaSuccess)
         return reject(SSM_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed");
     const size_t per_split = (size_t)2 * n_cols * n_cols;
     int n_split = gram_split_count(n_rows, n_cols);

@@ -53,7 +53,9 @@ def test_struct_layouts_match_header_sizes():
 
     assert C.sizeof(N.ssm_stencil) == 3 * 8 + 3 * 4 + 4 + 8 + 3 * 8
     assert C.sizeof(N.ssm_csr) == 5 * 8
-    assert C.sizeof(N.ssm_params) == 4 * 4 + 4 * 8 + 2 * 4 + 8
+    # ..., eps_floor, then damping (int32, padded to 8) and damping_lambda
+    assert C.sizeof(N.ssm_params) == 4 * 4 + 4 * 8 + 2 * 4 + 8 + 8 + 8
+    assert N.ssm_params.damping_lambda.offset == 72
     assert C.sizeof(N.ssm_stats) == 9 * 8 + 3 * 8
 
 
@@ -63,7 +65,8 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("field,value", [("degree", 7), ("degree", 0), ("n_v", 0), ("precision", 5),
-                                         ("n_theta", 3), ("options", 8)])
+                                         ("n_theta", 3), ("options", 8), ("damping", 3), ("damping", -1),
+                                         ("precision", 3)])
 def test_parameter_validation_before_any_cuda_call(lib, field, value):
     from paper_1504_07690_gb300 import _native as N
 
