@@ -113,8 +113,12 @@ typedef struct {
                            mixed stencil plan with n_tot <= 256 runs each recurrence step
                            and its tensor-core Gram products as one fused launch instead
                            of separate kernels (same float32 blocks; moments equal up to
-                           the grouping of float32 sums).  Other bits must be 0
-                           (SSM_EINVAL otherwise). */
+                           the grouping of float32 sums).  bit 3 (SSM_OPT_PINV): the
+                           per-point estimate is Tr[K_W(t)^+ K_Z(t)], the pseudo-inverse
+                           form the paper compares with Alg. 4 (Section 3.2, Fig. 2): the
+                           same truncation of K_W's eigenvalues (tau, rounding floor), then
+                           every generalised eigenvalue is summed (no range filter); needs
+                           n_vh = 0.  Other bits must be 0 (SSM_EINVAL otherwise). */
     double eps_floor;   /* rounding unit of the floor of Alg. 4's truncation: an eigenvalue
                            of K_W(t) is also dropped below
                            8 n_v eps_floor max_i X_0[i][i] sum_{l<=M/2} (l+1)|mu_l(t)|,
@@ -140,6 +144,7 @@ typedef struct {
 } ssm_params;
 
 enum { SSM_DAMP_NONE = 0, SSM_DAMP_JACKSON = 1, SSM_DAMP_LORENTZ = 2 };
+enum { SSM_OPT_CUDA_CORE_GRAM = 1, SSM_OPT_ADJOINT = 2, SSM_OPT_FUSED_STEP = 4, SSM_OPT_PINV = 8 };
 
 typedef struct ssm_plan_s* ssm_plan_t;
 

@@ -44,7 +44,7 @@ __all__ = [
     "g_sigma", "g_max", "dgc_coefficients", "squared_coefficients",
     "jackson_factors", "lorentz_factors", "damping_factors", "coefficient_tables",
     "moments_direct", "moments_doubling",
-    "kpm_dos", "assemble", "rounding_floor", "geneig", "ress_dos_point", "ress_dgc",
+    "kpm_dos", "assemble", "rounding_floor", "geneig", "ress_dos_point", "pinv_trace", "ress_dgc",
     "exact_dos", "relative_l1_error", "trace_grid", "deconvolve_h",
     "trace_f", "logdet_shifted",
 ]
@@ -355,19 +355,48 @@ def ress_dos_point(K_W, K_Z, K_C, K_Wt, gmax: float, tau: float = 1e-7,
     return phi, info
 
 
+def pinv_trace(K_W: np.ndarray, K_Z: np.ndarray, tau: float = 1e-7, flag_eps: float = 0.0, floor: float = 0.0):
+    """Tr[K_W^+ K_Z], the pseudo-inverse form of the estimate (Section 3.2).
+
+    K_W = U S U^T; the pseudo-inverse keeps s_j >= max(tau max s, floor) (the
+    paper drops negative eigenvalues and those below a 1e-7 fraction of the
+    largest; the floor is Alg. 4's, see rounding_floor) and
+    Tr[K_W^+ K_Z] = sum_kept (u_j^T K_Z u_j) / s_j.  Unlike Alg. 4 no range
+    filter follows: every direction kept contributes.  Returns (value, info)
+    with the kept rank and the threshold flag as in geneig.
+    """
+    s, U = np.linalg.eigh(0.5 * (K_W + K_W.T))
+    smax = float(np.max(s)) if s.size else 0.0
+    if smax <= 0.0:
+        return 0.0, dict(rank_s=0, rank_xi=0, flagged=False)
+    thr = max(tau * smax, floor)
+    keep = s >= thr
+    flagged = bool(flag_eps > 0.0 and np.any(np.abs(s - thr) <= flag_eps * smax))
+    Ut = U[:, keep]
+    val = float(np.sum(np.einsum("ij,ik,kj->j", Ut, 0.5 * (K_Z + K_Z.T), Ut) / s[keep]))
+    r = int(keep.sum())
+    return val, dict(rank_s=r, rank_xi=r, flagged=flagged)
+
+
 def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
              sigma: float, tau: float = 1e-7, kappa: float = 1e-6,
              interval: Optional[Tuple[float, float]] = None,
              n_theta: Optional[int] = None, flag_eps: float = 0.0,
              moments: str = "direct", eps_floor: float = EPS_FP64, damping: int = 0,
-             lam: float = 4.0) -> Dict[str, np.ndarray]:
+             lam: float = 4.0, estimator: str = "alg4") -> Dict[str, np.ndarray]:
     """RESS-DGC (Alg. 7) and the DGC/KPM line (Alg. 2) on the same probes.
 
     W_all = [W, W~] (N x (n_v + n_vh)).  eps_floor sets the rounding floor
     of Alg. 4's truncation (0 disables it).  damping / lam select optional
-    damping factors of the series (coefficient_tables).  Returns dos_ss,
-    dos_kpm, the kept ranks, the flags, the interval and the moments.
+    damping factors of the series (coefficient_tables).  estimator "pinv"
+    replaces Alg. 4 + Alg. 6 by Tr[K_W^+ K_Z] (pinv_trace; no hybrid block).
+    Returns dos_ss, dos_kpm, the kept ranks, the flags, the interval and the
+    moments.
     """
+    if estimator not in ("alg4", "pinv"):
+        raise ValueError(estimator)
+    if estimator == "pinv" and W_all.shape[1] != n_v:
+        raise ValueError("the pseudo-inverse form takes no hybrid block")
     A = sp.csr_matrix(A)
     N = A.shape[0]
     a, b = interval if interval is not None else spectral_interval(A)
@@ -383,7 +412,10 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
     for i in range(nt):
         K_W, K_Z, K_C, K_Wt = assemble(tab["mu_half"][i], tab["nu"][i], X, n_v)
         fl = rounding_floor(tab["mu_half"][i], X, n_v, eps_floor) if eps_floor > 0 else 0.0
-        dos_ss[i], info = ress_dos_point(K_W, K_Z, K_C, K_Wt, gm, tau, kappa, flag_eps, fl)
+        if estimator == "pinv":
+            dos_ss[i], info = pinv_trace(K_W, K_Z, tau, flag_eps, fl)
+        else:
+            dos_ss[i], info = ress_dos_point(K_W, K_Z, K_C, K_Wt, gm, tau, kappa, flag_eps, fl)
         rank_s[i], rank_xi[i], flags[i] = info["rank_s"], info["rank_xi"], info["flagged"]
     dos_kpm = kpm_dos(tab["mu_full"], X)
     return dict(dos_ss=dos_ss, dos_kpm=dos_kpm, rank_s=rank_s, rank_xi=rank_xi,

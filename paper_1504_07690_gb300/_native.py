@@ -19,6 +19,7 @@ SSM_DAMP_NONE, SSM_DAMP_JACKSON, SSM_DAMP_LORENTZ = 0, 1, 2
 SSM_OPT_CUDA_CORE_GRAM = 1
 SSM_OPT_ADJOINT = 2
 SSM_OPT_FUSED_STEP = 4  # mixed stencil plans: recurrence step and Gram products in one launch
+SSM_OPT_PINV = 8  # per-point estimate Tr[K_W^+ K_Z] (pseudo-inverse form, no range filter)
 
 
 class ssm_stencil(C.Structure):

@@ -475,7 +475,7 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
             }
             CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, xlo, xhi, muh, M + 1, K,
                                          floor_scale, h->d_solve, h->d_dos_ss + t0, h->d_rank + 2 * t0,
-                                         P.d_flag, P.stream, nullptr, perm));
+                                         P.d_flag, P.stream, nullptr, perm, (P.p.options & SSM_OPT_PINV) != 0));
             P.stats.launches++;
             h->sched_nt = single ? n_t : 0;
         }
@@ -556,7 +556,8 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
             CUDA_OR_FAIL(h, launch_solve(h->d_K, h->d_KZ, nb, nv, nvh, P.p.tau, 0.0, 0.0,
                                          P.p.damping ? h->d_muh : h->d_mu, M + 1, K, 0.0,
                                          h->d_solve, h->d_dos_ss + b0 * n_tp, h->d_rank + 2 * b0 * n_tp, P.d_flag,
-                                         P.stream, h->d_fpt + 3 * b0 * n_tp));
+                                         P.stream, h->d_fpt + 3 * b0 * n_tp, nullptr,
+                                         (P.p.options & SSM_OPT_PINV) != 0));
             P.stats.launches++;
         }
     }
@@ -764,7 +765,9 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
         return fail(nullptr, SSM_EINVAL, "SSM_FP64_TC plans take no adjoint or fused-step option");
     if (p.n_theta != 0 && p.n_theta <= p.degree) return fail(nullptr, SSM_EINVAL, "n_theta must exceed M");
     if (!isfinite(p.lo) || !isfinite(p.hi)) return fail(nullptr, SSM_EINVAL, "lo/hi must be finite");
-    if (p.options & ~7) return fail(nullptr, SSM_EINVAL, "unknown option bits");
+    if (p.options & ~15) return fail(nullptr, SSM_EINVAL, "unknown option bits");
+    if ((p.options & SSM_OPT_PINV) && p.n_vh != 0)
+        return fail(nullptr, SSM_EINVAL, "the pseudo-inverse estimate (option bit 3) takes no hybrid columns");
     if (p.damping < SSM_DAMP_NONE || p.damping > SSM_DAMP_LORENTZ)
         return fail(nullptr, SSM_EINVAL, "damping must be SSM_DAMP_NONE, SSM_DAMP_JACKSON or SSM_DAMP_LORENTZ");
     if (!isfinite(p.damping_lambda)) return fail(nullptr, SSM_EINVAL, "damping_lambda must be finite");

@@ -296,7 +296,8 @@ size_t solve_workspace_bytes(int n_v);
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh,
                          double tau, double xlo, double xhi, const double* mu, int ldmu, int K,
                          double floor_scale, void* work, double* dos, int32_t* rank, int* flag,
-                         cudaStream_t s, const double* floor_pt = nullptr, const int32_t* perm = nullptr);
+                         cudaStream_t s, const double* floor_pt = nullptr, const int32_t* perm = nullptr,
+                         bool pinv = false);
 // Resident solver CTAs on the device (SMs x CTAs per SM; 0 if not available): the
 // slots of one wave, the length of a schedule.
 int64_t solve_slots(int n_v);

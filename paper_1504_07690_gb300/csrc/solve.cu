@@ -10,6 +10,8 @@
 //   4. keep xi in [xlo, xhi] (the range of g_sigma with a rounding slack)
 //   5. C~ = U~ S~^-1/2 X~
 //   phi = sum xi~ + (Tr K_W~ - ||K_C C~||_F^2) / N~_v   (second term only if N~_v > 0)
+// or, in the pseudo-inverse form (pinv), phi = Tr[K_W^+ K_Z] = tr B: the same
+// truncation, every generalised eigenvalue summed (no range filter).
 //
 // Float64 runs at 1/58 of the float32 rate on this part (2 FMA/clk per SM), so the
 // routes below are chosen to do the fewest float64 operations that settle each point
@@ -1336,12 +1338,19 @@ __device__ bool eigh(double* __restrict__ A, double* __restrict__ Zt, int n, boo
     return ql_implicit(Zt, n, vectors, sh);
 }
 
+// Trace of an n x n matrix (row-major), the same value on every thread.
+__device__ double diag_sum(const double* M, int n, Shared& sh) {
+    double f = 0.0;
+    for (int i = threadIdx.x; i < n; i += (int)blockDim.x) f += M[(size_t)i * n + i];
+    return block_sum(f, sh.red);
+}
+
 __global__ void __launch_bounds__(NT, 3)
 solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, int64_t n_t, int nv, int nvh,
              double tau, double xlo, double xhi, const double* __restrict__ mu, int ldmu, int K,
              double floor_scale, double* __restrict__ work, double* __restrict__ dos,
              int32_t* __restrict__ rank, int* __restrict__ flag, const double* __restrict__ floor_pt,
-             const int32_t* __restrict__ perm, int64_t n_slot) {
+             const int32_t* __restrict__ perm, int64_t n_slot, bool pinv) {
     extern __shared__ __align__(16) double dyn[];
     const int n = nv;
     Shared sh;
@@ -1461,7 +1470,8 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 Y[e] = xh * kw - kz;
             }
             __syncthreads();
-            const bool inside = cholesky_lower(T1, n, sh) && cholesky_lower(Y, n, sh);
+            // (the pseudo-inverse form keeps every eigenvalue: no inertia test, the trace of C)
+            const bool inside = !pinv && cholesky_lower(T1, n, sh) && cholesky_lower(Y, n, sh);
             for (int e = tid; e < n * n; e += (int)blockDim.x) {
                 const int i = e / n, j = e - i * n;
                 Zt[e] = 0.5 * (Kt[(size_t)i * n_tot + j] + Kt[(size_t)j * n_tot + i]);
@@ -1488,7 +1498,12 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                         }
                     }
                     __syncthreads();
-                    phi = range_sum(A, n, xl, xh, sh, &rs);
+                    if (pinv) {
+                        phi = diag_sum(A, n, sh);
+                        rs = n;
+                    } else {
+                        phi = range_sum(A, n, xl, xh, sh, &rs);
+                    }
                 }
                 r = n;
                 done = true;
@@ -1578,7 +1593,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                     S2[e] = xh * lw - mz;
                 }
                 __syncthreads();
-                const bool inside = cholesky_lower(S1, rk, sh) && cholesky_lower(S2, rk, sh);
+                const bool inside = !pinv && cholesky_lower(S1, rk, sh) && cholesky_lower(S2, rk, sh);
                 if (cholesky_lower(Lw, rk, sh)) {
                     if (inside) {
                         phi = fma(xl, (double)rk, trtr_sumsq(Lw, S1, rk, sh));
@@ -1595,7 +1610,12 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                             }
                         }
                         __syncthreads();
-                        phi = range_sum(T1, rk, xl, xh, sh, &rs);
+                        if (pinv) {
+                            phi = diag_sum(T1, rk, sh);
+                            rs = rk;
+                        } else {
+                            phi = range_sum(T1, rk, xl, xh, sh, &rs);
+                        }
                     }
                     r = rk;
                     done = true;
@@ -1682,7 +1702,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
                 double f = 0.0;
                 for (int k = 0; k < r; ++k) {
                     const double xi = sh.d[k];
-                    if (xi >= xl && xi <= xh) {
+                    if (pinv || (xi >= xl && xi <= xh)) {
                         sh.sel[q++] = k;
                         f += xi;
                     }
@@ -1819,7 +1839,7 @@ __global__ void solve_schedule_kernel(const int32_t* __restrict__ rank_prev, int
 cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int n_v, int n_vh, double tau,
                          double xlo, double xhi, const double* mu, int ldmu, int K, double floor_scale, void* work,
                          double* dos, int32_t* rank, int* flag, cudaStream_t s, const double* floor_pt,
-                         const int32_t* perm) {
+                         const int32_t* perm, bool pinv) {
     if (n_t <= 0) return cudaSuccess;
     if (n_v > MAXN) return cudaErrorInvalidValue;
     const size_t smem = solve_smem(n_v);
@@ -1833,7 +1853,7 @@ cudaError_t launch_solve(const double* Kfull, const double* KZ, int64_t n_t, int
     if (grid > n_slot) grid = n_slot;
     solve_kernel<<<(int)grid, solve_threads(n_v), smem, s>>>(Kfull, KZ, n_t, n_v, n_vh, tau, xlo, xhi, mu, ldmu, K,
                                                    floor_scale, (double*)work, dos, rank, flag, floor_pt, perm,
-                                                   n_slot);
+                                                   n_slot, pinv);
     return cudaGetLastError();
 }
 

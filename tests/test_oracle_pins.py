@@ -434,3 +434,39 @@ def test_trace_of_log_from_exact_dos_matches_logdet():
     tr = c.n * dx * np.sum(ft * O.exact_dos(ev, x, 0.06))
     ld = O.logdet_shifted(A, 1.0)
     assert abs(tr - ld) <= 1e-6 * abs(ld), (tr, ld)
+
+
+# ---------------------------------------------------------------- pseudo-inverse form (Section 3.2)
+
+def test_pinv_trace_hand_example_and_printed_spurious_value():
+    # K_W = diag(1, 1e-6), K_Z = diag(0.5, 1e-3): both directions clear tau = 1e-7 and
+    # Tr[K_W^+ K_Z] = 0.5 + 1e-3 / 1e-6; tau = 1e-5 drops the second; Alg. 4 with the
+    # range [0, 1] keeps only xi = 0.5.  Rotated, the values are the same.
+    KW, KZ = np.diag([1.0, 1e-6]), np.diag([0.5, 1e-3])
+    v, info = O.pinv_trace(KW, KZ)
+    assert v == pytest.approx(1000.5, rel=1e-12) and info["rank_s"] == 2
+    assert O.pinv_trace(KW, KZ, tau=1e-5)[0] == pytest.approx(0.5, rel=1e-15)
+    assert np.sum(O.geneig(KW, KZ, 1.0)[0]) == pytest.approx(0.5, rel=1e-12)
+    Q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((2, 2)))
+    assert O.pinv_trace(Q @ KW @ Q.T, Q @ KZ @ Q.T)[0] == pytest.approx(1000.5, rel=1e-9)
+    # the paper's printed spurious eigenvalue (Section 3.2): the pseudo-inverse form keeps
+    # it, Alg. 4's range filter drops it
+    with open(os.path.join(GOLDEN, "worked_example_range_filter.json")) as f:
+        g = json.load(f)
+    gm = O.g_max(g["sigma"], g["N"])
+    xi = g["spurious_xi_printed"]
+    assert O.pinv_trace(np.array([[1.0]]), np.array([[xi]]))[0] == pytest.approx(xi, rel=1e-15)
+    assert O.geneig(np.array([[1.0]]), np.array([[xi]]), gm)[0].size == 0
+
+
+def test_pinv_equals_alg4_when_every_xi_is_in_range():
+    # identity probes with a resolved expansion: every generalised eigenvalue is a value
+    # of the polynomial in [0, g_max], so the filter removes nothing and both forms agree
+    A, lam, Q = _dense_sym(36, 6, -1.0, 1.0)
+    A = sp.csr_matrix(A)
+    t = np.linspace(-0.9, 0.9, 7)
+    kw = dict(interval=(-1.05, 1.05))
+    r4 = O.ress_dgc(A, np.eye(36), 36, t, 800, 0.12, **kw)
+    rp = O.ress_dgc(A, np.eye(36), 36, t, 800, 0.12, estimator="pinv", **kw)
+    assert np.all(r4["rank_xi"] == r4["rank_s"])
+    assert np.max(np.abs(rp["dos_ss"] - r4["dos_ss"])) <= 1e-9 * np.max(np.abs(r4["dos_ss"]))
