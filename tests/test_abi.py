@@ -65,7 +65,7 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("field,value", [("degree", 7), ("degree", 0), ("n_v", 0), ("precision", 5),
-                                         ("n_theta", 3), ("options", 8), ("damping", 3), ("damping", -1),
+                                         ("n_theta", 3), ("options", 16), ("damping", 3), ("damping", -1),
                                          ("precision", 3)])
 def test_parameter_validation_before_any_cuda_call(lib, field, value):
     from paper_1504_07690_gb300 import _native as N
