@@ -185,6 +185,11 @@ ssm_status ssm_plan_create_batched(ssm_plan_t* out, int32_t B, const ssm_csr* cs
 ssm_status ssm_batch_info(ssm_plan_t plan, int32_t b, double* a, double* bb, double* lo, double* hi,
                           int64_t* n);
 
+/* The CTA size the autotuner of a batched plan picked for the CSR recurrence
+ * step (64, 128 or 256 threads; 0 before the first ssm_moments).  SSM_EINVAL for
+ * other plans. */
+ssm_status ssm_batch_tuning(ssm_plan_t plan, int32_t* csr_threads);
+
 /* The plan's Chebyshev interval (a, b), its spectral bounds [lo, hi] (the
  * unpadded Gershgorin interval, or the caller's interval), and the problem
  * size.  Any output may be NULL. */

@@ -176,6 +176,14 @@ def ssm_batch_info(plan: Plan, b: int) -> dict:
     return dict(a=a.value, b=bb.value, lo=lo.value, hi=hi.value, n=n.value)
 
 
+def ssm_batch_tuning(plan: Plan) -> dict:
+    """ssm_batch_tuning: the autotuned CTA size of a batched plan's CSR step."""
+    lib = N.load()
+    ct = C.c_int32()
+    _check(lib, lib.ssm_batch_tuning(plan.handle, C.byref(ct)), plan.handle)
+    return {"csr_threads": ct.value}
+
+
 def ssm_plan_info(plan: Plan) -> dict:
     lib = N.load()
     a, b, lo, hi = C.c_double(), C.c_double(), C.c_double(), C.c_double()

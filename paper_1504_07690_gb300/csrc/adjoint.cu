@@ -364,7 +364,7 @@ __global__ void csr_sym_kernel(const int64_t* __restrict__ rowptr, const int32_t
 
 int rows_grid(int64_t n_rows) {
     int64_t b = (n_rows + 7) / 8;  // 8 warps (rows) per block
-    if (b > 152 * 64) b = 152 * 64;
+    if (b > (int64_t)device_sms() * 64) b = (int64_t)device_sms() * 64;
     return b < 1 ? 1 : (int)b;
 }
 
@@ -432,7 +432,7 @@ cudaError_t launch_adj_sum(const double* D, const double* E, int64_t n, double* 
 
 cudaError_t launch_scale(const double* x, double sc, int64_t n, double* y, cudaStream_t s) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     if (b < 1) b = 1;
     scale_kernel<<<(unsigned)b, 256, 0, s>>>(x, sc, n, y);
     return cudaGetLastError();
@@ -446,7 +446,7 @@ cudaError_t launch_kpm_adjoint(const double* mu, int ldmu, int64_t n_t, int L, c
 
 cudaError_t launch_csr_sym(const Plan& P, const double* F, double s, double* out, cudaStream_t st) {
     int64_t b = (P.n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     if (b < 1) b = 1;
     csr_sym_kernel<<<(unsigned)b, 256, 0, st>>>(P.d_rowptr, P.d_colind, F, P.n, s, out);
     return cudaGetLastError();

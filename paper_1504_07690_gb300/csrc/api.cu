@@ -1225,6 +1225,13 @@ ssm_status ssm_batch_info(ssm_plan_t h, int32_t b, double* a, double* bb, double
     return SSM_OK;
 }
 
+ssm_status ssm_batch_tuning(ssm_plan_t h, int32_t* csr_threads) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    if (h->P.B <= 0) return fail(h, SSM_EINVAL, "not a batched plan");
+    if (csr_threads) *csr_threads = h->P.csr_threads;
+    return SSM_OK;
+}
+
 ssm_status ssm_plan_info(ssm_plan_t h, double* a, double* b, double* lo, double* hi, int64_t* n, int64_t* nnz) {
     if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
     if (a) *a = h->P.a;

@@ -281,7 +281,7 @@ cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, in
 cudaError_t launch_split_pairs(const double* v, int64_t n, float* hi, float* lo, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     split_pairs_kernel<<<(unsigned)b, 256, 0, s>>>(v, n, hi, lo);
     return cudaGetLastError();
 }

@@ -210,7 +210,7 @@ __global__ void kpm_kernel(const double* __restrict__ mu, int ldmu, int64_t n_t,
 
 int nblocks(int64_t n, int per) {
     int64_t b = (n + per - 1) / per;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     return b < 1 ? 1 : (int)b;
 }
 

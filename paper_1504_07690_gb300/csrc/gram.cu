@@ -128,7 +128,7 @@ __global__ void reduce_gram_pair_kernel(const double* __restrict__ part, int n_s
 
 cudaError_t launch_reduce_gram_pair(const double* part, int n_split, int n, double* gaa, double* gab, cudaStream_t s) {
     int64_t b = ((int64_t)n * n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     if (b < 1) b = 1;
     reduce_gram_pair_kernel<<<(int)b, 256, 0, s>>>(part, n_split, n, gaa, gab);
     return cudaGetLastError();

@@ -533,14 +533,14 @@ size_t gram_tc_partial_floats_total(int n_e, int n_o, int n_tot) {
 cudaError_t launch_reduce_tc(const float* part, int n_e, int n_o, int n_tot, double* X, int step, cudaStream_t s) {
     const int64_t nn = (int64_t)n_tot * n_tot;
     int64_t b = (nn + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     if (b < 1) b = 1;
     const size_t pf = gram_tc_partial_floats(n_e, n_o, n_tot);
     // the float64 sums live after the float32 partials (8-byte aligned: pf is even)
     double* ge = reinterpret_cast<double*>(const_cast<float*>(part) + ((pf + 1) & ~(size_t)1));
     double* go = ge + nn;
     int64_t sb = (nn + 31) / 32;
-    if (sb > 152 * 8) sb = 152 * 8;
+    if (sb > (int64_t)device_sms() * 8) sb = (int64_t)device_sms() * 8;
     sum_tc_kernel<<<(int)sb, 256, 0, s>>>(part, n_e, part + (size_t)n_e * nn, step >= 0 ? n_o : 0, n_tot, ge, go);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

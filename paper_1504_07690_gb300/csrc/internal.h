@@ -149,6 +149,20 @@ struct Plan {
 // *status = 0 when the phase completed, 1 when the wait gave up.
 cudaError_t launch_selftest_wait(int polls, bool arrive, int* status, cudaStream_t s);
 
+// Streaming multiprocessors of the current device (queried once per device and kept):
+// grid caps of grid-stride kernels are multiples of it.
+inline int device_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
 // Message returned by ssm_last_error(NULL) (api.cu).
 void set_global_error(const char* msg);
 

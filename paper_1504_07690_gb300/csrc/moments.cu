@@ -57,7 +57,7 @@ __global__ void convert_in_kernel(const double* __restrict__ src, int64_t ldsrc,
 
 int blocks_for(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
     return b < 1 ? 1 : (int)b;
 }
 

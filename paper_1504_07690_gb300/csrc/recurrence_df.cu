@@ -256,7 +256,7 @@ cudaError_t launch_convert_in_df(const double* src, int64_t ldsrc, void* dst, in
     float* h = (float*)dst;
     float* l = h + (size_t)n_rows * ld;
     int64_t blocks = ((int64_t)n_rows * ld + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (int64_t)device_sms() * 16) blocks = (int64_t)device_sms() * 16;
     convert_in_df_kernel<<<(int)(blocks < 1 ? 1 : blocks), 256, (size_t)ld * 8, s>>>(
         src, ldsrc, h, l, (uint32_t)ld, (uint32_t)n_cols, (uint32_t)n_rows, cm, (uint32_t)nbucket);
     return cudaGetLastError();
@@ -293,7 +293,7 @@ __global__ void split_df_kernel(const double* __restrict__ v, int64_t n, float* 
 
 cudaError_t launch_split_df(const double* v, int64_t n, float* h, float* l, cudaStream_t s) {
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (int64_t)device_sms() * 16) blocks = (int64_t)device_sms() * 16;
     split_df_kernel<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(v, n, h, l);
     return cudaGetLastError();
 }
