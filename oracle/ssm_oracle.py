@@ -422,6 +422,60 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
                 flagged=flags, a=a, b=b, X=X, **tab)
 
 
+def ss_dgc(A: sp.spmatrix, W: np.ndarray, t: np.ndarray, M: int, sigma: float, tau: float = 1e-7,
+           kappa: float = 1e-6, interval: Optional[Tuple[float, float]] = None,
+           n_theta: Optional[int] = None, flag_eps: float = 0.0, eps_floor: float = EPS_FP64,
+           damping: int = 0, lam: float = 4.0, estimator: str = "alg4") -> Dict[str, np.ndarray]:
+    """SS-DGC (Alg. 5): the filtered blocks Z(t_i) are formed explicitly.
+
+    mu_l(t_i), l <= M, by Alg. 1 (the degree-M table, with the damping factors
+    of M+1 terms when damping is set); V_c <- W, V_m <- 0; for l = 0..M:
+    Z(t_i) += mu_l(t_i) V_c for every point, then V_p <- (2 - delta_l0) A~ V_c - V_m.
+    Per point the generalised problem Z^T Z C = W^T Z C Xi is solved by Alg. 4
+    (geneig) and the estimate is Tr Xi.  Readings: W^T Z, symmetric in exact
+    arithmetic, is symmetrised (geneig does so); Alg. 4's rounding floor is
+    rounding_floor over the degree-M table (K_W = sum_{l<=M} mu_l W^T V_l).
+    estimator "pinv" replaces Alg. 4 by Tr[K_W^+ K_Z] as in ress_dgc.
+    Memory: n_t blocks of N x n_v.
+    """
+    if estimator not in ("alg4", "pinv"):
+        raise ValueError(estimator)
+    A = sp.csr_matrix(A)
+    N = A.shape[0]
+    W = np.asarray(W, dtype=np.float64)
+    n_v = W.shape[1]
+    a, b = interval if interval is not None else spectral_interval(A)
+    At = transform(A, a, b)
+    tab = coefficient_tables(t, M, sigma, N, a, b, n_theta, damping, lam)
+    mu = tab["mu_full"]
+    nt = len(t)
+    Z = np.zeros((nt, N, n_v))
+    Vm = np.zeros_like(W)
+    Vc = W.copy()
+    for l in range(M + 1):
+        Z += mu[:, l][:, None, None] * Vc[None, :, :]
+        if l < M:
+            Vp = (1.0 if l == 0 else 2.0) * (At @ Vc) - Vm
+            Vm, Vc = Vc, Vp
+    X0 = (W.T @ W)[None]
+    gm = g_max(sigma, N)
+    dos = np.zeros(nt)
+    rank_s = np.zeros(nt, dtype=np.int64)
+    rank_xi = np.zeros(nt, dtype=np.int64)
+    flags = np.zeros(nt, dtype=bool)
+    for i in range(nt):
+        K_W = W.T @ Z[i]
+        K_Z = Z[i].T @ Z[i]
+        fl = rounding_floor(mu[i], X0, n_v, eps_floor) if eps_floor > 0 else 0.0
+        if estimator == "pinv":
+            dos[i], info = pinv_trace(K_W, K_Z, tau, flag_eps, fl)
+        else:
+            xi, _, info = geneig(K_W, K_Z, gm, tau, kappa, flag_eps, fl)
+            dos[i] = float(np.sum(xi))
+        rank_s[i], rank_xi[i], flags[i] = info["rank_s"], info["rank_xi"], info["flagged"]
+    return dict(dos_ss=dos, rank_s=rank_s, rank_xi=rank_xi, flagged=flags, a=a, b=b, mu_full=mu)
+
+
 # --------------------------------------------------------------------------
 # Reference quantities (Eq. DOS0, Eq. error)
 # --------------------------------------------------------------------------

@@ -470,3 +470,66 @@ def test_pinv_equals_alg4_when_every_xi_is_in_range():
     rp = O.ress_dgc(A, np.eye(36), 36, t, 800, 0.12, estimator="pinv", **kw)
     assert np.all(r4["rank_xi"] == r4["rank_s"])
     assert np.max(np.abs(rp["dos_ss"] - r4["dos_ss"])) <= 1e-9 * np.max(np.abs(r4["dos_ss"]))
+
+
+# ---------------------------------------------------------------- SS-DGC (Alg. 5)
+
+def test_ss_dgc_identity_probes_select_filtered_eigenvalues_of_degree_M_series():
+    # W = I: Z(t) = p_M(A~) with p_M the degree-M series of g_sigma(t - .), so
+    # K_W = p_M, K_Z = p_M^2 and Alg. 4 returns the eigenvalues p_M(lambda_i) that
+    # pass the truncation and the range filter.  RESS-DGC at the same M uses the
+    # degree-M/2 series instead; both are checked against dense eigenvalues.
+    A, lam, Q = _dense_sym(30, 43, -1.0, 1.0)
+    A = sp.csr_matrix(A)
+    N, M, sigma = 30, 16, 0.08
+    a, b = -1.05, 1.05
+    t = np.linspace(-0.8, 0.8, 9)
+    r = O.ss_dgc(A, np.eye(N), t, M, sigma, interval=(a, b))
+    lt = (2 * lam - (a + b)) / (b - a)
+    T = np.cos(np.outer(np.arccos(lt), np.arange(M + 1)))
+    gm = O.g_max(sigma, N)
+    for i, ti in enumerate(t):
+        mf = O.dgc_coefficients(ti, M, sigma, N, a, b, n_theta=2 * M)
+        p = T @ mf
+        keep = (p >= 1e-7 * p.max()) & (p <= (1 + 1e-6) * gm) & (p >= -1e-6 * gm)
+        assert abs(r["dos_ss"][i] - p[keep].sum()) < 1e-12 * gm
+        assert r["rank_xi"][i] == keep.sum()
+
+
+def test_ss_dgc_single_probe_is_a_rayleigh_quotient():
+    # N_v = 1: K_W = w^T p(A) w and K_Z = w^T p(A)^2 w are scalars, so the
+    # estimate is their ratio when it lies in [0, g_max] (and K_W is kept).
+    A, lam, Q = _dense_sym(25, 44, -1.0, 1.0)
+    N, M, sigma = 25, 40, 0.1
+    a, b = -1.02, 1.02
+    w = wl.random_block(N, 1, 45)
+    t = np.linspace(-0.9, 0.9, 13)
+    r = O.ss_dgc(sp.csr_matrix(A), w, t, M, sigma, interval=(a, b))
+    c2 = (Q.T @ w[:, 0]) ** 2
+    lt = (2 * lam - (a + b)) / (b - a)
+    T = np.cos(np.outer(np.arccos(lt), np.arange(M + 1)))
+    gm = O.g_max(sigma, N)
+    for i, ti in enumerate(t):
+        p = T @ O.dgc_coefficients(ti, M, sigma, N, a, b, n_theta=2 * M)
+        kw, kz = float(c2 @ p), float(c2 @ p ** 2)
+        want = kz / kw if kw > 0 and -1e-6 * gm <= kz / kw <= (1 + 1e-6) * gm else 0.0
+        assert abs(r["dos_ss"][i] - want) <= 1e-12 * gm
+
+
+def test_ss_dgc_recovers_low_rank_trace_and_equals_ress_at_twice_the_degree():
+    # Theorem 3 regime (r eigenvalues near t, N_v = r + 10): the estimate is the
+    # exact trace; and since Z^T Z and W^T Z are the degree-2M and degree-M
+    # series of the same moments, SS-DGC at degree M is RESS-DGC at degree 2M.
+    rng = np.random.default_rng(13)
+    N, r, sigma = 120, 6, 0.05
+    lam = np.concatenate([rng.uniform(-0.1, 0.1, r), rng.uniform(0.7, 0.95, N - r)])
+    Q, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    A = sp.csr_matrix(Q @ np.diag(lam) @ Q.T)
+    W = wl.random_block(N, r + 10, 14)
+    t = np.array([-0.05, 0.0, 0.04])
+    ss = O.ss_dgc(A, W, t, 600, sigma, interval=(-1.0, 1.0))
+    ex = O.exact_dos(lam, t, sigma)
+    assert np.max(np.abs(ss["dos_ss"] - ex)) < 1e-8 * np.max(ex)
+    ress = O.ress_dgc(A, W, r + 10, t, 1200, sigma, interval=(-1.0, 1.0))
+    assert np.max(np.abs(ss["dos_ss"] - ress["dos_ss"])) < 1e-9 * np.max(ex)
+    assert np.array_equal(ss["rank_s"], ress["rank_s"])
