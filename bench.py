@@ -292,10 +292,10 @@ def _rooflines_fp64tc(N, n_tot, stats, steps, rec_ms, hbm, bf16, peak_kind):
     g_ms = stats["ms_gram"] / gl
     g_flops = oz_issued_flops(N, n_tot)
     out = [dict(kernel="stencil_step_df_kernel", bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9, peak=hbm,
-                unit="GB/s", traffic=None, work_per_launch=rec_bytes, launch_ms=rec_ms,
+                unit="GB/s", traffic=_traffic("stencil_step_df_kernel"), work_per_launch=rec_bytes, launch_ms=rec_ms,
                 ms_per_step=stats["ms_recurrence"] / steps, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"),
            dict(kernel="gram_oz_kernel", bound="tensor", achieved=g_flops / (g_ms * 1e-3) / 1e12, peak=bf16,
-                unit="TFLOP/s", traffic=None, work_per_launch=g_flops, launch_ms=g_ms,
+                unit="TFLOP/s", traffic=_traffic("gram_oz_kernel"), work_per_launch=g_flops, launch_ms=g_ms,
                 ms_per_step=stats["ms_gram"] / steps,
                 peak_source=f"MEASURED_PEAKS.json bf16_tflops ({peak_kind}); issued bf16 slice products")]
     for r in out:
@@ -403,11 +403,14 @@ def l1_errors(ss, kpm, ref):
             "flagged": int((~ok).sum())}
 
 
-def time_precision(S, st, c, Wd, td, precision, units, warmup, steps):
-    """ms/step of one precision's plan (same step as the timed region), and its DOS lines."""
+def time_precision(S, st, c, Wd, td, precision, units, warmup, steps, n_v=None, n_vh=None):
+    """ms/step of one precision's plan (same step as the timed region), and its DOS lines;
+    n_v / n_vh split the same probe columns between W and the hybrid block W~."""
     import torch
 
-    plan = S.ssm_plan_create(stencil=st, n_v=c["n_v"], n_vh=c["n_vh"], degree=c["M"], precision=precision)
+    n_v = c["n_v"] if n_v is None else n_v
+    n_vh = c["n_vh"] if n_vh is None else n_vh
+    plan = S.ssm_plan_create(stencil=st, n_v=n_v, n_vh=n_vh, degree=c["M"], precision=precision)
 
     def step():
         S.ssm_moments(plan, Wd)
@@ -548,6 +551,17 @@ def run_gpu(args, c, st, W, csr):
             precisions["fp64"] = dict(f64, **l1_errors(ss_f, kp_f, ref))
         ok = [k for k in ("mixed", "fp64_tc", "fp64") if k in precisions and precisions[k]["ss_l1"] <= 1e-4]
         precisions["fastest_within_1e-4_ss"] = min(ok, key=lambda k: precisions[k]["ms_per_step"]) if ok else None
+        # the same 200 probe columns split N_v = N~_v = 100 (Alg. 7's hybrid), against the
+        # oracle's Alg. 7 loop on its own moments with the same split
+        from oracle import ssm_oracle as O
+        half = c["n_v"] // 2
+        ref_h = O.ress_from_moments(ref["X"], ref, half, O.g_max(sigma, st.n), flag_eps=1e-8)
+        ref_h["dos_kpm"] = ref["dos_kpm"]
+        ok_b = ~(ref["flagged"] | ref_h["flagged"])
+        precisions["oracle_hybrid_vs_single_l1"] = O.relative_l1_error(ref_h["dos_ss"][ok_b], ref["dos_ss"][ok_b])
+        for prec in ("mixed", "fp64_tc"):
+            hy, ss_h, kp_h = time_precision(S, st, c, Wd, td, prec, units, 1, 1, n_v=half, n_vh=c["n_v"] - half)
+            precisions[f"{prec}_hybrid_{half}_{c['n_v'] - half}"] = dict(hy, **l1_errors(ss_h, kp_h, ref_h))
 
     batched = adjoint = lap3d = None
     if rank == 0 and not args.no_lap3d:
@@ -556,6 +570,11 @@ def run_gpu(args, c, st, W, csr):
         batched = bench_batched(S, hbm)
     if rank == 0 and not args.no_adjoint:
         adjoint = bench_adjoint(S, hbm)
+    ssdgc = None
+    if rank == 0 and not args.no_ssdgc:
+        fp64_peak = max(args.fp64_gemm_tflops or 0.0, 152 * FP64_FMA_PER_SM_CLK * 2 * ((ck or {}).get("sm_mhz") or 2070.0)
+                        * 1e6 / 1e12)
+        ssdgc = bench_ssdgc(S, fp64_peak)
 
     if rank == 0:
         line = {
@@ -572,7 +591,7 @@ def run_gpu(args, c, st, W, csr):
             "gpu_launches": int(stats["launches"]),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
             "precisions": precisions,
-            "lap3d": lap3d, "batched": batched, "adjoint": adjoint,
+            "lap3d": lap3d, "batched": batched, "adjoint": adjoint, "ssdgc": ssdgc,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -680,6 +699,64 @@ def bench_lap3d(S, hbm, runs=(("mixed", 256, 0), ("fp64_tc", 256, 0), ("mixed", 
     return out
 
 
+def bench_ssdgc(S, fp64_peak, warmup: int = 1, steps: int = 2, n_t: int = 16):
+    """SS-DGC with explicit filtered blocks (Alg. 5, ssm_dos_explicit) on the benchmark operator
+    (Anderson 256^2, N_v = 200 Rademacher probes, M = 1000) at n_t sweep points inside the
+    spectrum: CUDA events over `steps` calls after `warmup`.  Alg. 5 adds every recurrence
+    block into all n_t blocks Z(t_i): 2 N N_v n_t (M+1) float64 flops in zacc_kernel, its
+    roofline against the float64 peak.  Beside it, RESS-DGC at degree 2M on the
+    float64-accurate tensor-core plan, which forms the same pencil from moments (K_W of
+    degree M, K_Z its square), and the relative L1 difference of the two estimates."""
+    import torch
+    c = dict(wl.CONFIGS["anderson2d_256"])
+    st = wl.make_operator("anderson2d_256")
+    nv, M = c["n_v"], c["M"]
+    W = torch.from_numpy(wl.random_block(st.n, nv, c["probe_seed"], c["probe"])).cuda()
+    plan = S.ssm_plan_create(stencil=st, n_v=nv, degree=M, precision="fp64")
+    info = S.ssm_plan_info(plan)
+    t = torch.from_numpy(wl.explicit_points(info["lo"], info["hi"], n_t)).cuda()
+    for _ in range(warmup):
+        S.ssm_dos_explicit(plan, W, t, c["sigma"], want_rank=False)
+    torch.cuda.synchronize()
+    S.ssm_stats_reset(plan)
+    S.ssm_timing_enable(plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        dos, _ = S.ssm_dos_explicit(plan, W, t, c["sigma"], want_rank=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    S.ssm_timing_enable(plan, False)
+    stt = S.ssm_stats_get(plan)
+    plan.close()
+    phases = {k: stt[k] / steps for k in ("ms_coeffs", "ms_recurrence", "ms_gram", "ms_assemble", "ms_solve")}
+    z_flops = 2.0 * st.n * nv * n_t * (M + 1)
+    z_ms = phases["ms_assemble"]
+    out = {"workload": "anderson2d_256 (N=65536, N_v=200 rademacher, M=1000, sigma=0.02) at %d points "
+                       "inside the spectrum; SS-DGC (Alg. 5), float64" % n_t,
+           "metric": "matrix-applies/s (nnz*N_v*M/s)", "ms_per_call": ms,
+           "value": float(info["nnz"]) * nv * M / (ms * 1e-3), "phases_ms_per_call": phases,
+           "roofline": {"kernel": "zacc_kernel", "bound": "alu", "achieved": z_flops / (z_ms * 1e-3) / 1e12,
+                        "peak": fp64_peak, "unit": "TFLOP/s", "frac": z_flops / (z_ms * 1e-3) / 1e12 / fp64_peak,
+                        "work_per_call": z_flops}}
+    # the same pencil from moments: RESS-DGC at degree 2M on the float64 tensor-core plan
+    p2 = S.ssm_plan_create(stencil=st, n_v=nv, degree=2 * M, precision="fp64_tc")
+    S.ssm_moments(p2, W)
+    ss2, _, _ = S.ssm_dos(p2, t, c["sigma"], want_kpm=False, want_rank=False)
+    torch.cuda.synchronize()
+    e0.record()
+    S.ssm_moments(p2, W)
+    ss2, _, _ = S.ssm_dos(p2, t, c["sigma"], want_kpm=False, want_rank=False)
+    e1.record()
+    torch.cuda.synchronize()
+    p2.close()
+    a, b = dos.cpu().numpy(), ss2.cpu().numpy()
+    out["ress_2M_fp64_tc_ms"] = e0.elapsed_time(e1)
+    out["l1_vs_ress_2M"] = float(np.abs(a - b).sum() / np.abs(b).sum())
+    return out
+
+
 def bench_adjoint(S, hbm, warmup: int = 1, steps: int = 2):
     """Row a10: KPM-DOS + Tr exp(-A) loss on the 100^3 potential workload, gradient by the adjoint."""
     import torch
@@ -757,6 +834,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-plan row (128 graphs)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint row (100^3 potential)")
     ap.add_argument("--no-lap3d", action="store_true", help="skip the 64^3 log-normal row (Tr log(A+I))")
+    ap.add_argument("--no-ssdgc", action="store_true", help="skip the explicit-block SS-DGC row (Alg. 5)")
     ap.add_argument("--ref-rec-steps", type=int, default=100)
     ap.add_argument("--ref-points", type=int, default=20)
     args = ap.parse_args()

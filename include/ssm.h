@@ -124,12 +124,15 @@ typedef struct {
                            8 n_v eps_floor max_i X_0[i][i] sum_{l<=M/2} (l+1)|mu_l(t)|,
                            the size of the rounding error of K_W(t), so that points where
                            K_W(t) is numerically zero give no spurious terms; 0 selects
-                           2^-52 for SSM_FP64 (the float64 unit) and 2^-36 for SSM_MIXED
-                           (the float32 recurrence and split-bf16 Gram products leave
-                           moment errors far below the float32 unit times this worst-case
-                           bound; 2^-36 was the best of 2^-30..2^-40 against the float64
-                           path on a 65536-row Anderson model), a negative value disables
-                           the floor */
+                           2^-52 for SSM_FP64 and SSM_FP64_TC (the float64 unit) and
+                           2^-36 for SSM_MIXED (the float32 recurrence and split-bf16 Gram
+                           products leave moment errors far below the float32 unit times
+                           this worst-case bound; 2^-36 gave the smallest DOS error against
+                           the float64-accurate path over 2^-30..2^-40 on three operators
+                           held out from the benchmark: another Anderson 256^2 disorder
+                           and probe draw, an Anderson 192^2 and a 40^3 log-normal 3D
+                           Laplacian), a negative value disables the floor.  For
+                           ssm_dos_explicit the sum runs over l <= M. */
     int32_t damping;    /* damping of the truncated Chebyshev series (the paper uses none; the
                            factors are those of the KPM literature its KPM remark cites, Weisse
                            et al., Rev. Mod. Phys. 78, 275 (2006)):  SSM_DAMP_NONE (0),
@@ -217,6 +220,27 @@ ssm_status ssm_moments(ssm_plan_t plan, const double* W, int64_t ldw, double* mo
  * moments, SSM_EINVAL for sigma <= 0 or n_t < 0 (n_t = 0 is a no-op). */
 ssm_status ssm_dos(ssm_plan_t plan, const double* t, int64_t n_t, double sigma,
                    double* dos_ss, double* dos_kpm, int32_t* rank);
+
+/* SS-DGC (Alg. 5): the DOS at n_t sweep points from explicitly formed
+ * filtered blocks Z(t_i) = sum_{l<=M} mu_l(t_i) T_l(A~) W, with mu the
+ * degree-M table of Alg. 1 (damped by the factors of M+1 terms when the plan
+ * sets damping).  Per point the pencil (Z^T Z, W^T Z) is solved by Alg. 4
+ * (W^T Z symmetrised; truncation floor as ssm_params.eps_floor with the sum
+ * over l <= M; options bit 3 selects Tr[K_W^+ K_Z] instead) and dos[i] is the
+ * sum of the kept generalised eigenvalues, an estimate of Tr g_sigma^M(t_i I - A).
+ * Unlike ssm_moments + ssm_dos (RESS-DGC) the recurrence runs M steps and every
+ * step is added into all blocks Z_i: N n_v n_t (M+1) float64 multiply-adds and
+ * n_t Gram pairs, for few sweep points.  The blocks of as many points as fit in
+ * half of the free device memory are held at a time; further chunks of points
+ * rerun the recurrence.  W: N x n_v float64 (host or device, leading
+ * dimension ldw >= n_v).  t: n_t points (host or device).  dos (n_t) and rank
+ * (n_t x 2 int32, ranks after the truncation and after the range filter) may
+ * each be NULL, on host or device.  Needs a single-operator SSM_FP64 plan
+ * with n_vh = 0 (SSM_EINVAL otherwise); independent of ssm_moments (the
+ * plan's moments are left as they are).  SSM_ENONFINITE if W is not finite,
+ * SSM_ENOMEM if one block Z does not fit. */
+ssm_status ssm_dos_explicit(ssm_plan_t plan, const double* W, int64_t ldw, const double* t, int64_t n_t,
+                            double sigma, double* dos, int32_t* rank);
 
 /* Tr f(A) (Section 5, Eq. hform, Eq. pifunc, Alg. 8).  The spectral bounds
  * [lo, hi] of the plan's Gershgorin interval are mapped onto [-a, a] of a

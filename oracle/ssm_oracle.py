@@ -403,8 +403,18 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
     At = transform(A, a, b)
     tab = coefficient_tables(t, M, sigma, N, a, b, n_theta, damping, lam)
     X = (moments_direct if moments == "direct" else moments_doubling)(At, W_all, M)
-    gm = g_max(sigma, N)
-    nt = len(t)
+    out = ress_from_moments(X, tab, n_v, g_max(sigma, N), tau, kappa, flag_eps, eps_floor, estimator)
+    out["dos_kpm"] = kpm_dos(tab["mu_full"], X)
+    return dict(out, a=a, b=b, X=X, **tab)
+
+
+def ress_from_moments(X: np.ndarray, tab: Dict[str, np.ndarray], n_v: int, gm: float, tau: float = 1e-7,
+                      kappa: float = 1e-6, flag_eps: float = 0.0, eps_floor: float = EPS_FP64,
+                      estimator: str = "alg4") -> Dict[str, np.ndarray]:
+    """Alg. 7's per-point loop on given moments: the first n_v columns of X are W, the
+    rest W~ (so one set of moments serves every split N_v + N~_v of the same probes).
+    tab holds the coefficient tables of coefficient_tables."""
+    nt = tab["mu_half"].shape[0]
     dos_ss = np.zeros(nt)
     rank_s = np.zeros(nt, dtype=np.int64)
     rank_xi = np.zeros(nt, dtype=np.int64)
@@ -417,9 +427,7 @@ def ress_dgc(A: sp.spmatrix, W_all: np.ndarray, n_v: int, t: np.ndarray, M: int,
         else:
             dos_ss[i], info = ress_dos_point(K_W, K_Z, K_C, K_Wt, gm, tau, kappa, flag_eps, fl)
         rank_s[i], rank_xi[i], flags[i] = info["rank_s"], info["rank_xi"], info["flagged"]
-    dos_kpm = kpm_dos(tab["mu_full"], X)
-    return dict(dos_ss=dos_ss, dos_kpm=dos_kpm, rank_s=rank_s, rank_xi=rank_xi,
-                flagged=flags, a=a, b=b, X=X, **tab)
+    return dict(dos_ss=dos_ss, rank_s=rank_s, rank_xi=rank_xi, flagged=flags)
 
 
 def ss_dgc(A: sp.spmatrix, W: np.ndarray, t: np.ndarray, M: int, sigma: float, tau: float = 1e-7,

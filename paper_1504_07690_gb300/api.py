@@ -222,6 +222,18 @@ def ssm_dos(plan: Plan, t, sigma: float, want_ss: bool = True, want_kpm: bool = 
     return ss, kp, rk
 
 
+def ssm_dos_explicit(plan: Plan, W, t, sigma: float, want_rank: bool = True):
+    """ssm_dos_explicit: (dos, rank) of SS-DGC (Alg. 5) with probes W at the sweep points t."""
+    lib = N.load()
+    Wb, Wp = _as_buffer(W, np.float64)
+    tb, tp = _as_buffer(t, np.float64)
+    n_t = int(tb.shape[0])
+    ds, dsp = _empty_like_input(t, (n_t,), np.float64)
+    rk, rkp = _empty_like_input(t, (n_t, 2), np.int32) if want_rank else (None, None)
+    _check(lib, lib.ssm_dos_explicit(plan.handle, Wp, Wb.shape[1], tp, n_t, float(sigma), dsp, rkp), plan.handle)
+    return ds, rk
+
+
 def ssm_coefficients(plan: Plan, t, sigma: float):
     """ssm_coefficients: (mu, nu), each n_t x (M+1)."""
     lib = N.load()

@@ -778,7 +778,7 @@ ssm_status ssm_plan_create(ssm_plan_t* out, const ssm_stencil* st, const ssm_csr
     if (P.p.tau <= 0.0) P.p.tau = 1e-7;
     if (P.p.kappa < 0.0) P.p.kappa = 1e-6;
     if (P.p.damping_lambda <= 0.0) P.p.damping_lambda = 4.0;
-    if (P.p.eps_floor == 0.0)  // 2^-36 (mixed, measured) and 2^-52 (float64 and float64 tensor-core)
+    if (P.p.eps_floor == 0.0)  // 2^-36 (mixed, tuned on held-out operators) and 2^-52 (float64, float64 tensor-core)
         P.eps_floor = (p.precision == SSM_MIXED) ? 1.0 / 68719476736.0 : 1.0 / 4503599627370496.0;
     else
         P.eps_floor = P.p.eps_floor > 0.0 ? P.p.eps_floor : 0.0;
@@ -1532,6 +1532,164 @@ ssm_status ssm_dos(ssm_plan_t h, const double* t, int64_t n_t, double sigma, dou
     if (dos_kpm) CUDA_OR_FAIL(h, from_device(dos_kpm, h->d_dos_kpm, n_t * sizeof(double), P.stream));
     if (rank) CUDA_OR_FAIL(h, from_device(rank, h->d_rank, 2 * n_t * sizeof(int32_t), P.stream));
     s = sync_and_settle(h);
+    if (s != SSM_OK) return s;
+    return check_solver_flag(h);
+}
+
+ssm_status ssm_dos_explicit(ssm_plan_t h, const double* W, int64_t ldw, const double* t, int64_t n_t, double sigma,
+                            double* dos, int32_t* rank) {
+    if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
+    Plan& P = h->P;
+    if (P.B > 0 || P.mixed || P.use_oz || P.p.precision != SSM_FP64)
+        return fail(h, SSM_EINVAL, "ssm_dos_explicit needs a single-operator SSM_FP64 plan");
+    if (P.p.n_vh != 0) return fail(h, SSM_EINVAL, "ssm_dos_explicit takes no hybrid block (n_vh must be 0)");
+    if (!W) return fail(h, SSM_EINVAL, "W is NULL");
+    if (ldw < P.n_tot) return fail(h, SSM_EINVAL, "ldw < n_v");
+    if (n_t < 0 || !(sigma > 0.0) || !isfinite(sigma)) return fail(h, SSM_EINVAL, "need n_t >= 0 and sigma > 0");
+    if (n_t == 0) return SSM_OK;
+    if (!t) return fail(h, SSM_EINVAL, "t is NULL");
+    CUDA_OR_FAIL(h, cudaSetDevice(P.device));
+    const int M = P.p.degree, nv = P.p.n_v, ld = P.ld;
+    const int64_t N = P.n;
+    const size_t blk = (size_t)N * ld;  // doubles per block
+    const int J = 8, R = J + 2;         // blocks per accumulation, ring of recurrence blocks
+    const int nsplit = gram_split_count(N, nv);
+    const size_t nn = (size_t)nv * nv;
+    // points per chunk: the Z blocks take at most half of the free memory left after
+    // the fixed buffers
+    size_t free_b = 0, total_b = 0;
+    CUDA_OR_FAIL(h, cudaMemGetInfo(&free_b, &total_b));
+    const size_t fixed = ((size_t)(R + 1) * blk + (size_t)n_t * (M + 3) + (size_t)nsplit * 2 * nn + 3 * nn) *
+                             sizeof(double) + (size_t)n_t * 2 * sizeof(int32_t);
+    if (fixed >= free_b) return fail(h, SSM_ENOMEM, "ssm_dos_explicit: not enough device memory");
+    int64_t n_c = (int64_t)(((free_b - fixed) / 2) / ((blk + 2 * nn) * sizeof(double)));
+    if (n_c < 1) return fail(h, SSM_ENOMEM, "ssm_dos_explicit: no room for one filtered block");
+    if (n_c > n_t) n_c = n_t;
+    // every buffer of the call, freed on every return
+    struct Bufs {
+        std::vector<void*> p;
+        ~Bufs() {
+            for (void* q : p) dev_free(q);
+        }
+    } bufs;
+    auto get = [&](size_t n_doubles, double** out) -> cudaError_t {
+        cudaError_t e = dmalloc((void**)out, n_doubles * sizeof(double));
+        if (e == cudaSuccess) bufs.p.push_back(*out);
+        return e;
+    };
+    double *d_W0, *d_ring, *d_Z, *d_mu, *d_t, *d_dos, *d_part, *d_K, *d_KZ, *d_G;
+    int32_t* d_rank = nullptr;
+    CUDA_OR_FAIL(h, get(blk, &d_W0));
+    CUDA_OR_FAIL(h, get((size_t)R * blk, &d_ring));
+    CUDA_OR_FAIL(h, get((size_t)n_c * blk, &d_Z));
+    CUDA_OR_FAIL(h, get((size_t)n_t * (M + 1), &d_mu));
+    CUDA_OR_FAIL(h, get((size_t)n_t, &d_t));
+    CUDA_OR_FAIL(h, get((size_t)n_t, &d_dos));
+    CUDA_OR_FAIL(h, get((size_t)nsplit * 2 * nn, &d_part));
+    CUDA_OR_FAIL(h, get((size_t)n_c * nn, &d_K));
+    CUDA_OR_FAIL(h, get((size_t)n_c * nn, &d_KZ));
+    CUDA_OR_FAIL(h, get(2 * nn, &d_G));
+    CUDA_OR_FAIL(h, dmalloc((void**)&d_rank, (size_t)n_t * 2 * sizeof(int32_t)));
+    bufs.p.push_back(d_rank);
+    if (!h->d_solve) CUDA_OR_FAIL(h, dmalloc((void**)&h->d_solve, solve_workspace_bytes(nv)));
+    cudaStream_t st = P.stream;
+    CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), st));
+    // W -> V_0 (zero-padded to ld)
+    const double* src = W;
+    int64_t ldsrc = ldw;
+    if (!is_device_ptr(W)) {
+        ssm_status s = ensure_stage(h, (size_t)N * nv * sizeof(double));
+        if (s != SSM_OK) return s;
+        CUDA_OR_FAIL(h, cudaMemcpy2DAsync(P.d_stage, nv * sizeof(double), W, ldw * sizeof(double),
+                                          nv * sizeof(double), N, cudaMemcpyHostToDevice, st));
+        src = P.d_stage;
+        ldsrc = nv;
+    }
+    if (ldsrc == nv) {
+        CUDA_OR_FAIL(h, launch_check_finite(src, N * (int64_t)nv, P.d_flag, st));
+        P.stats.launches++;
+    }
+    CUDA_OR_FAIL(h, launch_convert_in(src, ldsrc, d_W0, ld, N, nv, false, st));
+    P.stats.launches++;
+    int flag = 0;
+    {
+        ssm_status s = read_flag(h, &flag);
+        if (s != SSM_OK) return s;
+        if (flag) return fail(h, SSM_ENONFINITE, "W is not finite");
+    }
+    // max_i X_0[i][i] = max_i |w_i|^2 for Alg. 4's rounding floor
+    double x0max = 0.0;
+    {
+        Scope sc(h, PH_GRAM);
+        CUDA_OR_FAIL(h, launch_gram_f64(d_W0, nullptr, ld, nv, N, nsplit, d_part, st));
+        CUDA_OR_FAIL(h, launch_reduce_gram_pair(d_part, nsplit, nv, d_G, nullptr, st));
+        P.stats.launches += 2;
+    }
+    {
+        std::vector<double> g0(nn);
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(g0.data(), d_G, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(st));
+        for (int i = 0; i < nv; ++i) x0max = g0[(size_t)i * nv + i] > x0max ? g0[(size_t)i * nv + i] : x0max;
+    }
+    // mu_l(t_i), l <= M (Alg. 5, step 1; damped by the factors of M+1 terms when set)
+    CUDA_OR_FAIL(h, to_device(d_t, t, n_t * sizeof(double), st));
+    {
+        ssm_status s = coefficients_dev(h, d_t, n_t, sigma, d_mu, nullptr);
+        if (s != SSM_OK) return s;
+    }
+    const double gmax = 1.0 / ((double)N * sqrt(2.0 * M_PI * sigma * sigma));
+    const double xlo = -P.p.kappa * gmax, xhi = (1.0 + P.p.kappa) * gmax;
+    const double floor_scale = 8.0 * nv * P.eps_floor * x0max;
+    auto vblk = [&](int l) -> double* { return l == 0 ? d_W0 : d_ring + (size_t)((l - 1) % R) * blk; };
+    for (int64_t t0 = 0; t0 < n_t; t0 += n_c) {
+        const int64_t nc = (n_t - t0) < n_c ? (n_t - t0) : n_c;
+        const double* mu_c = d_mu + (size_t)t0 * (M + 1);
+        CUDA_OR_FAIL(h, cudaMemsetAsync(d_Z, 0, (size_t)nc * blk * sizeof(double), st));
+        // Alg. 5's loop: V_l by the three-term recurrence, Z_i += mu_l(t_i) V_l in groups of J steps
+        int l0 = 0;
+        for (int l = 0; l <= M; ++l) {
+            if (l >= 1) {
+                Scope sc(h, PH_REC);
+                const double c = l == 1 ? 0.5 : 1.0, d = l == 1 ? 0.0 : 1.0;
+                const double* Vc = vblk(l - 1);
+                const double* Vp = l == 1 ? d_W0 : vblk(l - 2);
+                double* Vn = vblk(l);
+                CUDA_OR_FAIL(h, P.is_stencil ? launch_stencil_step_f64(P, Vc, Vp, Vn, c, d, st)
+                                             : launch_csr_step_f64(P, Vc, Vp, Vn, c, d, st));
+                P.stats.launches++;
+                P.stats.recurrence_launches++;
+            }
+            if (l - l0 + 1 == J || l == M) {
+                Scope sc(h, PH_ASSEMBLE);
+                const double* Vs[8];
+                for (int j = 0; j <= l - l0; ++j) Vs[j] = vblk(l0 + j);
+                CUDA_OR_FAIL(h, launch_zacc(Vs, l - l0 + 1, mu_c, M + 1, l0, nc, d_Z, (int64_t)blk, st));
+                P.stats.launches++;
+                l0 = l + 1;
+            }
+        }
+        // K_Z = Z^T Z and K_W = sym(Z^T W) per point
+        {
+            Scope sc(h, PH_GRAM);
+            for (int64_t i = 0; i < nc; ++i) {
+                CUDA_OR_FAIL(h, launch_gram_f64(d_Z + (size_t)i * blk, d_W0, ld, nv, N, nsplit, d_part, st));
+                CUDA_OR_FAIL(h, launch_reduce_gram_pair(d_part, nsplit, nv, d_KZ + (size_t)i * nn, d_G, st));
+                CUDA_OR_FAIL(h, launch_sym_pack(d_G, nv, d_K + (size_t)i * nn, st));
+                P.stats.launches += 3;
+                P.stats.gram_launches++;
+            }
+        }
+        {
+            Scope sc(h, PH_SOLVE);
+            CUDA_OR_FAIL(h, launch_solve(d_K, d_KZ, nc, nv, 0, P.p.tau, xlo, xhi, mu_c, M + 1, M, floor_scale,
+                                         h->d_solve, d_dos + t0, d_rank + 2 * t0, P.d_flag, st, nullptr, nullptr,
+                                         (P.p.options & SSM_OPT_PINV) != 0));
+            P.stats.launches++;
+        }
+    }
+    if (dos) CUDA_OR_FAIL(h, from_device(dos, d_dos, n_t * sizeof(double), st));
+    if (rank) CUDA_OR_FAIL(h, from_device(rank, d_rank, 2 * n_t * sizeof(int32_t), st));
+    ssm_status s = sync_and_settle(h);
     if (s != SSM_OK) return s;
     return check_solver_flag(h);
 }

@@ -303,6 +303,13 @@ cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, in
                                   cudaStream_t s);
 cudaError_t launch_split_pairs(const double* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 
+// SS-DGC with explicit filtered blocks (ssdgc.cu, Alg. 5): Z_i += sum_{j<nj} mu[i][l0+j] V[j]
+// for the n_c blocks Z_i of n_elem doubles each (n_elem even, nj <= 8; mu rows ldmu apart),
+// and out = (G + G^T) / 2 for an n x n matrix G.
+cudaError_t launch_zacc(const double* const* V, int nj, const double* mu, int ldmu, int l0, int64_t n_c, double* Z,
+                        int64_t n_elem, cudaStream_t s);
+cudaError_t launch_sym_pack(const double* G, int n, double* out, cudaStream_t s);
+
 // Per-point Alg. 4 + Alg. 6 solve (solve.cu).
 size_t solve_workspace_bytes(int n_v);
 // floor(t) = floor_scale * sum_{l<=K} (l+1) |mu[t][l]| (see ssm_params.eps_floor).  floor_pt

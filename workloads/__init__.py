@@ -204,6 +204,12 @@ def sweep_points(lo: float, hi: float, n_t: int) -> np.ndarray:
     return np.linspace(lo, hi, n_t)
 
 
+def explicit_points(lo: float, hi: float, n_t: int = 16) -> np.ndarray:
+    """The few sweep points of the explicit-block (SS-DGC) runs: n_t points uniform
+    strictly inside [lo, hi] (the ends of a Gershgorin interval carry no spectrum)."""
+    return np.linspace(lo, hi, n_t + 2)[1:-1]
+
+
 # Workload recipes (operator seed 1000+k, probe seed 2000+k).
 CONFIGS = {
     "lap2d_dirichlet_32": dict(
