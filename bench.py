@@ -249,13 +249,13 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
     a_terms = n_t * ((M // 2 + 1) * n_tot * (n_tot + 1) / 2.0 + (M + 1) * nv * (nv + 1) / 2.0)
     a_ms = stats["ms_assemble"] / steps
     if mixed:
-        # compensated float-pair arithmetic: 12 float32 instructions per term (two-product,
-        # cross terms, two-sum, low-part update) against the float32 issue rate
-        a_ins = 12.0 * a_terms
-        out.append(dict(kernel="assemble_df_kernel", bound="alu", achieved=a_ins / (a_ms * 1e-3) / 1e12,
-                        peak=152 * 128 * sm_mhz * 1e6 / 1e12, unit="T float32 instructions/s", traffic=None,
-                        work_per_launch=a_ins / 2, launch_ms=a_ms / 2, ms_per_step=a_ms,
-                        peak_source="float32 issue: 152 SMs x 128 lanes x %.0f MHz" % sm_mhz))
+        # bf16 slice products issued by the two tensor-core assembly launches (the phase
+        # also holds the slicing of the moments and coefficients)
+        a_flops = asm_oz_issued_flops(n_t, M, n_tot, nv)
+        out.append(dict(kernel="assemble_oz_kernel", bound="tensor", achieved=a_flops / (a_ms * 1e-3) / 1e12,
+                        peak=bf16, unit="TFLOP/s", traffic=_traffic("assemble_oz_kernel"), work_per_launch=a_flops / 2,
+                        launch_ms=a_ms / 2, ms_per_step=a_ms,
+                        peak_source=f"MEASURED_PEAKS.json bf16_tflops ({peak_kind}); issued bf16 slice products"))
     else:
         a_flops = 2.0 * a_terms
         out.append(dict(kernel="assemble_kernel", bound="alu", achieved=a_flops / (a_ms * 1e-3) / 1e12,
@@ -270,6 +270,18 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
     for r in out:
         r["frac"] = r["achieved"] / r["peak"]
     return out
+
+
+def asm_oz_issued_flops(n_t: int, M: int, n_tot: int, nv: int) -> float:
+    """bf16 flops the tensor cores issue for the assembly of a mixed plan: K (n_tot(n_tot+1)/2
+    packed entries, l <= M/2) and K_Z (n_v(n_v+1)/2 entries, l <= M), 21 slice pairs each;
+    points rounded to 64, entries to 128, l to 16."""
+    def up(x, m):
+        return (x + m - 1) // m * m
+    tp = up(n_t, 64)
+    k = up(n_tot * (n_tot + 1) // 2, 128) * up(M // 2 + 1, 16)
+    kz = up(nv * (nv + 1) // 2, 128) * up(M + 1, 16)
+    return 21 * 2.0 * tp * (k + kz)
 
 
 def oz_issued_flops(N: int, n_tot: int) -> float:
@@ -559,6 +571,18 @@ def run_gpu(args, c, st, W, csr):
         ref_h["dos_kpm"] = ref["dos_kpm"]
         ok_b = ~(ref["flagged"] | ref_h["flagged"])
         precisions["oracle_hybrid_vs_single_l1"] = O.relative_l1_error(ref_h["dos_ss"][ok_b], ref["dos_ss"][ok_b])
+        # the oracle's estimates for three splits of the same probes: DOS mass over t and the
+        # distance to the (unbiased) KPM line
+        dt = float(t[1] - t[0])
+        study = {}
+        for nv_s in (c["n_v"], (3 * c["n_v"]) // 4, half):
+            d_s = ref["dos_ss"] if nv_s == c["n_v"] else (
+                ref_h["dos_ss"] if nv_s == half else
+                O.ress_from_moments(ref["X"], ref, nv_s, O.g_max(sigma, st.n))["dos_ss"])
+            study[f"{nv_s}+{c['n_v'] - nv_s}"] = {"integral": float(np.sum(d_s) * dt),
+                                                 "l1_vs_kpm": O.relative_l1_error(d_s, ref["dos_kpm"])}
+        study["kpm"] = {"integral": float(np.sum(ref["dos_kpm"]) * dt)}
+        precisions["oracle_split_study"] = study
         for prec in ("mixed", "fp64_tc"):
             hy, ss_h, kp_h = time_precision(S, st, c, Wd, td, prec, units, 1, 1, n_v=half, n_vh=c["n_v"] - half)
             precisions[f"{prec}_hybrid_{half}_{c['n_v'] - half}"] = dict(hy, **l1_errors(ss_h, kp_h, ref_h))

@@ -48,6 +48,18 @@ struct ssm_plan_s {
     size_t cap_xpair = 0;
     float* d_cpair = nullptr;
     size_t cap_cpair = 0;
+    // tensor-core assembly (mixed and SSM_FP64_TC single plans): packed upper-triangle
+    // entries (W block first), their scales, the moment slices (once per set of moments)
+    // and one batch's coefficient slices and point scales
+    int* d_pack = nullptr;
+    int* d_Ee = nullptr;
+    unsigned long long* d_Emx = nullptr;
+    uint8_t* d_xsl = nullptr;
+    bool have_xsl = false;
+    uint8_t* d_csl = nullptr;
+    size_t cap_csl = 0;
+    int* d_Et = nullptr;
+    size_t cap_Et = 0;
     // solver schedule: n_t of the last single-launch solve (its ranks in d_rank), 0 if none
     int32_t* d_perm = nullptr;
     size_t cap_perm = 0;
@@ -221,6 +233,7 @@ ssm_status check_solver_flag(ssm_plan_s* h) {
     ssm_status s = read_flag(h, &flag);
     if (s != SSM_OK) return s;
     if (flag & 4) return fail(h, SSM_ENOCONV, "an eigenvalue iteration of Alg. 4 did not converge within 60 sweeps");
+    if (flag & 2) return fail(h, SSM_ETIMEOUT, "a tensor-core assembly wait gave up (bounded mbarrier wait)");
     return SSM_OK;
 }
 
@@ -275,6 +288,12 @@ void free_plan(ssm_plan_s* h) {
     if (P.graph) cudaGraphExecDestroy(P.graph);
     if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
     dev_free(h->d_fpt);
+    dev_free(h->d_pack);
+    dev_free(h->d_Ee);
+    dev_free(h->d_Emx);
+    dev_free(h->d_xsl);
+    dev_free(h->d_csl);
+    dev_free(h->d_Et);
     dev_free(h->d_xpair);
     dev_free(h->d_cpair);
     dev_free(h->d_perm);
@@ -402,11 +421,73 @@ ssm_status split_moments(ssm_plan_s* h) {
 
 // K (from mu, K+1 terms) and K_Z (from nu, M+1 terms) of n_t points with
 // coefficient rows at mu/nu (leading dimension M+1) from the moments of matrix b.
+// Single mixed plans assemble on the tensor cores (assemble_oz.cu).  Its six slices
+// hold each term to about 2^-47 of the largest term of its entry and point: far below
+// the rounding of float32 moments, but on SSM_FP64_TC plans, whose RESS-DGC line
+// amplifies assembly errors like moment errors, the float64 assembly stays.
+bool asm_on_tc(const Plan& P) { return P.B <= 0 && P.mixed; }
+
+// Moment slices of the tensor-core assembly, once per set of moments.
+ssm_status prepare_asm_oz(ssm_plan_s* h) {
+    Plan& P = h->P;
+    const int M = P.p.degree, n_tot = P.n_tot, nv = P.p.n_v;
+    const int ne = n_tot * (n_tot + 1) / 2;
+    if (!h->d_pack) {
+        // packed upper triangle, the W block (i <= j < n_v) first
+        std::vector<int> pk;
+        pk.reserve(ne);
+        for (int i = 0; i < nv; ++i)
+            for (int j = i; j < nv; ++j) pk.push_back((i << 16) | j);
+        for (int i = 0; i < n_tot; ++i)
+            for (int j = (i < nv ? nv : i); j < n_tot; ++j) pk.push_back((i << 16) | j);
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_pack, (size_t)ne));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_Ee, (size_t)ne));
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_Emx, (size_t)ne));
+        CUDA_OR_FAIL(h, dmalloc((void**)&h->d_xsl, asm_oz_xslice_bytes(ne, M + 1)));
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_pack, pk.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice,
+                                        P.stream));
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    }
+    CUDA_OR_FAIL(h, launch_asm_oz_xslices(P.d_X, n_tot, M + 1, h->d_pack, ne, h->d_Ee, h->d_Emx, h->d_xsl,
+                                          P.stream));
+    P.stats.launches += 3;
+    h->have_xsl = true;
+    return SSM_OK;
+}
+
 ssm_status assemble_pencils(ssm_plan_s* h, const double* mu, const double* nu, int64_t n_t, int b, double* K_out,
                             double* KZ_out) {
     Plan& P = h->P;
     const int M = P.p.degree, K = M / 2, nv = P.p.n_v, n_tot = P.n_tot;
     const size_t xs = (size_t)(M + 1) * n_tot * n_tot;
+    if (asm_on_tc(P)) {
+        if (!h->have_xsl) {
+            ssm_status st = prepare_asm_oz(h);
+            if (st != SSM_OK) return st;
+        }
+        const size_t cb = asm_oz_cslice_bytes(n_t, M + 1);
+        if (cb > h->cap_csl) {
+            dev_free(h->d_csl);
+            h->d_csl = nullptr;
+            h->cap_csl = 0;
+            CUDA_OR_FAIL(h, dmalloc((void**)&h->d_csl, cb));
+            h->cap_csl = cb;
+        }
+        if ((size_t)n_t > h->cap_Et) {
+            dev_free(h->d_Et);
+            h->d_Et = nullptr;
+            h->cap_Et = 0;
+            CUDA_OR_FAIL(h, dev_alloc(&h->d_Et, (size_t)n_t));
+            h->cap_Et = (size_t)n_t;
+        }
+        const int ne = n_tot * (n_tot + 1) / 2, nez = nv * (nv + 1) / 2;
+        CUDA_OR_FAIL(h, launch_asm_oz(mu, M + 1, n_t, K + 1, h->d_xsl, M + 1, h->d_pack, h->d_Ee, ne, n_tot, K_out,
+                                      h->d_csl, h->d_Et, P.d_flag, P.stream));
+        CUDA_OR_FAIL(h, launch_asm_oz(nu, M + 1, n_t, M + 1, h->d_xsl, M + 1, h->d_pack, h->d_Ee, nez, nv, KZ_out,
+                                      h->d_csl, h->d_Et, P.d_flag, P.stream));
+        P.stats.launches += 6;
+        return SSM_OK;
+    }
     if (!P.mixed) {
         CUDA_OR_FAIL(h, launch_assemble(mu, M + 1, n_t, K + 1, P.d_X + b * xs, n_tot, n_tot, n_tot, K_out, P.stream));
         CUDA_OR_FAIL(h, launch_assemble(nu, M + 1, n_t, M + 1, P.d_X + b * xs, n_tot, nv, nv, KZ_out, P.stream));
@@ -435,7 +516,7 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
     const double gmax = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
     const double xlo = -P.p.kappa * gmax, xhi = (1.0 + P.p.kappa) * gmax;
     const int64_t bt = batch_points(P);
-    if (want_ss && P.mixed) {
+    if (want_ss && P.mixed && !asm_on_tc(P)) {
         Scope sc(h, PH_ASSEMBLE);
         ssm_status st = split_moments(h);
         if (st != SSM_OK) return st;
@@ -1250,6 +1331,7 @@ ssm_status ssm_moments(ssm_plan_t h, const double* W, int64_t ldw, double* momen
     if (ldw < P.n_tot) return fail(h, SSM_EINVAL, "ldw < n_v + n_vh");
     CUDA_OR_FAIL(h, cudaSetDevice(P.device));
     P.have_moments = false;
+    h->have_xsl = false;
     if (P.B > 0) return moments_batched(h, W, ldw, moments);
     const int M = P.p.degree, S = M / 2;
     const size_t nn = (size_t)P.n_tot * P.n_tot;

@@ -310,6 +310,21 @@ cudaError_t launch_zacc(const double* const* V, int nj, const double* mu, int ld
                         int64_t n_elem, cudaStream_t s);
 cudaError_t launch_sym_pack(const double* G, int n, double* out, cudaStream_t s);
 
+// Tensor-core assembly (assemble_oz.cu): out[t][i*ocols+j] = out[t][j*ocols+i] =
+// sum_{l<L} coef[t][l] X_l[i][j] for the first ne packed entries (pack[e] = i << 16 | j)
+// from bf16 slices of the moments (xsl, formed for xL values of l by
+// launch_asm_oz_xslices with the entry scales Ee) and of the coefficients (formed into
+// csl, asm_oz_cslice_bytes, with the point scales Et, n_t ints; mx: ne scratch words).
+// Status bit 2 of *flag
+// on a timed-out wait.
+size_t asm_oz_xslice_bytes(int ne, int L);
+size_t asm_oz_cslice_bytes(int64_t n_t, int L);
+cudaError_t launch_asm_oz_xslices(const double* X, int n_tot, int L, const int* pack, int ne, int* Ee,
+                                  unsigned long long* mx, uint8_t* xsl, cudaStream_t s);
+cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
+                          const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag,
+                          cudaStream_t s);
+
 // Per-point Alg. 4 + Alg. 6 solve (solve.cu).
 size_t solve_workspace_bytes(int n_v);
 // floor(t) = floor_scale * sum_{l<=K} (l+1) |mu[t][l]| (see ssm_params.eps_floor).  floor_pt

@@ -137,8 +137,18 @@ __device__ __forceinline__ void load_item(ItemLoads<T>& L, const RowInfo& ri, ui
     for (int a = 0; a < 3; ++a) {
         const bool lo = (ri.has >> (2 * a)) & 1u, hi = (ri.has >> (2 * a + 1)) & 1u;
         VT sacc = vzero(T(0));
-        if (lo) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a] * nchunk + cc));
-        if (hi) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a + 1] * nchunk + cc));
+        if constexpr (sizeof(T) == 8) {
+            // float64 issues at 2 per clock and SM on this part: one add per axis where
+            // both neighbours exist, none otherwise
+            if (lo) sacc = ldg_stream(vc + (size_t)ri.nb[2 * a] * nchunk + cc);
+            if (hi) {
+                const VT h = ldg_stream(vc + (size_t)ri.nb[2 * a + 1] * nchunk + cc);
+                sacc = lo ? vadd(sacc, h) : h;
+            }
+        } else {
+            if (lo) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a] * nchunk + cc));
+            if (hi) sacc = vadd(sacc, ldg_stream(vc + (size_t)ri.nb[2 * a + 1] * nchunk + cc));
+        }
         L.s[a] = sacc;
     }
     L.vp = need_vp ? ldg_stream(vp + base + cc) : vzero(T(0));
@@ -211,9 +221,16 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
                 VT out = vzero(T(0));
                 if (L[u].ok) {
                     VT acc = vscale(L[u].dg, L[u].x);
+                    if constexpr (sizeof(T) == 8) {  // skip inactive axes and a unit scale
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) acc = vfma(w[a], L[u].s[a], acc);
-                    out = vscale(c, acc);
+                        for (int a = 0; a < 3; ++a)
+                            if (g.active[a]) acc = vfma(w[a], L[u].s[a], acc);
+                        out = c == T(1) ? acc : vscale(c, acc);
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) acc = vfma(w[a], L[u].s[a], acc);
+                        out = vscale(c, acc);
+                    }
                     if (d != T(0)) out = vfma(-d, L[u].vp, out);
                     vn[(size_t)(pnl * 32 + rr[u]) * nchunk + cq[u]] = out;
                 }
