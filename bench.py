@@ -223,7 +223,14 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
     rl = max(1, stats["recurrence_launches"])
     rec_ms = stats["ms_recurrence"] / rl
     if args.precision == "fp64_tc":
-        return _rooflines_fp64tc(N, n_tot, stats, steps, rec_ms, hbm, bf16, peak_kind)
+        out = _rooflines_fp64tc(N, n_tot, stats, steps, rec_ms, hbm, bf16, peak_kind)
+        a_flops = asm_oz_issued_flops(n_t, M, n_tot, nv, slices=7)
+        a_ms = stats["ms_assemble"] / steps
+        r = dict(kernel="assemble_oz_kernel", bound="tensor", achieved=a_flops / (a_ms * 1e-3) / 1e12, peak=bf16,
+                 unit="TFLOP/s", traffic=None, work_per_launch=a_flops / 2, launch_ms=a_ms / 2, ms_per_step=a_ms,
+                 peak_source=f"MEASURED_PEAKS.json bf16_tflops ({peak_kind}); issued bf16 slice products (7 slices)")
+        r["frac"] = r["achieved"] / r["peak"]
+        return out + [r]
     rec_bytes = (3.0 * N * n_tot + N) * e
     out.append(dict(kernel="stencil_step_kernel", bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9,
                     peak=hbm, unit="GB/s", traffic=_traffic("stencil_step_kernel"), work_per_launch=rec_bytes,
@@ -272,16 +279,18 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
     return out
 
 
-def asm_oz_issued_flops(n_t: int, M: int, n_tot: int, nv: int) -> float:
-    """bf16 flops the tensor cores issue for the assembly of a mixed plan: K (n_tot(n_tot+1)/2
-    packed entries, l <= M/2) and K_Z (n_v(n_v+1)/2 entries, l <= M), 21 slice pairs each;
-    points rounded to 64, entries to 128, l to 16."""
+def asm_oz_issued_flops(n_t: int, M: int, n_tot: int, nv: int, slices: int = 6) -> float:
+    """bf16 flops the tensor cores issue for the tensor-core assembly: K (n_tot(n_tot+1)/2
+    packed entries, l <= M/2) and K_Z (n_v(n_v+1)/2 entries, l <= M), 21 slice pairs each
+    (six slices, mixed plans) or 28 (seven, float64-accurate plans); points rounded to 64,
+    entries to 128, l to 16."""
     def up(x, m):
         return (x + m - 1) // m * m
     tp = up(n_t, 64)
     k = up(n_tot * (n_tot + 1) // 2, 128) * up(M // 2 + 1, 16)
     kz = up(nv * (nv + 1) // 2, 128) * up(M + 1, 16)
-    return 21 * 2.0 * tp * (k + kz)
+    pairs = slices * (slices + 1) // 2
+    return pairs * 2.0 * tp * (k + kz)
 
 
 def oz_issued_flops(N: int, n_tot: int) -> float:

@@ -377,9 +377,15 @@ ssm_status ssm_coefficients(ssm_plan_t plan, const double* t, int64_t n_t, doubl
  * mbarrier expecting one arrival is tested at most `polls` times; with
  * arrive != 0 the arrival happens first.  Returns SSM_OK when the phase
  * completed and SSM_ETIMEOUT when the wait gave up; in both cases the kernel
- * returns normally and the device stays usable.  SSM_EINVAL for polls < 1. */
+ * returns normally and the device stays usable.  SSM_EINVAL for polls < 1.
+ *
+ * ssm_debug_explicit_chunk: caps the sweep points whose filtered blocks
+ * ssm_dos_explicit holds at a time (0: as many as half of the free device
+ * memory holds, the default), so that tests reach its chunked path on small
+ * problems.  SSM_EINVAL for max_points < 0.  Process-wide. */
 ssm_status ssm_debug_fail_alloc(int32_t after);
 ssm_status ssm_selftest_wait(int32_t polls, int32_t arrive, void* stream);
+ssm_status ssm_debug_explicit_chunk(int32_t max_points);
 
 /* Per-phase device times and launch counts, accumulated over calls since the
  * last reset while timing is enabled.  Timing records CUDA events on the

@@ -78,6 +78,7 @@ SIGNATURES = {
                                         C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssm_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssm_debug_fail_alloc": (C.c_int, [C.c_int32]),
+    "ssm_debug_explicit_chunk": (C.c_int, [C.c_int32]),
     "ssm_batch_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "ssm_dos_explicit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                    C.c_void_p, C.c_void_p]),

@@ -333,6 +333,12 @@ def ssm_gram_pair(A, B=None, stream=None):
     return gaa, gab
 
 
+def ssm_debug_explicit_chunk(max_points: int):
+    """ssm_debug_explicit_chunk: cap on the sweep points ssm_dos_explicit holds at a time (0: none)."""
+    lib = N.load()
+    _check(lib, lib.ssm_debug_explicit_chunk(int(max_points)), None)
+
+
 def ssm_debug_fail_alloc(after: int):
     """ssm_debug_fail_alloc: the device allocation that finds `after` earlier ones counted
     down fails with SSM_ENOMEM (-1 disables)."""

@@ -117,6 +117,7 @@ bool is_device_ptr(const void* p) {
 // were out of memory (cudaErrorMemoryAllocation, nothing allocated), so tests
 // can drive every SSM_ENOMEM path on the host.
 std::atomic<int> g_fail_alloc_after{-1};
+std::atomic<int> g_explicit_chunk{0};  // ssm_debug_explicit_chunk
 
 cudaError_t dmalloc(void** p, size_t bytes) {
     *p = nullptr;
@@ -421,11 +422,12 @@ ssm_status split_moments(ssm_plan_s* h) {
 
 // K (from mu, K+1 terms) and K_Z (from nu, M+1 terms) of n_t points with
 // coefficient rows at mu/nu (leading dimension M+1) from the moments of matrix b.
-// Single mixed plans assemble on the tensor cores (assemble_oz.cu).  Its six slices
-// hold each term to about 2^-47 of the largest term of its entry and point: far below
-// the rounding of float32 moments, but on SSM_FP64_TC plans, whose RESS-DGC line
-// amplifies assembly errors like moment errors, the float64 assembly stays.
-bool asm_on_tc(const Plan& P) { return P.B <= 0 && P.mixed; }
+// Single mixed and SSM_FP64_TC plans assemble on the tensor cores (assemble_oz.cu).
+// Six slices hold each term to about 2^-47 of the largest term of its entry and
+// point, far below the rounding of float32 moments; SSM_FP64_TC plans, whose
+// RESS-DGC line amplifies assembly errors like moment errors, take seven (~2^-54).
+bool asm_on_tc(const Plan& P) { return P.B <= 0 && (P.mixed || P.use_oz); }
+int asm_slices(const Plan& P) { return P.mixed ? 6 : 7; }
 
 // Moment slices of the tensor-core assembly, once per set of moments.
 ssm_status prepare_asm_oz(ssm_plan_s* h) {
@@ -443,13 +445,13 @@ ssm_status prepare_asm_oz(ssm_plan_s* h) {
         CUDA_OR_FAIL(h, dev_alloc(&h->d_pack, (size_t)ne));
         CUDA_OR_FAIL(h, dev_alloc(&h->d_Ee, (size_t)ne));
         CUDA_OR_FAIL(h, dev_alloc(&h->d_Emx, (size_t)ne));
-        CUDA_OR_FAIL(h, dmalloc((void**)&h->d_xsl, asm_oz_xslice_bytes(ne, M + 1)));
+        CUDA_OR_FAIL(h, dmalloc((void**)&h->d_xsl, asm_oz_xslice_bytes(ne, M + 1, asm_slices(P))));
         CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_pack, pk.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice,
                                         P.stream));
         CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
     }
     CUDA_OR_FAIL(h, launch_asm_oz_xslices(P.d_X, n_tot, M + 1, h->d_pack, ne, h->d_Ee, h->d_Emx, h->d_xsl,
-                                          P.stream));
+                                          asm_slices(P), P.stream));
     P.stats.launches += 3;
     h->have_xsl = true;
     return SSM_OK;
@@ -465,7 +467,7 @@ ssm_status assemble_pencils(ssm_plan_s* h, const double* mu, const double* nu, i
             ssm_status st = prepare_asm_oz(h);
             if (st != SSM_OK) return st;
         }
-        const size_t cb = asm_oz_cslice_bytes(n_t, M + 1);
+        const size_t cb = asm_oz_cslice_bytes(n_t, M + 1, asm_slices(P));
         if (cb > h->cap_csl) {
             dev_free(h->d_csl);
             h->d_csl = nullptr;
@@ -481,10 +483,11 @@ ssm_status assemble_pencils(ssm_plan_s* h, const double* mu, const double* nu, i
             h->cap_Et = (size_t)n_t;
         }
         const int ne = n_tot * (n_tot + 1) / 2, nez = nv * (nv + 1) / 2;
+        const int ns = asm_slices(P);
         CUDA_OR_FAIL(h, launch_asm_oz(mu, M + 1, n_t, K + 1, h->d_xsl, M + 1, h->d_pack, h->d_Ee, ne, n_tot, K_out,
-                                      h->d_csl, h->d_Et, P.d_flag, P.stream));
+                                      h->d_csl, h->d_Et, P.d_flag, ns, P.stream));
         CUDA_OR_FAIL(h, launch_asm_oz(nu, M + 1, n_t, M + 1, h->d_xsl, M + 1, h->d_pack, h->d_Ee, nez, nv, KZ_out,
-                                      h->d_csl, h->d_Et, P.d_flag, P.stream));
+                                      h->d_csl, h->d_Et, P.d_flag, ns, P.stream));
         P.stats.launches += 6;
         return SSM_OK;
     }
@@ -1647,6 +1650,8 @@ ssm_status ssm_dos_explicit(ssm_plan_t h, const double* W, int64_t ldw, const do
     int64_t n_c = (int64_t)(((free_b - fixed) / 2) / ((blk + 2 * nn) * sizeof(double)));
     if (n_c < 1) return fail(h, SSM_ENOMEM, "ssm_dos_explicit: no room for one filtered block");
     if (n_c > n_t) n_c = n_t;
+    const int cap = g_explicit_chunk.load();
+    if (cap > 0 && n_c > cap) n_c = cap;
     // every buffer of the call, freed on every return
     struct Bufs {
         std::vector<void*> p;
@@ -2142,6 +2147,12 @@ ssm_status ssm_gram_pair(const double* A, const double* B, int64_t n_rows, int32
 ssm_status ssm_debug_fail_alloc(int32_t after) {
     if (after < -1) return fail(nullptr, SSM_EINVAL, "after must be >= -1");
     g_fail_alloc_after.store(after);
+    return SSM_OK;
+}
+
+ssm_status ssm_debug_explicit_chunk(int32_t max_points) {
+    if (max_points < 0) return fail(nullptr, SSM_EINVAL, "max_points must be >= 0");
+    g_explicit_chunk.store(max_points);
     return SSM_OK;
 }
 

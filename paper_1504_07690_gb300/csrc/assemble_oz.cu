@@ -2,12 +2,15 @@
 //
 // K(t) = sum_{l<L} c_l(t) X_l over the stored moments is a dense product
 // [n_t x L] . [L x entries] (coefficients times moments).  Here it runs on the
-// 5th-generation tensor cores: both operands are split into six bf16 slices
+// 5th-generation tensor cores: both operands are split into NS bf16 slices
 // relative to their largest value (ozslice.cuh), so every term is held to about
-// 2^-47 of the largest term of its entry and point, and the slice products are
-// summed exactly in TMEM in four groups by i+j (as in gram_oz.cu), and every
-// 320 values of l the three exact groups are added to int64 running sums and
-// the fourth to a float one, held in the registers of the draining warps.
+// 2^-(8 NS - 1) of the largest term of its entry and point (NS = 6 for mixed
+// plans, 7 for the float64-accuracy plans), the slice products with i + j <= NS + 1
+// are summed in TMEM in groups by i+j: i+j = 2, 3, 4 (and 5 with seven slices)
+// exactly (each term an integer multiple of the group's unit, below 2^24 units
+// over 320 values of l), the rest in one float32 group.
+// Every 320 values of l the exact groups are added to an int64 running sum and
+// the last to a float one, held in the registers of the draining warps.
 //
 // Operands.  The moments are symmetric, so only the packed upper triangle of
 // each X_l enters; its entries e are ordered with the W block (i <= j < n_v)
@@ -22,9 +25,9 @@
 //
 // Product kernel.  One CTA per (128 entries) x (64 points) tile, the point tiles of
 // an entry tile adjacent in the launch order, 320 threads:
-// one thread issues the bulk copies into a four-stage ring, one issues the 21
-// MMAs of a stage (slice pairs i + j <= 7, M = 128 entries, N = 64 points,
-// K = 16 values of l) into four TMEM groups of 64 columns, and eight warps
+// one thread issues the bulk copies into a four-stage ring, one issues the 21 (28)
+// MMAs of a stage (slice pairs i + j <= NS + 1, M = 128 entries, N = 64 points,
+// K = 16 values of l) into four or five TMEM groups of 64 columns, and eight warps
 // drain the groups every 20 stages; at the end they scale the sums by
 // 2^(E_e + E_t) and store the value at (i, j) and (j, i) of the point's
 // matrix.  Every mbarrier wait is bounded; on expiry the CTA sets bit 2 of
@@ -45,12 +48,42 @@ constexpr int GB = 2 * 128 + 16;             // one 8-wide group of a stage slic
 constexpr int AW = 128, BW = 64;             // entries / points per tile
 constexpr int AG = AW / 8, BG = BW / 8;      // 8-wide groups per slice
 constexpr int A_SLICE = AG * GB, B_SLICE = BG * GB;
-constexpr int A_STAGE = NSL * A_SLICE, B_STAGE = NSL * B_SLICE;
+template <int NS> __host__ __device__ constexpr int a_stage() { return NS * A_SLICE; }
+template <int NS> __host__ __device__ constexpr int b_stage() { return NS * B_SLICE; }
+
+// Six slices (mixed plans) from the float pair of the value with float operations;
+// their digits reach 256 in slices 4..6, so exact groups i+j = 2, 3, 4 and a rounded
+// one for i+j >= 5.  Seven slices (float64-accuracy plans) from the float64 value
+// itself: every digit |d_k| <= 128, which keeps i+j = 5 exact too, and i+j >= 6 is
+// the rounded group.
+template <int NS> __host__ __device__ constexpr int ngrp() { return NS == 6 ? 4 : 5; }
+
+template <int NS>
+__device__ __forceinline__ void slice_value(double v, int E, float* sl) {
+    if constexpr (NS == 6) {
+        float hi, lo;
+        to_pair(v, hi, lo);
+        split_df(hi, lo, __int_as_float((127 - E) << 23), sl);
+    } else {
+        split_d<NS>(v, __longlong_as_double((long long)(1023 - E) << 52), sl);
+    }
+}
 constexpr int SST = 4;                       // stages in flight
 constexpr int DRAIN = 20;                    // stages per exact interval (320 values of l)
-constexpr int NGRP = 4;                      // groups i+j = 2, 3, 4, >= 5
+constexpr int MAXGRP = 5;
 constexpr int NTHREADS = 320;                // producer warp, MMA warp, 8 draining warps
 constexpr int NDRAIN = 8;
+
+// 2^E > m (E = 0 for m = 0), E clamped to [-lim, lim]: lim = 126 for the float-pair
+// splitting (2^-E a normal float), 1000 for the float64 one, whose scale need not be
+// a float (a point far outside the spectrum has coefficients near 1e-87 and keeps its
+// relative structure)
+__device__ __forceinline__ int exp_of(double m, int lim) {
+    if (!(m > 0.0)) return 0;
+    int e;
+    frexp(m, &e);
+    return e < -lim ? -lim : (e > lim ? lim : e);
+}
 
 // byte offset of element (k within the stage, column m within the group) of a slice group
 __device__ __forceinline__ int core_off(int k, int m) { return (k >> 3) * 128 + (k & 7) * 16 + m * 2; }
@@ -75,15 +108,17 @@ __global__ void xmax_kernel(const double* __restrict__ X, int n_tot, int L, cons
 }
 
 // E_e of every packed entry from its maximum.
-__global__ void xexp_kernel(const unsigned long long* __restrict__ mx, int ne, int* __restrict__ Ee) {
+__global__ void xexp_kernel(const unsigned long long* __restrict__ mx, int ne, int lim, int* __restrict__ Ee) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < ne) Ee[e] = col_exponent(__longlong_as_double((long long)mx[e]));
+    if (e < ne) Ee[e] = exp_of(__longlong_as_double((long long)mx[e]), lim);
 }
 
 // Slices of the moments: unit (stage s, entry tile et, group g, l within the stage):
 // eight entries of one X_l, six 16-byte slice rows.
+template <int NS>
 __global__ void xslice_kernel(const double* __restrict__ X, int n_tot, int L, const int* __restrict__ pack, int ne,
                               const int* __restrict__ Ee, int nstage, int64_t units, uint8_t* __restrict__ out) {
+    constexpr int A_STAGE = a_stage<NS>();
     const size_t nn = (size_t)n_tot * n_tot;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(u % KS);
@@ -93,21 +128,22 @@ __global__ void xslice_kernel(const double* __restrict__ X, int n_tot, int L, co
         const int s = (int)(r % nstage);
         const int et = (int)(r / nstage);
         const int l = s * KS + k;
-        float sl[8][NSL];
+        float sl[8][NS];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int e = et * AW + g * 8 + m;
-            float hi = 0.f, lo = 0.f, se = 1.f;
+            double v = 0.0;
+            int E = 0;
             if (l < L && e < ne) {
                 const int p = __ldg(pack + e);
-                to_pair(__ldg(X + (size_t)l * nn + (size_t)(p >> 16) * n_tot + (p & 0xFFFF)), hi, lo);
-                se = __int_as_float((127 - __ldg(Ee + e)) << 23);
+                v = __ldg(X + (size_t)l * nn + (size_t)(p >> 16) * n_tot + (p & 0xFFFF));
+                E = __ldg(Ee + e);
             }
-            split_df(hi, lo, se, sl[m]);
+            slice_value<NS>(v, E, sl[m]);
         }
         uint8_t* base = out + ((size_t)et * nstage + s) * A_STAGE + (size_t)g * GB + core_off(k, 0);
 #pragma unroll
-        for (int q = 0; q < NSL; ++q)
+        for (int q = 0; q < NS; ++q)
             *reinterpret_cast<uint4*>(base + (size_t)q * A_SLICE) =
                 make_uint4(pack_bf16(sl[0][q], sl[1][q]), pack_bf16(sl[2][q], sl[3][q]),
                            pack_bf16(sl[4][q], sl[5][q]), pack_bf16(sl[6][q], sl[7][q]));
@@ -115,7 +151,8 @@ __global__ void xslice_kernel(const double* __restrict__ X, int n_tot, int L, co
 }
 
 // E_t of every point: one warp per point.
-__global__ void cexp_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, int* __restrict__ Et) {
+__global__ void cexp_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, int lim,
+                            int* __restrict__ Et) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= n_t) return;
@@ -123,12 +160,14 @@ __global__ void cexp_kernel(const double* __restrict__ coef, int ldc, int64_t n_
     for (int l = lane; l < L; l += 32) m = fmax(m, fabs(coef[t * ldc + l]));
 #pragma unroll
     for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-    if (lane == 0) Et[t] = col_exponent(m);
+    if (lane == 0) Et[t] = exp_of(m, lim);
 }
 
 // Slices of the coefficients: unit (point tile tt, stage s, group g, l within the stage).
+template <int NS>
 __global__ void cslice_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L,
                               const int* __restrict__ Et, int nstage, int64_t units, uint8_t* __restrict__ out) {
+    constexpr int B_STAGE = b_stage<NS>();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(u % KS);
         int64_t r = u / KS;
@@ -137,20 +176,21 @@ __global__ void cslice_kernel(const double* __restrict__ coef, int ldc, int64_t 
         const int s = (int)(r % nstage);
         const int64_t tt = r / nstage;
         const int l = s * KS + k;
-        float sl[8][NSL];
+        float sl[8][NS];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int64_t t = tt * BW + g * 8 + m;
-            float hi = 0.f, lo = 0.f, se = 1.f;
+            double v = 0.0;
+            int E = 0;
             if (l < L && t < n_t) {
-                to_pair(__ldg(coef + t * ldc + l), hi, lo);
-                se = __int_as_float((127 - __ldg(Et + t)) << 23);
+                v = __ldg(coef + t * ldc + l);
+                E = __ldg(Et + t);
             }
-            split_df(hi, lo, se, sl[m]);
+            slice_value<NS>(v, E, sl[m]);
         }
         uint8_t* base = out + ((size_t)tt * nstage + s) * B_STAGE + (size_t)g * GB + core_off(k, 0);
 #pragma unroll
-        for (int q = 0; q < NSL; ++q)
+        for (int q = 0; q < NS; ++q)
             *reinterpret_cast<uint4*>(base + (size_t)q * B_SLICE) =
                 make_uint4(pack_bf16(sl[0][q], sl[1][q]), pack_bf16(sl[2][q], sl[3][q]),
                            pack_bf16(sl[4][q], sl[5][q]), pack_bf16(sl[6][q], sl[7][q]));
@@ -171,7 +211,9 @@ struct AsmArgs {
     int ne, ocols, xstages, nst;
 };
 
+template <int NS>
 __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
+    constexpr int A_STAGE = a_stage<NS>(), B_STAGE = b_stage<NS>();
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t full[SST], empty[SST], a_full, a_empty;
     __shared__ uint32_t tmem_slot;
@@ -183,7 +225,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
     const uint8_t* xsrc = P.xsl + (size_t)et * P.xstages * A_STAGE;
     const uint8_t* csrc = P.csl + (size_t)tt * nst * B_STAGE;
 
-    if (warp == 0) tmem_alloc(&tmem_slot, 256);
+    constexpr int NGRP = ngrp<NS>();
+    if (warp == 0) tmem_alloc(&tmem_slot, 512);  // NGRP x BW <= 320 columns used
     if (tid == 0) {
         for (int s = 0; s < SST; ++s) {
             mbar_init(&full[s], 1);
@@ -230,10 +273,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a0 = smem_u32(smem + (size_t)s * (A_STAGE + B_STAGE)), b0 = a0 + A_STAGE;
-                uint32_t started = pos != 0 ? 0xFu : 0u;
-                for (int i = 1; i <= NSL; ++i) {
-                    for (int j = 1; i + j <= NSL + 1; ++j) {
-                        const int g = (i + j < 5 ? i + j : 5) - 2;
+                uint32_t started = pos != 0 ? (1u << NGRP) - 1u : 0u;  // groups already holding a sum
+                for (int i = 1; i <= NS; ++i) {
+                    for (int j = 1; i + j <= NS + 1; ++j) {
+                        const int g = (i + j < NGRP + 1 ? i + j : NGRP + 1) - 2;
                         mma_bf16(tmem + (uint32_t)(g * BW), smem_desc(a0 + (uint32_t)(i - 1) * A_SLICE, 128, GB),
                                  smem_desc(b0 + (uint32_t)(j - 1) * B_SLICE, 128, GB), idesc, (started >> g) & 1u);
                         started |= 1u << g;
@@ -281,12 +324,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    // groups i+j = 2, 3, 4: integers in units of 2^-14, 2^-22, 2^-30 (< 2^24 of them)
+                    // exact groups i+j = 2, 3, 4 (, 5): integers in units of 2^-14, 2^-22,
+                    // 2^-30 (, 2^-38), fewer than 2^24 of them; the sum in units of 2^-38
                     const long long n2 = float_int(__uint_as_float(v[0][e]) * 16384.0f);
                     const long long n3 = float_int(__uint_as_float(v[1][e]) * 4194304.0f);
                     const long long n4 = float_int(__uint_as_float(v[2][e]) * 1073741824.0f);
-                    acc[8 * pc + e] += (n2 << 16) + (n3 << 8) + n4;
-                    r5[8 * pc + e] += __uint_as_float(v[3][e]);
+                    long long n = (n2 << 24) + (n3 << 16) + (n4 << 8);
+                    if constexpr (NGRP == 5) n += float_int(__uint_as_float(v[3][e]) * 274877906944.0f);
+                    acc[8 * pc + e] += n;
+                    r5[8 * pc + e] += __uint_as_float(v[NGRP - 1][e]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -301,7 +347,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
             for (int c = 0; c < 32; ++c) {
                 const int64_t t = (int64_t)tt * BW + 32 * half + c;
                 if (t < P.n_t) {
-                    const double v = ldexp((double)acc[c] * 0x1p-30 + (double)r5[c], Ee + P.Et[t]);
+                    const double v = ldexp((double)acc[c] * 0x1p-38 + (double)r5[c], Ee + P.Et[t]);
                     double* o = P.out + t * P.ostride;
                     o[(size_t)i * P.ocols + j] = v;
                     o[(size_t)j * P.ocols + i] = v;
@@ -312,7 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
     __syncthreads();
     if (fail && tid == 0) atomicOr(P.flag, 2);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 int grid_for(int64_t units) {
@@ -324,49 +370,52 @@ int grid_for(int64_t units) {
 
 }  // namespace
 
-size_t asm_oz_xslice_bytes(int ne, int L) {
-    return (size_t)((ne + AW - 1) / AW) * ((L + KS - 1) / KS) * A_STAGE;
+size_t asm_oz_xslice_bytes(int ne, int L, int ns) {
+    return (size_t)((ne + AW - 1) / AW) * ((L + KS - 1) / KS) * ns * A_SLICE;
 }
 
-size_t asm_oz_cslice_bytes(int64_t n_t, int L) {
-    return (size_t)((n_t + BW - 1) / BW) * ((L + KS - 1) / KS) * B_STAGE;
+size_t asm_oz_cslice_bytes(int64_t n_t, int L, int ns) {
+    return (size_t)((n_t + BW - 1) / BW) * ((L + KS - 1) / KS) * ns * B_SLICE;
 }
 
 cudaError_t launch_asm_oz_xslices(const double* X, int n_tot, int L, const int* pack, int ne, int* Ee,
-                                  unsigned long long* mx, uint8_t* xsl, cudaStream_t s) {
-    if (ne <= 0 || L <= 0 || n_tot > 0xFFFF) return cudaErrorInvalidValue;
+                                  unsigned long long* mx, uint8_t* xsl, int ns, cudaStream_t s) {
+    if (ne <= 0 || L <= 0 || n_tot > 0xFFFF || (ns != 6 && ns != 7)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)ne * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     xmax_kernel<<<dim3((ne + 255) / 256, (L + XL_CHUNK - 1) / XL_CHUNK), 256, 0, s>>>(X, n_tot, L, pack, ne, mx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    xexp_kernel<<<(ne + 255) / 256, 256, 0, s>>>(mx, ne, Ee);
+    xexp_kernel<<<(ne + 255) / 256, 256, 0, s>>>(mx, ne, ns == 6 ? 126 : 1000, Ee);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nstage = (L + KS - 1) / KS;
     const int64_t units = (int64_t)((ne + AW - 1) / AW) * nstage * AG * KS;
-    xslice_kernel<<<grid_for(units), 256, 0, s>>>(X, n_tot, L, pack, ne, Ee, nstage, units, xsl);
+    if (ns == 6)
+        xslice_kernel<6><<<grid_for(units), 256, 0, s>>>(X, n_tot, L, pack, ne, Ee, nstage, units, xsl);
+    else
+        xslice_kernel<7><<<grid_for(units), 256, 0, s>>>(X, n_tot, L, pack, ne, Ee, nstage, units, xsl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
-                          const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag,
-                          cudaStream_t s) {
-    if (n_t <= 0 || ne <= 0) return cudaSuccess;
-    if (L <= 0 || L > xL) return cudaErrorInvalidValue;
-    cexp_kernel<<<(unsigned)((n_t * 32 + 255) / 256), 256, 0, s>>>(coef, ldc, n_t, L, Et);
+namespace {
+
+template <int NS>
+cudaError_t asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
+                   const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag, cudaStream_t s) {
+    cexp_kernel<<<(unsigned)((n_t * 32 + 255) / 256), 256, 0, s>>>(coef, ldc, n_t, L, NS == 6 ? 126 : 1000, Et);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nst = (L + KS - 1) / KS;
     const int64_t tts = (n_t + BW - 1) / BW;
     const int64_t units = tts * nst * BG * KS;
-    cslice_kernel<<<grid_for(units), 256, 0, s>>>(coef, ldc, n_t, L, Et, nst, units, csl);
+    cslice_kernel<NS><<<grid_for(units), 256, 0, s>>>(coef, ldc, n_t, L, Et, nst, units, csl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)SST * (A_STAGE + B_STAGE);
+    const size_t smem = (size_t)SST * (a_stage<NS>() + b_stage<NS>());
     static bool attr = false;
     if (!attr) {
-        e = cudaFuncSetAttribute(assemble_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(assemble_oz_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -387,8 +436,19 @@ cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const
     a.xstages = (xL + KS - 1) / KS;
     a.nst = nst;
     const dim3 grid((unsigned)tts, (unsigned)ets);
-    assemble_oz_kernel<<<grid, NTHREADS, smem, s>>>(a);
+    assemble_oz_kernel<NS><<<grid, NTHREADS, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
+                          const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag, int ns,
+                          cudaStream_t s) {
+    if (n_t <= 0 || ne <= 0) return cudaSuccess;
+    if (L <= 0 || L > xL || (ns != 6 && ns != 7)) return cudaErrorInvalidValue;
+    return ns == 6 ? asm_oz<6>(coef, ldc, n_t, L, xsl, xL, pack, Ee, ne, ocols, out, csl, Et, flag, s)
+                   : asm_oz<7>(coef, ldc, n_t, L, xsl, xL, pack, Ee, ne, ocols, out, csl, Et, flag, s);
 }
 
 }  // namespace ssm

@@ -317,12 +317,13 @@ cudaError_t launch_sym_pack(const double* G, int n, double* out, cudaStream_t s)
 // csl, asm_oz_cslice_bytes, with the point scales Et, n_t ints; mx: ne scratch words).
 // Status bit 2 of *flag
 // on a timed-out wait.
-size_t asm_oz_xslice_bytes(int ne, int L);
-size_t asm_oz_cslice_bytes(int64_t n_t, int L);
+// ns = 6 or 7 slices per value (both operands).
+size_t asm_oz_xslice_bytes(int ne, int L, int ns);
+size_t asm_oz_cslice_bytes(int64_t n_t, int L, int ns);
 cudaError_t launch_asm_oz_xslices(const double* X, int n_tot, int L, const int* pack, int ne, int* Ee,
-                                  unsigned long long* mx, uint8_t* xsl, cudaStream_t s);
+                                  unsigned long long* mx, uint8_t* xsl, int ns, cudaStream_t s);
 cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
-                          const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag,
+                          const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag, int ns,
                           cudaStream_t s);
 
 // Per-point Alg. 4 + Alg. 6 solve (solve.cu).

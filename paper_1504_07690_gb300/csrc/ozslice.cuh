@@ -6,8 +6,8 @@
 // assembly of the per-point matrices (assemble_oz.cu).
 //
 // A value x of a column (or row) with scale 2^E > max |x| is split, as
-// x 2^-E = sum_k s_k + O(2^-48), into slices s_k = d_k 2^-(7+8(k-1)) with
-// integers |d_k| <= 256: each s_k is exact in bf16.  A product s_i s_j is then
+// x 2^-E = sum_k s_k + O(2^-48) (six slices), into slices s_k = d_k 2^-(7+8(k-1))
+// with integers |d_k| <= 256: each s_k is exact in bf16.  A product s_i s_j is then
 // an integer multiple of 2^-(14+8(i+j-2)), exact in float32; sums of such
 // products with equal i+j stay exact in float32 while they are below 2^24 of
 // their unit.
@@ -71,6 +71,22 @@ __device__ __forceinline__ void split_df(float hi, float lo, float se, float* s)
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+// NS slices of x 2^-E (|x 2^-E| < 1) from the float64 value itself: slice k is the
+// remainder rounded to a multiple of u_k = 2^-(7+8(k-1)) by q = (r + 1.5 2^52 u_k) -
+// 1.5 2^52 u_k, and r - q is exact.  Since |r| <= u_{k-1} / 2 before slice k, every slice
+// is d_k u_k with |d_k| <= 128 (exact in bf16), and x 2^-E = sum_k s_k + O(2^-(8 NS)).
+template <int NS>
+__device__ __forceinline__ void split_d(double x, double se, float* s) {
+    double r = x * se;  // exact: se = 2^-E
+#pragma unroll
+    for (int k = 1; k <= NS; ++k) {
+        const double M = __longlong_as_double((long long)(1023 + 52 - 7 - 8 * (k - 1)) << 52) * 1.5;
+        const double q = __dsub_rn(__dadd_rn(r, M), M);
+        r = __dsub_rn(r, q);
+        s[k - 1] = (float)q;
+    }
 }
 
 // Float pair of a float64 value: hi = rn(v), lo = rn(v - hi) (|lo| <= ulp(hi) / 2).

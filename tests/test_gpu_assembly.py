@@ -1,9 +1,10 @@
-"""The per-point assembly of mixed plans on the tensor cores.
+"""The per-point assembly of mixed and float64-accurate plans on the tensor cores.
 
-Single-operator mixed plans form K(t) = sum_l mu_l(t) X_l and
+Single-operator plans of these precisions form K(t) = sum_l mu_l(t) X_l and
 K_Z(t) = sum_l nu_l(t) X_l on the tensor cores, as exact products of bf16
-slices of the moments and of the coefficients (about 2^-47 of each entry's and
-each point's largest term).  To test that step and the solve after it apart
+slices of the moments and of the coefficients (six slices on mixed plans,
+about 2^-47 of each entry's and each point's largest term; seven on SSM_FP64_TC
+plans, 2^-55).  To test that step and the solve after it apart
 from the rounding of the recurrence, the RESS-DGC line of a plan is compared
 with the oracle's Alg. 7 loop run on the plan's own moments (returned by
 ssm_moments) with the plan's rounding floor: relative L1 1e-7 on the points the
@@ -22,7 +23,7 @@ from oracle import ssm_oracle as O  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-FLOOR = {"mixed": 2.0 ** -36}
+FLOOR = {"mixed": 2.0 ** -36, "fp64_tc": 2.0 ** -52}
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +36,8 @@ def S():
 
 
 CASES = [("mixed", 13, 0, 120, 70), ("mixed", 40, 0, 200, 101), ("mixed", 21, 10, 80, 130),
-         ("mixed", 150, 0, 60, 33), ("mixed", 24, 9, 60, 200)]
+         ("mixed", 150, 0, 60, 33), ("mixed", 24, 9, 60, 200), ("fp64_tc", 37, 0, 100, 65),
+         ("fp64_tc", 24, 9, 60, 33), ("fp64_tc", 140, 0, 40, 80)]
 
 
 @pytest.mark.parametrize("precision,nv,nvh,M,n_t", CASES,

@@ -118,6 +118,28 @@ def test_host_buffers_and_single_point(S):
     _check(st, W, 40, 0.2, t, info, dos_h, rank_h)
 
 
+def test_chunks_of_points_give_the_same_result(S):
+    # the filtered blocks of 3 points at a time (the recurrence reruns per chunk): every
+    # point's arithmetic is the same as with all points at once, so the results agree
+    # bit for bit; then against the oracle
+    st = wl.laplacian2d_dirichlet_potential(14, 86)
+    W = wl.random_block(st.n, 11, 87)
+    M, sigma = 50, 0.15
+    plan = S.ssm_plan_create(stencil=st, n_v=11, degree=M, precision="fp64")
+    info = S.ssm_plan_info(plan)
+    t = np.linspace(info["lo"], info["hi"], 11)
+    Wd, td = torch.from_numpy(W).cuda(), torch.from_numpy(t).cuda()
+    d_all, r_all = S.ssm_dos_explicit(plan, Wd, td, sigma)
+    try:
+        S.ssm_debug_explicit_chunk(3)
+        d_chk, r_chk = S.ssm_dos_explicit(plan, Wd, td, sigma)
+    finally:
+        S.ssm_debug_explicit_chunk(0)
+    plan.close()
+    assert torch.equal(d_all, d_chk) and torch.equal(r_all, r_chk)
+    _check(st, W, M, sigma, t, info, d_chk.cpu().numpy(), r_chk.cpu().numpy())
+
+
 def test_rejects_plans_it_does_not_serve(S):
     st = wl.laplacian2d_dirichlet_potential(12, 85)
     W = torch.zeros((st.n, 8), dtype=torch.float64, device="cuda")
