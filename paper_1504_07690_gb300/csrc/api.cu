@@ -40,9 +40,12 @@ struct ssm_plan_s {
     // trace buffers
     double* d_tr = nullptr;
     size_t cap_tr = 0;
-    // batched plans: per-point floor scale
+    // batched plans: per-point floor scale and filter, then per-point map and norm; the
+    // zeta of one chunk of matrices
     double* d_fpt = nullptr;
     size_t cap_fpt = 0;
+    double* d_zetab = nullptr;
+    size_t cap_zetab = 0;
     // mixed path: float pairs (hi, lo) of the moments and of one batch's mu and nu
     float* d_xpair = nullptr;
     size_t cap_xpair = 0;
@@ -289,6 +292,7 @@ void free_plan(ssm_plan_s* h) {
     if (P.graph) cudaGraphExecDestroy(P.graph);
     if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
     dev_free(h->d_fpt);
+    dev_free(h->d_zetab);
     dev_free(h->d_pack);
     dev_free(h->d_Ee);
     dev_free(h->d_Emx);
@@ -584,55 +588,97 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
     const size_t xs = (size_t)(M + 1) * n_tot * n_tot;
     int64_t mb = batch_points(P) / (n_tp > 0 ? n_tp : 1);
     if (mb < 1) mb = 1;
-    if ((size_t)(3 * n_t) > h->cap_fpt) {
+    // per point: rounding floor scale and range filter [xlo, xhi] of its matrix (fpt), and
+    // the matrix's map and norm for the coefficients (pp)
+    if ((size_t)(6 * n_t) > h->cap_fpt) {
         dev_free(h->d_fpt);
         h->d_fpt = nullptr;
         h->cap_fpt = 0;
-        CUDA_OR_FAIL(h, dev_alloc(&h->d_fpt, 3 * n_t));
-        h->cap_fpt = 3 * n_t;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_fpt, 6 * n_t));
+        h->cap_fpt = 6 * n_t;
     }
-    // per point: rounding floor scale and range filter [xlo, xhi] of its matrix
-    std::vector<double> fpt(3 * n_t);
+    std::vector<double> fpt(6 * n_t);
     std::vector<double> x0(P.B);
     CUDA_OR_FAIL(h, cudaMemcpyAsync(x0.data(), P.d_x0max, P.B * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
     CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
     for (int b = 0; b < P.B; ++b) {
         const double gmax = 1.0 / ((double)P.h_nb[b] * sqrt(2.0 * M_PI * sigma * sigma));
+        const double a = P.h_ab[6 * b], bb = P.h_ab[6 * b + 1];
         for (int64_t i = 0; i < n_tp; ++i) {
             double* q = &fpt[3 * (b * n_tp + i)];
             q[0] = 8.0 * nv * P.eps_floor * x0[b];
             q[1] = -P.p.kappa * gmax;
             q[2] = (1.0 + P.p.kappa) * gmax;
+            double* r = &fpt[3 * n_t + 3 * (b * n_tp + i)];
+            r[0] = 0.5 * (a + bb);
+            r[1] = 0.5 * (bb - a);
+            r[2] = gmax;  // 1 / (N_b sqrt(2 pi sigma^2))
         }
     }
-    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_fpt, fpt.data(), 3 * n_t * sizeof(double), cudaMemcpyHostToDevice,
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_fpt, fpt.data(), 6 * n_t * sizeof(double), cudaMemcpyHostToDevice,
                                     P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));  // fpt is a host temporary
+    const double* d_pp = h->d_fpt + 3 * n_t;
     if (want_ss && P.mixed) {
         Scope sc(h, PH_ASSEMBLE);
         ssm_status st = split_moments(h);
         if (st != SSM_OK) return st;
     }
+    if ((size_t)mb * (M + 1) > h->cap_zetab) {
+        dev_free(h->d_zetab);
+        h->d_zetab = nullptr;
+        h->cap_zetab = 0;
+        CUDA_OR_FAIL(h, dev_alloc(&h->d_zetab, (size_t)mb * (M + 1)));
+        h->cap_zetab = (size_t)mb * (M + 1);
+    }
     for (int64_t b0 = 0; b0 < P.B; b0 += mb) {
         const int64_t b1 = b0 + mb < P.B ? b0 + mb : P.B;
-        for (int64_t b = b0; b < b1; ++b) {
-            const int64_t off = (b - b0) * n_tp;
-            ssm_status st = coefficients_dev(h, d_tpts + b * n_tp, n_tp, sigma, h->d_mu + off * (M + 1),
-                                             want_ss ? h->d_nu + off * (M + 1) : nullptr, (int)b,
-                                             h->d_muh ? h->d_muh + off * (M + 1) : nullptr);
-            if (st != SSM_OK) return st;
-            if (want_ss) {
-                Scope sc(h, PH_ASSEMBLE);
-                st = assemble_pencils(h, (P.p.damping ? h->d_muh : h->d_mu) + off * (M + 1), h->d_nu + off * (M + 1),
-                                      n_tp, (int)b,
-                                      h->d_K + off * n_tot * n_tot, h->d_KZ + off * nv * nv);
-                if (st != SSM_OK) return st;
+        const int nbm = (int)(b1 - b0);
+        const int64_t nb = nbm * n_tp;
+        // the points of all matrices of the chunk at once: coefficients, assembly, KPM line
+        {
+            Scope sc(h, PH_COEFFS);
+            CUDA_OR_FAIL(h, launch_mu_pp(d_tpts + b0 * n_tp, nb, sigma, d_pp + 3 * b0 * n_tp, M, P.n_theta, P.d_ctab,
+                                         h->d_mu, M + 1, P.stream));
+            P.stats.launches++;
+            if (P.p.damping) {
+                CUDA_OR_FAIL(h, launch_damp(h->d_mu, M + 1, nb, M, P.p.damping, P.p.damping_lambda, h->d_muh,
+                                            P.stream));
+                P.stats.launches++;
             }
-            {
-                Scope sc(h, PH_KPM);
-                CUDA_OR_FAIL(h, launch_kpm(h->d_mu + off * (M + 1), M + 1, n_tp, M, P.d_X + b * xs, n_tot, h->d_zeta,
-                                           h->d_dos_kpm + b * n_tp, P.stream));
+            if (want_ss) {
+                CUDA_OR_FAIL(h, launch_nu(P.p.damping ? h->d_muh : h->d_mu, M + 1, nb, M, h->d_nu, M + 1, P.stream));
+                P.stats.launches++;
+            }
+        }
+        if (want_ss) {
+            Scope sc(h, PH_ASSEMBLE);
+            const double* muh = P.p.damping ? h->d_muh : h->d_mu;
+            if (P.mixed) {
+                const size_t nx = h->cap_xpair / 2, nc = (size_t)nb * (M + 1);
+                const float* xh = h->d_xpair + b0 * xs;
+                const float* xl = h->d_xpair + nx + b0 * xs;
+                float* c = h->d_cpair;
+                CUDA_OR_FAIL(h, launch_split_pairs(muh, (int64_t)nc, c, c + nc, P.stream));
+                CUDA_OR_FAIL(h, launch_split_pairs(h->d_nu, (int64_t)nc, c + 2 * nc, c + 3 * nc, P.stream));
+                CUDA_OR_FAIL(h, launch_assemble_pairs(c, c + nc, M + 1, n_tp, K + 1, xh, xl, n_tot, n_tot, n_tot,
+                                                      h->d_K, P.stream, nbm, (int64_t)xs));
+                CUDA_OR_FAIL(h, launch_assemble_pairs(c + 2 * nc, c + 3 * nc, M + 1, n_tp, M + 1, xh, xl, n_tot, nv,
+                                                      nv, h->d_KZ, P.stream, nbm, (int64_t)xs));
+                P.stats.launches += 4;
+            } else {
+                CUDA_OR_FAIL(h, launch_assemble(muh, M + 1, n_tp, K + 1, P.d_X + b0 * xs, n_tot, n_tot, n_tot, h->d_K,
+                                                P.stream, nbm, (int64_t)xs));
+                CUDA_OR_FAIL(h, launch_assemble(h->d_nu, M + 1, n_tp, M + 1, P.d_X + b0 * xs, n_tot, nv, nv, h->d_KZ,
+                                                P.stream, nbm, (int64_t)xs));
                 P.stats.launches += 2;
             }
+        }
+        {
+            Scope sc(h, PH_KPM);
+            CUDA_OR_FAIL(h, launch_kpm_batched(h->d_mu, M + 1, n_tp, nbm, M, P.d_X + b0 * xs, xs, n_tot, h->d_zetab,
+                                               h->d_dos_kpm + b0 * n_tp, P.stream));
+            P.stats.launches += 2;
         }
         if (want_ss) {
             Scope sc(h, PH_SOLVE);

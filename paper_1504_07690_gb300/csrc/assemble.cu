@@ -26,7 +26,11 @@ constexpr int TL = 16;   // l per slab
 
 __global__ void __launch_bounds__(256)
 assemble_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L, const double* __restrict__ X,
-                int n_tot, int rows, int cols, double* __restrict__ out) {
+                int n_tot, int rows, int cols, double* __restrict__ out, int64_t zc, int64_t zx, int64_t zo) {
+    // grid.z: matrices of a batched plan (coefficients, moments and outputs zc, zx, zo apart)
+    coef += blockIdx.z * zc;
+    X += blockIdx.z * zx;
+    out += blockIdx.z * zo;
     __shared__ double Cs[TL][TT + 1];
     __shared__ double Xs[TL][TE];
     __shared__ int xoff[TE];
@@ -135,7 +139,12 @@ __global__ void split_pairs_kernel(const double* __restrict__ v, int64_t n, floa
 __global__ void __launch_bounds__(256, 3)
 assemble_df_kernel(const float* __restrict__ coef_hi, const float* __restrict__ coef_lo, int ldc, int64_t n_t, int L,
                    const float* __restrict__ X_hi, const float* __restrict__ X_lo, int n_tot, int rows, int cols,
-                   double* __restrict__ out) {
+                   double* __restrict__ out, int64_t zc, int64_t zx, int64_t zo) {
+    coef_hi += blockIdx.z * zc;
+    coef_lo += blockIdx.z * zc;
+    X_hi += blockIdx.z * zx;
+    X_lo += blockIdx.z * zx;
+    out += blockIdx.z * zo;
     // two slab buffers: the next slab's values wait in registers while this one is summed
     __shared__ float Ch[2][TL][TT + 1], Cl[2][TL][TT + 1];
     __shared__ float Xh[2][TL][TE], Xl[2][TL][TE];
@@ -260,21 +269,23 @@ assemble_df_kernel(const float* __restrict__ coef_hi, const float* __restrict__ 
 }  // namespace
 
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X, int n_tot,
-                            int rows, int cols, double* out, cudaStream_t s) {
-    if (rows != cols) return cudaErrorInvalidValue;
+                            int rows, int cols, double* out, cudaStream_t s, int nz, int64_t zx) {
+    if (rows != cols || nz < 1 || nz > 65535) return cudaErrorInvalidValue;
     const int64_t ne = (int64_t)rows * (rows + 1) / 2;
-    dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
-    assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out);
+    dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT), (unsigned)nz);
+    assemble_kernel<<<grid, 256, 0, s>>>(coef, ldc, n_t, L, X, n_tot, rows, cols, out, n_t * ldc, zx,
+                                         n_t * rows * cols);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, int ldc, int64_t n_t, int L,
                                   const float* X_hi, const float* X_lo, int n_tot, int rows, int cols, double* out,
-                                  cudaStream_t s) {
-    if (rows != cols) return cudaErrorInvalidValue;
+                                  cudaStream_t s, int nz, int64_t zx) {
+    if (rows != cols || nz < 1 || nz > 65535) return cudaErrorInvalidValue;
     const int64_t ne = (int64_t)rows * (rows + 1) / 2;
-    dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT));
-    assemble_df_kernel<<<grid, 256, 0, s>>>(coef_hi, coef_lo, ldc, n_t, L, X_hi, X_lo, n_tot, rows, cols, out);
+    dim3 grid((unsigned)((ne + TE - 1) / TE), (unsigned)((n_t + TT - 1) / TT), (unsigned)nz);
+    assemble_df_kernel<<<grid, 256, 0, s>>>(coef_hi, coef_lo, ldc, n_t, L, X_hi, X_lo, n_tot, rows, cols, out,
+                                            n_t * ldc, zx, n_t * rows * cols);
     return cudaGetLastError();
 }
 

@@ -37,14 +37,17 @@ __global__ void cos_table_kernel(double* ctab, int n_theta) {
 // the sums of a chunk run over its nonzero span only (the zero terms it skips add
 // nothing, so the result is the same to the bit).
 __global__ void __launch_bounds__(256)
-mu_kernel(const double* __restrict__ t, int64_t n_t, double sigma, double inv_norm, double xc, double xh,
-          int M, int n_theta, const double* __restrict__ ctab, double* __restrict__ mu, int ldmu) {
+mu_kernel(const double* __restrict__ t, int64_t n_t, double sigma, double inv_norm0, double xc0, double xh0,
+          int M, int n_theta, const double* __restrict__ ctab, double* __restrict__ mu, int ldmu,
+          const double* __restrict__ pp) {
     __shared__ double gs[GCHUNK];
     __shared__ int span[2];  // first and last nonzero g of the chunk
     const int n2 = 2 * n_theta;
     const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
     for (int64_t it = blockIdx.x; it < n_t; it += gridDim.x) {
         const double ti = t[it];
+        const double xc = pp ? pp[3 * it] : xc0, xh = pp ? pp[3 * it + 1] : xh0;
+        const double inv_norm = pp ? pp[3 * it + 2] : inv_norm0;
         // per-thread partial sums for l = threadIdx.x + 256 r
         double accs[8];
         const int nl = (M + 1 + 255) / 256;
@@ -101,8 +104,9 @@ mu_kernel(const double* __restrict__ t, int64_t n_t, double sigma, double inv_no
 // Fallback for M >= 2048 (more than 8 coefficients per thread): one thread
 // per (t, l), g recomputed per chunk from the same formula.
 __global__ void __launch_bounds__(256)
-mu_kernel_wide(const double* __restrict__ t, int64_t n_t, double sigma, double inv_norm, double xc, double xh,
-               int M, int n_theta, const double* __restrict__ ctab, double* __restrict__ mu, int ldmu) {
+mu_kernel_wide(const double* __restrict__ t, int64_t n_t, double sigma, double inv_norm0, double xc0, double xh0,
+               int M, int n_theta, const double* __restrict__ ctab, double* __restrict__ mu, int ldmu,
+               const double* __restrict__ pp) {
     __shared__ double gs[GCHUNK];
     const int n2 = 2 * n_theta;
     const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
@@ -111,6 +115,8 @@ mu_kernel_wide(const double* __restrict__ t, int64_t n_t, double sigma, double i
         const int64_t it = bt / lblocks;
         const int l = (int)(bt - it * lblocks) * 256 + threadIdx.x;
         const double ti = t[it];
+        const double xc = pp ? pp[3 * it] : xc0, xh = pp ? pp[3 * it + 1] : xh0;
+        const double inv_norm = pp ? pp[3 * it + 2] : inv_norm0;
         double acc = 0.0;
         for (int j0 = 0; j0 <= n_theta; j0 += GCHUNK) {
             const int jn = min(GCHUNK, n_theta + 1 - j0);
@@ -184,23 +190,29 @@ __global__ void damp_kernel(double* __restrict__ mu, int ldmu, int64_t n_t, int 
     }
 }
 
-__global__ void zeta_kernel(const double* __restrict__ X, int n_tot, int M, double* __restrict__ zeta) {
+// zeta of nz matrices (moments xs values apart): zeta[z][l], grid-stride over (z, l).
+__global__ void zeta_kernel(const double* __restrict__ X, size_t xs, int nz, int n_tot, int M,
+                            double* __restrict__ zeta) {
     const size_t nn = (size_t)n_tot * n_tot;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= M; l += gridDim.x * blockDim.x) {
-        const double* x = X + (size_t)l * nn;
+    const int64_t total = (int64_t)nz * (M + 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t z = q / (M + 1);
+        const int l = (int)(q - z * (M + 1));
+        const double* x = X + z * xs + (size_t)l * nn;
         double s = 0.0;
         for (int i = 0; i < n_tot; ++i) s += x[(size_t)i * n_tot + i];
-        zeta[l] = s / n_tot;
+        zeta[q] = s / n_tot;
     }
 }
 
 // One warp per sweep point, fixed-order lane sums then a fixed shuffle tree.
 __global__ void kpm_kernel(const double* __restrict__ mu, int ldmu, int64_t n_t, int M,
-                           const double* __restrict__ zeta, double* __restrict__ out) {
+                           const double* __restrict__ zeta0, double* __restrict__ out, int64_t n_tp) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = w0; it < n_t; it += nw) {
+        const double* zeta = zeta0 + (n_tp > 0 ? (it / n_tp) * (M + 1) : 0);  // the point's matrix
         double s = 0.0;
         for (int l = lane; l <= M; l += 32) s = fma(mu[it * ldmu + l], zeta[l], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -221,17 +233,31 @@ cudaError_t launch_cos_table(double* ctab, int n_theta, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mu(const double* t, int64_t n_t, double sigma, double inv_norm, double a, double b,
-                      int M, int n_theta, const double* ctab, double* mu, int ldmu, cudaStream_t s) {
-    const double xc = 0.5 * (a + b), xh = 0.5 * (b - a);
+namespace {
+
+cudaError_t mu_launch(const double* t, int64_t n_t, double sigma, double inv_norm, double xc, double xh,
+                      const double* pp, int M, int n_theta, const double* ctab, double* mu, int ldmu,
+                      cudaStream_t s) {
     if (M + 1 <= 8 * 256) {
-        mu_kernel<<<nblocks(n_t, 1), 256, 0, s>>>(t, n_t, sigma, inv_norm, xc, xh, M, n_theta, ctab, mu, ldmu);
+        mu_kernel<<<nblocks(n_t, 1), 256, 0, s>>>(t, n_t, sigma, inv_norm, xc, xh, M, n_theta, ctab, mu, ldmu, pp);
     } else {
         const int64_t lb = (M + 1 + 255) / 256;
         mu_kernel_wide<<<nblocks(n_t * lb, 1), 256, 0, s>>>(t, n_t, sigma, inv_norm, xc, xh, M, n_theta, ctab,
-                                                           mu, ldmu);
+                                                           mu, ldmu, pp);
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mu(const double* t, int64_t n_t, double sigma, double inv_norm, double a, double b,
+                      int M, int n_theta, const double* ctab, double* mu, int ldmu, cudaStream_t s) {
+    return mu_launch(t, n_t, sigma, inv_norm, 0.5 * (a + b), 0.5 * (b - a), nullptr, M, n_theta, ctab, mu, ldmu, s);
+}
+
+cudaError_t launch_mu_pp(const double* t, int64_t n_t, double sigma, const double* pp, int M, int n_theta,
+                         const double* ctab, double* mu, int ldmu, cudaStream_t s) {
+    return mu_launch(t, n_t, sigma, 0.0, 0.0, 0.0, pp, M, n_theta, ctab, mu, ldmu, s);
 }
 
 cudaError_t launch_nu(const double* mu, int ldmu, int64_t n_t, int M, double* nu, int ldnu, cudaStream_t s) {
@@ -247,10 +273,19 @@ cudaError_t launch_damp(double* mu, int ldmu, int64_t n_t, int M, int kind, doub
 
 cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const double* X, int n_tot,
                        double* zeta, double* out, cudaStream_t s) {
-    zeta_kernel<<<nblocks(M + 1, 128), 128, 0, s>>>(X, n_tot, M, zeta);
+    zeta_kernel<<<nblocks(M + 1, 128), 128, 0, s>>>(X, 0, 1, n_tot, M, zeta);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    kpm_kernel<<<nblocks(n_t * 32, 256), 256, 0, s>>>(mu, ldmu, n_t, M, zeta, out);
+    kpm_kernel<<<nblocks(n_t * 32, 256), 256, 0, s>>>(mu, ldmu, n_t, M, zeta, out, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kpm_batched(const double* mu, int ldmu, int64_t n_tp, int nz, int M, const double* X, size_t xs,
+                               int n_tot, double* zeta, double* out, cudaStream_t s) {
+    zeta_kernel<<<nblocks((int64_t)nz * (M + 1), 128), 128, 0, s>>>(X, xs, nz, n_tot, M, zeta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kpm_kernel<<<nblocks(n_tp * nz * 32, 256), 256, 0, s>>>(mu, ldmu, n_tp * nz, M, zeta, out, n_tp);
     return cudaGetLastError();
 }
 

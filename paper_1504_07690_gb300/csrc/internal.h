@@ -284,6 +284,10 @@ cudaError_t launch_convert_in(const double* src, int64_t ldsrc, void* dst, int l
 cudaError_t launch_cos_table(double* ctab, int n_theta, cudaStream_t s);
 cudaError_t launch_mu(const double* t, int64_t n_t, double sigma, double inv_norm, double a, double b,
                       int M, int n_theta, const double* ctab, double* mu, int ldmu, cudaStream_t s);
+// The same with each point's map and norm from pp (3 per point: (a+b)/2, (b-a)/2,
+// 1/(N sqrt(2 pi sigma^2))): the points of many matrices of a batched plan at once.
+cudaError_t launch_mu_pp(const double* t, int64_t n_t, double sigma, const double* pp, int M, int n_theta,
+                         const double* ctab, double* mu, int ldmu, cudaStream_t s);
 cudaError_t launch_nu(const double* mu, int ldmu, int64_t n_t, int M, double* nu, int ldnu,
                       cudaStream_t s);
 // Damping: muh = factors of M/2+1 terms times mu (l <= M/2, zero above), then mu *= factors
@@ -292,15 +296,21 @@ cudaError_t launch_damp(double* mu, int ldmu, int64_t n_t, int M, int kind, doub
                         cudaStream_t s);
 cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const double* X, int n_tot,
                        double* zeta, double* out, cudaStream_t s);
+// KPM lines of nz matrices of a batched plan (moments xs values apart, n_tp points each,
+// zeta: nz x (M+1)).
+cudaError_t launch_kpm_batched(const double* mu, int ldmu, int64_t n_tp, int nz, int M, const double* X, size_t xs,
+                               int n_tot, double* zeta, double* out, cudaStream_t s);
 
 // Assembly: out[t][i*cols+j] = sum_{l<L} coef[t][l] X[l][i][j] (assemble.cu) in float64;
 // the mixed path's variant takes coef and X as float pairs (launch_split_pairs) and sums
 // in float-pair arithmetic.
+// nz > 1: nz matrices of a batched plan at once, n_t points each (coefficient rows and
+// outputs consecutive across matrices), their moments zx values apart.
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X,
-                            int n_tot, int rows, int cols, double* out, cudaStream_t s);
+                            int n_tot, int rows, int cols, double* out, cudaStream_t s, int nz = 1, int64_t zx = 0);
 cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, int ldc, int64_t n_t, int L,
                                   const float* X_hi, const float* X_lo, int n_tot, int rows, int cols, double* out,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int nz = 1, int64_t zx = 0);
 cudaError_t launch_split_pairs(const double* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 
 // SS-DGC with explicit filtered blocks (ssdgc.cu, Alg. 5): Z_i += sum_{j<nj} mu[i][l0+j] V[j]
