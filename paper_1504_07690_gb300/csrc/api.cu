@@ -291,6 +291,7 @@ void free_plan(ssm_plan_s* h) {
     delete[] P.h_ab;
     if (P.graph) cudaGraphExecDestroy(P.graph);
     if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
+    if (P.cap_stream2) cudaStreamDestroy(P.cap_stream2);
     dev_free(h->d_fpt);
     dev_free(h->d_zetab);
     dev_free(h->d_pack);
@@ -697,7 +698,12 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
 // Batched plans: the whole recurrence with its Gram products and reductions
 // (a3, a4 for every matrix) is one CUDA graph, captured on the first call and
 // replayed: one launch per ssm_moments, whatever the number of matrices.
-cudaError_t record_batched_moments(Plan& P, cudaStream_t cs) {
+// Two branches in the graph: the recurrence on cs, the Gram products and reductions on cs2,
+// so that the Gram of step k runs next to recurrence step k+1.  V_j's panels live in
+// d_panel[j % 3]; the Gram of step k reads V_{k+1}'s and V_k's panels (or blocks), and
+// recurrence step k overwrites the panel and block of V_{k-2}, last read by the Gram of
+// step k-1: step k waits for that Gram only.
+cudaError_t record_batched_moments(Plan& P, cudaStream_t cs, cudaStream_t cs2) {
     const int M = P.p.degree, S = M / 2, B = P.B;
     const size_t nn = (size_t)P.n_tot * P.n_tot, xs = (size_t)(M + 1) * nn;
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
@@ -706,38 +712,49 @@ cudaError_t record_batched_moments(Plan& P, cudaStream_t cs) {
     if (e == cudaSuccess && P.use_tc) e = launch_panelize(P, (const float*)P.d_V[0], P.d_panel[0], cs);
     auto gram_reduce = [&](const void* Vn, const void* Vc, int j, int step) -> cudaError_t {
         if (P.use_tc) {
-            cudaError_t r = launch_gram_tc(P.d_panel[j & 1], Vc ? P.d_panel[(j + 1) & 1] : nullptr, P.n_tot, P.n,
-                                           P.tc_ne, P.tc_no, P.d_part_tc, P.d_flag, cs, P.d_slabs);
+            cudaError_t r = launch_gram_tc(P.d_panel[j % 3], Vc ? P.d_panel[(j + 2) % 3] : nullptr, P.n_tot, P.n,
+                                           P.tc_ne, P.tc_no, P.d_part_tc, P.d_flag, cs2, P.d_slabs);
             if (r != cudaSuccess) return r;
             return launch_reduce_tc_seg(P.d_part_tc, P.tc_ne, P.n_tot, B, P.d_slabseg, P.d_ring_sum,
-                                        P.d_ring_sum + (size_t)B * nn, P.d_X, xs, step, cs);
+                                        P.d_ring_sum + (size_t)B * nn, P.d_X, xs, step, cs2);
         }
         for (int b = 0; b < B; ++b) {
             const size_t off = (size_t)P.h_row_off[b] * P.ld * esz;
             const void* A = (const uint8_t*)Vn + off;
             const void* C = Vc ? (const void*)((const uint8_t*)Vc + off) : nullptr;
             cudaError_t r = P.mixed ? launch_gram_f32((const float*)A, (const float*)C, P.ld, P.n_tot, P.h_nb[b],
-                                                      P.n_split, P.d_part, cs)
+                                                      P.n_split, P.d_part, cs2)
                                     : launch_gram_f64((const double*)A, (const double*)C, P.ld, P.n_tot, P.h_nb[b],
-                                                      P.n_split, P.d_part, cs);
-            if (r == cudaSuccess) r = launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X + b * xs, step, cs);
+                                                      P.n_split, P.d_part, cs2);
+            if (r == cudaSuccess) r = launch_reduce_moments(P.d_part, P.n_split, P.n_tot, P.d_X + b * xs, step, cs2);
             if (r != cudaSuccess) return r;
         }
         return cudaSuccess;
     };
+    // fork: the Gram of V_0 on the second branch
+    if (e == cudaSuccess) e = cudaEventRecord(P.ev_st[0], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, P.ev_st[0], 0);
     if (e == cudaSuccess) e = gram_reduce(P.d_V[0], nullptr, 0, -1);
+    if (e == cudaSuccess) e = cudaEventRecord(P.ev_gr[0], cs2);
     for (int k = 0; k < S && e == cudaSuccess; ++k) {
         void* Vc = P.d_V[k % 3];
         void* Vp = P.d_V[(k + 2) % 3];
         void* Vn = P.d_V[(k + 1) % 3];
         const double c = (k == 0) ? 0.5 : 1.0, d = (k == 0) ? 0.0 : 1.0;
+        if (k >= 1) e = cudaStreamWaitEvent(cs, P.ev_gr[(k - 1) % 3], 0);
+        if (e != cudaSuccess) break;
         if (P.mixed)
             e = launch_csr_step_f32(P, (const float*)Vc, (const float*)Vp, (float*)Vn, (float)c, (float)d,
-                                    P.use_tc ? P.d_panel[(k + 1) & 1] : nullptr, cs);
+                                    P.use_tc ? P.d_panel[(k + 1) % 3] : nullptr, cs);
         else
             e = launch_csr_step_f64(P, (const double*)Vc, (const double*)Vp, (double*)Vn, c, d, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(P.ev_st[(k + 1) % 3], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs2, P.ev_st[(k + 1) % 3], 0);
         if (e == cudaSuccess) e = gram_reduce(Vn, Vc, k + 1, k);
+        if (e == cudaSuccess) e = cudaEventRecord(P.ev_gr[(k + 1) % 3], cs2);
     }
+    // join the second branch before the check of the moments
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, P.ev_gr[S % 3], 0);
     if (e == cudaSuccess) e = launch_check_finite(P.d_X, (int64_t)B * (M + 1) * nn, P.d_flag, cs);
     return e;
 }
@@ -802,7 +819,7 @@ ssm_status moments_batched(ssm_plan_s* h, const double* W, int64_t ldw, double* 
         if (P.csr_threads == 0) CUDA_OR_FAIL(h, autotune_csr(P));
         CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
         CUDA_OR_FAIL(h, cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = record_batched_moments(P, P.cap_stream);
+        cudaError_t e = record_batched_moments(P, P.cap_stream, P.cap_stream2);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(P.cap_stream, &g);
         if (e == cudaSuccess) e = e2;
@@ -1336,6 +1353,11 @@ ssm_status ssm_plan_create_batched(ssm_plan_t* out, int32_t B, const ssm_csr* cs
         BCUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * B * nn));  // per-matrix float64 slab sums
     }
     BCUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+    BCUDA(cudaStreamCreateWithFlags(&P.cap_stream2, cudaStreamNonBlocking));
+    for (auto& ev : P.ev_st)
+        if (!ev) BCUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    for (auto& ev : P.ev_gr)
+        if (!ev) BCUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     BCUDA(cudaStreamSynchronize(P.stream));
 #undef BCUDA
     *out = h;

@@ -81,7 +81,7 @@ struct Plan {
     uint8_t* d_fmeta = nullptr;        // neighbour tables of the fused step
     int panel_groups = 0;              // split-bf16 panels: column groups of 8
     int64_t n_panels = 0;              // panels of 32 rows
-    uint8_t* d_panel[3] = {nullptr, nullptr, nullptr};  // panels of V_j in d_panel[j % 3] (batched: j % 2)
+    uint8_t* d_panel[3] = {nullptr, nullptr, nullptr};  // panels of V_j in d_panel[j % 3]
     cudaStream_t gstream = nullptr;    // Gram products of step k, next to the recurrence of step k+1
     cudaEvent_t ev_st[3] = {nullptr, nullptr, nullptr};  // recurrence step done
     cudaEvent_t ev_gr[3] = {nullptr, nullptr, nullptr};  // Gram of step j done
@@ -132,7 +132,8 @@ struct Plan {
     int2* d_slabs = nullptr;           // tensor-core Gram slab table [n_e + n_o] (panel ranges)
     int* d_slabseg = nullptr;          // per-matrix slab ranges: se[B+1], so[B+1]
     double* d_x0max = nullptr;         // per-matrix max_i X_0[i][i] (B)
-    cudaStream_t cap_stream = nullptr; // capture stream of the batched recurrence graph
+    cudaStream_t cap_stream = nullptr; // capture streams of the batched recurrence graph (the
+    cudaStream_t cap_stream2 = nullptr; // recurrence branch and the Gram branch)
     cudaGraphExec_t graph = nullptr;
     int csr_threads = 0;               // block size of the CSR step (autotuned for batched plans)
 
