@@ -670,7 +670,8 @@ def bench_batched(S, hbm, warmup: int = 1, steps: int = 2):
                        "(sum N = %d, nnz = %d), N_v=64 gaussian, M=500, 200 points each, sigma=0.05, mixed" % (N, nnz),
            "metric": "batched matrix-applies/s (sum_b nnz_b*N_v*M/s)", "value": nnz * nv * M / (ms * 1e-3),
            "ms_per_step": ms, "phases_ms_per_step": {k: v / steps for k, v in st.items() if k.startswith("ms_")},
-           "csr_threads_autotuned": S.ssm_batch_tuning(plan)["csr_threads"], "graph_launches_per_step": 1,
+           "csr_threads_autotuned": S.ssm_batch_tuning(plan)["csr_threads"],
+           "gram_slabs_autotuned": S.ssm_batch_tuning(plan)["gram_slabs"], "graph_launches_per_step": 1,
            "roofline": {"kernel": "recurrence graph (CSR step + tensor-core Gram + reduction), per step",
                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "traffic": None, "bytes_per_step": step_bytes}}

@@ -79,7 +79,7 @@ SIGNATURES = {
     "ssm_timing_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "ssm_debug_fail_alloc": (C.c_int, [C.c_int32]),
     "ssm_debug_explicit_chunk": (C.c_int, [C.c_int32]),
-    "ssm_batch_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "ssm_batch_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ssm_dos_explicit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_double,
                                    C.c_void_p, C.c_void_p]),
     "ssm_selftest_wait": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p]),

@@ -177,11 +177,11 @@ def ssm_batch_info(plan: Plan, b: int) -> dict:
 
 
 def ssm_batch_tuning(plan: Plan) -> dict:
-    """ssm_batch_tuning: the autotuned CTA size of a batched plan's CSR step."""
+    """ssm_batch_tuning: the autotuned CSR CTA size and Gram slab count of a batched plan."""
     lib = N.load()
-    ct = C.c_int32()
-    _check(lib, lib.ssm_batch_tuning(plan.handle, C.byref(ct)), plan.handle)
-    return {"csr_threads": ct.value}
+    ct, gs = C.c_int32(), C.c_int32()
+    _check(lib, lib.ssm_batch_tuning(plan.handle, C.byref(ct), C.byref(gs)), plan.handle)
+    return {"csr_threads": ct.value, "gram_slabs": gs.value}
 
 
 def ssm_plan_info(plan: Plan) -> dict:

@@ -759,6 +759,123 @@ cudaError_t record_batched_moments(Plan& P, cudaStream_t cs, cudaStream_t cs2) {
     return e;
 }
 
+// Gram slab table of a batched plan: each matrix's panels in ~equal slabs of at most
+// `pe` (Ge) and `po` (Go) panels, Ge slabs first; seg: per-matrix slab ranges.
+void build_slabs(const int64_t* row_off, int B, int64_t pe, int64_t po, std::vector<int2>& slabs,
+                 std::vector<int>& seg, int& ne) {
+    slabs.clear();
+    seg.assign(2 * (B + 1), 0);
+    for (int pass = 0; pass < 2; ++pass) {
+        const int64_t per = pass == 0 ? (pe < 1 ? 1 : pe) : (po < 1 ? 1 : po);
+        const int base = (int)slabs.size();
+        for (int b = 0; b < B; ++b) {
+            seg[pass * (B + 1) + b] = (int)slabs.size() - base;
+            const int64_t p0 = row_off[b] / 32, p1 = row_off[b + 1] / 32;
+            const int64_t k = (p1 - p0 + per - 1) / per;
+            for (int64_t j = 0; j < k; ++j) {
+                const int64_t a0 = p0 + (p1 - p0) * j / k, a1 = p0 + (p1 - p0) * (j + 1) / k;
+                slabs.push_back(make_int2((int)a0, (int)a1));
+            }
+        }
+        seg[pass * (B + 1) + B] = (int)slabs.size() - base;
+        if (pass == 0) ne = (int)slabs.size();
+    }
+}
+
+// Install the slab table with slabs of `div`-th of the default size (the default: one Ge
+// slab per SM's share of the panels, Go slabs half of that).
+cudaError_t install_slabs(Plan& P, int div) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tot_pan = P.h_row_off[P.B] / 32;
+    const int64_t pe = (tot_pan + (int64_t)sms * div - 1) / ((int64_t)sms * div);
+    const int64_t po = (tot_pan + 2LL * sms * div - 1) / (2LL * sms * div);
+    std::vector<int2> slabs;
+    std::vector<int> seg;
+    int ne = 0;
+    build_slabs(P.h_row_off, P.B, pe, po, slabs, seg, ne);
+    const int no = (int)slabs.size() - ne;
+    const size_t need = gram_tc_partial_floats(ne, no, P.n_tot);
+    if (slabs.size() > P.cap_slabs || need > P.cap_part_tc) {
+        dev_free(P.d_slabs);
+        dev_free(P.d_part_tc);
+        P.d_slabs = nullptr;
+        P.d_part_tc = nullptr;
+        P.cap_slabs = P.cap_part_tc = 0;
+        cudaError_t e = dev_alloc(&P.d_slabs, slabs.size());
+        if (e == cudaSuccess) e = dev_alloc(&P.d_part_tc, need);
+        if (e != cudaSuccess) return e;
+        P.cap_slabs = slabs.size();
+        P.cap_part_tc = need;
+    }
+    if (!P.d_slabseg) {
+        cudaError_t e = dev_alloc(&P.d_slabseg, seg.size());
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(P.d_slabs, slabs.data(), slabs.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                    P.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.d_slabseg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, P.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.stream);  // host vectors are temporaries
+    P.tc_ne = ne;
+    P.tc_no = no;
+    P.tc_slab_div = div;
+    return e;
+}
+
+// Project autotuner of the batched Gram: times one step of the recurrence graph's two
+// branches as they run there, a CSR step beside the Gram products and their per-matrix
+// reduction (on the plan's zeroed blocks and panels; the work does not depend on the
+// values), with slabs of 1/1, 1/2 and 1/4 of the default size, and keeps the fastest.
+// Runs after autotune_csr (the CSR step with its tuned CTA size).
+cudaError_t autotune_gram(Plan& P) {
+    const size_t nn = (size_t)P.n_tot * P.n_tot, xs = (size_t)(P.p.degree + 1) * nn;
+    cudaStream_t s2 = P.cap_stream2;
+    cudaEvent_t e0, e1, ef, ej;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreateWithFlags(&ef, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ej, cudaEventDisableTiming);
+    float best = 1e30f;
+    int pick = 1;
+    const int cand[3] = {1, 2, 4};
+    cudaError_t err = cudaSuccess;
+    for (int ci = 0; ci < 3 && err == cudaSuccess; ++ci) {
+        err = install_slabs(P, cand[ci]);
+        float ms = 0.f;
+        for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
+            if (r == 1) cudaEventRecord(e0, P.stream);
+            err = cudaEventRecord(ef, P.stream);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(s2, ef, 0);
+            if (err == cudaSuccess)
+                err = launch_gram_tc(P.d_panel[1], P.d_panel[0], P.n_tot, P.n, P.tc_ne, P.tc_no, P.d_part_tc,
+                                     P.d_flag, s2, P.d_slabs);
+            if (err == cudaSuccess)
+                err = launch_reduce_tc_seg(P.d_part_tc, P.tc_ne, P.n_tot, P.B, P.d_slabseg, P.d_ring_sum,
+                                           P.d_ring_sum + (size_t)P.B * nn, P.d_X, xs, 0, s2);
+            if (err == cudaSuccess)
+                err = launch_csr_step_f32(P, (const float*)P.d_V[0], (const float*)P.d_V[1], (float*)P.d_V[2], 1.f,
+                                          1.f, P.d_panel[2], P.stream);
+            if (err == cudaSuccess) err = cudaEventRecord(ej, s2);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(P.stream, ej, 0);
+        }
+        cudaEventRecord(e1, P.stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            pick = cand[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(ef);
+    cudaEventDestroy(ej);
+    if (err == cudaSuccess) err = install_slabs(P, pick);
+    return err;
+}
+
 // Project autotuner of the batched recurrence: times the CSR step with 64,
 // 128 and 256 threads per 32-row panel on the plan's own operator and keeps
 // the fastest (CUDA events, 2 warm-up and 3 timed launches each).
@@ -817,6 +934,10 @@ ssm_status moments_batched(ssm_plan_s* h, const double* W, int64_t ldw, double* 
     CUDA_OR_FAIL(h, cudaMemsetAsync(P.d_flag, 0, sizeof(int), P.stream));
     if (!P.graph) {
         if (P.csr_threads == 0) CUDA_OR_FAIL(h, autotune_csr(P));
+        if (P.use_tc && P.tc_tuned == 0) {
+            CUDA_OR_FAIL(h, autotune_gram(P));
+            P.tc_tuned = 1;
+        }
         CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
         CUDA_OR_FAIL(h, cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = record_batched_moments(P, P.cap_stream, P.cap_stream2);
@@ -1321,35 +1442,7 @@ ssm_status ssm_plan_create_batched(ssm_plan_t* out, int32_t B, const ssm_csr* cs
         dev_free(P.d_ring_sum);
         P.d_part_tc = P.d_ring = nullptr;
         P.d_ring_sum = nullptr;
-        int dev = 0, sms = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int64_t tot_pan = NR / 32;
-        const int64_t pe = (tot_pan + sms - 1) / sms, po = (tot_pan + 2 * sms - 1) / (2 * sms);
-        std::vector<int2> slabs;
-        std::vector<int> seg(2 * (B + 1), 0);
-        for (int pass = 0; pass < 2; ++pass) {
-            const int64_t per = pass == 0 ? (pe < 1 ? 1 : pe) : (po < 1 ? 1 : po);
-            const int base = (int)slabs.size();
-            for (int b = 0; b < B; ++b) {
-                seg[pass * (B + 1) + b] = (int)slabs.size() - base;
-                const int64_t p0 = row_off[b] / 32, p1 = row_off[b + 1] / 32;
-                const int64_t k = (p1 - p0 + per - 1) / per;
-                for (int64_t j = 0; j < k; ++j) {
-                    const int64_t a0 = p0 + (p1 - p0) * j / k, a1 = p0 + (p1 - p0) * (j + 1) / k;
-                    slabs.push_back(make_int2((int)a0, (int)a1));
-                }
-            }
-            seg[pass * (B + 1) + B] = (int)slabs.size() - base;
-            if (pass == 0) P.tc_ne = (int)slabs.size();
-        }
-        P.tc_no = (int)slabs.size() - P.tc_ne;
-        BCUDA(dev_alloc(&P.d_slabs, slabs.size()));
-        BCUDA(dev_alloc(&P.d_slabseg, seg.size()));
-        BCUDA(cudaMemcpyAsync(P.d_slabs, slabs.data(), slabs.size() * sizeof(int2), cudaMemcpyHostToDevice,
-                              P.stream));
-        BCUDA(cudaMemcpyAsync(P.d_slabseg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, P.stream));
-        BCUDA(dev_alloc(&P.d_part_tc, gram_tc_partial_floats(P.tc_ne, P.tc_no, P.n_tot)));
+        BCUDA(install_slabs(P, 1));
         BCUDA(dev_alloc(&P.d_ring_sum, (size_t)2 * B * nn));  // per-matrix float64 slab sums
     }
     BCUDA(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
@@ -1377,10 +1470,11 @@ ssm_status ssm_batch_info(ssm_plan_t h, int32_t b, double* a, double* bb, double
     return SSM_OK;
 }
 
-ssm_status ssm_batch_tuning(ssm_plan_t h, int32_t* csr_threads) {
+ssm_status ssm_batch_tuning(ssm_plan_t h, int32_t* csr_threads, int32_t* gram_slabs) {
     if (!h) return fail(nullptr, SSM_EINVAL, "plan is NULL");
     if (h->P.B <= 0) return fail(h, SSM_EINVAL, "not a batched plan");
     if (csr_threads) *csr_threads = h->P.csr_threads;
+    if (gram_slabs) *gram_slabs = h->P.use_tc && h->P.tc_tuned ? h->P.tc_ne + h->P.tc_no : 0;
     return SSM_OK;
 }
 

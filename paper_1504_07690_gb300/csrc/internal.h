@@ -71,6 +71,9 @@ struct Plan {
     float* d_ozpart = nullptr;                  // running sums of the Gram CTAs
     double* d_ozG = nullptr;                    // V_k^T V_k of the last step (n_tot^2)
     int tc_ne = 0, tc_no = 0;
+    size_t cap_slabs = 0, cap_part_tc = 0;  // capacities of d_slabs, d_part_tc (batched plans)
+    int tc_slab_div = 1;               // batched Gram slabs: 1/div of the default size (autotuned)
+    int tc_tuned = 0;
     float* d_part_tc = nullptr;        // [tc_ne + tc_no][n_tot][n_tot]
     float* d_ring = nullptr;           // ring of tc_ring partial slots (steps >= 1)
     double* d_ring_sum = nullptr;      // 2 x tc_ring x n_tot^2 float64 slab sums

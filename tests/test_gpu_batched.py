@@ -116,6 +116,19 @@ def test_batched_mixed_ss_per_matrix_from_its_moments(S):
         assert O.relative_l1_error(got[ok], r["dos_ss"][ok]) <= 1e-6, b
 
 
+def test_batched_autotuner_reports_its_choices(S):
+    csrs = _graphs()
+    plan = S.ssm_plan_create_batched(csrs, n_v=16, degree=20, precision="mixed")
+    assert S.ssm_batch_tuning(plan) == {"csr_threads": 0, "gram_slabs": 0}  # before the first moments
+    W = np.vstack([wl.random_block(c.n, 16, 5 + k) for k, c in enumerate(csrs)])
+    S.ssm_moments(plan, W)
+    tuned = S.ssm_batch_tuning(plan)
+    assert tuned["csr_threads"] in (64, 128, 256)
+    # at least one Ge and one Go slab per matrix
+    assert tuned["gram_slabs"] >= 2 * len(csrs)
+    plan.close()
+
+
 def test_batched_repeat_and_single(S):
     # the captured graph replays with new probe contents; B = 1 is a plain batch
     csrs = _graphs()[:1]
