@@ -46,6 +46,12 @@ struct ssm_plan_s {
     size_t cap_fpt = 0;
     double* d_zetab = nullptr;
     size_t cap_zetab = 0;
+    // batched plans: shared coefficient tables (points, maps, norms, mu, muh, nu) and the
+    // representative of each matrix
+    double* d_cs = nullptr;
+    size_t cap_cs = 0;
+    int* d_csrc = nullptr;
+    size_t cap_csrc = 0;
     // mixed path: float pairs (hi, lo) of the moments and of one batch's mu and nu
     float* d_xpair = nullptr;
     size_t cap_xpair = 0;
@@ -294,6 +300,8 @@ void free_plan(ssm_plan_s* h) {
     if (P.cap_stream2) cudaStreamDestroy(P.cap_stream2);
     dev_free(h->d_fpt);
     dev_free(h->d_zetab);
+    dev_free(h->d_cs);
+    dev_free(h->d_csrc);
     dev_free(h->d_pack);
     dev_free(h->d_Ee);
     dev_free(h->d_Emx);
@@ -625,6 +633,85 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
         ssm_status st = split_moments(h);
         if (st != SSM_OK) return st;
     }
+    // Matrices with the same interval and the same sweep points (normalised Laplacians of a
+    // batch all have [0, 2]) differ in their coefficients only by the norm 1/(N_b sqrt(2 pi
+    // sigma^2)): the tables are then computed once per distinct (interval, points), with
+    // norm 1, and each matrix's rows are those times its norm (nu: its square).
+    std::vector<double> th(n_t);
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(th.data(), d_tpts, n_t * sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    std::vector<int> src(P.B), reps;
+    for (int b = 0; b < P.B; ++b) {
+        int found = -1;
+        for (size_t r = 0; r < reps.size() && found < 0; ++r) {
+            const int q = reps[r];
+            if (P.h_ab[6 * q] == P.h_ab[6 * b] && P.h_ab[6 * q + 1] == P.h_ab[6 * b + 1] &&
+                memcmp(&th[(size_t)q * n_tp], &th[(size_t)b * n_tp], (size_t)n_tp * sizeof(double)) == 0)
+                found = (int)r;
+        }
+        if (found < 0) {
+            found = (int)reps.size();
+            reps.push_back(b);
+        }
+        src[b] = found;
+    }
+    const bool share = (int)reps.size() < P.B;
+    const int64_t nrp = (int64_t)reps.size() * n_tp;  // points of the representative tables
+    double *d_cmu = nullptr, *d_cmuh = nullptr, *d_cnu = nullptr, *d_sc = nullptr;
+    int* d_src = nullptr;
+    if (share) {
+        const size_t tab = (size_t)nrp * (M + 1);
+        const size_t need = (size_t)nrp * 4 + (size_t)P.B + 3 * tab;
+        if (need > h->cap_cs) {
+            dev_free(h->d_cs);
+            h->d_cs = nullptr;
+            h->cap_cs = 0;
+            CUDA_OR_FAIL(h, dev_alloc(&h->d_cs, need));
+            h->cap_cs = need;
+        }
+        if ((size_t)P.B > h->cap_csrc) {
+            dev_free(h->d_csrc);
+            h->d_csrc = nullptr;
+            h->cap_csrc = 0;
+            CUDA_OR_FAIL(h, dev_alloc(&h->d_csrc, (size_t)P.B));
+            h->cap_csrc = (size_t)P.B;
+        }
+        std::vector<double> host((size_t)nrp * 4 + P.B);
+        for (size_t r = 0; r < reps.size(); ++r) {
+            const int b = reps[r];
+            const double a = P.h_ab[6 * b], bb = P.h_ab[6 * b + 1];
+            for (int64_t i = 0; i < n_tp; ++i) {
+                host[r * n_tp + i] = th[(size_t)b * n_tp + i];
+                double* q = &host[(size_t)nrp + 3 * (r * n_tp + i)];
+                q[0] = 0.5 * (a + bb);
+                q[1] = 0.5 * (bb - a);
+                q[2] = 1.0;
+            }
+        }
+        for (int b = 0; b < P.B; ++b) host[(size_t)nrp * 4 + b] = fpt[3 * n_t + 3 * (b * n_tp) + 2];  // the norm
+        double* d_ct = h->d_cs;
+        double* d_cpp = d_ct + nrp;
+        d_sc = d_cpp + 3 * nrp;
+        d_cmu = d_sc + P.B;
+        d_cmuh = d_cmu + tab;
+        d_cnu = d_cmuh + tab;
+        d_src = h->d_csrc;
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_cs, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                        P.stream));
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(d_src, src.data(), P.B * sizeof(int), cudaMemcpyHostToDevice, P.stream));
+        Scope sc(h, PH_COEFFS);
+        CUDA_OR_FAIL(h, launch_mu_pp(d_ct, nrp, sigma, d_cpp, M, P.n_theta, P.d_ctab, d_cmu, M + 1, P.stream));
+        P.stats.launches++;
+        if (P.p.damping) {
+            CUDA_OR_FAIL(h, launch_damp(d_cmu, M + 1, nrp, M, P.p.damping, P.p.damping_lambda, d_cmuh, P.stream));
+            P.stats.launches++;
+        }
+        if (want_ss) {
+            CUDA_OR_FAIL(h, launch_nu(P.p.damping ? d_cmuh : d_cmu, M + 1, nrp, M, d_cnu, M + 1, P.stream));
+            P.stats.launches++;
+        }
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));  // `host` is a temporary
+    }
     if ((size_t)mb * (M + 1) > h->cap_zetab) {
         dev_free(h->d_zetab);
         h->d_zetab = nullptr;
@@ -637,7 +724,14 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
         const int nbm = (int)(b1 - b0);
         const int64_t nb = nbm * n_tp;
         // the points of all matrices of the chunk at once: coefficients, assembly, KPM line
-        {
+        if (share) {
+            Scope sc(h, PH_COEFFS);
+            CUDA_OR_FAIL(h, launch_expand_coeffs(d_cmu, P.p.damping ? d_cmuh : nullptr, want_ss ? d_cnu : nullptr,
+                                                 d_src, d_sc, n_tp, b0 * n_tp, nb, M, h->d_mu,
+                                                 P.p.damping ? h->d_muh : nullptr, want_ss ? h->d_nu : nullptr,
+                                                 P.stream));
+            P.stats.launches++;
+        } else {
             Scope sc(h, PH_COEFFS);
             CUDA_OR_FAIL(h, launch_mu_pp(d_tpts + b0 * n_tp, nb, sigma, d_pp + 3 * b0 * n_tp, M, P.n_theta, P.d_ctab,
                                          h->d_mu, M + 1, P.stream));

@@ -220,6 +220,28 @@ __global__ void kpm_kernel(const double* __restrict__ mu, int ldmu, int64_t n_t,
     }
 }
 
+// Coefficient rows of the points g0 .. g0+nb-1 of a batched plan from the tables of a
+// representative matrix with the same interval and sweep points, computed with norm 1:
+// point g of matrix b = g / n_tp takes row src[b] * n_tp + g % n_tp, times sc[b] (mu, muh)
+// or sc[b]^2 (nu: the square of the series).  Rows are M+1 wide (ld M+1).
+__global__ void expand_coeffs_kernel(const double* __restrict__ cmu, const double* __restrict__ cmuh,
+                                     const double* __restrict__ cnu, const int* __restrict__ src,
+                                     const double* __restrict__ sc, int64_t n_tp, int64_t g0, int64_t nb, int M,
+                                     double* __restrict__ mu, double* __restrict__ muh, double* __restrict__ nu) {
+    const int64_t total = nb * (int64_t)(M + 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t it = e / (M + 1);
+        const int l = (int)(e - it * (M + 1));
+        const int64_t g = g0 + it, b = g / n_tp;
+        const int64_t row = (int64_t)src[b] * n_tp + (g - b * n_tp);
+        const double s = sc[b];
+        const size_t from = (size_t)row * (M + 1) + l, to = (size_t)it * (M + 1) + l;
+        mu[to] = s * cmu[from];
+        if (muh) muh[to] = s * cmuh[from];
+        if (nu) nu[to] = s * s * cnu[from];
+    }
+}
+
 int nblocks(int64_t n, int per) {
     int64_t b = (n + per - 1) / per;
     if (b > (int64_t)device_sms() * 16) b = (int64_t)device_sms() * 16;
@@ -277,6 +299,15 @@ cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const dou
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     kpm_kernel<<<nblocks(n_t * 32, 256), 256, 0, s>>>(mu, ldmu, n_t, M, zeta, out, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_coeffs(const double* cmu, const double* cmuh, const double* cnu, const int* src,
+                                 const double* sc, int64_t n_tp, int64_t g0, int64_t nb, int M, double* mu, double* muh,
+                                 double* nu, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    expand_coeffs_kernel<<<nblocks(nb * (M + 1), 256), 256, 0, s>>>(cmu, cmuh, cnu, src, sc, n_tp, g0, nb, M, mu, muh,
+                                                                     nu);
     return cudaGetLastError();
 }
 

@@ -300,6 +300,12 @@ cudaError_t launch_damp(double* mu, int ldmu, int64_t n_t, int M, int kind, doub
                         cudaStream_t s);
 cudaError_t launch_kpm(const double* mu, int ldmu, int64_t n_t, int M, const double* X, int n_tot,
                        double* zeta, double* out, cudaStream_t s);
+// Batched plans whose matrices share intervals and sweep points: the coefficient rows of
+// points g0 .. g0+nb-1 from a representative's tables computed with norm 1 (row src[b] n_tp
+// + point, scaled by sc[b], nu by sc[b]^2; cmuh/muh and cnu/nu nullable).
+cudaError_t launch_expand_coeffs(const double* cmu, const double* cmuh, const double* cnu, const int* src,
+                                 const double* sc, int64_t n_tp, int64_t g0, int64_t nb, int M, double* mu, double* muh,
+                                 double* nu, cudaStream_t s);
 // KPM lines of nz matrices of a batched plan (moments xs values apart, n_tp points each,
 // zeta: nz x (M+1)).
 cudaError_t launch_kpm_batched(const double* mu, int ldmu, int64_t n_tp, int nz, int M, const double* X, size_t xs,

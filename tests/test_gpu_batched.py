@@ -148,3 +148,35 @@ def test_batched_repeat_and_single(S):
     S.ssm_moments(plan2, np.vstack([wl.random_block(c.n, 4, 3) for c in _graphs()[:2]]))
     with pytest.raises(S.SSMError, match="EINVAL"):
         S.ssm_dos(plan2, np.zeros(3), 0.1)  # 3 points do not split into B = 2 equal blocks
+
+
+@pytest.mark.parametrize("damping,kind", [(None, 0), ("jackson", 1)])
+def test_batched_shared_interval_coefficients_fp64(S, damping, kind):
+    # Matrices with one interval (here the normalised Laplacians' [0, 2], padded by 1e-3 of its
+    # width) and the same sweep points share one coefficient table scaled by each matrix's
+    # norm 1/(N_b sqrt(2 pi sigma^2)) (nu: its square).  Matrix 2 gets other points, so two
+    # tables are built; every matrix is checked against the oracle run on it alone.
+    csrs = _graphs()
+    n_v, M, sigma, n_tp = 8, 40, 0.05, 24
+    lo, hi = -2e-3, 2.0 + 2e-3
+    plan = S.ssm_plan_create_batched(csrs, n_v=n_v, degree=M, precision="fp64", lo=lo, hi=hi, damping=damping)
+    Ws = [wl.random_block(c.n, n_v, 177 + k, "rademacher") for k, c in enumerate(csrs)]
+    S.ssm_moments(plan, torch.from_numpy(np.vstack(Ws)).cuda())
+    base = np.linspace(0.0, 2.0, n_tp)
+    ts = [base if b != 2 else base * 0.9 + 0.05 for b in range(len(csrs))]
+    ss, kpm, rk = (x.cpu().numpy() for x in S.ssm_dos(plan, torch.from_numpy(np.concatenate(ts)).cuda(), sigma))
+    for b, c in enumerate(csrs):
+        i = S.ssm_batch_info(plan, b)
+        assert (i["a"], i["b"]) == (lo, hi)
+        A = O.csr_matrix(c.n, c.rowptr, c.colind, c.val)
+        kw = dict(interval=(lo, hi), flag_eps=1e-8, damping=kind)
+        r = O.ress_dgc(A, Ws[b], n_v, ts[b], M, sigma, **kw)
+        r2 = O.ress_dgc(A, Ws[b], n_v, ts[b], M, sigma, moments="doubling", **kw)
+        sl = slice(b * n_tp, (b + 1) * n_tp)
+        assert O.relative_l1_error(kpm[sl], r["dos_kpm"]) <= 1e-10, b
+        ok = ~r["flagged"] & ~r2["flagged"]
+        assert ok.mean() >= 0.8, b
+        tol = max(1e-10, 10.0 * O.relative_l1_error(r2["dos_ss"][ok], r["dos_ss"][ok]))
+        assert O.relative_l1_error(ss[sl][ok], r["dos_ss"][ok]) <= tol, b
+        assert np.array_equal(rk[sl, 0][ok], r["rank_s"][ok]), b
+    plan.close()
