@@ -240,6 +240,101 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
     }
 }
 
+// Float32 stencil step on grids whose axis 0 is inactive (2D and 1D grids): a thread
+// owns one 16-byte chunk of R consecutive rows of a 32-row panel and loads the centre
+// rows row0-1 .. row0+R once; they are also the axis-2 neighbours of the group's rows
+// wherever those are the adjacent rows (a wrapped neighbour is loaded where it is used).
+// Against one (row, chunk) item a thread this issues 5 instead of 6 loads a row on a 2D
+// grid, all of a group's loads before the first use.  Same operations in the same order
+// as stencil_step_kernel, so the outputs are the same bits.  Each CTA takes
+// MARCH_UNITS consecutive (row group, chunk) units, K a thread.
+constexpr int MARCH_R = 2, MARCH_K = 4, MARCH_T = 256;
+constexpr uint32_t MARCH_UNITS = (uint32_t)MARCH_T * MARCH_K;
+
+template <bool PANEL>
+__global__ void __launch_bounds__(MARCH_T)
+stencil_march_kernel(const float* __restrict__ Vc, const float* __restrict__ Vp, float* __restrict__ Vn,
+                     const float* __restrict__ diag2, StencilGeom g, float o1, float o2, float c, float d,
+                     uint32_t nchunk, uint32_t n_rows, PanelOut po) {
+    constexpr int R = MARCH_R;
+    const float4* vc = reinterpret_cast<const float4*>(Vc);
+    const float4* vp = reinterpret_cast<const float4*>(Vp);
+    float4* vn = reinterpret_cast<float4*>(Vn);
+    const uint32_t s1 = g.d2;
+    const float w1 = g.active[1] ? o1 : 0.f, w2 = g.active[2] ? o2 : 0.f;
+    const uint64_t units = (uint64_t)((n_rows + 31) / 32) * (32 / R) * nchunk;
+    const bool need_vp = d != 0.f;
+    const uint64_t u0 = (uint64_t)blockIdx.x * MARCH_UNITS + threadIdx.x;
+    for (int k = 0; k < MARCH_K; ++k) {
+        const uint64_t u = u0 + (uint64_t)k * MARCH_T;
+        if (u >= units) break;
+        const uint32_t grp = (uint32_t)(u / nchunk), cc = (uint32_t)(u - (uint64_t)grp * nchunk);
+        const uint32_t row0 = grp * R;
+        const uint32_t c2s = row0 % g.d2, c1s = (row0 / g.d2) % g.d1;
+        float4 x[R + 2], a1[R][2], vpr[R];
+        float dg[R];
+        x[0] = (row0 >= 1 && c2s > 0 && g.active[2]) ? ldg_stream(vc + (size_t)(row0 - 1) * nchunk + cc) : vzero(0.f);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            x[r + 1] = row0 + r < n_rows ? ldg_stream(vc + (size_t)(row0 + r) * nchunk + cc) : vzero(0.f);
+        {
+            const uint32_t rl = row0 + R, cl = (c2s + R - 1) % g.d2;
+            x[R + 1] = (rl < n_rows && cl + 1 < g.d2 && g.active[2]) ? ldg_stream(vc + (size_t)rl * nchunk + cc)
+                                                                     : vzero(0.f);
+        }
+        uint32_t c2 = c2s, c1 = c1s;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t i = row0 + r;
+            a1[r][0] = a1[r][1] = vpr[r] = vzero(0.f);
+            dg[r] = 0.f;
+            if (i < n_rows) {
+                if (g.active[1]) {
+                    if (c1 > 0 || g.per[1])
+                        a1[r][0] = ldg_stream(vc + (size_t)(c1 > 0 ? i - s1 : i + (g.d1 - 1) * s1) * nchunk + cc);
+                    if (c1 + 1 < g.d1 || g.per[1])
+                        a1[r][1] = ldg_stream(vc + (size_t)(c1 + 1 < g.d1 ? i + s1 : i - (g.d1 - 1) * s1) * nchunk + cc);
+                }
+                dg[r] = __ldg(diag2 + i);
+                if (need_vp) vpr[r] = ldg_stream(vp + (size_t)i * nchunk + cc);
+            }
+            if (++c2 == g.d2) {
+                c2 = 0;
+                if (++c1 == g.d1) c1 = 0;
+            }
+        }
+        c2 = c2s;
+        c1 = c1s;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t i = row0 + r;
+            float4 out = vzero(0.f);
+            if (i < n_rows) {
+                // per axis (0 + lo) + hi, then dg x + w0 s0 + w1 s1 + w2 s2 as in the per-item kernel
+                float4 s1v = vzero(0.f), s2v = vzero(0.f);
+                if (g.active[1] && (c1 > 0 || g.per[1])) s1v = vadd(s1v, a1[r][0]);
+                if (g.active[1] && (c1 + 1 < g.d1 || g.per[1])) s1v = vadd(s1v, a1[r][1]);
+                if (g.active[2] && (c2 > 0 || g.per[2]))
+                    s2v = vadd(s2v, c2 > 0 ? x[r] : ldg_stream(vc + (size_t)(i + (g.d2 - 1)) * nchunk + cc));
+                if (g.active[2] && (c2 + 1 < g.d2 || g.per[2]))
+                    s2v = vadd(s2v, c2 + 1 < g.d2 ? x[r + 2] : ldg_stream(vc + (size_t)(i - (g.d2 - 1)) * nchunk + cc));
+                float4 acc = vscale(dg[r], x[r + 1]);
+                acc = vfma(0.f, vzero(0.f), acc);
+                acc = vfma(w1, s1v, acc);
+                acc = vfma(w2, s2v, acc);
+                out = vscale(c, acc);
+                if (need_vp) out = vfma(-d, vpr[r], out);
+                vn[(size_t)i * nchunk + cc] = out;
+            }
+            if constexpr (PANEL) panel_store4(po, i >> 5, i & 31, 4 * cc, out);
+            if (++c2 == g.d2) {
+                c2 = 0;
+                if (++c1 == g.d1) c1 = 0;
+            }
+        }
+    }
+}
+
 template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
@@ -326,6 +421,19 @@ static cudaError_t stencil_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, 
                                 T o0, T o1, T o2, T c, T d, uint8_t* panel, cudaStream_t s) {
     const uint32_t nchunk = (uint32_t)(P.ld / Vec16<T>::W);
     const PanelOut po{panel, (uint32_t)P.panel_groups};
+    if constexpr (sizeof(T) == 4) {
+        if (!P.geom.active[0]) {  // 2D / 1D grid: the row-group kernel (5 loads a row instead of 6)
+            const uint64_t units = (uint64_t)((P.n + 31) / 32) * (32 / MARCH_R) * nchunk;
+            const int grid = (int)((units + MARCH_UNITS - 1) / MARCH_UNITS);
+            if (panel)
+                stencil_march_kernel<true><<<grid, MARCH_T, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o1, o2, c,
+                                                                     d, nchunk, (uint32_t)P.n, po);
+            else
+                stencil_march_kernel<false><<<grid, MARCH_T, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o1, o2, c,
+                                                                      d, nchunk, (uint32_t)P.n, po);
+            return cudaGetLastError();
+        }
+    }
     if (panel)
         stencil_step_kernel<T, true><<<panel_grid(P.n), stencil_threads(nchunk), 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o0,
                                                                         o1, o2, c, d, nchunk, (uint32_t)P.n, po);
