@@ -52,11 +52,12 @@ struct ssm_plan_s {
     size_t cap_cs = 0;
     int* d_csrc = nullptr;
     size_t cap_csrc = 0;
-    // mixed path: float pairs (hi, lo) of the moments and of one batch's mu and nu
-    float* d_xpair = nullptr;
-    size_t cap_xpair = 0;
-    float* d_cpair = nullptr;
-    size_t cap_cpair = 0;
+    // batched mixed plans: the tensor-core assembly's moment slices and scales of a chunk
+    uint8_t* d_bxsl = nullptr;
+    size_t cap_bxsl = 0;
+    int* d_bEe = nullptr;
+    unsigned long long* d_bEmx = nullptr;
+    size_t cap_bEe = 0;
     // tensor-core assembly (mixed and SSM_FP64_TC single plans): packed upper-triangle
     // entries (W block first), their scales, the moment slices (once per set of moments)
     // and one batch's coefficient slices and point scales
@@ -302,14 +303,15 @@ void free_plan(ssm_plan_s* h) {
     dev_free(h->d_zetab);
     dev_free(h->d_cs);
     dev_free(h->d_csrc);
+    dev_free(h->d_bxsl);
+    dev_free(h->d_bEe);
+    dev_free(h->d_bEmx);
     dev_free(h->d_pack);
     dev_free(h->d_Ee);
     dev_free(h->d_Emx);
     dev_free(h->d_xsl);
     dev_free(h->d_csl);
     dev_free(h->d_Et);
-    dev_free(h->d_xpair);
-    dev_free(h->d_cpair);
     dev_free(h->d_perm);
     dev_free(h->d_t);
     dev_free(h->d_mu);
@@ -408,31 +410,6 @@ ssm_status coefficients_dev(ssm_plan_s* h, const double* d_tpts, int64_t n, doub
     return SSM_OK;
 }
 
-// Mixed path: the float pairs of all moments of the plan (B (M+1) n_tot^2 values,
-// split once per DOS call) and room for the pairs of one batch's mu and nu.
-ssm_status split_moments(ssm_plan_s* h) {
-    Plan& P = h->P;
-    const size_t nx = (size_t)(P.B > 1 ? P.B : 1) * (P.p.degree + 1) * P.n_tot * P.n_tot;
-    const size_t nc = 4 * h->cap_batch * (P.p.degree + 1);
-    if (2 * nx > h->cap_xpair) {
-        dev_free(h->d_xpair);
-        h->d_xpair = nullptr;
-        h->cap_xpair = 0;
-        CUDA_OR_FAIL(h, dev_alloc(&h->d_xpair, 2 * nx));
-        h->cap_xpair = 2 * nx;
-    }
-    if (nc > h->cap_cpair) {
-        dev_free(h->d_cpair);
-        h->d_cpair = nullptr;
-        h->cap_cpair = 0;
-        CUDA_OR_FAIL(h, dev_alloc(&h->d_cpair, nc));
-        h->cap_cpair = nc;
-    }
-    CUDA_OR_FAIL(h, launch_split_pairs(P.d_X, (int64_t)nx, h->d_xpair, h->d_xpair + nx, P.stream));
-    P.stats.launches++;
-    return SSM_OK;
-}
-
 // K (from mu, K+1 terms) and K_Z (from nu, M+1 terms) of n_t points with
 // coefficient rows at mu/nu (leading dimension M+1) from the moments of matrix b.
 // Single mixed and SSM_FP64_TC plans assemble on the tensor cores (assemble_oz.cu).
@@ -442,26 +419,36 @@ ssm_status split_moments(ssm_plan_s* h) {
 bool asm_on_tc(const Plan& P) { return P.B <= 0 && (P.mixed || P.use_oz); }
 int asm_slices(const Plan& P) { return P.mixed ? 6 : 7; }
 
+// Packed upper triangle of the moments for the tensor-core assembly, the W block
+// (i <= j < n_v) first, so that K_Z's entries are a prefix.
+ssm_status ensure_pack(ssm_plan_s* h) {
+    Plan& P = h->P;
+    if (h->d_pack) return SSM_OK;
+    const int n_tot = P.n_tot, nv = P.p.n_v, ne = n_tot * (n_tot + 1) / 2;
+    std::vector<int> pk;
+    pk.reserve(ne);
+    for (int i = 0; i < nv; ++i)
+        for (int j = i; j < nv; ++j) pk.push_back((i << 16) | j);
+    for (int i = 0; i < n_tot; ++i)
+        for (int j = (i < nv ? nv : i); j < n_tot; ++j) pk.push_back((i << 16) | j);
+    CUDA_OR_FAIL(h, dev_alloc(&h->d_pack, (size_t)ne));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_pack, pk.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice,
+                                    P.stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
+    return SSM_OK;
+}
+
 // Moment slices of the tensor-core assembly, once per set of moments.
 ssm_status prepare_asm_oz(ssm_plan_s* h) {
     Plan& P = h->P;
-    const int M = P.p.degree, n_tot = P.n_tot, nv = P.p.n_v;
+    const int M = P.p.degree, n_tot = P.n_tot;
     const int ne = n_tot * (n_tot + 1) / 2;
-    if (!h->d_pack) {
-        // packed upper triangle, the W block (i <= j < n_v) first
-        std::vector<int> pk;
-        pk.reserve(ne);
-        for (int i = 0; i < nv; ++i)
-            for (int j = i; j < nv; ++j) pk.push_back((i << 16) | j);
-        for (int i = 0; i < n_tot; ++i)
-            for (int j = (i < nv ? nv : i); j < n_tot; ++j) pk.push_back((i << 16) | j);
-        CUDA_OR_FAIL(h, dev_alloc(&h->d_pack, (size_t)ne));
+    if (!h->d_xsl) {
+        ssm_status st = ensure_pack(h);
+        if (st != SSM_OK) return st;
         CUDA_OR_FAIL(h, dev_alloc(&h->d_Ee, (size_t)ne));
         CUDA_OR_FAIL(h, dev_alloc(&h->d_Emx, (size_t)ne));
         CUDA_OR_FAIL(h, dmalloc((void**)&h->d_xsl, asm_oz_xslice_bytes(ne, M + 1, asm_slices(P))));
-        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->d_pack, pk.data(), (size_t)ne * sizeof(int), cudaMemcpyHostToDevice,
-                                        P.stream));
-        CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));
     }
     CUDA_OR_FAIL(h, launch_asm_oz_xslices(P.d_X, n_tot, M + 1, h->d_pack, ne, h->d_Ee, h->d_Emx, h->d_xsl,
                                           asm_slices(P), P.stream));
@@ -510,18 +497,7 @@ ssm_status assemble_pencils(ssm_plan_s* h, const double* mu, const double* nu, i
         P.stats.launches += 2;
         return SSM_OK;
     }
-    const size_t nx = h->cap_xpair / 2, nc = (size_t)n_t * (M + 1);
-    const float* xh = h->d_xpair + b * xs;
-    const float* xl = h->d_xpair + nx + b * xs;
-    float* c = h->d_cpair;
-    CUDA_OR_FAIL(h, launch_split_pairs(mu, (int64_t)nc, c, c + nc, P.stream));
-    CUDA_OR_FAIL(h, launch_split_pairs(nu, (int64_t)nc, c + 2 * nc, c + 3 * nc, P.stream));
-    CUDA_OR_FAIL(h, launch_assemble_pairs(c, c + nc, M + 1, n_t, K + 1, xh, xl, n_tot, n_tot, n_tot, K_out,
-                                          P.stream));
-    CUDA_OR_FAIL(h, launch_assemble_pairs(c + 2 * nc, c + 3 * nc, M + 1, n_t, M + 1, xh, xl, n_tot, nv, nv, KZ_out,
-                                          P.stream));
-    P.stats.launches += 4;
-    return SSM_OK;
+    return fail(h, SSM_EINVAL, "internal: no assembly route for this plan");
 }
 
 // DOS at n device points d_tpts into h->d_dos_ss / h->d_dos_kpm (device), ranks into h->d_rank.
@@ -532,11 +508,6 @@ ssm_status dos_dev(ssm_plan_s* h, const double* d_tpts, int64_t n_t, double sigm
     const double gmax = 1.0 / ((double)P.n * sqrt(2.0 * M_PI * sigma * sigma));
     const double xlo = -P.p.kappa * gmax, xhi = (1.0 + P.p.kappa) * gmax;
     const int64_t bt = batch_points(P);
-    if (want_ss && P.mixed && !asm_on_tc(P)) {
-        Scope sc(h, PH_ASSEMBLE);
-        ssm_status st = split_moments(h);
-        if (st != SSM_OK) return st;
-    }
     for (int64_t t0 = 0; t0 < n_t; t0 += bt) {
         const int64_t nb = (n_t - t0) < bt ? (n_t - t0) : bt;
         ssm_status st = coefficients_dev(h, d_tpts + t0, nb, sigma, h->d_mu, want_ss ? h->d_nu : nullptr, -1,
@@ -628,11 +599,6 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
                                     P.stream));
     CUDA_OR_FAIL(h, cudaStreamSynchronize(P.stream));  // fpt is a host temporary
     const double* d_pp = h->d_fpt + 3 * n_t;
-    if (want_ss && P.mixed) {
-        Scope sc(h, PH_ASSEMBLE);
-        ssm_status st = split_moments(h);
-        if (st != SSM_OK) return st;
-    }
     // Matrices with the same interval and the same sweep points (normalised Laplacians of a
     // batch all have [0, 2]) differ in their coefficients only by the norm 1/(N_b sqrt(2 pi
     // sigma^2)): the tables are then computed once per distinct (interval, points), with
@@ -750,17 +716,51 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
             Scope sc(h, PH_ASSEMBLE);
             const double* muh = P.p.damping ? h->d_muh : h->d_mu;
             if (P.mixed) {
-                const size_t nx = h->cap_xpair / 2, nc = (size_t)nb * (M + 1);
-                const float* xh = h->d_xpair + b0 * xs;
-                const float* xl = h->d_xpair + nx + b0 * xs;
-                float* c = h->d_cpair;
-                CUDA_OR_FAIL(h, launch_split_pairs(muh, (int64_t)nc, c, c + nc, P.stream));
-                CUDA_OR_FAIL(h, launch_split_pairs(h->d_nu, (int64_t)nc, c + 2 * nc, c + 3 * nc, P.stream));
-                CUDA_OR_FAIL(h, launch_assemble_pairs(c, c + nc, M + 1, n_tp, K + 1, xh, xl, n_tot, n_tot, n_tot,
-                                                      h->d_K, P.stream, nbm, (int64_t)xs));
-                CUDA_OR_FAIL(h, launch_assemble_pairs(c + 2 * nc, c + 3 * nc, M + 1, n_tp, M + 1, xh, xl, n_tot, nv,
-                                                      nv, h->d_KZ, P.stream, nbm, (int64_t)xs));
-                P.stats.launches += 4;
+                // the tensor-core assembly of single mixed plans, all matrices of the chunk at
+                // once: each matrix's moment slices and entry scales, point tiles per matrix
+                const int ne = n_tot * (n_tot + 1) / 2, nez = nv * (nv + 1) / 2, ns = 6;
+                ssm_status st = ensure_pack(h);
+                if (st != SSM_OK) return st;
+                const size_t xb = (size_t)nbm * asm_oz_xslice_bytes(ne, M + 1, ns);
+                if (xb > h->cap_bxsl) {
+                    dev_free(h->d_bxsl);
+                    h->d_bxsl = nullptr;
+                    h->cap_bxsl = 0;
+                    CUDA_OR_FAIL(h, dmalloc((void**)&h->d_bxsl, xb));
+                    h->cap_bxsl = xb;
+                }
+                if ((size_t)nbm * ne > h->cap_bEe) {
+                    dev_free(h->d_bEe);
+                    dev_free(h->d_bEmx);
+                    h->d_bEe = nullptr;
+                    h->d_bEmx = nullptr;
+                    h->cap_bEe = 0;
+                    CUDA_OR_FAIL(h, dev_alloc(&h->d_bEe, (size_t)nbm * ne));
+                    CUDA_OR_FAIL(h, dev_alloc(&h->d_bEmx, (size_t)nbm * ne));
+                    h->cap_bEe = (size_t)nbm * ne;
+                }
+                const size_t cb = asm_oz_cslice_bytes(nb, M + 1, ns, n_tp);
+                if (cb > h->cap_csl) {
+                    dev_free(h->d_csl);
+                    h->d_csl = nullptr;
+                    h->cap_csl = 0;
+                    CUDA_OR_FAIL(h, dmalloc((void**)&h->d_csl, cb));
+                    h->cap_csl = cb;
+                }
+                if ((size_t)nb > h->cap_Et) {
+                    dev_free(h->d_Et);
+                    h->d_Et = nullptr;
+                    h->cap_Et = 0;
+                    CUDA_OR_FAIL(h, dev_alloc(&h->d_Et, (size_t)nb));
+                    h->cap_Et = (size_t)nb;
+                }
+                CUDA_OR_FAIL(h, launch_asm_oz_xslices(P.d_X + b0 * xs, n_tot, M + 1, h->d_pack, ne, h->d_bEe,
+                                                      h->d_bEmx, h->d_bxsl, ns, P.stream, nbm, xs));
+                CUDA_OR_FAIL(h, launch_asm_oz(muh, M + 1, nb, K + 1, h->d_bxsl, M + 1, h->d_pack, h->d_bEe, ne, n_tot,
+                                              h->d_K, h->d_csl, h->d_Et, P.d_flag, ns, P.stream, n_tp, ne));
+                CUDA_OR_FAIL(h, launch_asm_oz(h->d_nu, M + 1, nb, M + 1, h->d_bxsl, M + 1, h->d_pack, h->d_bEe, nez,
+                                              nv, h->d_KZ, h->d_csl, h->d_Et, P.d_flag, ns, P.stream, n_tp, ne));
+                P.stats.launches += 9;
             } else {
                 CUDA_OR_FAIL(h, launch_assemble(muh, M + 1, n_tp, K + 1, P.d_X + b0 * xs, n_tot, n_tot, n_tot, h->d_K,
                                                 P.stream, nbm, (int64_t)xs));

@@ -94,10 +94,12 @@ __device__ __forceinline__ int core_off(int k, int m) { return (k >> 3) * 128 + 
 // (grid.y over the chunks of l): atomicMax of the bit pattern, which orders like the
 // value for nonnegative doubles (mx zeroed before).
 constexpr int XL_CHUNK = 32;
-__global__ void xmax_kernel(const double* __restrict__ X, int n_tot, int L, const int* __restrict__ pack, int ne,
-                            unsigned long long* __restrict__ mx) {
+__global__ void xmax_kernel(const double* __restrict__ X, size_t xs, int n_tot, int L, const int* __restrict__ pack,
+                            int ne, unsigned long long* __restrict__ mx) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
+    X += blockIdx.z * xs;  // matrix z of a batch
+    mx += (size_t)blockIdx.z * ne;
     const int p = pack[e], i = p >> 16, j = p & 0xFFFF;
     const size_t nn = (size_t)n_tot * n_tot, off = (size_t)i * n_tot + j;
     const int l0 = blockIdx.y * XL_CHUNK, l1 = l0 + XL_CHUNK < L ? l0 + XL_CHUNK : L;
@@ -113,14 +115,20 @@ __global__ void xexp_kernel(const unsigned long long* __restrict__ mx, int ne, i
     if (e < ne) Ee[e] = exp_of(__longlong_as_double((long long)mx[e]), lim);
 }
 
-// Slices of the moments: unit (stage s, entry tile et, group g, l within the stage):
-// eight entries of one X_l, six 16-byte slice rows.
+// Slices of the moments: unit (matrix b, entry tile et, stage s, group g, l within the
+// stage): eight entries of one X_l, NS 16-byte slice rows.  Matrix b's moments at
+// X + b xs, its scales at Ee + b ne, its slices at out + b xbytes.
 template <int NS>
-__global__ void xslice_kernel(const double* __restrict__ X, int n_tot, int L, const int* __restrict__ pack, int ne,
-                              const int* __restrict__ Ee, int nstage, int64_t units, uint8_t* __restrict__ out) {
+__global__ void xslice_kernel(const double* __restrict__ X, size_t xs, int n_tot, int L, const int* __restrict__ pack,
+                              int ne, const int* __restrict__ Ee, int nstage, int64_t units, int nz, size_t xbytes,
+                              uint8_t* __restrict__ out) {
     constexpr int A_STAGE = a_stage<NS>();
     const size_t nn = (size_t)n_tot * n_tot;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < units * nz;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = w / units, u = w - b * units;
+        const double* Xb = X + b * xs;
+        const int* Eb = Ee + b * ne;
         const int k = (int)(u % KS);
         int64_t r = u / KS;
         const int g = (int)(r % AG);
@@ -136,12 +144,12 @@ __global__ void xslice_kernel(const double* __restrict__ X, int n_tot, int L, co
             int E = 0;
             if (l < L && e < ne) {
                 const int p = __ldg(pack + e);
-                v = __ldg(X + (size_t)l * nn + (size_t)(p >> 16) * n_tot + (p & 0xFFFF));
-                E = __ldg(Ee + e);
+                v = __ldg(Xb + (size_t)l * nn + (size_t)(p >> 16) * n_tot + (p & 0xFFFF));
+                E = __ldg(Eb + e);
             }
             slice_value<NS>(v, E, sl[m]);
         }
-        uint8_t* base = out + ((size_t)et * nstage + s) * A_STAGE + (size_t)g * GB + core_off(k, 0);
+        uint8_t* base = out + b * xbytes + ((size_t)et * nstage + s) * A_STAGE + (size_t)g * GB + core_off(k, 0);
 #pragma unroll
         for (int q = 0; q < NS; ++q)
             *reinterpret_cast<uint4*>(base + (size_t)q * A_SLICE) =
@@ -164,9 +172,12 @@ __global__ void cexp_kernel(const double* __restrict__ coef, int ldc, int64_t n_
 }
 
 // Slices of the coefficients: unit (point tile tt, stage s, group g, l within the stage).
+// Point tiles do not straddle matrices: tile tt = b ttm + q holds points b tpm + q BW ..
+// of matrix b (tpm points a matrix, ttm tiles a matrix).
 template <int NS>
 __global__ void cslice_kernel(const double* __restrict__ coef, int ldc, int64_t n_t, int L,
-                              const int* __restrict__ Et, int nstage, int64_t units, uint8_t* __restrict__ out) {
+                              const int* __restrict__ Et, int nstage, int64_t units, int64_t tpm, int64_t ttm,
+                              uint8_t* __restrict__ out) {
     constexpr int B_STAGE = b_stage<NS>();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(u % KS);
@@ -179,10 +190,10 @@ __global__ void cslice_kernel(const double* __restrict__ coef, int ldc, int64_t 
         float sl[8][NS];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int64_t t = tt * BW + g * 8 + m;
+            const int64_t b = tt / ttm, ql = (tt - b * ttm) * BW + g * 8 + m, t = b * tpm + ql;
             double v = 0.0;
             int E = 0;
-            if (l < L && t < n_t) {
+            if (l < L && ql < tpm && t < n_t) {
                 v = __ldg(coef + t * ldc + l);
                 E = __ldg(Et + t);
             }
@@ -208,7 +219,9 @@ struct AsmArgs {
     double* out;          // point t's matrix at out + t * ostride, entry (i, j) at i * ocols + j
     int* flag;
     int64_t n_t, ostride;
-    int ne, ocols, xstages, nst;
+    int64_t tpm, ttm;     // points and point tiles a matrix (batches: tile x = b ttm + q)
+    size_t xbytes;        // slices of one matrix (batches: matrix b's at xsl + b xbytes)
+    int ne, ne_ld, ocols, xstages, nst;  // ne_ld: scales of matrix b at Ee + b ne_ld
 };
 
 template <int NS>
@@ -221,8 +234,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tt = blockIdx.x, et = blockIdx.y;  // the point tiles of an entry tile run together:
                                                  // its moment slices come from L2 after the first
+    const int64_t mb = tt / P.ttm, q0 = (tt - mb * P.ttm) * BW;  // matrix, first point within it
     const int nst = P.nst, niv = (nst + DRAIN - 1) / DRAIN;
-    const uint8_t* xsrc = P.xsl + (size_t)et * P.xstages * A_STAGE;
+    const uint8_t* xsrc = P.xsl + mb * P.xbytes + (size_t)et * P.xstages * A_STAGE;
     const uint8_t* csrc = P.csl + (size_t)tt * nst * B_STAGE;
 
     constexpr int NGRP = ngrp<NS>();
@@ -342,11 +356,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) assemble_oz_kernel(AsmArgs P) {
         const int e = et * AW + m;
         if (alive && e < P.ne) {
             const int p = P.pack[e], i = p >> 16, j = p & 0xFFFF;
-            const int Ee = P.Ee[e];
+            const int Ee = P.Ee[mb * P.ne_ld + e];
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-                const int64_t t = (int64_t)tt * BW + 32 * half + c;
-                if (t < P.n_t) {
+                const int64_t ql = q0 + 32 * half + c, t = mb * P.tpm + ql;
+                if (ql < P.tpm && t < P.n_t) {
                     const double v = ldexp((double)acc[c] * 0x1p-38 + (double)r5[c], Ee + P.Et[t]);
                     double* o = P.out + t * P.ostride;
                     o[(size_t)i * P.ocols + j] = v;
@@ -374,27 +388,34 @@ size_t asm_oz_xslice_bytes(int ne, int L, int ns) {
     return (size_t)((ne + AW - 1) / AW) * ((L + KS - 1) / KS) * ns * A_SLICE;
 }
 
-size_t asm_oz_cslice_bytes(int64_t n_t, int L, int ns) {
-    return (size_t)((n_t + BW - 1) / BW) * ((L + KS - 1) / KS) * ns * B_SLICE;
+size_t asm_oz_cslice_bytes(int64_t n_t, int L, int ns, int64_t tpm) {
+    const int64_t per = tpm > 0 ? tpm : n_t, nz = tpm > 0 ? (n_t + tpm - 1) / tpm : 1;
+    return (size_t)(nz * ((per + BW - 1) / BW)) * ((L + KS - 1) / KS) * ns * B_SLICE;
 }
 
 cudaError_t launch_asm_oz_xslices(const double* X, int n_tot, int L, const int* pack, int ne, int* Ee,
-                                  unsigned long long* mx, uint8_t* xsl, int ns, cudaStream_t s) {
-    if (ne <= 0 || L <= 0 || n_tot > 0xFFFF || (ns != 6 && ns != 7)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)ne * sizeof(unsigned long long), s);
+                                  unsigned long long* mx, uint8_t* xsl, int ns, cudaStream_t s, int nz, size_t xs) {
+    if (ne <= 0 || L <= 0 || nz <= 0 || nz > 65535 || n_tot > 0xFFFF || (ns != 6 && ns != 7))
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(mx, 0, (size_t)nz * ne * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    xmax_kernel<<<dim3((ne + 255) / 256, (L + XL_CHUNK - 1) / XL_CHUNK), 256, 0, s>>>(X, n_tot, L, pack, ne, mx);
+    xmax_kernel<<<dim3((ne + 255) / 256, (L + XL_CHUNK - 1) / XL_CHUNK, nz), 256, 0, s>>>(X, xs, n_tot, L, pack, ne,
+                                                                                          mx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    xexp_kernel<<<(ne + 255) / 256, 256, 0, s>>>(mx, ne, ns == 6 ? 126 : 1000, Ee);
+    const int64_t nen = (int64_t)nz * ne;
+    xexp_kernel<<<(unsigned)((nen + 255) / 256), 256, 0, s>>>(mx, (int)nen, ns == 6 ? 126 : 1000, Ee);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nstage = (L + KS - 1) / KS;
     const int64_t units = (int64_t)((ne + AW - 1) / AW) * nstage * AG * KS;
+    const size_t xbytes = asm_oz_xslice_bytes(ne, L, ns);
     if (ns == 6)
-        xslice_kernel<6><<<grid_for(units), 256, 0, s>>>(X, n_tot, L, pack, ne, Ee, nstage, units, xsl);
+        xslice_kernel<6><<<grid_for(units * nz), 256, 0, s>>>(X, xs, n_tot, L, pack, ne, Ee, nstage, units, nz, xbytes,
+                                                                xsl);
     else
-        xslice_kernel<7><<<grid_for(units), 256, 0, s>>>(X, n_tot, L, pack, ne, Ee, nstage, units, xsl);
+        xslice_kernel<7><<<grid_for(units * nz), 256, 0, s>>>(X, xs, n_tot, L, pack, ne, Ee, nstage, units, nz, xbytes,
+                                                                xsl);
     return cudaGetLastError();
 }
 
@@ -402,14 +423,15 @@ namespace {
 
 template <int NS>
 cudaError_t asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
-                   const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag, cudaStream_t s) {
+                   const int* Ee, int ne, int ne_ld, int ocols, double* out, uint8_t* csl, int* Et, int* flag,
+                   int64_t tpm, cudaStream_t s) {
     cexp_kernel<<<(unsigned)((n_t * 32 + 255) / 256), 256, 0, s>>>(coef, ldc, n_t, L, NS == 6 ? 126 : 1000, Et);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nst = (L + KS - 1) / KS;
-    const int64_t tts = (n_t + BW - 1) / BW;
+    const int64_t ttm = (tpm + BW - 1) / BW, tts = ((n_t + tpm - 1) / tpm) * ttm;
     const int64_t units = tts * nst * BG * KS;
-    cslice_kernel<NS><<<grid_for(units), 256, 0, s>>>(coef, ldc, n_t, L, Et, nst, units, csl);
+    cslice_kernel<NS><<<grid_for(units), 256, 0, s>>>(coef, ldc, n_t, L, Et, nst, units, tpm, ttm, csl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)SST * (a_stage<NS>() + b_stage<NS>());
@@ -431,7 +453,11 @@ cudaError_t asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_
     a.flag = flag;
     a.n_t = n_t;
     a.ostride = (int64_t)ocols * ocols;
+    a.tpm = tpm;
+    a.ttm = ttm;
+    a.xbytes = asm_oz_xslice_bytes(ne_ld, xL, NS);
     a.ne = ne;
+    a.ne_ld = ne_ld;
     a.ocols = ocols;
     a.xstages = (xL + KS - 1) / KS;
     a.nst = nst;
@@ -444,11 +470,13 @@ cudaError_t asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_
 
 cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
                           const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag, int ns,
-                          cudaStream_t s) {
+                          cudaStream_t s, int64_t tpm, int ne_ld) {
     if (n_t <= 0 || ne <= 0) return cudaSuccess;
-    if (L <= 0 || L > xL || (ns != 6 && ns != 7)) return cudaErrorInvalidValue;
-    return ns == 6 ? asm_oz<6>(coef, ldc, n_t, L, xsl, xL, pack, Ee, ne, ocols, out, csl, Et, flag, s)
-                   : asm_oz<7>(coef, ldc, n_t, L, xsl, xL, pack, Ee, ne, ocols, out, csl, Et, flag, s);
+    if (tpm <= 0) tpm = n_t;
+    if (ne_ld <= 0) ne_ld = ne;
+    if (L <= 0 || L > xL || ne > ne_ld || (ns != 6 && ns != 7)) return cudaErrorInvalidValue;
+    return ns == 6 ? asm_oz<6>(coef, ldc, n_t, L, xsl, xL, pack, Ee, ne, ne_ld, ocols, out, csl, Et, flag, tpm, s)
+                   : asm_oz<7>(coef, ldc, n_t, L, xsl, xL, pack, Ee, ne, ne_ld, ocols, out, csl, Et, flag, tpm, s);
 }
 
 }  // namespace ssm

@@ -311,17 +311,12 @@ cudaError_t launch_expand_coeffs(const double* cmu, const double* cmuh, const do
 cudaError_t launch_kpm_batched(const double* mu, int ldmu, int64_t n_tp, int nz, int M, const double* X, size_t xs,
                                int n_tot, double* zeta, double* out, cudaStream_t s);
 
-// Assembly: out[t][i*cols+j] = sum_{l<L} coef[t][l] X[l][i][j] (assemble.cu) in float64;
-// the mixed path's variant takes coef and X as float pairs (launch_split_pairs) and sums
-// in float-pair arithmetic.
+// Assembly: out[t][i*cols+j] = sum_{l<L} coef[t][l] X[l][i][j] (assemble.cu) in float64
+// on the CUDA cores (float64 plans; mixed and SSM_FP64_TC plans use assemble_oz.cu).
 // nz > 1: nz matrices of a batched plan at once, n_t points each (coefficient rows and
 // outputs consecutive across matrices), their moments zx values apart.
 cudaError_t launch_assemble(const double* coef, int ldc, int64_t n_t, int L, const double* X,
                             int n_tot, int rows, int cols, double* out, cudaStream_t s, int nz = 1, int64_t zx = 0);
-cudaError_t launch_assemble_pairs(const float* coef_hi, const float* coef_lo, int ldc, int64_t n_t, int L,
-                                  const float* X_hi, const float* X_lo, int n_tot, int rows, int cols, double* out,
-                                  cudaStream_t s, int nz = 1, int64_t zx = 0);
-cudaError_t launch_split_pairs(const double* v, int64_t n, float* hi, float* lo, cudaStream_t s);
 
 // SS-DGC with explicit filtered blocks (ssdgc.cu, Alg. 5): Z_i += sum_{j<nj} mu[i][l0+j] V[j]
 // for the n_c blocks Z_i of n_elem doubles each (n_elem even, nj <= 8; mu rows ldmu apart),
@@ -335,16 +330,18 @@ cudaError_t launch_sym_pack(const double* G, int n, double* out, cudaStream_t s)
 // from bf16 slices of the moments (xsl, formed for xL values of l by
 // launch_asm_oz_xslices with the entry scales Ee) and of the coefficients (formed into
 // csl, asm_oz_cslice_bytes, with the point scales Et, n_t ints; mx: ne scratch words).
-// Status bit 2 of *flag
-// on a timed-out wait.
+// Batches of nz matrices: the slices of matrix b from X + b xs (asm_oz_xslice_bytes apart,
+// scales b ne_ld apart, mx nz ne words), and points b tpm .. (b+1) tpm - 1 belong to
+// matrix b (tpm = 0: one matrix).  Status bit 2 of *flag on a timed-out wait.
 // ns = 6 or 7 slices per value (both operands).
 size_t asm_oz_xslice_bytes(int ne, int L, int ns);
-size_t asm_oz_cslice_bytes(int64_t n_t, int L, int ns);
+size_t asm_oz_cslice_bytes(int64_t n_t, int L, int ns, int64_t tpm = 0);
 cudaError_t launch_asm_oz_xslices(const double* X, int n_tot, int L, const int* pack, int ne, int* Ee,
-                                  unsigned long long* mx, uint8_t* xsl, int ns, cudaStream_t s);
+                                  unsigned long long* mx, uint8_t* xsl, int ns, cudaStream_t s, int nz = 1,
+                                  size_t xs = 0);
 cudaError_t launch_asm_oz(const double* coef, int ldc, int64_t n_t, int L, const uint8_t* xsl, int xL, const int* pack,
                           const int* Ee, int ne, int ocols, double* out, uint8_t* csl, int* Et, int* flag, int ns,
-                          cudaStream_t s);
+                          cudaStream_t s, int64_t tpm = 0, int ne_ld = 0);
 
 // Per-point Alg. 4 + Alg. 6 solve (solve.cu).
 size_t solve_workspace_bytes(int n_v);
