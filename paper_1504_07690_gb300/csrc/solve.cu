@@ -1758,7 +1758,7 @@ solve_kernel(const double* __restrict__ Kfull, const double* __restrict__ KZ, in
 // Threads per CTA: one per row of the per-point matrices up to 256 (smaller
 // problems, e.g. n_v = 64 in batched plans, get small CTAs and more of them
 // per SM).
-int solve_threads(int n_v) { return n_v <= 64 ? 64 : (n_v <= 128 ? 128 : NT); }
+int solve_threads(int n_v) { return n_v <= 128 ? 128 : NT; }
 
 // CTAs with a private workspace: 4 x (256 / threads) per SM to overlap the
 // serial QL chains, fewer when 4 n^2 doubles per CTA would exceed 2 GiB in total.
