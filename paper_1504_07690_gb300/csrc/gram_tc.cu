@@ -44,9 +44,7 @@ using namespace tc;
 
 constexpr int KC = 32;                 // rows per panel (K of one pipeline stage)
 constexpr int KG = KC / 8;             // 8-row core groups per panel
-constexpr int STAGES_E = 4;            // one-source stages (33 KB each)
-constexpr int STAGES_O = 2;            // two-source stages (66 KB each)
-constexpr int STAGES = 6;              // barrier slots
+constexpr int STAGES = 16;             // barrier slots (most stages in flight)
 constexpr int NTHREADS = 128;
 // A column group of a panel is 4 core matrices (512 B) plus a 16-byte pad:
 // with a 528-byte group stride the M/N groups of an MMA operand start on
@@ -55,8 +53,10 @@ constexpr int GROUP_BYTES = KG * 128 + 16;
 constexpr int PART_BYTES = 32 * GROUP_BYTES;  // one part of one stage: 32 column groups
 constexpr int TMEM_COLS = 512;
 // > half of an SM (one Gram CTA per SM, it owns all 512 TMEM columns) and small enough
-// that two recurrence CTAs (34 KB each) share the SM with it
-constexpr int SMEM_BYTES = STAGES_E * 2 * PART_BYTES + 1024;
+// that two recurrence CTAs (34 KB each) share the SM with it: four one-source stages of
+// 32 column groups.  Stages hold the panels' G groups only, so narrow blocks get more
+// of them in flight (n_tot = 64: 15 one-source or 7 two-source stages).
+constexpr int SMEM_BYTES = 4 * 2 * PART_BYTES + 1024;
 
 struct TcArgs {
     const uint8_t* PX;  // panels of V_{k+1}
@@ -91,14 +91,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     if (p1 > P.n_panels) p1 = P.n_panels;
     const int nch = p1 > p0 ? (int)(p1 - p0) : 0;
     const int nsrc = cross ? 2 : 1;
-    const int nstage = cross ? STAGES_O : STAGES_E;
     const int n_tot = P.n_tot, G = P.G;
     const int ntp = G * 8;
-    const uint32_t stage_bytes = (uint32_t)nsrc * 2 * PART_BYTES;
+    // a stage: nsrc sources x (hi, lo) parts of G groups; an M = 128 operand of the last
+    // part reads up to 16 (G <= 16) or 32 groups from its start, so that much room
+    // follows the ring (rows >= n_tot of the accumulator, never stored)
+    const uint32_t part_bytes = (uint32_t)G * GROUP_BYTES;
+    const uint32_t stage_bytes = (uint32_t)nsrc * 2 * part_bytes;
+    const uint32_t over = (uint32_t)((G <= 16 ? 16 : 32) - G) * GROUP_BYTES;
+    int nstage = (int)((SMEM_BYTES - over) / stage_bytes);
+    if (nstage > STAGES) nstage = STAGES;
+    if (nstage < 1) nstage = 1;
     float* out = cross ? P.part_o + (size_t)slab * n_tot * n_tot : P.part_e + (size_t)slab * n_tot * n_tot;
 
-    // zero the stages once: column groups >= G are never copied and must read as 0
-    for (uint32_t t = tid; t < (uint32_t)nstage * stage_bytes / 16; t += NTHREADS)
+    // zero the ring once, so that what an operand reads past the copied groups is 0
+    for (uint32_t t = tid; t < (uint32_t)SMEM_BYTES / 16; t += NTHREADS)
         reinterpret_cast<uint4*>(smem)[t] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 0) {
@@ -147,8 +154,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
                 const int64_t pnl = p0 + c;
                 for (int src = 0; src < nsrc; ++src) {
                     const uint8_t* base = (src == 0 ? P.PX : P.PY) + (size_t)pnl * 2 * G * GROUP_BYTES;
-                    bulk_copy(dst + (2 * src) * PART_BYTES, base, copy, &full[s]);
-                    bulk_copy(dst + (2 * src + 1) * PART_BYTES, base + (size_t)G * GROUP_BYTES, copy, &full[s]);
+                    bulk_copy(dst + (2 * src) * part_bytes, base, copy, &full[s]);
+                    bulk_copy(dst + (2 * src + 1) * part_bytes, base + (size_t)G * GROUP_BYTES, copy, &full[s]);
                 }
             }
         }
@@ -164,9 +171,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t xhi = smem_u32(smem + s * stage_bytes), xlo = xhi + PART_BYTES;
-                const uint32_t yhi = cross ? xhi + 2 * PART_BYTES : xhi;
-                const uint32_t ylo = cross ? xhi + 3 * PART_BYTES : xlo;
+                const uint32_t xhi = smem_u32(smem + s * stage_bytes), xlo = xhi + part_bytes;
+                const uint32_t yhi = cross ? xhi + 2 * part_bytes : xhi;
+                const uint32_t ylo = cross ? xhi + 3 * part_bytes : xlo;
                 for (int t = 0; t < nt; ++t) {
                     const uint32_t idesc = instr_desc(t_n[t]);
                     const uint32_t dt = tmem + (uint32_t)t_dc[t];
