@@ -789,6 +789,9 @@ ssm_status dos_dev_batched(ssm_plan_s* h, const double* d_tpts, int64_t n_t, dou
     return SSM_OK;
 }
 
+// Batched plans with n_tot <= 128: one Gram CTA forms both products of its slab.
+bool gram_both(const Plan& P) { return P.n_tot <= 128; }
+
 // Batched plans: the whole recurrence with its Gram products and reductions
 // (a3, a4 for every matrix) is one CUDA graph, captured on the first call and
 // replayed: one launch per ssm_moments, whatever the number of matrices.
@@ -807,7 +810,7 @@ cudaError_t record_batched_moments(Plan& P, cudaStream_t cs, cudaStream_t cs2) {
     auto gram_reduce = [&](const void* Vn, const void* Vc, int j, int step) -> cudaError_t {
         if (P.use_tc) {
             cudaError_t r = launch_gram_tc(P.d_panel[j % 3], Vc ? P.d_panel[(j + 2) % 3] : nullptr, P.n_tot, P.n,
-                                           P.tc_ne, P.tc_no, P.d_part_tc, P.d_flag, cs2, P.d_slabs);
+                                           P.tc_ne, P.tc_no, P.d_part_tc, P.d_flag, cs2, P.d_slabs, gram_both(P));
             if (r != cudaSuccess) return r;
             return launch_reduce_tc_seg(P.d_part_tc, P.tc_ne, P.n_tot, B, P.d_slabseg, P.d_ring_sum,
                                         P.d_ring_sum + (size_t)B * nn, P.d_X, xs, step, cs2);
@@ -884,7 +887,9 @@ cudaError_t install_slabs(Plan& P, int div) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tot_pan = P.h_row_off[P.B] / 32;
     const int64_t pe = (tot_pan + (int64_t)sms * div - 1) / ((int64_t)sms * div);
-    const int64_t po = (tot_pan + 2LL * sms * div - 1) / (2LL * sms * div);
+    // Go slabs: half as long (their CTAs read two blocks), or the Ge slabs again when
+    // one CTA forms both products
+    const int64_t po = gram_both(P) ? pe : (tot_pan + 2LL * sms * div - 1) / (2LL * sms * div);
     std::vector<int2> slabs;
     std::vector<int> seg;
     int ne = 0;
@@ -944,7 +949,7 @@ cudaError_t autotune_gram(Plan& P) {
             if (err == cudaSuccess) err = cudaStreamWaitEvent(s2, ef, 0);
             if (err == cudaSuccess)
                 err = launch_gram_tc(P.d_panel[1], P.d_panel[0], P.n_tot, P.n, P.tc_ne, P.tc_no, P.d_part_tc,
-                                     P.d_flag, s2, P.d_slabs);
+                                     P.d_flag, s2, P.d_slabs, gram_both(P));
             if (err == cudaSuccess)
                 err = launch_reduce_tc_seg(P.d_part_tc, P.tc_ne, P.n_tot, P.B, P.d_slabseg, P.d_ring_sum,
                                            P.d_ring_sum + (size_t)P.B * nn, P.d_X, xs, 0, s2);

@@ -15,7 +15,8 @@
 // no-swizzle shared-memory operand layout of tcgen05 (K stride 128 B, MN
 // stride 528 B).  This kernel
 // therefore does no conversion: one thread streams panels into a shared-
-// memory ring (4 stages of 33 KB for Ge, 2 of 66 KB for Go) with 1-D bulk TMA copies (cp.async.bulk, completion
+// memory ring (stages of the panels' column groups, as many as fit in 133 KB) with
+// 1-D bulk TMA copies (cp.async.bulk, completion
 // counted in bytes on an mbarrier), one thread issues M=128
 // tcgen05.mma.kind::f16 into TMEM and releases each stage through
 // tcgen05.commit (waiting threads are suspended on the mbarriers, not polling),
@@ -25,6 +26,9 @@
 //
 // Work split: a CTA owns one slab of panels and one of the two products
 // ("Ge" or "Go"); Go CTAs read two blocks, so their slabs are half as long.
+// With a slab table and n_tot <= 128 a CTA may instead form both products of its
+// slab ("both": Ge in TMEM columns 0.., Go next to it), reading every panel of
+// V_{k+1} once instead of twice.
 //
 // TMEM: Ge uses ntp (+ ntp-128) columns, Go ntp (+ ntp) columns, ntp = n_tot
 // rounded up to 16, n_tot <= 256; a CTA allocates all 512 columns and its
@@ -70,6 +74,7 @@ struct TcArgs {
     float* part_o;      // [n_o][n_tot][n_tot]
     int* flag;
     const int2* slabs;  // NULL: uniform slabs; else panel range [x, y) of every CTA
+    int both;           // every CTA forms Ge and Go of its slab (n_tot <= 128, PY given)
 };
 
 __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
@@ -78,9 +83,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     __shared__ uint32_t tmem_slot;
     __shared__ int fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool cross = (int)blockIdx.x >= P.n_e;
-    const int slab = cross ? (int)blockIdx.x - P.n_e : (int)blockIdx.x;
-    const int64_t pan = cross ? P.pan_o : P.pan_e;
+    const bool both = P.both != 0;
+    const bool cross = both || (int)blockIdx.x >= P.n_e;  // reads V_k's panels too
+    const int slab = (cross && !both) ? (int)blockIdx.x - P.n_e : (int)blockIdx.x;
+    const int64_t pan = (cross && !both) ? P.pan_o : P.pan_e;
     int64_t p0 = (int64_t)slab * pan;
     int64_t p1 = p0 + pan;
     if (P.slabs) {
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     int nstage = (int)((SMEM_BYTES - over) / stage_bytes);
     if (nstage > STAGES) nstage = STAGES;
     if (nstage < 1) nstage = 1;
-    float* out = cross ? P.part_o + (size_t)slab * n_tot * n_tot : P.part_e + (size_t)slab * n_tot * n_tot;
+    float* out = (cross && !both) ? P.part_o + (size_t)slab * n_tot * n_tot : P.part_e + (size_t)slab * n_tot * n_tot;
 
     // zero the ring once, so that what an operand reads past the copied groups is 0
     for (uint32_t t = tid; t < (uint32_t)SMEM_BYTES / 16; t += NTHREADS)
@@ -129,7 +135,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
     int nt = 1;
     int t_ag[2] = {0, 16}, t_bg[2] = {0, 0}, t_n[2] = {ntp, 0}, t_dc[2] = {0, ntp}, t_m0[2] = {0, 128},
         t_n0[2] = {0, 0};
-    if (ntp > 128) {
+    bool t_y[2] = {cross, cross};  // B operand from V_k's panels
+    float* t_out[2] = {out, out};
+    if (both) {  // ntp <= 128: tile 0 = Ge, tile 1 = Go in the next ntp columns
+        nt = 2;
+        t_y[0] = false;
+        t_ag[1] = 0;
+        t_n[1] = ntp;
+        t_m0[1] = 0;
+        t_out[1] = P.part_o + (size_t)slab * n_tot * n_tot;
+    } else if (ntp > 128) {
         nt = 2;
         if (!cross) {  // upper blocks only
             t_bg[1] = 16;
@@ -172,9 +187,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t xhi = smem_u32(smem + s * stage_bytes), xlo = xhi + part_bytes;
-                const uint32_t yhi = cross ? xhi + 2 * part_bytes : xhi;
-                const uint32_t ylo = cross ? xhi + 3 * part_bytes : xlo;
                 for (int t = 0; t < nt; ++t) {
+                    const uint32_t yhi = t_y[t] ? xhi + 2 * part_bytes : xhi;
+                    const uint32_t ylo = t_y[t] ? xhi + 3 * part_bytes : xlo;
                     const uint32_t idesc = instr_desc(t_n[t]);
                     const uint32_t dt = tmem + (uint32_t)t_dc[t];
 #pragma unroll
@@ -227,7 +242,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) gram_tc_kernel(TcArgs P) {
                 const int col = t_n0[t] + cc + lane;
                 for (int rr = 0; rr < 32; ++rr) {
                     const int m = mrow0 + rr;
-                    if (m < n_tot && lane < w && col < n_tot) out[(size_t)m * n_tot + col] = tbuf[rr * 33 + lane];
+                    if (m < n_tot && lane < w && col < n_tot) t_out[t][(size_t)m * n_tot + col] = tbuf[rr * 33 + lane];
                 }
                 __syncwarp();
             }
@@ -511,7 +526,8 @@ void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o) {
 size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot) { return (size_t)(n_e + n_o) * n_tot * n_tot; }
 
 cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int64_t n_rows, int n_e, int n_o,
-                           float* part, int* flag, cudaStream_t s, const int2* slabs) {
+                           float* part, int* flag, cudaStream_t s, const int2* slabs, bool both) {
+    if (both && (!slabs || n_o != n_e || n_tot > 128)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     TcArgs a;
@@ -528,7 +544,8 @@ cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int6
     a.part_o = part + (size_t)n_e * n_tot * n_tot;
     a.flag = flag;
     a.slabs = slabs;
-    gram_tc_kernel<<<a.n_e + a.n_o, NTHREADS, SMEM_BYTES, s>>>(a);
+    a.both = both && PY;
+    gram_tc_kernel<<<a.both ? a.n_e : a.n_e + a.n_o, NTHREADS, SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -247,8 +247,10 @@ void gram_tc_slabs(int64_t n_rows, int* n_e, int* n_o);
 size_t gram_tc_partial_floats(int n_e, int n_o, int n_tot);
 size_t gram_tc_partial_floats_total(int n_e, int n_o, int n_tot);  // + room for the float64 sums
 int gram_tc_groups(int n_tot);  // 8-column groups of a panel (n_tot rounded up to 16)
+// both: with a slab table whose Go slabs repeat its Ge slabs (n_o = n_e) and n_tot <= 128,
+// one CTA per slab forms both products (V_{k+1}'s panels read once).
 cudaError_t launch_gram_tc(const uint8_t* PX, const uint8_t* PY, int n_tot, int64_t n_rows, int n_e, int n_o,
-                           float* part, int* flag, cudaStream_t s, const int2* slabs = nullptr);
+                           float* part, int* flag, cudaStream_t s, const int2* slabs = nullptr, bool both = false);
 // Batched plans: per-matrix slab sums (matrix b owns Ge slabs [se[b], se[b+1]) and Go
 // slabs [so[b], so[b+1]); seg = se (B+1) followed by so (B+1)) and the moments of step
 // `step` (-1: X_0) into X + b * xstride.
