@@ -245,9 +245,10 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
 // rows row0-1 .. row0+R once; they are also the axis-2 neighbours of the group's rows
 // wherever those are the adjacent rows (a wrapped neighbour is loaded where it is used).
 // Against one (row, chunk) item a thread this issues 5 instead of 6 loads a row on a 2D
-// grid, all of a group's loads before the first use.  Same operations in the same order
-// as stencil_step_kernel, so the outputs are the same bits.  Each CTA takes
-// MARCH_UNITS consecutive (row group, chunk) units, K a thread.
+// grid, all of a group's loads before the first use.  The operations of
+// stencil_step_kernel on the same grid, the inactive axis first, so the outputs are the
+// same values (a zero may change sign).  Each CTA takes MARCH_UNITS consecutive (row
+// group, chunk) units, K a thread.
 constexpr int MARCH_R = 2, MARCH_K = 4, MARCH_T = 256;
 constexpr uint32_t MARCH_UNITS = (uint32_t)MARCH_T * MARCH_K;
 
@@ -422,14 +423,33 @@ static cudaError_t stencil_step(const Plan& P, const T* Vc, const T* Vp, T* Vn, 
     const uint32_t nchunk = (uint32_t)(P.ld / Vec16<T>::W);
     const PanelOut po{panel, (uint32_t)P.panel_groups};
     if constexpr (sizeof(T) == 4) {
-        if (!P.geom.active[0]) {  // 2D / 1D grid: the row-group kernel (5 loads a row instead of 6)
+        // Trailing axes of extent 1 (always inactive) change no row index: (d0, d1, 1) is
+        // the grid (1, d0, d1).  With axis 0 then inactive (2D and 1D grids) the row-group
+        // kernel runs, marching along the unit-stride axis (5 loads a row instead of 6).
+        StencilGeom gn = P.geom;
+        float w[3] = {o0, o1, o2};
+        for (int sh = 0; sh < 2 && gn.d2 == 1; ++sh) {
+            gn.d2 = gn.d1;
+            gn.d1 = gn.d0;
+            gn.d0 = 1;
+            gn.per[2] = gn.per[1];
+            gn.per[1] = gn.per[0];
+            gn.per[0] = 0;
+            gn.active[2] = gn.active[1];
+            gn.active[1] = gn.active[0];
+            gn.active[0] = 0;
+            w[2] = w[1];
+            w[1] = w[0];
+            w[0] = 0.f;
+        }
+        if (!gn.active[0]) {
             const uint64_t units = (uint64_t)((P.n + 31) / 32) * (32 / MARCH_R) * nchunk;
             const int grid = (int)((units + MARCH_UNITS - 1) / MARCH_UNITS);
             if (panel)
-                stencil_march_kernel<true><<<grid, MARCH_T, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o1, o2, c,
-                                                                     d, nchunk, (uint32_t)P.n, po);
+                stencil_march_kernel<true><<<grid, MARCH_T, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, gn, w[1], w[2], c, d,
+                                                                     nchunk, (uint32_t)P.n, po);
             else
-                stencil_march_kernel<false><<<grid, MARCH_T, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, P.geom, o1, o2, c,
+                stencil_march_kernel<false><<<grid, MARCH_T, 0, s>>>(Vc, Vp ? Vp : Vc, Vn, diag2, gn, w[1], w[2], c,
                                                                       d, nchunk, (uint32_t)P.n, po);
             return cudaGetLastError();
         }
