@@ -190,11 +190,22 @@ def solve_flops(ranks, n: int) -> float:
     return tot
 
 
+def stencil_kernel_name(st, mixed: bool) -> str:
+    """The float32 step of a grid whose axes other than the last two have extent 1 (after
+    dropping trailing axes of extent 1) is the row-group kernel; every other step the
+    per-item kernel."""
+    d = list(st.dims)
+    while len(d) > 1 and d[-1] == 1:
+        d.pop()
+    return "stencil_march_kernel" if mixed and all(x == 1 for x in d[:-2]) else "stencil_step_kernel"
+
+
 def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=None):
     """Per-kernel algorithmic work / measured launch time against its bound.
 
     Algorithmic work per launch:
-      stencil_step_kernel  bytes = (3 N n_tot + N) e   (read V_k, V_{k-1}, diag; write V_{k+1})
+      stencil_step_kernel  bytes = (3 N n_tot + N) e   (read V_k, V_{k-1}, diag; write V_{k+1}); on 2D
+                           grids in float32 the row-group stencil_march_kernel, same bytes
       gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
       gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
       assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step
@@ -232,8 +243,9 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
         r["frac"] = r["achieved"] / r["peak"]
         return out + [r]
     rec_bytes = (3.0 * N * n_tot + N) * e
-    out.append(dict(kernel="stencil_step_kernel", bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9,
-                    peak=hbm, unit="GB/s", traffic=_traffic("stencil_step_kernel"), work_per_launch=rec_bytes,
+    sk = stencil_kernel_name(st, mixed)
+    out.append(dict(kernel=sk, bound="hbm", achieved=rec_bytes / (rec_ms * 1e-3) / 1e9,
+                    peak=hbm, unit="GB/s", traffic=_traffic(sk), work_per_launch=rec_bytes,
                     launch_ms=rec_ms, ms_per_step=stats["ms_recurrence"] / steps,
                     peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"))
     gl = max(1, stats["gram_launches"])
