@@ -549,6 +549,9 @@ def run_gpu(args, c, st, W, csr):
 
         step_host()
         torch.cuda.synchronize()
+        # the same per-phase CUDA events as in the device-timed region, so that the two
+        # numbers differ by the copies and the host clock only
+        S.ssm_timing_enable(plan, True)
         if dist is not None:
             dist.barrier()
         h0 = time.perf_counter()
@@ -556,6 +559,7 @@ def run_gpu(args, c, st, W, csr):
             step_host()
         torch.cuda.synchronize()
         hs = (time.perf_counter() - h0) / args.steps
+        S.ssm_timing_enable(plan, False)
         if dist is not None:
             tt = torch.tensor([hs], device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
