@@ -330,6 +330,36 @@ def test_mixed_tensor_core_moments(S, nv, nvh, nx):
     assert np.array_equal(Xtc, np.transpose(Xtc, (0, 2, 1)))
 
 
+# ------------------------------------------------------------------ row-group stencil step
+
+MARCH_SHAPES = [
+    # (dims, periodic, offdiag): float32 grids whose axis 0 is inactive once trailing
+    # extent-1 axes are dropped run the row-group kernel.  Lines of 3 and 2 rows (a row pair
+    # straddles lines, wrapped neighbours), a 1D ring, a 1D chain given as (n, 1, 1), an
+    # open axis next to a periodic one, a ragged last panel
+    ((5, 3, 1), (True, True, False), (-1.0, -0.7, 0.0)),
+    ((1, 4, 2), (False, True, True), (0.0, -1.0, -0.5)),
+    ((1, 1, 10), (False, False, True), (0.0, 0.0, -1.0)),
+    ((9, 1, 1), (False, False, False), (-1.0, 0.0, 0.0)),
+    ((1, 33, 7), (False, False, True), (0.0, -1.0, -1.3)),
+    ((17, 6, 1), (True, False, False), (-0.9, -1.1, 0.0)),
+]
+
+
+@pytest.mark.parametrize("dims,per,off", MARCH_SHAPES, ids=[f"{d[0]}x{d[1]}x{d[2]}" for d, _, _ in MARCH_SHAPES])
+def test_row_group_stencil_geometries(S, dims, per, off):
+    n = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(n + 5)
+    st = wl.Stencil(dims=dims, periodic=per, diag=rng.uniform(-2, 2, n), offdiag=off)
+    nv, M = 13, 40
+    W = wl.random_block(n, nv, 31 + n, "gaussian")
+    plan = S.ssm_plan_create(stencil=st, n_v=nv, degree=M, precision="mixed")
+    X = S.ssm_moments(plan, torch.from_numpy(W).cuda(), return_moments=True).cpu().numpy()
+    info = S.ssm_plan_info(plan)
+    X64 = O.moments_direct(O.transform(_csr_A(st), info["a"], info["b"]), W, M)
+    assert np.max(np.abs(X - X64)) <= 2e-5 * np.max(np.abs(X64))
+
+
 # ------------------------------------------------------------------ fused recurrence + Gram step
 
 FUSED_SHAPES = [
