@@ -56,6 +56,23 @@ def _dist():
     return ws, rank, local
 
 
+def over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest of every rank's x (its time per step): the job's time is its slowest
+    replica's.  dist: torch.distributed with an initialised process group, or None."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(units_per_replica: float, ws: int, seconds_per_step: float) -> float:
+    """Throughput of the whole job: every replica processes the same units (weak scaling)."""
+    return units_per_replica * ws / seconds_per_step
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -514,14 +531,10 @@ def run_gpu(args, c, st, W, csr):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     S.ssm_timing_enable(plan, False)
     stats = S.ssm_stats_get(plan)
-    value = units * ws / (ms * 1e-3)
+    value = whole_job_value(units, ws, ms * 1e-3)
 
     # rooflines of the main kernels; "roofline" is the dominant one of the timed region
     hbm, bf16, bf16s, peak_kind = _peaks()
@@ -560,11 +573,8 @@ def run_gpu(args, c, st, W, csr):
         torch.cuda.synchronize()
         hs = (time.perf_counter() - h0) / args.steps
         S.ssm_timing_enable(plan, False)
-        if dist is not None:
-            tt = torch.tensor([hs], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            hs = float(tt.item())
-        e2e = {"value": units * ws / hs, "unit": "matrix-applies/s (nnz*n_tot*M/s)",
+        hs = over_ranks(hs, dist, dev)
+        e2e = {"value": whole_job_value(units, ws, hs), "unit": "matrix-applies/s (nnz*n_tot*M/s)",
                "h2d_bytes_per_step": int(W.nbytes + t.nbytes), "d2h_bytes_per_step": int(2 * t.nbytes)}
 
     cpu = None
