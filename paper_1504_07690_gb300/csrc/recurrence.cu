@@ -248,8 +248,11 @@ stencil_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __res
 // grid, all of a group's loads before the first use.  The operations of
 // stencil_step_kernel on the same grid, the inactive axis first, so the outputs are the
 // same values (a zero may change sign).  Each CTA takes MARCH_UNITS consecutive (row
-// group, chunk) units, K a thread.
-constexpr int MARCH_R = 2, MARCH_K = 4, MARCH_T = 256;
+// group, chunk) units, K a thread.  One unit a thread: next to the Gram kernel on the
+// other stream, short CTAs let the two interleave on the SMs (the mixed step on a 256^2
+// grid: 62.0 ms against 62.8 with two units a thread, 65.2 with four, 69.2 with eight;
+// four rows a thread 63.5, eight 74.1).
+constexpr int MARCH_R = 2, MARCH_K = 1, MARCH_T = 256;
 constexpr uint32_t MARCH_UNITS = (uint32_t)MARCH_T * MARCH_K;
 
 template <bool PANEL>
