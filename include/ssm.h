@@ -191,9 +191,11 @@ ssm_status ssm_batch_info(ssm_plan_t plan, int32_t b, double* a, double* bb, dou
 /* What the autotuner of a batched plan picked at its first ssm_moments: the CTA
  * size of the CSR recurrence step (64, 128 or 256 threads) and the number of
  * row slabs of the tensor-core Gram products (slabs of 1, 1/2 or 1/4 of the
- * default size, the fastest Gram + reduction); 0 before the first ssm_moments
- * (and gram_slabs 0 on plans without tensor-core Grams).  Either output may be
- * NULL.  SSM_EINVAL for other plans. */
+ * default size).  On tensor-core plans the pair is the fastest one step of the
+ * recurrence graph's two branches (a CSR step beside a Gram + reduction); on
+ * the others the CSR size is the fastest step alone.  0 before the first
+ * ssm_moments (and gram_slabs 0 on plans without tensor-core Grams).  Either
+ * output may be NULL.  SSM_EINVAL for other plans. */
 ssm_status ssm_batch_tuning(ssm_plan_t plan, int32_t* csr_threads, int32_t* gram_slabs);
 
 /* The plan's Chebyshev interval (a, b), its spectral bounds [lo, hi] (the

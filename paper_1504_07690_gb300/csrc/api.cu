@@ -923,11 +923,13 @@ cudaError_t install_slabs(Plan& P, int div) {
     return e;
 }
 
-// Project autotuner of the batched Gram: times one step of the recurrence graph's two
-// branches as they run there, a CSR step beside the Gram products and their per-matrix
-// reduction (on the plan's zeroed blocks and panels; the work does not depend on the
-// values), with slabs of 1/1, 1/2 and 1/4 of the default size, and keeps the fastest.
-// Runs after autotune_csr (the CSR step with its tuned CTA size).
+// Project autotuner of the batched recurrence graph, tensor-core plans: times one step of
+// its two branches as they run there, a CSR step beside the Gram products and their
+// per-matrix reduction (on the plan's zeroed blocks and panels; the work does not depend
+// on the values), for every CSR CTA size (64, 128, 256 threads) and Gram slabs of 1/1,
+// 1/2 and 1/4 of the default size, and keeps the fastest pair: the two kernels share the
+// SMs, so the CSR size that is fastest alone need not be fastest there.
+// Runs after autotune_csr, whose choice it replaces.
 cudaError_t autotune_gram(Plan& P) {
     const size_t nn = (size_t)P.n_tot * P.n_tot, xs = (size_t)(P.p.degree + 1) * nn;
     cudaStream_t s2 = P.cap_stream2;
@@ -937,10 +939,12 @@ cudaError_t autotune_gram(Plan& P) {
     cudaEventCreateWithFlags(&ef, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&ej, cudaEventDisableTiming);
     float best = 1e30f;
-    int pick = 1;
-    const int cand[3] = {1, 2, 4};
+    int pick = 1, pick_t = P.csr_threads;
+    const int cand[3] = {1, 2, 4}, tcand[3] = {64, 128, 256};
     cudaError_t err = cudaSuccess;
-    for (int ci = 0; ci < 3 && err == cudaSuccess; ++ci) {
+    for (int ct = 0; ct < 9 && err == cudaSuccess; ++ct) {
+        const int ci = ct % 3;
+        P.csr_threads = tcand[ct / 3];
         err = install_slabs(P, cand[ci]);
         float ms = 0.f;
         for (int r = 0; r < 4 && err == cudaSuccess; ++r) {
@@ -965,12 +969,14 @@ cudaError_t autotune_gram(Plan& P) {
         if (err == cudaSuccess && ms < best) {
             best = ms;
             pick = cand[ci];
+            pick_t = P.csr_threads;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(ef);
     cudaEventDestroy(ej);
+    P.csr_threads = pick_t;
     if (err == cudaSuccess) err = install_slabs(P, pick);
     return err;
 }
