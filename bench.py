@@ -225,9 +225,9 @@ def kernel_rooflines(st, c, stats, args, hbm, bf16, peak_kind, clocks, ranks=Non
                            grids in float32 the row-group stencil_march_kernel, same bytes
       gram_tc_kernel       flops = 3 x 2 N (n_tot(n_tot+1)/2 + n_tot^2)   (split-bf16 products)
       gram_kernel (fp32)   flops = 2 N (n_tot(n_tot+1)/2 + n_tot^2)
-      assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step
-      assemble_df_kernel   12 float32 instructions per term of the same sums (mixed plans); its time is
-                           the assembly phase, which also holds the float-pair split launches
+      assemble_kernel      flops = 2 n_t ((M/2+1) n_tot(n_tot+1)/2 + (M+1) n_v(n_v+1)/2)   per step (fp64)
+      assemble_oz_kernel   bf16 slice products issued for the same sums (mixed: 6 slices, fp64_tc: 7;
+                           asm_oz_issued_flops); its time is the assembly phase, slicing included
       solve_kernel         flops = sum over points of the route's count (solve_flops)
     """
     N = st.n
