@@ -189,7 +189,7 @@ ssm_status ssm_batch_info(ssm_plan_t plan, int32_t b, double* a, double* bb, dou
                           int64_t* n);
 
 /* What the autotuner of a batched plan picked at its first ssm_moments: the CTA
- * size of the CSR recurrence step (64, 128 or 256 threads) and the number of
+ * size of the CSR recurrence step (64, 128, 256 or 512 threads) and the number of
  * row slabs of the tensor-core Gram products (slabs of 1, 1/2 or 1/4 of the
  * default size).  On tensor-core plans the pair is the fastest one step of the
  * recurrence graph's two branches (a CSR step beside a Gram + reduction); on

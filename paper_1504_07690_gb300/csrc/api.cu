@@ -926,7 +926,7 @@ cudaError_t install_slabs(Plan& P, int div) {
 // Project autotuner of the batched recurrence graph, tensor-core plans: times one step of
 // its two branches as they run there, a CSR step beside the Gram products and their
 // per-matrix reduction (on the plan's zeroed blocks and panels; the work does not depend
-// on the values), for every CSR CTA size (64, 128, 256 threads) and Gram slabs of 1/1,
+// on the values), for every CSR CTA size (64 .. 512 threads) and Gram slabs of 1/1,
 // 1/2 and 1/4 of the default size, and keeps the fastest pair: the two kernels share the
 // SMs, so the CSR size that is fastest alone need not be fastest there.
 // Runs after autotune_csr, whose choice it replaces.
@@ -940,9 +940,9 @@ cudaError_t autotune_gram(Plan& P) {
     cudaEventCreateWithFlags(&ej, cudaEventDisableTiming);
     float best = 1e30f;
     int pick = 1, pick_t = P.csr_threads;
-    const int cand[3] = {1, 2, 4}, tcand[3] = {64, 128, 256};
+    const int cand[3] = {1, 2, 4}, tcand[4] = {64, 128, 256, 512};
     cudaError_t err = cudaSuccess;
-    for (int ct = 0; ct < 9 && err == cudaSuccess; ++ct) {
+    for (int ct = 0; ct < 12 && err == cudaSuccess; ++ct) {
         const int ci = ct % 3;
         P.csr_threads = tcand[ct / 3];
         err = install_slabs(P, cand[ci]);
@@ -982,7 +982,7 @@ cudaError_t autotune_gram(Plan& P) {
 }
 
 // Project autotuner of the batched recurrence: times the CSR step with 64,
-// 128 and 256 threads per 32-row panel on the plan's own operator and keeps
+// 128, 256 and 512 threads per 32-row panel on the plan's own operator and keeps
 // the fastest (CUDA events, 2 warm-up and 3 timed launches each).
 cudaError_t autotune_csr(Plan& P) {
     const size_t esz = P.mixed ? sizeof(float) : sizeof(double);
@@ -995,9 +995,9 @@ cudaError_t autotune_csr(Plan& P) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     int pick = 256;
-    const int cand[3] = {64, 128, 256};
+    const int cand[4] = {64, 128, 256, 512};
     cudaError_t err = cudaSuccess;
-    for (int ci = 0; ci < 3 && err == cudaSuccess; ++ci) {
+    for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
         P.csr_threads = cand[ci];
         float ms = 0.f;
         for (int r = 0; r < 5 && err == cudaSuccess; ++r) {

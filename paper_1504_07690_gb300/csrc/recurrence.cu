@@ -340,7 +340,7 @@ stencil_march_kernel(const float* __restrict__ Vc, const float* __restrict__ Vp,
 }
 
 template <typename T, bool PANEL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 csr_step_kernel(const T* __restrict__ Vc, const T* __restrict__ Vp, T* __restrict__ Vn,
                 const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                 const T* __restrict__ val2, T beta, const T* __restrict__ beta_row, T c, T d, uint32_t nchunk,

@@ -126,7 +126,7 @@ def test_batched_autotuner_reports_its_choices(S):
     W = np.vstack([wl.random_block(c.n, 16, 5 + k) for k, c in enumerate(csrs)])
     S.ssm_moments(plan, W)
     tuned = S.ssm_batch_tuning(plan)
-    assert tuned["csr_threads"] in (64, 128, 256)
+    assert tuned["csr_threads"] in (64, 128, 256, 512)
     # at least one Ge and one Go slab per matrix
     assert tuned["gram_slabs"] >= 2 * len(csrs)
     plan.close()
