@@ -68,6 +68,17 @@ def over_ranks(x: float, dist=None, device=None) -> float:
     return float(tt.item())
 
 
+UNIT = "matrix-applies/s (nnz*n_tot*M/s)"
+
+
+def bench_config(nnz: int, ws: int) -> dict:
+    """The workload both arms (this GPU path and the CPU oracle) are measured on."""
+    return {"workload": "anderson2d_256: 2D Anderson 256x256 periodic, N=65536, nnz=%d, N_v=200 "
+                        "rademacher, M=1000, 400 sweep points, sigma=0.02" % nnz,
+            "l2": "inputs larger than L2 (3 recurrence blocks of 52 MB + 320 MB of moments)",
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def whole_job_value(units_per_replica: float, ws: int, seconds_per_step: float) -> float:
     """Throughput of the whole job: every replica processes the same units (weak scaling)."""
     return units_per_replica * ws / seconds_per_step
@@ -417,14 +428,13 @@ def run_reference(args, c, st, W, csr):
     value = units / t_step
     line = {
         "impl": "reference", "metric": "ssm_dos_effective_matrix_applies_per_s", "value": value,
-        "unit": "matrix-applies/s (nnz*n_tot*M/s)", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "anderson2d_256: N=65536 nnz=327680, N_v=200 rademacher, M=1000, "
-                               "400 sweep points, sigma=0.02", "l2": "working set > L2"},
-        "cpu_baseline": {"value": value, "unit": "matrix-applies/s", "cores": _blas_threads(), "kind": "oracle",
+        "dtype": "f64", "data": "synthetic", "precision": "float64 CPU oracle",
+        "config": bench_config(nnz, ws),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
                          "sample": sample},
-        "e2e": {"value": value, "unit": "matrix-applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -574,7 +584,7 @@ def run_gpu(args, c, st, W, csr):
         hs = (time.perf_counter() - h0) / args.steps
         S.ssm_timing_enable(plan, False)
         hs = over_ranks(hs, dist, dev)
-        e2e = {"value": whole_job_value(units, ws, hs), "unit": "matrix-applies/s (nnz*n_tot*M/s)",
+        e2e = {"value": whole_job_value(units, ws, hs), "unit": UNIT,
                "h2d_bytes_per_step": int(W.nbytes + t.nbytes), "d2h_bytes_per_step": int(2 * t.nbytes)}
 
     cpu = None
@@ -638,14 +648,11 @@ def run_gpu(args, c, st, W, csr):
     if rank == 0:
         line = {
             "metric": "ssm_dos_effective_matrix_applies_per_s", "value": value,
-            "unit": "matrix-applies/s (nnz*n_tot*M/s)", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "f32", "fp64": "f64", "fp64_tc": "f32x2"}[args.precision], "data": "synthetic",
-            "config": {"workload": "anderson2d_256: 2D Anderson 256x256 periodic, N=65536, nnz=%d, N_v=200 "
-                                   "rademacher, M=1000, 400 sweep points, sigma=0.02" % nnz,
-                       "precision": args.precision,
-                       "l2": "inputs larger than L2 (3 recurrence blocks of 52 MB + 320 MB of moments)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+            "precision": args.precision,
+            "config": bench_config(nnz, ws),
             "roofline": roofline, "rooflines": roofs, "phases_ms_per_step": phases,
             "gpu_launches": int(stats["launches"]),
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
